@@ -1,0 +1,302 @@
+"""FP64 CPU oracle for SNG-DBSCAN -- test infrastructure, not part of the product.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import this package.  The CUDA library never calls it,
+and it imports nothing from ``paper_2006_06743_gb300``: the two sides share no
+kernels, headers, helpers or constants.  Seeded inputs come from
+``paper_2006_06743_gb300.datagen`` (random inputs only, none of the method's
+arithmetic), which tests hand to both sides.
+
+Contents
+  * ``sng_oracle.c`` (built here with gcc, FP64, ``-ffp-contract=off``):
+    Algorithm 1 of Jiang, Jang & Lacki (NeurIPS 2020), Section 3 -- partner
+    draws, the sampled eps-graph, degrees, core mask, core components (BFS and
+    union-find), border labels -- plus textbook brute-force DBSCAN.
+  * ``ari``: the adjusted Rand index of Hubert & Arabie (1985), the score the
+    paper's Section 5 evaluates clusterings with.
+  * ``mlp``: FP64 forward/backward/Adam for the core-point surrogate network.
+
+Parity status per function is listed in each docstring; every function here is
+pinned by a ``-m "not gpu"`` test against something other than itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sng_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``sng_oracle.c`` into ``oracle/_build/liboracle.so`` (gcc, FP64,
+    no contraction, no fast-math).  Rebuilds when the source is newer."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("num_edges", ctypes.c_int64),
+                ("row_ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("col", ctypes.POINTER(ctypes.c_int32)), ("band_pairs", ctypes.c_int64)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64, i32, u64, f32, f64 = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                   ctypes.c_float, ctypes.c_double)
+        lib.orc_mix64.argtypes = [u64]
+        lib.orc_mix64.restype = u64
+        lib.orc_partner.argtypes = [u64, i64, i64, i64, i32]
+        lib.orc_partner.restype = i64
+        lib.orc_partners.argtypes = [u64, i64, i64, i64, i64, i32, P]
+        lib.orc_partners.restype = None
+        lib.orc_dist2.argtypes = [P, P, i32]
+        lib.orc_dist2.restype = f64
+        lib.orc_build_rows.argtypes = [i64, i32, i64, P, f32, u64, i64, i32, f64, P, i64,
+                                       ctypes.POINTER(_Graph), P]
+        lib.orc_build_rows.restype = i32
+        lib.orc_graph_free.argtypes = [ctypes.POINTER(_Graph)]
+        lib.orc_graph_free.restype = None
+        lib.orc_degrees.argtypes = [i64, P, P, i32, P]
+        lib.orc_degrees.restype = i32
+        lib.orc_components_bfs.argtypes = [i64, P, P, P, P]
+        lib.orc_components_bfs.restype = i64
+        lib.orc_components_uf.argtypes = [i64, P, P, P, P]
+        lib.orc_components_uf.restype = i64
+        lib.orc_border_labels.argtypes = [i64, P, P, P, P, P]
+        lib.orc_border_labels.restype = None
+        lib.orc_cluster_graph.argtypes = [i64, P, P, i32, i32, P, P, P, P]
+        lib.orc_cluster_graph.restype = i32
+        lib.orc_cluster.argtypes = [i64, i32, i64, P, f32, u64, i64, i32, i32, i32, f64, P, P,
+                                    P, P, P]
+        lib.orc_cluster.restype = i32
+        lib.orc_dbscan_bruteforce.argtypes = [i64, i32, i64, P, f32, i32, P, P]
+        lib.orc_dbscan_bruteforce.restype = i32
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32_rows(x) -> tuple[np.ndarray, int, int, int]:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if x.ndim != 2:
+        raise ValueError("x must be 2-D (n, d)")
+    return x, x.shape[0], x.shape[1], x.shape[1]
+
+
+# ------------------------------------------------------------------ hash
+
+def mix64(z: int) -> int:
+    """SplitMix64 output function (Steele, Lea & Flood 2014).  Pinned by the
+    generator's published output vectors."""
+    return int(_load().orc_mix64(ctypes.c_uint64(z & (2**64 - 1))))
+
+
+def partner(seed: int, i: int, j: int, n: int, sample_all: bool = False) -> int:
+    """Partner j of point i (Algorithm 1, step 2), never i itself."""
+    return int(_load().orc_partner(seed & (2**64 - 1), i, j, n, int(sample_all)))
+
+
+def partners(seed: int, n: int, i0: int, ni: int, m: int, sample_all: bool = False) -> np.ndarray:
+    """All partners of rows i0..i0+ni-1 as an (ni, m) int64 array."""
+    out = np.empty((ni, m), dtype=np.int64)
+    _load().orc_partners(seed & (2**64 - 1), n, i0, ni, m, int(sample_all), _ptr(out))
+    return out
+
+
+def dist2(a, b) -> float:
+    """FP64 squared distance, summed left to right without fused operations."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    return float(_load().orc_dist2(_ptr(a), _ptr(b), a.size))
+
+
+# ------------------------------------------------------------ graph build
+
+def build_rows(x, eps: float, seed: int, m: int, sample_all: bool = False,
+               band_rel: float = 1e-5, rows=None):
+    """Algorithm 1, step 2 for the given rows (default all).
+
+    Returns ``(row_ptr int64[nr+1], col int32[E], band_pairs, band_point uint8[n])``.
+    """
+    x, n, d, ld = _f32_rows(x)
+    lib = _load()
+    g = _Graph()
+    bp = np.zeros(n, dtype=np.uint8)
+    if rows is None:
+        rows_arr, nr, rp = None, n, None
+    else:
+        rows_arr = np.ascontiguousarray(rows, dtype=np.int64)
+        nr, rp = rows_arr.size, _ptr(rows_arr)
+    rc = lib.orc_build_rows(n, d, ld, _ptr(x), ctypes.c_float(eps), seed & (2**64 - 1), m,
+                            int(sample_all), band_rel, rp, nr, ctypes.byref(g), _ptr(bp))
+    if rc != 0:
+        raise ValueError("orc_build_rows failed (bad arguments or out of memory)")
+    try:
+        row_ptr = np.ctypeslib.as_array(g.row_ptr, shape=(g.n_rows + 1,)).copy()
+        ne = int(g.num_edges)
+        col = (np.ctypeslib.as_array(g.col, shape=(ne,)).copy() if ne
+               else np.zeros(0, dtype=np.int32))
+        band_pairs = int(g.band_pairs)
+    finally:
+        lib.orc_graph_free(ctypes.byref(g))
+    return row_ptr, col, band_pairs, bp
+
+
+def degrees(n: int, row_ptr, col, mode: int = 0) -> np.ndarray:
+    """Vertex degrees (Algorithm 1, step 3); mode 0 undirected multigraph,
+    1 out-degree, 2 distinct neighbours."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    deg = np.empty(n, dtype=np.int32)
+    if _load().orc_degrees(n, _ptr(rp), _ptr(cl), mode, _ptr(deg)) != 0:
+        raise ValueError("orc_degrees failed")
+    return deg
+
+
+def components(n: int, row_ptr, col, core, method: str = "bfs") -> tuple[np.ndarray, int]:
+    """Components of the core subgraph (Algorithm 1, step 3); label = min index."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    cr = np.ascontiguousarray(core, dtype=np.uint8)
+    comp = np.empty(n, dtype=np.int32)
+    fn = _load().orc_components_bfs if method == "bfs" else _load().orc_components_uf
+    k = fn(n, _ptr(rp), _ptr(cl), _ptr(cr), _ptr(comp))
+    if k < 0:
+        raise MemoryError("oracle components: out of memory")
+    return comp, int(k)
+
+
+def border_labels(n: int, row_ptr, col, core, comp) -> np.ndarray:
+    """Algorithm 1, steps 4-5 (border points take the smallest adjacent label)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    cr = np.ascontiguousarray(core, dtype=np.uint8)
+    cp = np.ascontiguousarray(comp, dtype=np.int32)
+    labels = np.empty(n, dtype=np.int32)
+    _load().orc_border_labels(n, _ptr(rp), _ptr(cl), _ptr(cr), _ptr(cp), _ptr(labels))
+    return labels
+
+
+def cluster_graph(n: int, row_ptr, col, min_pts: int, deg_mode: int = 0) -> dict:
+    """Algorithm 1, steps 3-5 on a given sampled graph (CSR by source)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    labels = np.empty(n, dtype=np.int32)
+    core = np.empty(n, dtype=np.uint8)
+    deg = np.empty(n, dtype=np.int32)
+    stats = np.zeros(8, dtype=np.int64)
+    if _load().orc_cluster_graph(n, _ptr(rp), _ptr(cl), deg_mode, min_pts, _ptr(labels),
+                                 _ptr(core), _ptr(deg), _ptr(stats)) != 0:
+        raise MemoryError("orc_cluster_graph failed")
+    return dict(labels=labels, core=core, deg=deg, kept_edges=int(stats[1]),
+                cores=int(stats[4]), clusters=int(stats[5]), noise=int(stats[6]))
+
+
+def cluster(x, eps: float, seed: int, m: int, min_pts: int, deg_mode: int = 0,
+            sample_all: bool = False, band_rel: float = 1e-5) -> dict:
+    """The whole of Algorithm 1 in FP64.  Returns labels (int32, -1 noise, else
+    the smallest core index of the cluster), core mask, degrees, band points
+    and the counters (queries, kept edges, band pairs/points, cores, clusters,
+    noise)."""
+    x, n, d, ld = _f32_rows(x)
+    labels = np.empty(n, dtype=np.int32)
+    core = np.empty(n, dtype=np.uint8)
+    deg = np.empty(n, dtype=np.int32)
+    bp = np.zeros(n, dtype=np.uint8)
+    stats = np.zeros(8, dtype=np.int64)
+    rc = _load().orc_cluster(n, d, ld, _ptr(x), ctypes.c_float(eps), seed & (2**64 - 1), m,
+                             int(sample_all), deg_mode, min_pts, band_rel, _ptr(labels),
+                             _ptr(core), _ptr(deg), _ptr(bp), _ptr(stats))
+    if rc != 0:
+        raise ValueError("orc_cluster failed (bad arguments or out of memory)")
+    return dict(labels=labels, core=core, deg=deg, band_point=bp, queries=int(stats[0]),
+                kept_edges=int(stats[1]), band_pairs=int(stats[2]), band_points=int(stats[3]),
+                cores=int(stats[4]), clusters=int(stats[5]), noise=int(stats[6]))
+
+
+def dbscan_bruteforce(x, eps: float, min_pts_db: int) -> tuple[np.ndarray, np.ndarray]:
+    """Textbook DBSCAN (Ester et al. 1996) from all n^2 FP64 distances; the
+    neighbourhood counts the point itself; border -> smallest adjacent label."""
+    x, n, d, ld = _f32_rows(x)
+    labels = np.empty(n, dtype=np.int32)
+    core = np.empty(n, dtype=np.uint8)
+    if _load().orc_dbscan_bruteforce(n, d, ld, _ptr(x), ctypes.c_float(eps), min_pts_db,
+                                     _ptr(labels), _ptr(core)) != 0:
+        raise MemoryError("orc_dbscan_bruteforce failed")
+    return labels, core
+
+
+# --------------------------------------------------------------- metrics
+
+def ari(a, b) -> float:
+    """Adjusted Rand index (Hubert & Arabie 1985) from the contingency table,
+    in FP64 (exact integer pair counts).  Noise (-1) is one label."""
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    if a.shape != b.shape:
+        raise ValueError("label arrays differ in length")
+    n = a.size
+    if n < 2:
+        return 1.0
+    _, ia = np.unique(a, return_inverse=True)
+    _, ib = np.unique(b, return_inverse=True)
+    pair = ia.astype(np.int64) * (int(ib.max()) + 1) + ib
+    _, nij = np.unique(pair, return_counts=True)
+    ai = np.bincount(ia)
+    bj = np.bincount(ib)
+
+    def c2(v):
+        v = np.asarray(v, dtype=np.int64)
+        return int(np.sum(v * (v - 1) // 2))
+
+    index = c2(nij)
+    sa, sb = c2(ai), c2(bj)
+    total = n * (n - 1) // 2
+    expected = sa * sb / total
+    max_index = 0.5 * (sa + sb)
+    if max_index == expected:
+        return 1.0
+    return float((index - expected) / (max_index - expected))
+
+
+def canonical(labels) -> np.ndarray:
+    """Relabel a partition so every cluster carries its smallest point index
+    (noise stays -1)."""
+    labels = np.asarray(labels)
+    out = np.full(labels.shape, -1, dtype=np.int64)
+    mask = labels >= 0
+    idx = np.nonzero(mask)[0]
+    if idx.size:
+        lab = labels[mask]
+        first = {}
+        for i, l in zip(idx.tolist(), lab.tolist()):
+            if l not in first:
+                first[l] = i
+        out[mask] = np.array([first[l] for l in lab.tolist()], dtype=np.int64)
+    return out
