@@ -1,0 +1,319 @@
+"""Benchmark: SNG-DBSCAN on one GB300, n = 1,000,000 points in d = 64.
+
+Workload (the headline configuration): a mixture of 100 Gaussians in R^64
+(centres N(0, 4 I), per-cluster std U[0.5, 1], Dirichlet(1) sizes) plus 2%
+uniform noise in the bounding box; s = 0.001 (m = 1000 partner draws per
+point, 1e9 distance queries); eps = the 1% quantile of distances over 1e6
+seeded random pairs; MinPts = 10.  Synthetic data of the shape of the paper's
+million-point datasets (Section 5), which are not available here.
+
+One step = one whole pass of Algorithm 1 on the device-resident points:
+partner draws + eps-test + FP64 guard-band recheck (gather), row-pointer scan,
+CSR fill, core mask + union-find components, border labels, finalize.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (n, d, k, noise, s, min_pts)
+    "mixture-n1M-d64": (1_000_000, 64, 100, 0.02, 0.001, 10),
+    "mixture-n100k-d64": (100_000, 64, 100, 0.02, 0.01, 10),
+}
+
+
+def make_workload(name: str, seed: int = 0):
+    from paper_2006_06743_gb300 import datagen
+    n, d, k, noise, s, min_pts = WORKLOADS[name]
+    x, truth = datagen.gaussian_mixture(n, d, k, noise, seed=seed, return_truth=True)
+    eps = datagen.eps_quantile(x, q=0.01, n_pairs=1_000_000, seed=seed)
+    return dict(x=x, truth=truth, n=n, d=d, s=s, min_pts=min_pts, eps=eps, seed=seed,
+                m=int(math.ceil(s * n)))
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def gather_algorithmic_bytes(n: int, d: int, m: int, esize: int, kept: int) -> int:
+    """Bytes the gather must move per launch: one partner row per query, each
+    point's own row once, its keep-bit words and row count once, and a 4-byte
+    read-modify-write degree update per kept draw (in-degree) and per row."""
+    words = (m + 31) // 32
+    return n * m * d * esize + n * d * esize + n * words * 4 + n * 4 + kept * 8 + n * 8
+
+
+def run_cpu_baseline(w: dict, budget_s: float = 12.0) -> dict:
+    """The FP64 oracle (single-threaded C, as written) on a bounded sample of
+    source rows of the same workload; queries/s scaled by the rows sampled."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    x, n, m = w["x"], w["n"], w["m"]
+    rng = np.random.default_rng(1)
+    probe = np.sort(rng.choice(n, size=200, replace=False))
+    t0 = time.perf_counter()
+    oracle.build_rows(x, w["eps"], w["seed"], m, rows=probe)
+    dt = time.perf_counter() - t0
+    rows = int(min(n, max(200, budget_s / max(dt, 1e-6) * 200)))
+    sample = np.sort(rng.choice(n, size=rows, replace=False))
+    t0 = time.perf_counter()
+    oracle.build_rows(x, w["eps"], w["seed"], m, rows=sample)
+    dt = time.perf_counter() - t0
+    q = rows * m
+    return {"value": q / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "seconds": dt, "sample": f"eps-graph rows of {rows} random source points "
+                                    f"({q:.3g} FP64 queries, step 2 of Algorithm 1)"}
+
+
+def bench_sng(args, w):
+    import numpy as np
+    import torch
+
+    import paper_2006_06743_gb300 as sng
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    # weak scaling: every rank clusters its own independent dataset (no
+    # collective on the data path); rank r uses seed base + r
+    if rank > 0:
+        w = make_workload(args.workload, seed=args.seed + rank)
+    x_host = torch.from_numpy(w["x"]).pin_memory()
+    x = x_host.to(dev)
+    n, d, m = w["n"], w["d"], w["m"]
+    params = sng.Params(eps=w["eps"], min_pts=w["min_pts"], s=w["s"], seed=w["seed"],
+                        flags=sng.SNG_FLAG_TIMING, map_group=args.map_group,
+                        map_unroll=args.map_unroll, map_block=args.map_block)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        labels, st = sng.cluster(x, params)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    launches0 = sng.launch_count()
+    step_ms, gather_ms, stats = [], [], None
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1)                      # evict L2 between steps (512 MB > 129 MB L2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        labels, stats = sng.cluster(x, params)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        gather_ms.append(stats["ms"]["gather"])
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier()
+    launches = sng.launch_count() - launches0
+    t_step = statistics.mean(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    # end to end through the public API: pinned host points in, labels out
+    e2e_ms = []
+    labels_host = torch.empty(n, dtype=torch.int32).pin_memory()
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        xd = x_host.to(dev, non_blocking=True)
+        lab, _ = sng.cluster(xd, params)
+        labels_host.copy_(lab, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        del xd
+    t_e2e = statistics.mean(e2e_ms)
+
+    Q = n * m
+    peak, peak_kind = peaks()
+    g_ms = statistics.mean(gather_ms)
+    alg = gather_algorithmic_bytes(n, d, m, 4, stats["kept_edges"])
+    achieved = alg / (g_ms * 1e-3) / 1e9
+    truth = w["truth"].astype(np.int32)
+    ari_truth = sng.ari(labels, torch.from_numpy(truth).to(dev))
+    out = {
+        "metric": "sampled eps-queries/s (whole SNG-DBSCAN pass), n=1M d=64",
+        "value": Q * world / (t_step * 1e-3),
+        "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded Gaussian mixture, no dataset)",
+        "config": {"workload": args.workload, "n": n, "d": d, "m": m, "s": w["s"],
+                   "eps": w["eps"], "min_pts": w["min_pts"], "queries_per_step": Q,
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"dp{world}"},
+        "e2e": {"value": Q * world / (t_e2e * 1e-3), "unit": "queries/s",
+                "seconds": t_e2e * 1e-3,
+                "h2d_bytes_per_step": int(x_host.numel() * 4),
+                "d2h_bytes_per_step": int(n * 4)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "gather_kernel", "peak_kind": peak_kind,
+                     "algorithmic_bytes": alg, "kernel_ms": g_ms},
+        "phases_ms": {k: v for k, v in stats["ms"].items()},
+        "stats": {k: stats[k] for k in ("kept_edges", "band_pairs", "band_points", "cores",
+                                        "clusters", "noise", "recheck_pairs")},
+        "ari_vs_generating_mixture": ari_truth,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = run_cpu_baseline(w, budget_s=args.cpu_budget)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def bench_reference(args, w):
+    """The reference arm: the FP64 CPU oracle, timed as it stands on the host."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    steps = []
+    base = None
+    for k in range(args.warmup + args.steps):
+        base = run_cpu_baseline(w, budget_s=args.ref_budget)
+        if k >= args.warmup:
+            steps.append(base["value"])
+    v = statistics.mean(steps)
+    return {"impl": "reference",
+            "metric": "sampled eps-queries/s (whole SNG-DBSCAN pass), n=1M d=64",
+            "value": v, "unit": "queries/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sng", choices=["sng", "reference"])
+    ap.add_argument("--workload", default="mixture-n1M-d64", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--map-group", type=int, default=0)
+    ap.add_argument("--map-unroll", type=int, default=0)
+    ap.add_argument("--map-block", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=8.0)
+    args = ap.parse_args()
+    rank, world, _ = dist_env()
+    if args.impl == "reference" and rank != 0:
+        return
+    w = make_workload(args.workload, seed=args.seed)
+    if args.impl == "reference":
+        out = bench_reference(args, w)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        out = bench_sng(args, w)
+    if out is not None and rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * sng.h -- C ABI of the GB300 (sm_103a) SNG-DBSCAN library (libsng.so).
+ *
+ * SNG-DBSCAN is Algorithm 1 of Jiang, Jang & Lacki, "Faster DBSCAN via
+ * subsampled similarity queries" (NeurIPS 2020), Section 3.  Its inputs are
+ * the points X, a sampling rate s, a radius eps and MinPts; its output is a
+ * partition of the points into clusters plus noise.  Steps:
+ *   2  every point draws ceil(s n) partners and keeps an edge to each partner
+ *      within distance eps                              (sng_build_graph)
+ *   3  points of degree >= MinPts are core points; the connected components
+ *      of the core subgraph are the cluster cores
+ *   4  a non-core point with an edge to a core joins that core's cluster
+ *   5  every other point is noise                       (sng_cluster)
+ *
+ * Conventions shared by every call
+ *  - Pointers named "device" must be CUDA device (or managed) memory on the
+ *    current device; "host" pointers are ordinary host memory.  Nothing in
+ *    this header depends on a framework: plain pointers and sizes only.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls return once it is enqueued unless
+ *    stated otherwise.
+ *  - The caller owns inputs and outputs.  Library-owned memory appears only in
+ *    sng_graph (freed by sng_graph_free) and in plan objects.
+ *  - Every call returns an sng_status.  Invalid arguments are rejected with
+ *    SNG_EINVAL before any work is enqueued; sng_last_error() returns a
+ *    one-line reason.  No call aborts or throws across the ABI.
+ *  - Partner draws (step 2) are fixed by a counter-based hash so that any
+ *    implementation sees the same pairs: mix = SplitMix64 output function,
+ *    k_i = mix(seed ^ mix(i)), h = mix(k_i ^ j), r = h mod (n-1),
+ *    partner(i,j) = r + (r >= i), for j = 0..m-1, m = ceil(s n).
+ *  - The eps-test keeps (i,p) iff d2(x_i,x_p) <= eps^2 where d2 is the FP64
+ *    sum of squared coordinate differences, left to right.  The kernels test
+ *    in FP32 and recompute in FP64, in exactly that order, every pair whose
+ *    FP32 value lies within a guard band of eps^2, so FP32 inputs give the
+ *    FP64 decision on every pair.
+ *  - Labels: -1 = noise; otherwise the smallest core-point index of the
+ *    cluster (a border point adjacent to several clusters takes the smallest
+ *    such label: the paper's "choose one arbitrarily" fixed to the minimum).
+ */
+#ifndef SNG_H
+#define SNG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sng_status;
+#define SNG_OK 0
+#define SNG_EINVAL (-1)     /* bad argument; nothing was enqueued             */
+#define SNG_ENOMEM (-2)     /* a device allocation failed; nothing leaked     */
+#define SNG_ECUDA (-3)      /* a CUDA runtime call failed                     */
+#define SNG_ETIMEOUT (-4)   /* a bounded device loop gave up (status word)    */
+#define SNG_EINTERNAL (-5)  /* a device-side consistency check failed         */
+
+/* element type of X */
+#define SNG_F32 0
+#define SNG_BF16 1          /* bfloat16 bit patterns, uint16 per element       */
+
+/* degree used by the MinPts test (Algorithm 1, step 3) */
+#define SNG_DEG_UNDIRECTED_MULTI 0 /* each kept draw (i,p) adds 1 to i and to p */
+#define SNG_DEG_OUT 1              /* kept draws of i only (the count thresholded in
+                                      the proof of Lemma 2)                      */
+
+/* how partners are drawn (Algorithm 1, step 2) */
+#define SNG_SAMPLE_HASH 0   /* m hashed draws with replacement, never i itself */
+#define SNG_SAMPLE_ALL 1    /* every other point once (m = n-1): s = 1, textbook
+                               DBSCAN's full eps-neighbourhood graph           */
+
+/* flags */
+#define SNG_FLAG_TIMING 1u  /* fill sng_stats.ms with per-phase CUDA-event times */
+
+typedef struct {
+    int64_t n;            /* number of points, 2 <= n <= 2^31 - 1            */
+    int32_t d;            /* dimensions, >= 1                                */
+    int32_t ld;           /* row stride of X in elements, >= d               */
+    int32_t dtype;        /* SNG_F32 or SNG_BF16                             */
+    int32_t degree_mode;  /* SNG_DEG_*                                       */
+    int32_t sample_mode;  /* SNG_SAMPLE_*                                    */
+    int32_t min_pts;      /* MinPts, >= 1                                    */
+    float eps;            /* radius, finite, 1e-15 <= eps <= 1e18            */
+    float band_rel;       /* half-width of the reported band |d2-eps^2| <=
+                             band_rel*eps^2; 0 selects 1e-5 (F32) / 1e-3 (BF16) */
+    double s;             /* sampling rate in (0, 1]; m = ceil(s*n)          */
+    int64_t m_override;   /* > 0: use this m instead of ceil(s*n)            */
+    uint64_t seed;        /* partner-hash seed                               */
+    const float *x_f32_master; /* device, n x ld FP32; BF16 form: the FP32 values
+                             the FP64 recheck reads (required for SNG_BF16)    */
+    uint32_t flags;       /* SNG_FLAG_*                                      */
+    int32_t map_group;    /* gather mapping override: lanes per pair (1..32,
+                             power of two), 0 = library default             */
+    int32_t map_unroll;   /* partner batches in flight per warp, 0 = default */
+    int32_t map_block;    /* threads per block of the gather, 0 = default    */
+    int32_t map_tile;     /* batched form: source rows per work item, 0 = default */
+} sng_params;
+
+typedef struct {
+    int64_t queries;      /* sampled distance queries = n * m (hash mode)    */
+    int64_t kept_edges;   /* kept draws, E                                   */
+    int64_t band_pairs;   /* draws with |d2_fp64 - eps^2| <= band_rel*eps^2  */
+    int64_t band_points;  /* points touching at least one band pair          */
+    int64_t cores;        /* points with degree >= MinPts                    */
+    int64_t clusters;     /* connected components of the core subgraph       */
+    int64_t noise;        /* points labelled -1                              */
+    int64_t recheck_pairs;/* draws recomputed in FP64 (guard band)           */
+    float ms[8];          /* SNG_FLAG_TIMING: [0] gather [1] scan [2] fill
+                             [3] core+union [4] labels [5] finalize [6] total */
+} sng_stats;
+
+typedef struct {
+    int64_t n;            /* points                                          */
+    int64_t m;            /* draws per point                                 */
+    int64_t num_edges;    /* E                                               */
+    int64_t *row_ptr;     /* device, n+1: row i = col[row_ptr[i]..row_ptr[i+1]) */
+    int32_t *col;         /* device, E: kept partners of each row in draw order */
+    int32_t *deg;         /* device, n: degree per params.degree_mode        */
+    uint8_t *core;        /* device, n: deg >= min_pts                       */
+} sng_graph;
+
+/*
+ * Algorithm 1, step 2 (and the degree / core mask of step 3): the sampled
+ * eps-neighbourhood graph of X as CSR by source point.  x: device, n rows of
+ * ld elements of params->dtype.  On SNG_OK `out` holds library-owned device
+ * arrays; release them with sng_graph_free.  Synchronises `stream` once (to
+ * size col) and again at the end when stats != NULL.
+ */
+sng_status sng_build_graph(const void *x, const sng_params *params, sng_graph *out,
+                           sng_stats *stats, void *stream);
+
+/* Frees the arrays of a graph from sng_build_graph (device-synchronising). */
+void sng_graph_free(sng_graph *g);
+
+/*
+ * The whole of Algorithm 1: graph (step 2), degrees and core mask, core
+ * components (step 3), border labels (step 4), noise (step 5).
+ * x: device, n x ld.  labels: device int32[n] (output).  core: device
+ * uint8[n] (output) or NULL.  Synchronises `stream` once mid-way (to size the
+ * edge list) and at the end when stats != NULL.
+ */
+sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
+                       uint8_t *core, sng_stats *stats, void *stream);
+
+/*
+ * Many independent point clouds in one persistent launch.  x_concat: device,
+ * clouds stored back to back (rows of ld elements, F32 only).  offsets: HOST
+ * int64[n_clouds+1], cloud b = rows offsets[b]..offsets[b+1]-1, each cloud
+ * 2..2^31-1 points.  base: shared parameters; cloud b uses seed base->seed + b
+ * and m = m_per_cloud[b] (HOST, nullable) else base->m_override else
+ * ceil(base->s * n_b).  labels: device int32[total], cloud-local indices.
+ * Equivalent to calling sng_cluster on every cloud.  Synchronises `stream`
+ * when stats != NULL.
+ */
+sng_status sng_cluster_batched(const void *x_concat, const int64_t *offsets, int32_t n_clouds,
+                               const sng_params *base, const int64_t *m_per_cloud,
+                               int32_t *labels, sng_stats *stats, void *stream);
+
+/* Reusable form of sng_cluster_batched: the plan holds the validated cloud
+ * table and device scratch, and sng_batch_run replays the launch as a CUDA
+ * graph (captured on the first run for a given x/labels/stream). */
+typedef struct sng_batch_plan sng_batch_plan;
+sng_status sng_batch_plan_create(const int64_t *offsets, int32_t n_clouds, const sng_params *base,
+                                 const int64_t *m_per_cloud, sng_batch_plan **plan);
+sng_status sng_batch_run(sng_batch_plan *plan, const void *x_concat, int32_t *labels,
+                         sng_stats *stats, void *stream);
+void sng_batch_plan_destroy(sng_batch_plan *plan);
+
+/*
+ * Partner draws of Algorithm 1, step 2, materialised for checking: out[r*m+j]
+ * = partner(i0 + r, j) for r < rows, j < m.  out: device int32[rows*m].
+ */
+sng_status sng_sample_partners(int64_t n, uint64_t seed, int64_t i0, int64_t rows, int64_t m,
+                               int32_t sample_mode, int32_t *out, void *stream);
+
+/* Adjusted Rand index (Hubert & Arabie 1985; the score of the paper's
+ * Section 5) of two labelings a, b (device int32[n], values in [-1, 2^31)),
+ * noise as one label.  Synchronises `stream`; result in *ari (host). */
+sng_status sng_ari(const int32_t *a, const int32_t *b, int64_t n, double *ari, void *stream);
+
+/* Number of kernels this library has launched in this process. */
+int64_t sng_launch_count(void);
+
+/* One-line reason for the last non-OK status on this thread. */
+const char *sng_last_error(void);
+const char *sng_strerror(sng_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNG_H */

@@ -1,0 +1,488 @@
+// api.cu -- the extern "C" entry points of libsng.so (declared in include/sng.h).
+//
+// Host-side work only: argument validation, the gather mapping policy, the
+// FP32 guard band, device scratch (stream-ordered pool allocations) and the
+// order of kernel launches for Algorithm 1 (Jiang, Jang & Lacki 2020, Sec. 3).
+#include <atomic>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "api_common.cuh"
+#include "gather.cuh"
+#include "graph.cuh"
+
+namespace sng {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+
+static thread_local std::string g_last_error;
+
+sng_status fail(sng_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+sng_status cuda_fail(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(SNG_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(SNG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int device_sms() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cache[dev]) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = sms > 0 ? sms : 148;
+    // keep freed pool memory for reuse instead of returning it to the driver
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  return cache[dev];
+}
+
+// ------------------------------------------------------------- scratch
+
+static std::atomic<int64_t> g_alloc_seq{0};
+
+Scratch::~Scratch() { release(); }
+
+void Scratch::release() {
+  for (void *p : ptrs) cudaFreeAsync(p, stream);
+  ptrs.clear();
+}
+
+sng_status Scratch::alloc(void **out, size_t bytes, const char *what) {
+  *out = nullptr;
+  const char *fault = std::getenv("SNG_FAULT_ALLOC");
+  const int64_t seq = g_alloc_seq.fetch_add(1) + 1;
+  if (fault && *fault) {
+    // SNG_FAULT_ALLOC=k: the k-th allocation counted from the moment the
+    // variable was first seen fails (host-side fault injection for tests).
+    static std::atomic<int64_t> base{-1};
+    int64_t expect = -1;
+    base.compare_exchange_strong(expect, seq - 1);
+    if (seq - base.load() == std::atoll(fault))
+      return fail(SNG_ENOMEM, "injected allocation failure (%s)", what);
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, what);
+  }
+  ptrs.push_back(p);
+  *out = p;
+  return SNG_OK;
+}
+
+// ------------------------------------------------------------ validation
+
+static int64_t ceil_s_n(double s, int64_t n) { return (int64_t)std::ceil(s * (double)n); }
+
+sng_status validate(const void *x, const sng_params *p, Resolved *r) {
+  if (!p) return fail(SNG_EINVAL, "params is NULL");
+  if (!x) return fail(SNG_EINVAL, "x is NULL");
+  if (p->n < 2 || p->n > 0x7fffffffLL) return fail(SNG_EINVAL, "n must be in [2, 2^31-1]");
+  if (p->d < 1) return fail(SNG_EINVAL, "d must be >= 1");
+  if (p->ld < p->d) return fail(SNG_EINVAL, "ld must be >= d");
+  if (p->dtype != SNG_F32 && p->dtype != SNG_BF16) return fail(SNG_EINVAL, "unknown dtype");
+  if (p->degree_mode != SNG_DEG_UNDIRECTED_MULTI && p->degree_mode != SNG_DEG_OUT)
+    return fail(SNG_EINVAL, "unknown degree_mode");
+  if (p->sample_mode != SNG_SAMPLE_HASH && p->sample_mode != SNG_SAMPLE_ALL)
+    return fail(SNG_EINVAL, "unknown sample_mode");
+  if (p->min_pts < 1) return fail(SNG_EINVAL, "min_pts must be >= 1");
+  if (!std::isfinite(p->eps) || p->eps < 1e-15f || p->eps > 1e18f)
+    return fail(SNG_EINVAL, "eps must be finite and in [1e-15, 1e18]");
+  if (!(p->band_rel >= 0.f) || p->band_rel > 0.25f)
+    return fail(SNG_EINVAL, "band_rel must be in [0, 0.25]");
+  const size_t esize = p->dtype == SNG_F32 ? 4 : 2;
+  if ((uintptr_t)x % esize) return fail(SNG_EINVAL, "x is not aligned to its element size");
+  if (p->dtype == SNG_BF16) {
+    if (!p->x_f32_master) return fail(SNG_EINVAL, "BF16 form needs x_f32_master");
+    if ((uintptr_t)p->x_f32_master % 4) return fail(SNG_EINVAL, "x_f32_master misaligned");
+  }
+  int64_t m;
+  if (p->sample_mode == SNG_SAMPLE_ALL) {
+    m = p->n - 1;
+  } else if (p->m_override > 0) {
+    m = p->m_override;
+  } else {
+    if (!(p->s > 0.0) || !(p->s <= 1.0)) return fail(SNG_EINVAL, "s must be in (0, 1]");
+    m = ceil_s_n(p->s, p->n);
+  }
+  if (m < 1 || m > 0x7fffffffLL) return fail(SNG_EINVAL, "m must be in [1, 2^31-1]");
+  r->n = p->n;
+  r->d = p->d;
+  r->m = m;
+  r->W = (int32_t)((m + 31) / 32);
+  r->band_rel = p->band_rel > 0.f ? p->band_rel : (p->dtype == SNG_BF16 ? 1e-3f : 1e-5f);
+
+  // gather mapping: widest aligned vector, then lanes per pair
+  const int vmax = p->dtype == SNG_F32 ? 4 : 8;
+  int vec = vmax;
+  while (vec > 1 && ((p->ld % vec) != 0 || ((uintptr_t)x % (vec * esize)) != 0)) vec >>= 1;
+  const int chunks = (p->d + vec - 1) / vec;
+  int group, nch;
+  auto pow2ceil = [](int v) {
+    int q = 1;
+    while (q < v) q <<= 1;
+    return q;
+  };
+  if (p->map_group > 0) {
+    group = p->map_group;
+    if (group > 32 || (group & (group - 1))) return fail(SNG_EINVAL, "map_group must be 1..32, pow2");
+    nch = pow2ceil((chunks + group - 1) / group);
+  } else if (chunks <= 4 && vec <= 2) {
+    group = 1;
+    nch = pow2ceil(chunks);
+  } else {
+    group = pow2ceil(chunks);
+    if (group > 32) group = 32;
+    nch = pow2ceil((chunks + group - 1) / group);
+  }
+  if (nch > 8)
+    return fail(SNG_EINVAL, "d = %d is wider than the compiled gather mappings (d <= %d)", p->d,
+                32 * 8 * vec);
+  r->map.vec = vec;
+  r->map.group = group;
+  r->map.nch = nch;
+  r->map.unroll = p->map_unroll > 0 ? p->map_unroll : 4;
+  r->map.block = p->map_block > 0 ? p->map_block : 256;
+  if (r->map.block % 32 || r->map.block < 32 || r->map.block > 256)
+    return fail(SNG_EINVAL, "map_block must be a multiple of 32 in [32, 256]");
+  if (p->map_tile < 0) return fail(SNG_EINVAL, "map_tile must be >= 0");
+
+  // eps^2 in FP64 exactly as the oracle forms it; the FP32 screen is widened
+  // by twice a bound on the FP32 relative error of the kernel's sum: one
+  // rounding for the difference, one per fused multiply-add in a lane
+  // (nch*vec), one per shuffle level (log2 group), plus slack.
+  r->eps2 = (double)p->eps * (double)p->eps;
+  r->band = (double)r->band_rel * r->eps2;
+  int lg = 0;
+  while ((1 << lg) < group) ++lg;
+  const double u = std::ldexp(1.0, -24);
+  const double delta = 2.0 * (double)(nch * vec + lg + 3) * u + std::ldexp(1.0, -22);
+  const double screen = (double)r->band_rel + delta;
+  const double lo = r->eps2 * (1.0 - screen), hi = r->eps2 * (1.0 + screen);
+  float lof = (float)lo, hif = (float)hi;
+  if ((double)lof > lo) lof = std::nextafter(lof, 0.f);
+  if ((double)hif < hi) hif = std::nextafter(hif, INFINITY);
+  r->lo_thr = lof;
+  r->hi_thr = hif;
+  return SNG_OK;
+}
+
+bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, GatherArgs *g) {
+  g->x = x;
+  g->ld = p->ld;
+  g->xm = p->dtype == SNG_F32 ? static_cast<const float *>(x) : p->x_f32_master;
+  g->ldm = p->ld;
+  g->n = (int32_t)r.n;
+  g->d = r.d;
+  g->m = (int32_t)r.m;
+  g->W = r.W;
+  g->seed = p->seed;
+  g->fm = make_fastmod(r.n);
+  g->lo_thr = r.lo_thr;
+  g->hi_thr = r.hi_thr;
+  g->eps2 = r.eps2;
+  g->band = r.band;
+  g->sample_all = p->sample_mode == SNG_SAMPLE_ALL;
+  g->deg_mode = p->degree_mode;
+  g->m_row = nullptr;
+  return true;
+}
+
+int gather_grid(int dtype, const GatherMap &map, int64_t n) {
+  const int sms = device_sms();
+  int per_sm = gather_max_blocks_per_sm(dtype, map);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t warps_per_block = map.block / 32;
+  int64_t need = (n + warps_per_block - 1) / warps_per_block;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > need) grid = need;
+  return (int)(grid < 1 ? 1 : grid);
+}
+
+// Steps shared by sng_build_graph and sng_cluster: the gather (step 2 with the
+// degree counts of step 3), the row-pointer scan and the CSR fill.
+sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scratch &s,
+                     GraphBufs *gb, const int32_t *m_row, Timer *tm) {
+  cudaStream_t st = s.stream;
+  const int64_t n = r.n;
+  sng_status rc;
+  if ((rc = s.alloc((void **)&gb->bitmask, (size_t)n * r.W * 4, "keep bits"))) return rc;
+  if ((rc = s.alloc((void **)&gb->out_cnt, (size_t)n * 4, "row counts"))) return rc;
+  if ((rc = s.alloc((void **)&gb->deg, (size_t)n * 4, "degrees"))) return rc;
+  if ((rc = s.alloc((void **)&gb->band_flag, (size_t)n, "band flags"))) return rc;
+  if ((rc = s.alloc((void **)&gb->counters, kCntSlots * 8, "counters"))) return rc;
+  if ((rc = s.alloc((void **)&gb->tile_tmp, (size_t)scan_tiles(n) * 8, "scan tiles"))) return rc;
+  if ((rc = s.alloc((void **)&gb->row_ptr, (size_t)(n + 1) * 8, "row_ptr"))) return rc;
+  cudaMemsetAsync(gb->deg, 0, (size_t)n * 4, st);
+  cudaMemsetAsync(gb->band_flag, 0, (size_t)n, st);
+  cudaMemsetAsync(gb->counters, 0, kCntSlots * 8, st);
+
+  GatherArgs ga;
+  fill_gather_args(x, p, r, &ga);
+  ga.m_row = m_row;
+  ga.bitmask = gb->bitmask;
+  ga.out_cnt = gb->out_cnt;
+  ga.deg = gb->deg;
+  ga.band_flag = gb->band_flag;
+  ga.counters = gb->counters;
+  tm->mark(st, 0);
+  const int grid = gather_grid(p->dtype, r.map, n);
+  if (!launch_gather(p->dtype, r.map, ga, grid, st))
+    return fail(SNG_EINVAL, "no compiled gather for vec=%d group=%d nch=%d unroll=%d",
+                r.map.vec, r.map.group, r.map.nch, r.map.unroll);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+  tm->mark(st, 1);
+  launch_scan(gb->out_cnt, n, gb->tile_tmp, gb->row_ptr, gb->counters, st);
+  tm->mark(st, 2);
+  unsigned long long E = 0;
+  e = cudaMemcpyAsync(&E, gb->counters + kCntEdges, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "edge count read-back");
+  gb->num_edges = (int64_t)E;
+  if (gb->col_owned_by_caller) {
+    e = cudaMalloc((void **)&gb->col, (size_t)(E ? E : 1) * 4);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "col");
+    }
+  } else if ((rc = s.alloc((void **)&gb->col, (size_t)E * 4, "col"))) {
+    return rc;
+  }
+  tm->mark(st, 8);
+  FillArgs fa;
+  fa.n = n;
+  fa.W = r.W;
+  fa.sample_all = p->sample_mode == SNG_SAMPLE_ALL;
+  fa.seed = p->seed;
+  fa.fm = make_fastmod(n);
+  fa.bitmask = gb->bitmask;
+  fa.row_ptr = gb->row_ptr;
+  fa.col = gb->col;
+  launch_fill(fa, device_sms(), st);
+  tm->mark(st, 3);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fill launch");
+  return SNG_OK;
+}
+
+sng_status read_stats(const unsigned long long *counters, const Resolved &r, sng_stats *stats,
+                      cudaStream_t st, const Timer *tm) {
+  unsigned long long c[kCntSlots];
+  cudaError_t e = cudaMemcpyAsync(c, counters, sizeof(c), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stats read-back");
+  const uint32_t status = (uint32_t)c[kCntStatus];
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->queries = r.n * r.m;
+    stats->kept_edges = (int64_t)c[kCntEdges];
+    stats->band_pairs = (int64_t)c[kCntBandPairs];
+    stats->band_points = (int64_t)c[kCntBandPoints];
+    stats->cores = (int64_t)c[kCntCores];
+    stats->clusters = (int64_t)c[kCntClusters];
+    stats->noise = (int64_t)c[kCntNoise];
+    stats->recheck_pairs = (int64_t)c[kCntRecheck];
+    if (tm) tm->fill(stats->ms);
+  }
+  if (status & (kErrUnionLimit | kErrFindLimit | kErrBatchLimit))
+    return fail(SNG_ETIMEOUT, "a bounded device loop gave up (status 0x%x)", status);
+  if (status & kErrIndex) return fail(SNG_EINTERNAL, "device index check failed (0x%x)", status);
+  return SNG_OK;
+}
+
+// ----------------------------------------------------------------- timer
+
+Timer::Timer(bool on) : on_(on) {
+  if (!on_) return;
+  for (int k = 0; k < kMarks; ++k) cudaEventCreate(&ev_[k]);
+}
+Timer::~Timer() {
+  if (!on_) return;
+  for (int k = 0; k < kMarks; ++k) cudaEventDestroy(ev_[k]);
+}
+void Timer::mark(cudaStream_t st, int k) {
+  if (on_ && k < kMarks) {
+    cudaEventRecord(ev_[k], st);
+    used_[k] = true;
+  }
+}
+void Timer::fill(float *ms) const {
+  if (!on_) return;
+  // ms[0] gather (0->1), [1] scan (1->2), [2] fill (2->3 after the host
+  // read-back: 3 is recorded after the fill launch), [3] core+union (4->5),
+  // [4] labels (5->6), [5] finalize (6->7), [6] total (0->7)
+  const int pairs[7][2] = {{0, 1}, {1, 2}, {8, 3}, {3, 5}, {5, 6}, {6, 7}, {0, 7}};
+  for (int q = 0; q < 7; ++q) {
+    const int a = pairs[q][0], b = pairs[q][1];
+    float v = 0.f;
+    if (used_[a] && used_[b]) cudaEventElapsedTime(&v, ev_[a], ev_[b]);
+    ms[q] = v;
+  }
+}
+
+}  // namespace sng
+
+using namespace sng;
+
+extern "C" {
+
+int64_t sng_launch_count(void) { return g_launches.load(); }
+
+const char *sng_last_error(void) { return g_last_error.c_str(); }
+
+const char *sng_strerror(sng_status s) {
+  switch (s) {
+    case SNG_OK: return "ok";
+    case SNG_EINVAL: return "invalid argument";
+    case SNG_ENOMEM: return "out of device memory";
+    case SNG_ECUDA: return "CUDA runtime error";
+    case SNG_ETIMEOUT: return "bounded device loop gave up";
+    case SNG_EINTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels, uint8_t *core,
+                       sng_stats *stats, void *stream) {
+  Resolved r;
+  sng_status rc = validate(x, params, &r);
+  if (rc) return rc;
+  if (!labels) return fail(SNG_EINVAL, "labels is NULL");
+  device_sms();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch s(st);
+  Timer tm((params->flags & SNG_FLAG_TIMING) != 0);
+  GraphBufs gb;
+  if ((rc = run_graph(x, params, r, s, &gb, nullptr, &tm))) return rc;
+  uint8_t *core_buf = core;
+  int32_t *parent = nullptr;
+  if (!core_buf && (rc = s.alloc((void **)&core_buf, (size_t)r.n, "core"))) return rc;
+  if ((rc = s.alloc((void **)&parent, (size_t)r.n * 4, "parent"))) return rc;
+  const int sms = device_sms();
+  CoreArgs ca{r.n, params->min_pts, gb.deg, nullptr, core_buf, parent, labels};
+  launch_core_init(ca, sms, st);
+  tm.mark(st, 4);
+  UnionArgs ua{r.n, gb.row_ptr, gb.col, core_buf, parent, labels, gb.counters};
+  launch_union(ua, sms, st);
+  tm.mark(st, 5);
+  launch_label(ua, sms, st);
+  tm.mark(st, 6);
+  FinalizeArgs fa{r.n, core_buf, gb.band_flag, labels, gb.counters};
+  launch_finalize(fa, sms, st);
+  tm.mark(st, 7);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "cluster launches");
+  rc = read_stats(gb.counters, r, stats, st, &tm);
+  s.release();
+  return rc;
+}
+
+sng_status sng_build_graph(const void *x, const sng_params *params, sng_graph *out,
+                           sng_stats *stats, void *stream) {
+  Resolved r;
+  sng_status rc = validate(x, params, &r);
+  if (rc) return rc;
+  if (!out) return fail(SNG_EINVAL, "out is NULL");
+  std::memset(out, 0, sizeof(*out));
+  device_sms();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch s(st);
+  Timer tm((params->flags & SNG_FLAG_TIMING) != 0);
+  GraphBufs gb;
+  gb.col_owned_by_caller = true;
+  rc = run_graph(x, params, r, s, &gb, nullptr, &tm);
+  if (rc) {
+    if (gb.col) cudaFree(gb.col);
+    return rc;
+  }
+  // library-owned outputs (plain allocations, released by sng_graph_free)
+  int64_t *row_ptr = nullptr;
+  int32_t *deg = nullptr;
+  uint8_t *core = nullptr;
+  int32_t *parent = nullptr, *labels = nullptr;
+  cudaError_t e = cudaMalloc((void **)&row_ptr, (size_t)(r.n + 1) * 8);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&deg, (size_t)r.n * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&core, (size_t)r.n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(row_ptr);
+    cudaFree(deg);
+    cudaFree(core);
+    cudaFree(gb.col);
+    return cuda_fail(e, "graph outputs");
+  }
+  auto free_all = [&]() {
+    cudaFree(row_ptr);
+    cudaFree(deg);
+    cudaFree(core);
+    cudaFree(gb.col);
+  };
+  if ((rc = s.alloc((void **)&parent, (size_t)r.n * 4, "parent")) ||
+      (rc = s.alloc((void **)&labels, (size_t)r.n * 4, "labels"))) {
+    cudaStreamSynchronize(st);
+    free_all();
+    return rc;
+  }
+  cudaMemcpyAsync(row_ptr, gb.row_ptr, (size_t)(r.n + 1) * 8, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(deg, gb.deg, (size_t)r.n * 4, cudaMemcpyDeviceToDevice, st);
+  CoreArgs ca{r.n, params->min_pts, gb.deg, nullptr, core, parent, labels};
+  launch_core_init(ca, device_sms(), st);
+  rc = read_stats(gb.counters, r, stats, st, &tm);
+  if (rc) {
+    free_all();
+    return rc;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    free_all();
+    return cuda_fail(e, "build_graph");
+  }
+  out->n = r.n;
+  out->m = r.m;
+  out->num_edges = gb.num_edges;
+  out->row_ptr = row_ptr;
+  out->col = gb.col;
+  out->deg = deg;
+  out->core = core;
+  s.release();
+  cudaStreamSynchronize(st);
+  return SNG_OK;
+}
+
+void sng_graph_free(sng_graph *g) {
+  if (!g) return;
+  cudaFree(g->row_ptr);
+  cudaFree(g->col);
+  cudaFree(g->deg);
+  cudaFree(g->core);
+  std::memset(g, 0, sizeof(*g));
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// api_common.cuh -- host-side helpers shared by the entry-point files.
+#pragma once
+
+#include <vector>
+
+#include "gather.cuh"
+
+namespace sng {
+
+// Parameters after validation, with the derived quantities the kernels use.
+struct Resolved {
+  int64_t n = 0;
+  int32_t d = 0;
+  int64_t m = 0;        // draws per point
+  int32_t W = 0;        // keep-bit words per row
+  float band_rel = 0.f;
+  double eps2 = 0.0, band = 0.0;
+  float lo_thr = 0.f, hi_thr = 0.f;
+  GatherMap map{};
+};
+
+// Stream-ordered device scratch, released on scope exit.
+struct Scratch {
+  explicit Scratch(cudaStream_t s) : stream(s) {}
+  ~Scratch();
+  sng_status alloc(void **out, size_t bytes, const char *what);
+  void release();
+  cudaStream_t stream;
+  std::vector<void *> ptrs;
+};
+
+// Per-phase CUDA-event marks for sng_stats.ms (SNG_FLAG_TIMING).
+class Timer {
+ public:
+  static constexpr int kMarks = 9;
+  explicit Timer(bool on);
+  ~Timer();
+  void mark(cudaStream_t st, int k);
+  void fill(float *ms) const;
+
+ private:
+  bool on_;
+  cudaEvent_t ev_[kMarks] = {};
+  bool used_[kMarks] = {};
+};
+
+struct GraphBufs {
+  uint32_t *bitmask = nullptr;
+  int32_t *out_cnt = nullptr;
+  int32_t *deg = nullptr;
+  uint8_t *band_flag = nullptr;
+  unsigned long long *counters = nullptr;
+  int64_t *tile_tmp = nullptr;
+  int64_t *row_ptr = nullptr;
+  int32_t *col = nullptr;
+  int64_t num_edges = 0;
+  bool col_owned_by_caller = false;  // true: col from cudaMalloc, not scratch
+};
+
+sng_status fail(sng_status st, const char *fmt, ...);
+sng_status cuda_fail(cudaError_t e, const char *what);
+int device_sms();
+sng_status validate(const void *x, const sng_params *p, Resolved *r);
+bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, GatherArgs *g);
+int gather_grid(int dtype, const GatherMap &map, int64_t n);
+sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scratch &s,
+                     GraphBufs *gb, const int32_t *m_row, Timer *tm);
+sng_status read_stats(const unsigned long long *counters, const Resolved &r, sng_stats *stats,
+                      cudaStream_t st, const Timer *tm);
+
+}  // namespace sng

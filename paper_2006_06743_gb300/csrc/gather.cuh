@@ -1,0 +1,218 @@
+// gather.cuh -- the sampled eps-graph kernel (Algorithm 1, step 2).
+//
+// One warp owns one source point i at a time and walks its m partner draws.
+// The warp is split into R = 32/G groups of G lanes; each group tests one
+// pair (i, p) per step: lane l of the group loads NCH vector chunks of VEC
+// elements of row p (coalesced 16-byte loads for FP32 float4 / BF16 x8),
+// accumulates squared differences against the same slice of row i held in
+// registers, and the group reduces with xor-shuffles.  Partner indices for
+// the next 32*U draws are hashed one per lane and staged in shared memory, so
+// U pair-loads per lane are in flight at once.  Keep bits are gathered with a
+// warp ballot into 32-bit words (bit j of word w = draw 32w + j), giving a
+// compact, deterministic record of the kept draws from which the CSR edge list
+// is filled in draw order.
+//
+// Decision rule: the FP32 value certifies the decision outside a guard band
+// [lo_thr, hi_thr] around eps^2 that is wider than the FP32 rounding error;
+// inside it the group leader recomputes d2 in FP64 in the oracle's order
+// (left to right, no contraction) from the FP32 values, so FP32 inputs give
+// the FP64 decision on every pair.  For BF16 inputs the band is a heuristic
+// (quantisation error is not bounded by it) and the recheck reads the FP32
+// master copy.
+#pragma once
+
+#include "sng_internal.cuh"
+
+namespace sng {
+
+struct GatherArgs {
+  const void *x;          // n x ld, element type T
+  int64_t ld;
+  const float *xm;        // FP32 values for the FP64 recheck (x itself for F32)
+  int64_t ldm;
+  int32_t n, d, m, W;     // W = ceil(m/32) words per bitmask row
+  uint64_t seed;
+  FastMod fm;
+  float lo_thr, hi_thr;   // d2 < lo_thr: keep; d2 > hi_thr: drop; else FP64
+  double eps2;            // (double)eps * (double)eps
+  double band;            // band_rel * eps2 (reported band half-width)
+  int32_t sample_all;
+  int32_t deg_mode;
+  const int32_t *m_row;   // nullable: draws of row i (<= m)
+  uint32_t *bitmask;      // n x W
+  int32_t *out_cnt;       // n, nullable
+  int32_t *deg;           // n (zeroed before launch in multigraph mode)
+  uint8_t *band_flag;     // n
+  unsigned long long *counters;
+};
+
+template <typename T>
+__device__ __forceinline__ bool recheck_pair(const GatherArgs &a, int32_t i, int32_t p) {
+  const double s = dist2_fp64(a.xm + (int64_t)i * a.ldm, a.xm + (int64_t)p * a.ldm, a.d);
+  atomicAdd(a.counters + kCntRecheck, 1ull);
+  if (fabs(__dsub_rn(s, a.eps2)) <= a.band) {
+    atomicAdd(a.counters + kCntBandPairs, 1ull);
+    a.band_flag[i] = 1;
+    a.band_flag[p] = 1;
+  }
+  return s <= a.eps2;
+}
+
+// One source row: draws 0..mi-1 of point i, keep bits into bitmask row i,
+// in-degree atomics; returns the row's kept count (same value on all lanes).
+// `sp` is this warp's 32*U-entry shared-memory partner buffer.
+template <typename T, int VEC, int G, int NCH, int U>
+__device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_t mi,
+                                          int32_t *sp, int lane) {
+  constexpr int R = 32 / G;      // pairs per warp step
+  constexpr int S = 32 * U;      // draws per stage
+  constexpr int STEPS = S / R;   // warp steps per stage
+  const int grp = lane / G;
+  const int gl = lane % G;
+  const T *X = static_cast<const T *>(a.x);
+  const int d = a.d;
+  const uint64_t key = row_key(a.seed, i);
+
+  // this lane's slice of row i; elements at or past d read as zero
+  float xi[NCH][VEC];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int off = (c * G + gl) * VEC;
+    if (off < d) {
+      Chunk<T, VEC>::load(X + (int64_t)i * a.ld + off, xi[c]);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k)
+        if (off + k >= d) xi[c][k] = 0.f;
+    } else {
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) xi[c][k] = 0.f;
+    }
+  }
+
+  int cnt = 0;
+  int jb = 0;
+  for (; jb < mi; jb += S) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t j = (int64_t)jb + u * 32 + lane;
+      int32_t p = -1;
+      if (j < mi) p = a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm);
+      sp[u * 32 + lane] = p;
+    }
+    __syncwarp();
+    uint32_t myword = 0;
+#pragma unroll 1
+    for (int t0 = 0; t0 < STEPS; t0 += U) {
+      float v[U][NCH][VEC];
+      int32_t pv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int t = t0 + u;
+        const int32_t p = sp[t * R + grp];
+        pv[u] = p;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const int off = (c * G + gl) * VEC;
+          if (p >= 0 && off < d) {
+            Chunk<T, VEC>::load(X + (int64_t)p * a.ld + off, v[u][c]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) v[u][c][k] = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int t = t0 + u;
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const int off = (c * G + gl) * VEC;
+          if (off + VEC <= d) {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+              const float diff = xi[c][k] - v[u][c][k];
+              acc = fmaf(diff, diff, acc);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+              float diff = xi[c][k] - v[u][c][k];
+              if (off + k >= d) diff = 0.f;
+              acc = fmaf(diff, diff, acc);
+            }
+          }
+        }
+#pragma unroll
+        for (int o = G / 2; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+        bool keep = false;
+        const int32_t p = pv[u];
+        if (gl == 0 && p >= 0) {
+          if (acc < a.lo_thr) {
+            keep = true;
+          } else if (!(acc > a.hi_thr)) {
+            keep = recheck_pair<T>(a, i, p);
+          }
+          if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, 1);
+        }
+        const uint32_t b = __ballot_sync(kFullMask, keep);
+        uint32_t bits;
+        if (G == 1) {
+          bits = b;
+        } else {
+          bits = 0;
+#pragma unroll
+          for (int g = 0; g < R; ++g) bits |= ((b >> (g * G)) & 1u) << g;
+        }
+        const int first = t * R;  // draw index within the stage
+        if (lane == (first >> 5)) myword |= bits << (first & 31);
+      }
+    }
+    const int w = (jb >> 5) + lane;
+    if (lane < U && w < a.W) a.bitmask[(int64_t)i * a.W + w] = myword;
+    cnt += __popc(myword);
+    __syncwarp();
+  }
+  // words past this row's draws (per-row draw counts) are zero
+  for (int w = (jb >> 5) + lane; w < a.W; w += 32) a.bitmask[(int64_t)i * a.W + w] = 0u;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) cnt += __shfl_xor_sync(kFullMask, cnt, o);
+  if (lane == 0) {
+    if (a.out_cnt) a.out_cnt[i] = cnt;
+    if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) {
+      if (cnt) atomicAdd(a.deg + i, cnt);
+    } else {
+      a.deg[i] = cnt;
+    }
+  }
+  return cnt;
+}
+
+template <typename T, int VEC, int G, int NCH, int U>
+__global__ void __launch_bounds__(256, 2) gather_kernel(GatherArgs a) {
+  extern __shared__ int32_t smem_partner[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  int32_t *sp = smem_partner + warp * 32 * U;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < a.n;
+       row += warps_total) {
+    const int32_t i = (int32_t)row;
+    const int32_t mi = a.m_row ? a.m_row[i] : a.m;
+    gather_row<T, VEC, G, NCH, U>(a, i, mi, sp, lane);
+  }
+}
+
+// Mapping of the gather: lanes per pair, chunks per lane, vector width,
+// batches in flight, block size.
+struct GatherMap {
+  int vec, group, nch, unroll, block;
+};
+
+// Host-side launcher; returns false if no compiled variant matches `map`.
+bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
+                   cudaStream_t stream);
+size_t gather_smem_bytes(const GatherMap &map);
+int gather_max_blocks_per_sm(int dtype, const GatherMap &map);
+
+}  // namespace sng

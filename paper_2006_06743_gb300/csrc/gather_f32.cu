@@ -1,0 +1,25 @@
+// gather_f32.cu -- FP32 gather mappings (float4 / float2 / scalar rows).
+#include "gather_inst.cuh"
+
+namespace sng {
+
+bool launch_gather_f32(const GatherMap &map, const GatherArgs &args, int grid,
+                       cudaStream_t stream) {
+  SNG_SHAPES_U(float, 4, 2, SNG_TRY)
+  SNG_SHAPES_U(float, 4, 4, SNG_TRY)
+  SNG_SHAPES_U(float, 4, 8, SNG_TRY)
+  SNG_SHAPES_U(float, 2, 4, SNG_TRY)
+  SNG_SHAPES_U(float, 1, 4, SNG_TRY)
+  return false;
+}
+
+int occ_gather_f32(const GatherMap &map) {
+  SNG_SHAPES_U(float, 4, 2, SNG_OCC)
+  SNG_SHAPES_U(float, 4, 4, SNG_OCC)
+  SNG_SHAPES_U(float, 4, 8, SNG_OCC)
+  SNG_SHAPES_U(float, 2, 4, SNG_OCC)
+  SNG_SHAPES_U(float, 1, 4, SNG_OCC)
+  return 0;
+}
+
+}  // namespace sng

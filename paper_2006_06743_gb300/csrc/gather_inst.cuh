@@ -1,0 +1,44 @@
+// gather_inst.cuh -- compiled mappings of the gather kernel and their dispatch.
+// Each translation unit that includes this defines SNG_GATHER_T / SNG_GATHER_VEC_MAX
+// and instantiates the kernel for the (group, chunks, unroll) combinations the
+// mapping policy and the autotuner choose from.
+#pragma once
+#include "gather.cuh"
+
+namespace sng {
+
+template <typename T, int VEC, int G, int NCH, int U>
+static bool try_launch(const GatherMap &m, const GatherArgs &args, int grid, cudaStream_t st) {
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return false;
+  const size_t smem = (size_t)(m.block / 32) * 32 * U * sizeof(int32_t);
+  gather_kernel<T, VEC, G, NCH, U><<<grid, m.block, smem, st>>>(args);
+  return true;
+}
+
+template <typename T, int VEC, int G, int NCH, int U>
+static int occ_blocks(const GatherMap &m) {
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return -1;
+  int blocks = 0;
+  const size_t smem = (size_t)(m.block / 32) * 32 * U * sizeof(int32_t);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, gather_kernel<T, VEC, G, NCH, U>,
+                                                    m.block, smem) != cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+// (group, chunks) shapes: thread-per-pair for tiny rows, sub-warp groups for
+// medium rows, whole warps (several chunks per lane) for wide rows.
+#define SNG_SHAPES_U(T, V, U, X)                                                         \
+  X(T, V, 1, 1, U) X(T, V, 2, 1, U) X(T, V, 4, 1, U) X(T, V, 8, 1, U) X(T, V, 16, 1, U) \
+  X(T, V, 32, 1, U) X(T, V, 16, 2, U) X(T, V, 32, 2, U) X(T, V, 32, 4, U)                \
+  X(T, V, 32, 8, U) X(T, V, 1, 2, U) X(T, V, 1, 4, U)
+
+#define SNG_TRY(T, V, G, N, U) \
+  if (try_launch<T, V, G, N, U>(map, args, grid, stream)) return true;
+#define SNG_OCC(T, V, G, N, U)                 \
+  {                                            \
+    int b = occ_blocks<T, V, G, N, U>(map);    \
+    if (b >= 0) return b;                      \
+  }
+
+}  // namespace sng

@@ -1,0 +1,266 @@
+// graph.cu -- CSR assembly and Algorithm 1, steps 3-5, on the device.
+//
+//  scan      exclusive prefix sum of kept draws per row -> row_ptr (int64)
+//  fill      row i's kept draws, in draw order, from its keep-bit words:
+//            a warp scans the popcounts of the row's words and every lane
+//            re-derives the partner of each set bit from the hash
+//  core      core[i] = deg[i] >= MinPts (step 3); parent[i] = i
+//  union     for every core-core edge, join the two components (step 3);
+//            the smaller index always wins, so each root is the component's
+//            smallest core index
+//  label     cores take their root; a non-core point adjacent (either
+//            direction) to a core takes the smallest adjacent root (step 4)
+//  finalize  untouched points become noise, -1 (step 5); counters for stats
+#include "graph.cuh"
+
+namespace sng {
+
+// ------------------------------------------------------------------ scan
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *total) {
+  __shared__ int64_t warp_sums[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(kFullMask, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t s = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(kFullMask, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const int64_t before = warp > 0 ? warp_sums[warp - 1] : 0;
+  if (total) *total = warp_sums[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tile_sums(const int32_t *cnt, int64_t n,
+                                                               int64_t *tile_sum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+    if (i < n) s += cnt[i];
+  }
+  int64_t total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+// One block scans all tile sums in place (exclusive), carrying across chunks.
+__global__ void __launch_bounds__(kScanThreads) scan_tile_offsets(int64_t *tile_sum,
+                                                                  int64_t ntiles,
+                                                                  unsigned long long *counters) {
+  int64_t carry = 0;
+  for (int64_t b = 0; b < ntiles; b += kScanThreads) {
+    const int64_t k = b + threadIdx.x;
+    const int64_t v = k < ntiles ? tile_sum[k] : 0;
+    int64_t total;
+    const int64_t ex = block_exclusive_scan(v, &total);
+    if (k < ntiles) tile_sum[k] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) counters[kCntEdges] = (unsigned long long)carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply(const int32_t *cnt, int64_t n,
+                                                           const int64_t *tile_off,
+                                                           int64_t *row_ptr) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + k;
+    v[k] = i < n ? cnt[i] : 0;
+    s += v[k];
+  }
+  int64_t ex = block_exclusive_scan(s, nullptr) + tile_off[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + k;
+    if (i < n) row_ptr[i] = ex;
+    ex += v[k];
+    if (i == n - 1) row_ptr[n] = ex;
+  }
+}
+
+int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+void launch_scan(const int32_t *cnt, int64_t n, int64_t *tile_tmp, int64_t *row_ptr,
+                 unsigned long long *counters, cudaStream_t st) {
+  const int64_t nt = scan_tiles(n);
+  scan_tile_sums<<<(unsigned)nt, kScanThreads, 0, st>>>(cnt, n, tile_tmp);
+  scan_tile_offsets<<<1, kScanThreads, 0, st>>>(tile_tmp, nt, counters);
+  scan_apply<<<(unsigned)nt, kScanThreads, 0, st>>>(cnt, n, tile_tmp, row_ptr);
+  note_launch(3);
+}
+
+// ------------------------------------------------------------------ fill
+
+__global__ void __launch_bounds__(256) fill_kernel(FillArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < a.n;
+       row += warps_total) {
+    const int32_t i = (int32_t)row;
+    const uint64_t key = row_key(a.seed, i);
+    int64_t pos = a.row_ptr[i];
+    const uint32_t *words = a.bitmask + (int64_t)i * a.W;
+    for (int wb = 0; wb < a.W; wb += 32) {
+      const int w = wb + lane;
+      uint32_t word = w < a.W ? words[w] : 0u;
+      const int c = __popc(word);
+      int ex = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFullMask, ex, o);
+        if (lane >= o) ex += y;
+      }
+      const int total = __shfl_sync(kFullMask, ex, 31);
+      int64_t at = pos + ex - c;
+      while (word) {
+        const int bit = __ffs(word) - 1;
+        word &= word - 1;
+        const int64_t j = (int64_t)w * 32 + bit;
+        a.col[at++] = a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm);
+      }
+      pos += total;
+    }
+  }
+}
+
+// ---------------------------------------------------- steps 3-5 (CC, labels)
+
+__global__ void core_init_kernel(CoreArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    uint8_t c = a.deg[i] >= a.min_pts ? 1 : 0;
+    if (a.forced) {
+      const uint8_t f = a.forced[i];
+      if (f == 1) c = 1;
+      if (f == 2) c = 0;
+    }
+    a.core[i] = c;
+    a.parent[i] = (int32_t)i;
+    a.labels[i] = c ? (int32_t)i : kNoLabel;
+  }
+}
+
+// Thread per row: join i with every core partner it kept.
+__global__ void union_kernel(UnionArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    if (!a.core[i]) continue;
+    const int64_t e1 = a.row_ptr[i + 1];
+    for (int64_t e = a.row_ptr[i]; e < e1; ++e) {
+      const int32_t p = a.col[e];
+      if (a.core[p]) uf_unite(a.parent, (int32_t)i, p, status);
+    }
+  }
+}
+
+__global__ void label_kernel(UnionArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const int64_t e0 = a.row_ptr[i], e1 = a.row_ptr[i + 1];
+    if (a.core[i]) {
+      const int32_t r = uf_root(a.parent, (int32_t)i, status);
+      a.labels[i] = r;
+      for (int64_t e = e0; e < e1; ++e) {
+        const int32_t p = a.col[e];
+        if (!a.core[p]) atomicMin(a.labels + p, r);
+      }
+    } else {
+      int32_t best = kNoLabel;
+      for (int64_t e = e0; e < e1; ++e) {
+        const int32_t p = a.col[e];
+        if (a.core[p]) {
+          const int32_t r = uf_root(a.parent, p, status);
+          best = r < best ? r : best;
+        }
+      }
+      if (best != kNoLabel) atomicMin(a.labels + i, best);
+    }
+  }
+}
+
+__global__ void finalize_kernel(FinalizeArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long cores = 0, clusters = 0, noise = 0, band = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    int32_t l = a.labels[i];
+    if (l == kNoLabel) {
+      l = -1;
+      a.labels[i] = -1;
+    }
+    const bool c = a.core[i] != 0;
+    cores += c;
+    clusters += (c && l == (int32_t)i);
+    noise += (l < 0);
+    if (a.band_flag) band += a.band_flag[i] != 0;
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    cores += __shfl_xor_sync(kFullMask, cores, o);
+    clusters += __shfl_xor_sync(kFullMask, clusters, o);
+    noise += __shfl_xor_sync(kFullMask, noise, o);
+    band += __shfl_xor_sync(kFullMask, band, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (cores) atomicAdd(a.counters + kCntCores, cores);
+    if (clusters) atomicAdd(a.counters + kCntClusters, clusters);
+    if (noise) atomicAdd(a.counters + kCntNoise, noise);
+    if (band) atomicAdd(a.counters + kCntBandPoints, band);
+  }
+}
+
+static int grid_for(int64_t n, int threads, int max_blocks) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > max_blocks) b = max_blocks;
+  return (int)(b < 1 ? 1 : b);
+}
+
+void launch_fill(const FillArgs &a, int sms, cudaStream_t st) {
+  fill_kernel<<<grid_for(a.n * 32, 256, sms * 8), 256, 0, st>>>(a);
+  note_launch();
+}
+
+void launch_core_init(const CoreArgs &a, int sms, cudaStream_t st) {
+  core_init_kernel<<<grid_for(a.n, 256, sms * 16), 256, 0, st>>>(a);
+  note_launch();
+}
+
+void launch_union(const UnionArgs &a, int sms, cudaStream_t st) {
+  union_kernel<<<grid_for(a.n, 256, sms * 16), 256, 0, st>>>(a);
+  note_launch();
+}
+
+void launch_label(const UnionArgs &a, int sms, cudaStream_t st) {
+  label_kernel<<<grid_for(a.n, 256, sms * 16), 256, 0, st>>>(a);
+  note_launch();
+}
+
+void launch_finalize(const FinalizeArgs &a, int sms, cudaStream_t st) {
+  finalize_kernel<<<grid_for(a.n, 256, sms * 8), 256, 0, st>>>(a);
+  note_launch();
+}
+
+}  // namespace sng

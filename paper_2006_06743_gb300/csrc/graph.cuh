@@ -1,0 +1,56 @@
+// graph.cuh -- launchers for CSR assembly and the core/component/label steps.
+#pragma once
+
+#include "sng_internal.cuh"
+
+namespace sng {
+
+struct FillArgs {
+  int64_t n;
+  int32_t W;
+  int32_t sample_all;
+  uint64_t seed;
+  FastMod fm;
+  const uint32_t *bitmask;
+  const int64_t *row_ptr;
+  int32_t *col;
+};
+
+struct CoreArgs {
+  int64_t n;
+  int32_t min_pts;
+  const int32_t *deg;
+  const uint8_t *forced;  // nullable: 1 = core, 2 = not core, 0 = by degree
+  uint8_t *core;
+  int32_t *parent;
+  int32_t *labels;
+};
+
+struct UnionArgs {
+  int64_t n;
+  const int64_t *row_ptr;
+  const int32_t *col;
+  const uint8_t *core;
+  int32_t *parent;
+  int32_t *labels;
+  unsigned long long *counters;
+};
+
+struct FinalizeArgs {
+  int64_t n;
+  const uint8_t *core;
+  const uint8_t *band_flag;  // nullable
+  int32_t *labels;
+  unsigned long long *counters;
+};
+
+int64_t scan_tiles(int64_t n);
+void launch_scan(const int32_t *cnt, int64_t n, int64_t *tile_tmp, int64_t *row_ptr,
+                 unsigned long long *counters, cudaStream_t st);
+void launch_fill(const FillArgs &a, int sms, cudaStream_t st);
+void launch_core_init(const CoreArgs &a, int sms, cudaStream_t st);
+void launch_union(const UnionArgs &a, int sms, cudaStream_t st);
+void launch_label(const UnionArgs &a, int sms, cudaStream_t st);
+void launch_finalize(const FinalizeArgs &a, int sms, cudaStream_t st);
+
+}  // namespace sng

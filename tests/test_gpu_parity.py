@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Integer outputs (partners, CSR, degrees, core mask,
+labels) must be bit-exact; FP32 inputs give FP64 decisions on every pair
+thanks to the in-kernel FP64 recheck inside the guard band."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import BAND_F32, need_gpu, padded
+from paper_2006_06743_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n", [2, 3, 17, 1000, 123_457, 2**31 - 1])
+def test_partners_match_oracle(orc, n):
+    torch, sng = need_gpu()
+    rows = min(n, 64)
+    for seed in (0, 12345, 2**64 - 1):
+        for i0 in (0, max(0, n - rows)):
+            g = sng.sample_partners(n, seed, i0, rows, 97).cpu().numpy()
+            o = orc.partners(seed, n, i0, rows, 97)
+            np.testing.assert_array_equal(g, o)
+
+
+def test_partners_sample_all(orc):
+    torch, sng = need_gpu()
+    g = sng.sample_partners(50, 0, 0, 50, 49, sample_all=True).cpu().numpy()
+    np.testing.assert_array_equal(g, orc.partners(0, 50, 0, 50, 49, sample_all=True))
+
+
+def _compare_graph(orc, x_np, xg, p, sng, master=None):
+    n = x_np.shape[0]
+    m = p.draws(n)
+    g = sng.build_graph(xg, p, x_master=master)
+    rp, col, band_pairs, bp = orc.build_rows(x_np, p.eps, p.seed, m,
+                                             sample_all=p.sample_mode == 1, band_rel=BAND_F32)
+    np.testing.assert_array_equal(g["row_ptr"].cpu().numpy(), rp)
+    np.testing.assert_array_equal(g["col"].cpu().numpy(), col)
+    deg = orc.degrees(n, rp, col, mode=p.degree_mode)
+    np.testing.assert_array_equal(g["deg"].cpu().numpy(), deg)
+    np.testing.assert_array_equal(g["core"].cpu().numpy(), (deg >= p.min_pts).astype(np.uint8))
+    assert g["stats"]["kept_edges"] == col.size
+    assert g["stats"]["band_pairs"] == band_pairs
+    return g
+
+
+SHAPES = [(2, 1), (3, 2), (257, 1), (300, 2), (500, 3), (777, 4), (1000, 7), (1200, 8),
+          (900, 16), (1500, 31), (2000, 32), (1000, 64), (1500, 65), (600, 128), (400, 200)]
+
+
+@pytest.mark.parametrize("n,d", SHAPES)
+def test_graph_matches_oracle(orc, n, d):
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=n * 31 + d)
+    eps = float(np.float32(0.12 * math.sqrt(d) if d > 1 else 0.05))
+    p = sng.Params(eps=eps, min_pts=4, m=min(150, 3 * n), seed=d)
+    xg = torch.from_numpy(x).cuda()
+    _compare_graph(orc, x, xg, p, sng)
+
+
+@pytest.mark.parametrize("n,d,ld", [(500, 3, 4), (500, 3, 3), (700, 5, 9), (300, 64, 72),
+                                    (400, 33, 33), (350, 2, 6), (600, 17, 20)])
+def test_graph_padded_rows(orc, n, d, ld):
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=ld)
+    eps = float(np.float32(0.15 * math.sqrt(d)))
+    xg, _buf = padded(torch, x, ld)
+    assert xg.stride(0) == ld
+    p = sng.Params(eps=eps, min_pts=3, m=120, seed=ld + 1)
+    _compare_graph(orc, x, xg, p, sng)
+
+
+COMPILED_SHAPES = [(1, 1), (2, 1), (4, 1), (8, 1), (16, 1), (32, 1), (16, 2), (32, 2), (32, 4),
+                   (32, 8), (1, 2), (1, 4)]
+
+
+@pytest.mark.parametrize("group,nch", COMPILED_SHAPES)
+@pytest.mark.parametrize("unroll", [2, 4, 8])
+def test_mapping_overrides_agree(orc, group, nch, unroll):
+    """Every compiled lanes-per-pair / chunks / batches-in-flight mapping gives
+    the oracle's graph (rows one element short of the mapping's width)."""
+    torch, sng = need_gpu()
+    d = group * nch * 4 - 1
+    n = 600
+    x = datagen.random_points(n, d, seed=group * 10 + nch)
+    xg, _buf = padded(torch, x, d + 1)
+    p = sng.Params(eps=float(np.float32(0.12 * math.sqrt(d))), min_pts=4, m=150, seed=9,
+                   map_group=group, map_unroll=unroll)
+    _compare_graph(orc, x, xg, p, sng)
+
+
+def _compare_cluster(orc, x_np, xg, p, sng):
+    n = x_np.shape[0]
+    m = p.draws(n)
+    labels, core, st = sng.cluster(xg, p, want_core=True)
+    r = orc.cluster(x_np, p.eps, p.seed, m, p.min_pts, deg_mode=p.degree_mode,
+                    sample_all=p.sample_mode == 1, band_rel=BAND_F32)
+    np.testing.assert_array_equal(core.cpu().numpy(), r["core"])
+    np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
+    for k in ("kept_edges", "band_pairs", "band_points", "cores", "clusters", "noise"):
+        assert st[k] == r[k], (k, st[k], r[k])
+    assert st["queries"] == n * m
+    return labels, st
+
+
+@pytest.mark.parametrize("n,d,m,mp", [(2, 1, 1, 1), (50, 2, 49, 2), (3000, 2, 60, 3),
+                                      (5000, 3, 100, 4), (4000, 8, 200, 6), (3000, 64, 300, 10),
+                                      (2500, 128, 128, 8)])
+@pytest.mark.parametrize("deg_mode", [0, 1])
+def test_cluster_matches_oracle(orc, n, d, m, mp, deg_mode):
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=n + d)
+    eps = float(np.float32(0.1 * math.sqrt(d)))
+    p = sng.Params(eps=eps, min_pts=mp, m=m, seed=n, degree_mode=deg_mode)
+    _compare_cluster(orc, x, torch.from_numpy(x).cuda(), p, sng)
+
+
+def test_config_small_2d_mixture(orc):
+    """n = 10,000 points in d = 2 (95% from 5 Gaussians, 5% uniform), s = 0.01,
+    eps = 0.03, MinPts = 3, seed 0: every label equal to the oracle's."""
+    torch, sng = need_gpu()
+    x = datagen.mixture_2d(10_000, seed=0)
+    p = sng.Params(eps=0.03, min_pts=3, s=0.01, seed=0)
+    assert p.draws(10_000) == 100
+    labels, st = _compare_cluster(orc, x, torch.from_numpy(x).cuda(), p, sng)
+    assert st["clusters"] >= 1
+
+
+@pytest.mark.parametrize("seed,n,d,m_db", [(0, 400, 2, 3), (1, 600, 3, 4), (2, 300, 8, 2)])
+def test_sample_all_equals_textbook_dbscan(orc, seed, n, d, m_db):
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=seed)
+    eps = float(np.float32(0.08 * math.sqrt(d)))
+    p = sng.Params(eps=eps, min_pts=2 * (m_db - 1), sample_mode=1)
+    labels, st = sng.cluster(torch.from_numpy(x).cuda(), p)
+    bl, _ = orc.dbscan_bruteforce(x, eps, m_db)
+    np.testing.assert_array_equal(labels.cpu().numpy(), bl)
+
+
+def test_integer_grid_ties_at_eps(orc):
+    """Small-integer points put many pairs exactly at eps (d2 == eps^2): the
+    closed ball keeps them, on both sides."""
+    torch, sng = need_gpu()
+    x = datagen.random_points(4000, 3, seed=8, kind="grid")
+    p = sng.Params(eps=2.0, min_pts=6, m=300, seed=3)
+    labels, st = _compare_cluster(orc, x, torch.from_numpy(x).cuda(), p, sng)
+    assert st["band_pairs"] > 0 and st["band_points"] > 0
+
+
+def test_degenerate_all_noise_and_single_cluster(orc):
+    torch, sng = need_gpu()
+    x = datagen.random_points(3000, 4, seed=2)
+    xg = torch.from_numpy(x).cuda()
+    labels, st = sng.cluster(xg, sng.Params(eps=1e-6, min_pts=2, m=50, seed=1))
+    assert (labels.cpu().numpy() == -1).all() and st["kept_edges"] == 0 and st["clusters"] == 0
+    labels, st = _compare_cluster(orc, x, xg, sng.Params(eps=10.0, min_pts=2, m=50, seed=1), sng)
+    assert (labels.cpu().numpy() == 0).all() and st["clusters"] == 1
+
+
+def test_duplicate_points(orc):
+    """All points identical: every draw is kept at distance 0."""
+    torch, sng = need_gpu()
+    x = np.ones((1000, 5), dtype=np.float32)
+    labels, st = _compare_cluster(orc, x, torch.from_numpy(x).cuda(),
+                                  sng.Params(eps=1e-3, min_pts=3, m=40, seed=4), sng)
+    assert st["kept_edges"] == 40_000
+
+
+def test_nonfinite_coordinates(orc):
+    """NaN and inf rows never pass the eps-test (on both sides)."""
+    torch, sng = need_gpu()
+    x = datagen.random_points(2000, 3, seed=6)
+    x[5] = np.nan
+    x[17, 1] = np.inf
+    x[18, 2] = -np.inf
+    _compare_cluster(orc, x, torch.from_numpy(x).cuda(),
+                     sng.Params(eps=0.2, min_pts=4, m=200, seed=6), sng)
+
+
+def test_repeat_calls_identical():
+    torch, sng = need_gpu()
+    x = torch.from_numpy(datagen.random_points(20_000, 16, seed=1)).cuda()
+    p = sng.Params(eps=0.3, min_pts=5, m=100, seed=2)
+    a, _ = sng.cluster(x, p)
+    b, _ = sng.cluster(x, p)
+    assert torch.equal(a, b)
+
+
+def test_ari_kernel_matches_oracle(orc):
+    torch, sng = need_gpu()
+    rng = np.random.default_rng(0)
+    for n in (2, 10, 5000, 200_000):
+        a = rng.integers(-1, max(1, n // 7), size=n).astype(np.int32)
+        b = np.where(rng.uniform(size=n) < 0.8, a, rng.integers(-1, n, size=n)).astype(np.int32)
+        got = sng.ari(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+        assert abs(got - orc.ari(a, b)) < 1e-9
