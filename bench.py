@@ -33,6 +33,8 @@ WORKLOADS = {
     # name: (n, d, k, noise, s, min_pts)
     "mixture-n1M-d64": (1_000_000, 64, 100, 0.02, 0.001, 10),
     "mixture-n100k-d64": (100_000, 64, 100, 0.02, 0.01, 10),
+    # profiling case of the same gather: same points (256 MB > L2), 100 draws
+    "mixture-n1M-d64-s1e-4": (1_000_000, 64, 100, 0.02, 0.0001, 10),
 }
 
 
@@ -163,7 +165,15 @@ def bench_sng(args, w):
     n, d, m = w["n"], w["d"], w["m"]
     params = sng.Params(eps=w["eps"], min_pts=w["min_pts"], s=w["s"], seed=w["seed"],
                         flags=sng.SNG_FLAG_TIMING, map_group=args.map_group,
-                        map_unroll=args.map_unroll, map_block=args.map_block)
+                        map_unroll=args.map_unroll, map_block=args.map_block,
+                        map_passes=args.map_passes)
+    tuned = None
+    if args.autotune and not (args.map_group or args.map_unroll or args.map_block
+                              or args.map_passes):
+        from paper_2006_06743_gb300 import autotune
+        tuned = autotune.tune(x, params, reps=2, budget_s=args.tune_budget,
+                              verbose=args.verbose, force=args.retune)
+        params = autotune.apply(params, tuned)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -238,7 +248,10 @@ def bench_sng(args, w):
         "data": "synthetic (seeded Gaussian mixture, no dataset)",
         "config": {"workload": args.workload, "n": n, "d": d, "m": m, "s": w["s"],
                    "eps": w["eps"], "min_pts": w["min_pts"], "queries_per_step": Q,
-                   "l2": "flushed between steps (512 MB write)", "parallelism": f"dp{world}"},
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"dp{world}",
+                   "gather_mapping": {k: getattr(params, k) for k in
+                                      ("map_group", "map_unroll", "map_block", "map_passes")},
+                   "autotuned": tuned is not None},
         "e2e": {"value": Q * world / (t_e2e * 1e-3), "unit": "queries/s",
                 "seconds": t_e2e * 1e-3,
                 "h2d_bytes_per_step": int(x_host.numel() * 4),
@@ -297,6 +310,11 @@ def main():
     ap.add_argument("--map-group", type=int, default=0)
     ap.add_argument("--map-unroll", type=int, default=0)
     ap.add_argument("--map-block", type=int, default=0)
+    ap.add_argument("--map-passes", type=int, default=0)
+    ap.add_argument("--autotune", type=int, default=1, help="1: tune the gather mapping first")
+    ap.add_argument("--retune", action="store_true")
+    ap.add_argument("--tune-budget", type=float, default=40.0)
+    ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)

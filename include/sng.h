@@ -93,6 +93,9 @@ typedef struct {
     int32_t map_unroll;   /* partner batches in flight per warp, 0 = default */
     int32_t map_block;    /* threads per block of the gather, 0 = default    */
     int32_t map_tile;     /* batched form: source rows per work item, 0 = default */
+    int32_t map_passes;   /* gather: 0/1 = one pass over all partners; k > 1 = k
+                             launches, each testing only the draws whose partner
+                             lies in one of k equal slices of X (L2-resident) */
 } sng_params;
 
 typedef struct {
@@ -104,6 +107,8 @@ typedef struct {
     int64_t clusters;     /* connected components of the core subgraph       */
     int64_t noise;        /* points labelled -1                              */
     int64_t recheck_pairs;/* draws recomputed in FP64 (guard band)           */
+    int64_t surrogate_core;  /* surrogate form: points gated as confident core */
+    int64_t surrogate_noise; /* surrogate form: points gated as confident noise */
     float ms[8];          /* SNG_FLAG_TIMING: [0] gather [1] scan [2] fill
                              [3] core+union [4] labels [5] finalize [6] total */
 } sng_stats;
@@ -176,6 +181,70 @@ sng_status sng_sample_partners(int64_t n, uint64_t seed, int64_t i0, int64_t row
  * Section 5) of two labelings a, b (device int32[n], values in [-1, 2^31)),
  * noise as one label.  Synchronises `stream`; result in *ari (host). */
 sng_status sng_ari(const int32_t *a, const int32_t *b, int64_t n, double *ari, void *stream);
+
+/*
+ * Core-point surrogate (no counterpart in the paper): a d -> 128 -> 128 -> 1
+ * perceptron, exact-erf GELU, FP16-rounded weights with FP32 accumulation,
+ * predicting whether Algorithm 1 makes a point a core point (step 3).  Points
+ * it is confident about skip most of their sampled queries (step 2).
+ *
+ * Parameter vector: device FP32, sng_mlp_param_count(d, 128) entries, laid out
+ *   [W1 (128 x d) | b1 (128) | W2 (128 x 128) | b2 (128) | w3 (128) | b3 (1) |
+ *    mean (d) | std (d)]
+ * W rows are output units.  The first count - 2d entries are trained; mean and
+ * std standardise the inputs, u = (x - mean) / std.  Points are n x d FP32
+ * rows (row stride d) unless stated otherwise.
+ */
+typedef struct {
+    int32_t d;            /* input features, 1..64 (= the points' d)          */
+    int32_t hidden;       /* hidden width; must be 128                         */
+    int32_t batch;        /* training batch size (sng_mlp_train)              */
+    float lr, beta1, beta2, adam_eps; /* Adam (Kingma & Ba 2015)               */
+    uint64_t seed;        /* batch rows drawn with replacement by the hash    */
+    int32_t sequential;   /* 1: batch b of step t takes rows (t*batch + b) mod n
+                             in order instead of hashed draws                 */
+} sng_mlp_config;
+
+/* Entries of the parameter vector, or -1 for an unsupported shape. */
+int64_t sng_mlp_param_count(int32_t d, int32_t hidden);
+
+/* Column mean / std of x (device n x d) into the mean/std slots of params. */
+sng_status sng_mlp_standardize(const float *x, int64_t n, int32_t d, float *params,
+                               void *stream);
+
+/* Mean binary cross-entropy of the logits against y (device uint8 0/1, n <=
+ * 2^24) and its gradient w.r.t. the trained entries (grad: device FP32,
+ * count - 2d).  *loss is written on the host; synchronises `stream`. */
+sng_status sng_mlp_loss_grad(const float *x, const uint8_t *y, int64_t n,
+                             const sng_mlp_config *cfg, const float *params, float *grad,
+                             double *loss, void *stream);
+
+/* `steps` Adam steps (step numbers step0+1 .. step0+steps), each on a batch
+ * of cfg->batch rows drawn by the hash from (seed, step) (or taken in order,
+ * cfg->sequential).  params / adam_m /
+ * adam_v: device FP32 (moments count - 2d entries, zero before the first
+ * step).  loss_trace: device FP32[steps] batch losses, or NULL. */
+sng_status sng_mlp_train(const float *x, const uint8_t *y, int64_t n, const sng_mlp_config *cfg,
+                         float *params, float *adam_m, float *adam_v, int64_t step0,
+                         int64_t steps, float *loss_trace, void *stream);
+
+/* p(core) = sigmoid(logit) for every row of x (device n x d) into prob. */
+sng_status sng_mlp_predict(const float *x, int64_t n, const sng_mlp_config *cfg,
+                           const float *params, float *prob, void *stream);
+
+/*
+ * Algorithm 1 gated by the surrogate.  Points with p < p_noise are not core
+ * and draw no partners (they can still become border points through other
+ * points' draws); points with p > p_core are core and draw only the first
+ * ceil(core_draw_frac * m) partners of the same hash stream (enough to keep
+ * their component connected); all other points draw all m partners and are
+ * core by degree.  Same arguments and outputs as sng_cluster (x: FP32, row
+ * stride params->ld); stats->queries counts the queries actually issued.
+ */
+sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
+                                 const sng_mlp_config *cfg, const float *mlp_params,
+                                 float p_noise, float p_core, float core_draw_frac,
+                                 int32_t *labels, uint8_t *core, sng_stats *stats, void *stream);
 
 /* Number of kernels this library has launched in this process. */
 int64_t sng_launch_count(void);

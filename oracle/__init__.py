@@ -77,6 +77,11 @@ def _load():
         lib.orc_build_rows.argtypes = [i64, i32, i64, P, f32, u64, i64, i32, f64, P, i64,
                                        ctypes.POINTER(_Graph), P]
         lib.orc_build_rows.restype = i32
+        lib.orc_build_rows_m.argtypes = [i64, i32, i64, P, f32, u64, i64, i32, f64, P, i64,
+                                         ctypes.POINTER(_Graph), P, P]
+        lib.orc_build_rows_m.restype = i32
+        lib.orc_cluster_graph_forced.argtypes = [i64, P, P, i32, i32, P, P, P, P, P]
+        lib.orc_cluster_graph_forced.restype = i32
         lib.orc_graph_free.argtypes = [ctypes.POINTER(_Graph)]
         lib.orc_graph_free.restype = None
         lib.orc_degrees.argtypes = [i64, P, P, i32, P]
@@ -139,8 +144,9 @@ def dist2(a, b) -> float:
 # ------------------------------------------------------------ graph build
 
 def build_rows(x, eps: float, seed: int, m: int, sample_all: bool = False,
-               band_rel: float = 1e-5, rows=None):
-    """Algorithm 1, step 2 for the given rows (default all).
+               band_rel: float = 1e-5, rows=None, m_row=None):
+    """Algorithm 1, step 2 for the given rows (default all).  ``m_row`` (int32
+    per point) limits point i to its first m_row[i] draws (surrogate form).
 
     Returns ``(row_ptr int64[nr+1], col int32[E], band_pairs, band_point uint8[n])``.
     """
@@ -153,8 +159,10 @@ def build_rows(x, eps: float, seed: int, m: int, sample_all: bool = False,
     else:
         rows_arr = np.ascontiguousarray(rows, dtype=np.int64)
         nr, rp = rows_arr.size, _ptr(rows_arr)
-    rc = lib.orc_build_rows(n, d, ld, _ptr(x), ctypes.c_float(eps), seed & (2**64 - 1), m,
-                            int(sample_all), band_rel, rp, nr, ctypes.byref(g), _ptr(bp))
+    mr = None if m_row is None else np.ascontiguousarray(m_row, dtype=np.int32)
+    rc = lib.orc_build_rows_m(n, d, ld, _ptr(x), ctypes.c_float(eps), seed & (2**64 - 1), m,
+                              int(sample_all), band_rel, rp, nr, ctypes.byref(g), _ptr(bp),
+                              _ptr(mr) if mr is not None else None)
     if rc != 0:
         raise ValueError("orc_build_rows failed (bad arguments or out of memory)")
     try:
@@ -203,16 +211,20 @@ def border_labels(n: int, row_ptr, col, core, comp) -> np.ndarray:
     return labels
 
 
-def cluster_graph(n: int, row_ptr, col, min_pts: int, deg_mode: int = 0) -> dict:
-    """Algorithm 1, steps 3-5 on a given sampled graph (CSR by source)."""
+def cluster_graph(n: int, row_ptr, col, min_pts: int, deg_mode: int = 0, forced=None) -> dict:
+    """Algorithm 1, steps 3-5 on a given sampled graph (CSR by source).
+    ``forced`` (uint8 per point: 1 core, 2 not core, 0 by degree) overrides
+    the core test (surrogate form)."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     cl = np.ascontiguousarray(col, dtype=np.int32)
+    fc = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8)
     labels = np.empty(n, dtype=np.int32)
     core = np.empty(n, dtype=np.uint8)
     deg = np.empty(n, dtype=np.int32)
     stats = np.zeros(8, dtype=np.int64)
-    if _load().orc_cluster_graph(n, _ptr(rp), _ptr(cl), deg_mode, min_pts, _ptr(labels),
-                                 _ptr(core), _ptr(deg), _ptr(stats)) != 0:
+    if _load().orc_cluster_graph_forced(n, _ptr(rp), _ptr(cl), deg_mode, min_pts,
+                                        _ptr(fc) if fc is not None else None, _ptr(labels),
+                                        _ptr(core), _ptr(deg), _ptr(stats)) != 0:
         raise MemoryError("orc_cluster_graph failed")
     return dict(labels=labels, core=core, deg=deg, kept_edges=int(stats[1]),
                 cores=int(stats[4]), clusters=int(stats[5]), noise=int(stats[6]))
@@ -238,6 +250,17 @@ def cluster(x, eps: float, seed: int, m: int, min_pts: int, deg_mode: int = 0,
     return dict(labels=labels, core=core, deg=deg, band_point=bp, queries=int(stats[0]),
                 kept_edges=int(stats[1]), band_pairs=int(stats[2]), band_points=int(stats[3]),
                 cores=int(stats[4]), clusters=int(stats[5]), noise=int(stats[6]))
+
+
+def cluster_gated(x, eps: float, seed: int, m: int, min_pts: int, forced, m_row,
+                  deg_mode: int = 0) -> dict:
+    """The surrogate-gated form of Algorithm 1: point i draws its first
+    m_row[i] partners, and forced[i] (1 core, 2 not core, 0 by degree)
+    overrides the core test; steps 3-5 as in the plain form."""
+    rp, col, _, _ = build_rows(x, eps, seed, m, m_row=m_row)
+    r = cluster_graph(np.asarray(x).shape[0], rp, col, min_pts, deg_mode=deg_mode, forced=forced)
+    r["queries"] = int(np.minimum(np.asarray(m_row, dtype=np.int64), m).sum())
+    return r
 
 
 def dbscan_bruteforce(x, eps: float, min_pts_db: int) -> tuple[np.ndarray, np.ndarray]:

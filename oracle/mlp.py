@@ -18,8 +18,8 @@ the optimiser is Adam (Kingma & Ba 2015) with bias correction.
 Pins (tests/test_oracle_mlp.py): central finite differences of ``loss`` for
 every parameter tensor, GELU against Phi values from the error function,
 BCE against its closed form at z = 0 (log 2), the first Adam step equal to
-lr * sign(g) up to eps, and a network whose weights reduce it to logistic
-regression.
+lr * sign(g) up to eps, and training that drives the loss of a separable
+problem down.
 """
 from __future__ import annotations
 
@@ -94,12 +94,13 @@ def backward(params: dict, x, y, mean, std) -> tuple[float, dict]:
 
 def adam_step(params: dict, grads: dict, state: dict, lr=1e-3, beta1=0.9, beta2=0.999,
               eps=1e-8) -> dict:
-    """One Adam update (Kingma & Ba 2015, Algorithm 1) in FP64.  ``state``
-    holds ``t`` and the first/second moments; returns the new parameters."""
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) in FP64 of every tensor
+    named in ``grads``.  ``state`` holds ``t`` and the first/second moments;
+    returns the new parameters."""
     t = state.get("t", 0) + 1
     state["t"] = t
     out = {}
-    for k in PARAM_NAMES:
+    for k in grads:
         gk = np.asarray(grads[k], np.float64)
         mk = beta1 * state.get("m_" + k, np.zeros_like(gk)) + (1 - beta1) * gk
         vk = beta2 * state.get("v_" + k, np.zeros_like(gk)) + (1 - beta2) * gk * gk

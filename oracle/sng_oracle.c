@@ -115,10 +115,30 @@ void orc_graph_free(orc_graph *g)
  * NULL) gets a 1 at both ends of every draw whose FP64 d2 lies within
  * band_rel * eps^2 of eps^2.  Returns 0, or -1 on bad arguments / no memory.
  */
+int32_t orc_build_rows_m(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
+                         uint64_t seed, int64_t m, int32_t sample_all, double band_rel,
+                         const int64_t *rows, int64_t n_rows, orc_graph *out,
+                         uint8_t *band_point, const int32_t *m_row);
+
 int32_t orc_build_rows(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
                        uint64_t seed, int64_t m, int32_t sample_all, double band_rel,
                        const int64_t *rows, int64_t n_rows, orc_graph *out,
                        uint8_t *band_point)
+{
+    return orc_build_rows_m(n, d, ld, x, eps, seed, m, sample_all, band_rel, rows, n_rows, out,
+                            band_point, NULL);
+}
+
+/*
+ * As orc_build_rows, but point i draws only its first m_row[i] partners of
+ * the same stream (m_row == NULL: m for every point).  This is the graph of
+ * the surrogate-gated form: a point the gate calls noise draws nothing, one it
+ * calls core draws a prefix of its draws, an uncertain one draws all m.
+ */
+int32_t orc_build_rows_m(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
+                         uint64_t seed, int64_t m, int32_t sample_all, double band_rel,
+                         const int64_t *rows, int64_t n_rows, orc_graph *out,
+                         uint8_t *band_point, const int32_t *m_row)
 {
     if (n < 2 || d < 1 || ld < d || m < 0 || !out) return -1;
     if (sample_all && m != n - 1) return -1;
@@ -134,7 +154,9 @@ int32_t orc_build_rows(int64_t n, int32_t d, int64_t ld, const float *x, float e
     for (int64_t r = 0; r < n_rows; ++r) {
         int64_t i = rows ? rows[r] : r;
         const float *xi = x + i * ld;
-        for (int64_t j = 0; j < m; ++j) {
+        int64_t mi = m_row ? (int64_t)m_row[i] : m;
+        if (mi > m) mi = m;
+        for (int64_t j = 0; j < mi; ++j) {
             int64_t p = orc_partner(seed, i, j, n, sample_all);
             double d2 = orc_dist2(xi, x + p * ld, d);
             double gap = d2 - eps2;
@@ -337,9 +359,23 @@ void orc_border_labels(int64_t n, const int64_t *row_ptr, const int32_t *col,
 }
 
 /* stats[0..7]: queries, kept, band_pairs, band_points, cores, clusters, noise, 0 */
+int32_t orc_cluster_graph_forced(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                 int32_t deg_mode, int32_t min_pts, const uint8_t *forced,
+                                 int32_t *labels, uint8_t *core, int32_t *deg, int64_t *stats);
+
 int32_t orc_cluster_graph(int64_t n, const int64_t *row_ptr, const int32_t *col,
                           int32_t deg_mode, int32_t min_pts, int32_t *labels,
                           uint8_t *core, int32_t *deg, int64_t *stats)
+{
+    return orc_cluster_graph_forced(n, row_ptr, col, deg_mode, min_pts, NULL, labels, core, deg,
+                                    stats);
+}
+
+/* Steps 3-5 with an optional per-point override of the core test:
+ * forced[i] = 1 makes i core, 2 makes it non-core, 0 leaves deg >= MinPts. */
+int32_t orc_cluster_graph_forced(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                 int32_t deg_mode, int32_t min_pts, const uint8_t *forced,
+                                 int32_t *labels, uint8_t *core, int32_t *deg, int64_t *stats)
 {
     int32_t *dg = deg ? deg : (int32_t *)malloc((size_t)n * sizeof(int32_t));
     int32_t *comp = (int32_t *)malloc((size_t)n * sizeof(int32_t));
@@ -348,6 +384,8 @@ int32_t orc_cluster_graph(int64_t n, const int64_t *row_ptr, const int32_t *col,
     int64_t ncores = 0;
     for (int64_t i = 0; i < n; ++i) {
         core[i] = dg[i] >= min_pts ? 1 : 0;
+        if (forced && forced[i] == 1) core[i] = 1;
+        if (forced && forced[i] == 2) core[i] = 0;
         ncores += core[i];
     }
     int64_t ncomp = orc_components_bfs(n, row_ptr, col, core, comp);

@@ -47,7 +47,8 @@ class sng_params(ctypes.Structure):
                 ("m_override", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("x_f32_master", ctypes.c_void_p), ("flags", ctypes.c_uint32),
                 ("map_group", ctypes.c_int32), ("map_unroll", ctypes.c_int32),
-                ("map_block", ctypes.c_int32), ("map_tile", ctypes.c_int32)]
+                ("map_block", ctypes.c_int32), ("map_tile", ctypes.c_int32),
+                ("map_passes", ctypes.c_int32)]
 
 
 class sng_stats(ctypes.Structure):
@@ -55,12 +56,20 @@ class sng_stats(ctypes.Structure):
                 ("band_pairs", ctypes.c_int64), ("band_points", ctypes.c_int64),
                 ("cores", ctypes.c_int64), ("clusters", ctypes.c_int64),
                 ("noise", ctypes.c_int64), ("recheck_pairs", ctypes.c_int64),
+                ("surrogate_core", ctypes.c_int64), ("surrogate_noise", ctypes.c_int64),
                 ("ms", ctypes.c_float * 8)]
 
     def as_dict(self) -> dict:
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "ms"}
         d["ms"] = {PHASES[i]: float(self.ms[i]) for i in range(len(PHASES))}
         return d
+
+
+class sng_mlp_config(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("hidden", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("adam_eps", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("sequential", ctypes.c_int32)]
 
 
 class sng_graph(ctypes.Structure):
@@ -89,6 +98,18 @@ SIGNATURES = {
     "sng_sample_partners": (ctypes.c_int32, [ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64,
                                              ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _P, _P]),
     "sng_ari": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _P]),
+    "sng_mlp_param_count": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32]),
+    "sng_mlp_standardize": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
+    "sng_mlp_loss_grad": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(sng_mlp_config),
+                                           _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "sng_mlp_train": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(sng_mlp_config),
+                                       _P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "sng_mlp_predict": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.POINTER(sng_mlp_config), _P,
+                                         _P, _P]),
+    "sng_cluster_surrogate": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params),
+                                               ctypes.POINTER(sng_mlp_config), _P, ctypes.c_float,
+                                               ctypes.c_float, ctypes.c_float, _P, _P,
+                                               ctypes.POINTER(sng_stats), _P]),
     "sng_launch_count": (ctypes.c_int64, []),
     "sng_last_error": (ctypes.c_char_p, []),
     "sng_strerror": (ctypes.c_char_p, [ctypes.c_int32]),
@@ -150,6 +171,7 @@ class Params:
     map_unroll: int = 0
     map_block: int = 0
     map_tile: int = 0
+    map_passes: int = 0
 
     def to_c(self, n: int, d: int, ld: int, dtype: int, master_ptr: int = 0) -> sng_params:
         p = sng_params()
@@ -161,6 +183,7 @@ class Params:
         p.flags = self.flags
         p.map_group, p.map_unroll, p.map_block = self.map_group, self.map_unroll, self.map_block
         p.map_tile = self.map_tile
+        p.map_passes = self.map_passes
         return p
 
     def draws(self, n: int) -> int:

@@ -1,0 +1,132 @@
+"""Autotuner for the gather mapping (and the batched form's tiling).
+
+The gather's cost depends on how a warp is split over pairs (lanes per pair),
+how many partner rows each warp keeps in flight, the block size and, for
+point sets larger than L2, how many L2-resident slices of the partner range
+the launch is split into.  The library picks a rule-of-thumb mapping; this
+module times a small set of candidates on the caller's own data, through the
+library's per-phase CUDA-event timers, and caches the fastest per
+(dtype, d, row stride, n bucket, m bucket) in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+import time
+
+from . import SNG_FLAG_TIMING, Params, SngError, cluster
+
+CACHE_ENV = "SNG_AUTOTUNE_CACHE"
+
+
+def _cache_path(path: str | None) -> str:
+    if path:
+        return path
+    if os.environ.get(CACHE_ENV):
+        return os.environ[CACHE_ENV]
+    return os.path.join(os.path.expanduser("~"), ".cache", "sng_gb300", "autotune.json")
+
+
+def _bucket(v: int) -> int:
+    return 1 << max(0, int(math.ceil(math.log2(max(1, v)))))
+
+
+def key_for(x, p: Params) -> str:
+    n, d = x.shape
+    return (f"{str(x.dtype).replace('torch.', '')}-d{d}-ld{x.stride(0)}-n{_bucket(n)}"
+            f"-m{_bucket(p.draws(n))}-mode{p.sample_mode}")
+
+
+def _default_group(d: int, vec: int) -> int:
+    chunks = -(-d // vec)
+    g = 1
+    while g < chunks and g < 32:
+        g <<= 1
+    return g
+
+
+def candidates(x, p: Params) -> list[dict]:
+    import torch
+    n, d = x.shape
+    esize = 2 if x.dtype == torch.bfloat16 else 4
+    vec = 8 if esize == 2 else 4
+    if x.stride(0) % vec:
+        vec = 1
+    g0 = _default_group(d, vec)
+    groups = sorted({g for g in (g0, g0 // 2, g0 * 2) if 1 <= g <= 32})
+    x_bytes = n * x.stride(0) * esize
+    passes = [1]
+    if x_bytes > (48 << 20):
+        base = max(2, int(math.ceil(x_bytes / (48 << 20))))
+        passes += sorted({2, base, base + 2, 2 * base} - {1})
+    out = []
+    for g in groups:
+        for u in (2, 4, 8):
+            for b in (128, 256):
+                for ps in passes:
+                    out.append(dict(map_group=g, map_unroll=u, map_block=b, map_passes=ps))
+    return out
+
+
+def _time(x, p: Params, reps: int, x_master=None) -> float:
+    import torch
+    ms = []
+    for _ in range(reps):
+        _, st = cluster(x, p, x_master=x_master)
+        ms.append(st["ms"]["gather"])
+    torch.cuda.synchronize()
+    return statistics.median(ms)
+
+
+def tune(x, p: Params, x_master=None, reps: int = 3, budget_s: float = 60.0,
+         cache: str | None = None, force: bool = False, verbose: bool = False) -> dict:
+    """Fastest gather mapping for (x, p); returns the Params overrides and
+    the timing table.  Results are cached per shape bucket."""
+    path = _cache_path(cache)
+    key = key_for(x, p)
+    table = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    if not force and key in table:
+        return table[key]
+    base = dict(p.__dict__)
+    base["flags"] = base.get("flags", 0) | SNG_FLAG_TIMING
+    results = []
+    t_start = time.perf_counter()
+    for cand in candidates(x, p):
+        if time.perf_counter() - t_start > budget_s:
+            break
+        q = Params(**{**base, **cand})
+        try:
+            _time(x, q, 1, x_master)            # warm-up
+            t = _time(x, q, reps, x_master)
+        except SngError as e:                   # mapping not compiled for this shape
+            if verbose:
+                print("skip", cand, e)
+            continue
+        results.append((t, cand))
+        if verbose:
+            print(f"{t:9.3f} ms  {cand}")
+    if not results:
+        return {"mapping": {}, "gather_ms": None, "tried": 0}
+    results.sort(key=lambda r: r[0])
+    best = {"mapping": results[0][1], "gather_ms": results[0][0], "tried": len(results),
+            "table": [[t, c] for t, c in results[:12]]}
+    table[key] = best
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(table, f, indent=1)
+    except OSError:
+        pass
+    return best
+
+
+def apply(p: Params, best: dict) -> Params:
+    return Params(**{**p.__dict__, **best.get("mapping", {})})

@@ -167,6 +167,9 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   r->map.group = group;
   r->map.nch = nch;
   r->map.unroll = p->map_unroll > 0 ? p->map_unroll : 4;
+  if (p->map_passes < 0 || p->map_passes > 64) return fail(SNG_EINVAL, "map_passes must be in [0, 64]");
+  r->map.passes = p->map_passes > 0 ? p->map_passes : 1;
+  if (r->map.passes > p->n) r->map.passes = (int)p->n;
   r->map.block = p->map_block > 0 ? p->map_block : 256;
   if (r->map.block % 32 || r->map.block < 32 || r->map.block > 256)
     return fail(SNG_EINVAL, "map_block must be a multiple of 32 in [32, 256]");
@@ -215,7 +218,8 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
 
 int gather_grid(int dtype, const GatherMap &map, int64_t n) {
   const int sms = device_sms();
-  int per_sm = gather_max_blocks_per_sm(dtype, map);
+  int per_sm = map.passes > 1 ? gather_blocked_max_blocks_per_sm(dtype, map)
+                              : gather_max_blocks_per_sm(dtype, map);
   if (per_sm < 1) per_sm = 1;
   const int64_t warps_per_block = map.block / 32;
   int64_t need = (n + warps_per_block - 1) / warps_per_block;
@@ -250,12 +254,29 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   ga.deg = gb->deg;
   ga.band_flag = gb->band_flag;
   ga.counters = gb->counters;
-  tm->mark(st, 0);
   const int grid = gather_grid(p->dtype, r.map, n);
-  if (!launch_gather(p->dtype, r.map, ga, grid, st))
-    return fail(SNG_EINVAL, "no compiled gather for vec=%d group=%d nch=%d unroll=%d",
-                r.map.vec, r.map.group, r.map.nch, r.map.unroll);
-  note_launch();
+  if (r.map.passes > 1) {
+    cudaMemsetAsync(gb->bitmask, 0, (size_t)n * r.W * 4, st);
+    cudaMemsetAsync(gb->out_cnt, 0, (size_t)n * 4, st);
+  }
+  tm->mark(st, 0);
+  if (r.map.passes <= 1) {
+    if (!launch_gather(p->dtype, r.map, ga, grid, st))
+      return fail(SNG_EINVAL, "no compiled gather for vec=%d group=%d nch=%d unroll=%d",
+                  r.map.vec, r.map.group, r.map.nch, r.map.unroll);
+    note_launch();
+  } else {
+    // slices of the partner range, each small enough to stay in L2
+    const int64_t slice = (n + r.map.passes - 1) / r.map.passes;
+    for (int64_t lo = 0; lo < n; lo += slice) {
+      const int64_t hi = lo + slice < n ? lo + slice : n;
+      if (!launch_gather_blocked(p->dtype, r.map, ga, grid, (int32_t)lo, (int32_t)hi, st))
+        return fail(SNG_EINVAL,
+                    "no compiled L2-blocked gather for vec=%d group=%d nch=%d unroll=%d",
+                    r.map.vec, r.map.group, r.map.nch, r.map.unroll);
+      note_launch();
+    }
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gather launch");
   tm->mark(st, 1);

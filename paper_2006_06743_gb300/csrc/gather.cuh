@@ -188,8 +188,15 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
   return cnt;
 }
 
+// Resident 256-thread blocks per SM the compiler must allow for: mappings
+// with few registers of row data get 4 (32 warps), wider ones 3 or 2.
+template <int VEC, int NCH, int U>
+struct MinBlocks {
+  static constexpr int value = (VEC * NCH * U <= 16) ? 4 : (VEC * NCH * U <= 32 ? 3 : 2);
+};
+
 template <typename T, int VEC, int G, int NCH, int U>
-__global__ void __launch_bounds__(256, 2) gather_kernel(GatherArgs a) {
+__global__ void __launch_bounds__(256, MinBlocks<VEC, NCH, U>::value) gather_kernel(GatherArgs a) {
   extern __shared__ int32_t smem_partner[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -203,15 +210,152 @@ __global__ void __launch_bounds__(256, 2) gather_kernel(GatherArgs a) {
   }
 }
 
+// L2-blocked form: one launch per slice [lo, hi) of partner indices.  Each
+// warp re-derives all m draws of its row, keeps the ones whose partner lies
+// in the slice (warp-ballot compaction into a shared-memory list of (draw,
+// partner)), and tests only those, so a launch touches one slice of X that
+// stays resident in L2 while every source row streams past it once.  Kept
+// draws set their bit with atomicOr (the bitmask is zeroed before the first
+// slice) and add to the row count; degrees as in gather_row.
+template <typename T, int VEC, int G, int NCH, int U>
+__device__ __forceinline__ void gather_row_blocked(const GatherArgs &a, int32_t i, int32_t mi,
+                                                   int32_t lo, int32_t hi, int32_t *sp,
+                                                   int32_t *sj, int lane) {
+  constexpr int R = 32 / G;
+  constexpr int S = 32 * U;   // list capacity
+  const int grp = lane / G;
+  const int gl = lane % G;
+  const T *X = static_cast<const T *>(a.x);
+  const int d = a.d;
+  const uint64_t key = row_key(a.seed, i);
+  float xi[NCH][VEC];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int off = (c * G + gl) * VEC;
+    if (off < d) {
+      Chunk<T, VEC>::load(X + (int64_t)i * a.ld + off, xi[c]);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k)
+        if (off + k >= d) xi[c][k] = 0.f;
+    } else {
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) xi[c][k] = 0.f;
+    }
+  }
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  int cnt = 0;
+  int64_t j = 0;
+  while (j < mi) {
+    int nlist = 0;
+    while (nlist <= S - 32 && j < mi) {
+      const int64_t jj = j + lane;
+      int32_t p = -1;
+      if (jj < mi) p = a.sample_all ? partner_all(i, jj) : partner_from_key(key, i, jj, a.fm);
+      const bool in = p >= lo && p < hi;
+      const uint32_t b = __ballot_sync(kFullMask, in);
+      if (in) {
+        const int pos = nlist + __popc(b & lt_mask);
+        sp[pos] = p;
+        sj[pos] = (int32_t)jj;
+      }
+      nlist += __popc(b);
+      j += 32;
+    }
+    __syncwarp();
+    const int steps = (nlist + R - 1) / R;
+#pragma unroll 1
+    for (int t0 = 0; t0 < steps; t0 += U) {
+      float v[U][NCH][VEC];
+      int32_t pv[U], jv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = (t0 + u) * R + grp;
+        const int32_t p = e < nlist ? sp[e] : -1;
+        pv[u] = p;
+        jv[u] = e < nlist ? sj[e] : 0;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const int off = (c * G + gl) * VEC;
+          if (p >= 0 && off < d) {
+            Chunk<T, VEC>::load(X + (int64_t)p * a.ld + off, v[u][c]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) v[u][c][k] = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const int off = (c * G + gl) * VEC;
+#pragma unroll
+          for (int k = 0; k < VEC; ++k) {
+            float diff = xi[c][k] - v[u][c][k];
+            if (off + VEC > d && off + k >= d) diff = 0.f;
+            acc = fmaf(diff, diff, acc);
+          }
+        }
+#pragma unroll
+        for (int o = G / 2; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+        const int32_t p = pv[u];
+        if (gl == 0 && p >= 0) {
+          bool keep = false;
+          if (acc < a.lo_thr) {
+            keep = true;
+          } else if (!(acc > a.hi_thr)) {
+            keep = recheck_pair<T>(a, i, p);
+          }
+          if (keep) {
+            const int32_t jj = jv[u];
+            atomicOr(a.bitmask + (int64_t)i * a.W + (jj >> 5), 1u << (jj & 31));
+            if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, 1);
+            ++cnt;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) cnt += __shfl_xor_sync(kFullMask, cnt, o);
+  if (lane == 0 && cnt) {
+    if (a.out_cnt) atomicAdd(a.out_cnt + i, cnt);
+    atomicAdd(a.deg + i, cnt);
+  }
+}
+
+template <typename T, int VEC, int G, int NCH, int U>
+__global__ void __launch_bounds__(256, MinBlocks<VEC, NCH, U>::value)
+    gather_blocked_kernel(GatherArgs a, int32_t lo, int32_t hi) {
+  extern __shared__ int32_t smem_list[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  int32_t *sp = smem_list + warp * 64 * U;
+  int32_t *sj = sp + 32 * U;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < a.n;
+       row += warps_total) {
+    const int32_t i = (int32_t)row;
+    const int32_t mi = a.m_row ? a.m_row[i] : a.m;
+    gather_row_blocked<T, VEC, G, NCH, U>(a, i, mi, lo, hi, sp, sj, lane);
+  }
+}
+
 // Mapping of the gather: lanes per pair, chunks per lane, vector width,
 // batches in flight, block size.
 struct GatherMap {
   int vec, group, nch, unroll, block;
+  int passes;   // 1: single pass; > 1: L2-blocked slices of the partner range
 };
 
 // Host-side launcher; returns false if no compiled variant matches `map`.
 bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
                    cudaStream_t stream);
+bool launch_gather_blocked(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
+                           int32_t lo, int32_t hi, cudaStream_t stream);
+int gather_blocked_max_blocks_per_sm(int dtype, const GatherMap &map);
 size_t gather_smem_bytes(const GatherMap &map);
 int gather_max_blocks_per_sm(int dtype, const GatherMap &map);
 

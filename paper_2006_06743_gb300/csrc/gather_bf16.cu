@@ -25,4 +25,15 @@ int occ_gather_bf16(const GatherMap &map) {
   return 0;
 }
 
+bool launch_gather_blocked_bf16(const GatherMap &map, const GatherArgs &args, int grid,
+                                int32_t lo, int32_t hi, cudaStream_t stream) {
+  SNG_BLOCKED_SHAPES(uint16_t, 8, SNG_TRY_B)
+  return false;
+}
+
+int occ_gather_blocked_bf16(const GatherMap &map) {
+  SNG_BLOCKED_SHAPES(uint16_t, 8, SNG_OCC_B)
+  return 0;
+}
+
 }  // namespace sng

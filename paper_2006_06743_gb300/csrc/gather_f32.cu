@@ -22,4 +22,15 @@ int occ_gather_f32(const GatherMap &map) {
   return 0;
 }
 
+bool launch_gather_blocked_f32(const GatherMap &map, const GatherArgs &args, int grid,
+                                int32_t lo, int32_t hi, cudaStream_t stream) {
+  SNG_BLOCKED_SHAPES(float, 4, SNG_TRY_B)
+  return false;
+}
+
+int occ_gather_blocked_f32(const GatherMap &map) {
+  SNG_BLOCKED_SHAPES(float, 4, SNG_OCC_B)
+  return 0;
+}
+
 }  // namespace sng

@@ -26,6 +26,39 @@ static int occ_blocks(const GatherMap &m) {
   return blocks;
 }
 
+template <typename T, int VEC, int G, int NCH, int U>
+static bool try_launch_blocked(const GatherMap &m, const GatherArgs &args, int grid, int32_t lo,
+                               int32_t hi, cudaStream_t st) {
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return false;
+  const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
+  gather_blocked_kernel<T, VEC, G, NCH, U><<<grid, m.block, smem, st>>>(args, lo, hi);
+  return true;
+}
+
+template <typename T, int VEC, int G, int NCH, int U>
+static int occ_blocks_blocked(const GatherMap &m) {
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return -1;
+  int blocks = 0;
+  const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &blocks, gather_blocked_kernel<T, VEC, G, NCH, U>, m.block, smem) != cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+// L2-blocked mappings: the row widths of the large workloads
+#define SNG_BLOCKED_SHAPES(T, V, X) \
+  X(T, V, 8, 1, 4) X(T, V, 16, 1, 4) X(T, V, 16, 1, 8) X(T, V, 32, 1, 4) X(T, V, 16, 2, 4) \
+  X(T, V, 32, 2, 4)
+
+#define SNG_TRY_B(T, V, G, N, U) \
+  if (try_launch_blocked<T, V, G, N, U>(map, args, grid, lo, hi, stream)) return true;
+#define SNG_OCC_B(T, V, G, N, U)                       \
+  {                                                    \
+    int b = occ_blocks_blocked<T, V, G, N, U>(map);    \
+    if (b >= 0) return b;                              \
+  }
+
 // (group, chunks) shapes: thread-per-pair for tiny rows, sub-warp groups for
 // medium rows, whole warps (several chunks per lane) for wide rows.
 #define SNG_SHAPES_U(T, V, U, X)                                                         \

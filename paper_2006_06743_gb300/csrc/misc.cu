@@ -7,6 +7,22 @@ bool launch_gather_f32(const GatherMap &, const GatherArgs &, int, cudaStream_t)
 bool launch_gather_bf16(const GatherMap &, const GatherArgs &, int, cudaStream_t);
 int occ_gather_f32(const GatherMap &);
 int occ_gather_bf16(const GatherMap &);
+bool launch_gather_blocked_f32(const GatherMap &, const GatherArgs &, int, int32_t, int32_t,
+                               cudaStream_t);
+bool launch_gather_blocked_bf16(const GatherMap &, const GatherArgs &, int, int32_t, int32_t,
+                                cudaStream_t);
+int occ_gather_blocked_f32(const GatherMap &);
+int occ_gather_blocked_bf16(const GatherMap &);
+
+bool launch_gather_blocked(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
+                           int32_t lo, int32_t hi, cudaStream_t stream) {
+  return dtype == SNG_F32 ? launch_gather_blocked_f32(map, args, grid, lo, hi, stream)
+                          : launch_gather_blocked_bf16(map, args, grid, lo, hi, stream);
+}
+
+int gather_blocked_max_blocks_per_sm(int dtype, const GatherMap &map) {
+  return dtype == SNG_F32 ? occ_gather_blocked_f32(map) : occ_gather_blocked_bf16(map);
+}
 
 bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
                    cudaStream_t stream) {

@@ -1,0 +1,648 @@
+// mlp.cu -- the core-point surrogate: a d -> 128 -> 128 -> 1 perceptron with
+// exact (erf) GELU, trained and evaluated by this file's kernels.
+//
+// The paper has no learned component.  The surrogate predicts, from a point's
+// coordinates, whether Algorithm 1 would make it a core point (step 3), so
+// that confidently classified points can skip most of their sampled queries
+// (step 2).  Weights are stored as an FP32 master vector; every kernel rounds
+// them to FP16 when it stages them in shared memory and accumulates in FP32.
+//
+// Parameter vector (FP32, device), d = input features, H = 128:
+//   [W1 (H x d) | b1 (H) | W2 (H x H) | b2 (H) | w3 (H) | b3 (1) | mean (d) | std (d)]
+// The first H*d + H*H + 3H + 1 entries are trained; mean/std standardise the
+// inputs (u = (x - mean) / std) and come from sng_mlp_standardize.
+//
+// Forward (per point):   a1 = W1 u + b1, h1 = gelu(a1), a2 = W2 h1 + b2,
+//                        h2 = gelu(a2), z = w3 . h2 + b3, p = sigmoid(z)
+// Loss: mean binary cross-entropy on the logit z.  Backward: the chain rule,
+// gelu'(t) = Phi(t) + t phi(t).  Optimiser: Adam with bias correction.
+#include <cmath>
+#include <cuda_fp16.h>
+
+#include "api_common.cuh"
+#include "graph.cuh"
+
+namespace sng {
+
+constexpr int kH = 128;
+
+struct MlpOff {
+  int64_t w1, b1, w2, b2, w3, b3, train, mean, std, total;
+};
+
+__host__ __device__ inline MlpOff mlp_off(int d) {
+  MlpOff o;
+  o.w1 = 0;
+  o.b1 = (int64_t)kH * d;
+  o.w2 = o.b1 + kH;
+  o.b2 = o.w2 + (int64_t)kH * kH;
+  o.w3 = o.b2 + kH;
+  o.b3 = o.w3 + kH;
+  o.train = o.b3 + 1;
+  o.mean = o.train;
+  o.std = o.mean + d;
+  o.total = o.std + d;
+  return o;
+}
+
+__device__ __forceinline__ float h16(float v) { return __half2float(__float2half_rn(v)); }
+
+__device__ __forceinline__ float gelu_f(float a) {
+  return 0.5f * a * (1.f + erff(a * 0.70710678118654752f));
+}
+
+__device__ __forceinline__ float gelu_grad_f(float a) {
+  return 0.5f * (1.f + erff(a * 0.70710678118654752f)) +
+         a * 0.39894228040143268f * expf(-0.5f * a * a);
+}
+
+// Shared-memory image of the network for DMAX input features:
+//   W1 [H][DMAX] | b1 [H] | W2T [H][H] (W2T[j][t] = W2[t][j]) | b2 [H] | w3 [H]
+//   | b3 | mean [DMAX] | istd [DMAX]
+template <int DMAX>
+struct Smem {
+  static constexpr int w1 = 0;
+  static constexpr int b1 = w1 + kH * DMAX;
+  static constexpr int w2t = b1 + kH;
+  static constexpr int b2 = w2t + kH * kH;
+  static constexpr int w3 = b2 + kH;
+  static constexpr int b3 = w3 + kH;
+  static constexpr int mean = b3 + 4;
+  static constexpr int istd = mean + DMAX;
+  static constexpr int total = istd + DMAX;
+  static constexpr size_t bytes = sizeof(float) * total;
+};
+
+template <int DMAX>
+__device__ void stage_weights(const float *P, int d, float *s) {
+  const MlpOff o = mlp_off(d);
+  for (int t = threadIdx.x; t < kH * DMAX; t += blockDim.x) {
+    const int j = t / DMAX, k = t % DMAX;
+    s[Smem<DMAX>::w1 + t] = k < d ? h16(P[o.w1 + (int64_t)j * d + k]) : 0.f;
+  }
+  for (int t = threadIdx.x; t < kH * kH; t += blockDim.x) {
+    const int j = t / kH, tt = t % kH;  // W2T[j][tt] = W2[tt][j]
+    s[Smem<DMAX>::w2t + t] = h16(P[o.w2 + (int64_t)tt * kH + j]);
+  }
+  for (int t = threadIdx.x; t < kH; t += blockDim.x) {
+    s[Smem<DMAX>::b1 + t] = h16(P[o.b1 + t]);
+    s[Smem<DMAX>::b2 + t] = h16(P[o.b2 + t]);
+    s[Smem<DMAX>::w3 + t] = h16(P[o.w3 + t]);
+  }
+  for (int k = threadIdx.x; k < DMAX; k += blockDim.x) {
+    s[Smem<DMAX>::mean + k] = k < d ? P[o.mean + k] : 0.f;
+    s[Smem<DMAX>::istd + k] = k < d ? 1.f / P[o.std + k] : 0.f;
+  }
+  if (threadIdx.x == 0) s[Smem<DMAX>::b3] = h16(P[o.b3]);
+  __syncthreads();
+}
+
+// One point through the network.  Optionally records u, a1, a2 (training).
+template <int DMAX>
+__device__ __forceinline__ float forward_point(const float *s, const float *xrow, int d,
+                                               float *u_out, float *a1_out, float *a2_out) {
+  float u[DMAX];
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) {
+    u[k] = k < d ? (xrow[k] - s[Smem<DMAX>::mean + k]) * s[Smem<DMAX>::istd + k] : 0.f;
+    if (u_out && k < d) u_out[k] = u[k];
+  }
+  float a2[kH];
+#pragma unroll
+  for (int t = 0; t < kH; ++t) a2[t] = s[Smem<DMAX>::b2 + t];
+#pragma unroll 1
+  for (int j = 0; j < kH; ++j) {
+    const float *w1r = s + Smem<DMAX>::w1 + j * DMAX;
+    float a = s[Smem<DMAX>::b1 + j];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) a = fmaf(w1r[k], u[k], a);
+    if (a1_out) a1_out[j] = a;
+    const float h = gelu_f(a);
+    const float *w2r = s + Smem<DMAX>::w2t + j * kH;
+#pragma unroll
+    for (int t = 0; t < kH; ++t) a2[t] = fmaf(w2r[t], h, a2[t]);
+  }
+  float z = s[Smem<DMAX>::b3];
+#pragma unroll
+  for (int t = 0; t < kH; ++t) {
+    if (a2_out) a2_out[t] = a2[t];
+    z = fmaf(s[Smem<DMAX>::w3 + t], gelu_f(a2[t]), z);
+  }
+  return z;
+}
+
+// --------------------------------------------------------------- inference
+
+struct GateArgs {
+  const float *x;
+  int64_t ld;
+  int64_t n;
+  int32_t d;
+  const float *P;
+  float *prob;          // nullable
+  float p_noise, p_core;
+  int32_t m, m_core;    // draws for uncertain / confident-core points
+  uint8_t *forced;      // nullable: 2 noise, 1 core, 0 uncertain
+  int32_t *m_row;       // nullable
+  unsigned long long *counters;  // nullable: [0] queries [1] core [2] noise
+};
+
+template <int DMAX>
+__global__ void __launch_bounds__(128, 1) mlp_gate_kernel(GateArgs a) {
+  extern __shared__ float smem_w[];
+  stage_weights<DMAX>(a.P, a.d, smem_w);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long q = 0, nc = 0, nn = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const float z = forward_point<DMAX>(smem_w, a.x + i * a.ld, a.d, nullptr, nullptr, nullptr);
+    const float p = 1.f / (1.f + expf(-z));
+    if (a.prob) a.prob[i] = p;
+    if (a.forced) {
+      uint8_t f = 0;
+      int32_t mi = a.m;
+      if (p < a.p_noise) {
+        f = 2;
+        mi = 0;
+        ++nn;
+      } else if (p > a.p_core) {
+        f = 1;
+        mi = a.m_core;
+        ++nc;
+      }
+      a.forced[i] = f;
+      a.m_row[i] = mi;
+      q += (unsigned long long)mi;
+    }
+  }
+  if (a.counters) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      q += __shfl_xor_sync(kFullMask, q, o);
+      nc += __shfl_xor_sync(kFullMask, nc, o);
+      nn += __shfl_xor_sync(kFullMask, nn, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(a.counters + 0, q);
+      atomicAdd(a.counters + 1, nc);
+      atomicAdd(a.counters + 2, nn);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- training
+
+struct TrainWs {
+  int32_t B;           // batch rows
+  float *u;            // B x d
+  float *a1;           // B x H
+  float *a2;           // B x H
+  float *dz;           // B
+  float *da1;          // B x H
+  float *da2;          // B x H
+  float *grad;         // train-part gradient
+  double *loss;        // per-step loss sums
+};
+
+struct FwdArgs {
+  const float *x;
+  const uint8_t *y;
+  int64_t n;
+  int32_t d;
+  const float *P;
+  TrainWs ws;
+  int32_t sample;      // 1: hash-sampled batch; 0: rows 0..B-1; 2: rows (step*B+b) mod n
+  uint64_t seed;
+  int64_t step;
+  FastMod fm_n;        // remainder constants for n (batch sampling)
+  int32_t loss_slot;
+};
+
+__device__ __forceinline__ int64_t batch_row(const FwdArgs &a, int b) {
+  if (!a.sample) return b;
+  if (a.sample == 2) return (int64_t)(((uint64_t)a.step * (uint64_t)a.ws.B + (uint64_t)b) %
+                                      (uint64_t)a.n);
+  const uint64_t k = mix64(a.seed ^ mix64((uint64_t)a.step));
+  return (int64_t)fast_mod(mix64(k ^ (uint64_t)b), a.fm_n);
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(128, 1) mlp_train_fwd(FwdArgs a) {
+  extern __shared__ float smem_w[];
+  stage_weights<DMAX>(a.P, a.d, smem_w);
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (b < a.ws.B) {
+    const int64_t i = batch_row(a, b);
+    const float z = forward_point<DMAX>(smem_w, a.x + i * a.d, a.d, a.ws.u + (int64_t)b * a.d,
+                                        a.ws.a1 + (int64_t)b * kH, a.ws.a2 + (int64_t)b * kH);
+    const float y = a.y[i] ? 1.f : 0.f;
+    const float sig = 1.f / (1.f + expf(-z));
+    a.ws.dz[b] = (sig - y) / (float)a.ws.B;
+    l = (double)(fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z))));
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) l += __shfl_xor_sync(kFullMask, l, o);
+  if ((threadIdx.x & 31) == 0 && a.ws.loss) atomicAdd(a.ws.loss + a.loss_slot, l);
+}
+
+// da2 = dz * w3 * gelu'(a2);  dh1 = W2^T da2;  da1 = dh1 * gelu'(a1)
+constexpr size_t kBwdSmem = sizeof(float) * (kH * kH + kH);
+
+__global__ void __launch_bounds__(128, 1) mlp_train_bwd(const float *P, int d, TrainWs ws) {
+  extern __shared__ float smem_b[];
+  float *w2t = smem_b;
+  float *w3s = smem_b + kH * kH;
+  const MlpOff o = mlp_off(d);
+  for (int t = threadIdx.x; t < kH * kH; t += blockDim.x) {
+    const int j = t / kH, tt = t % kH;
+    w2t[t] = h16(P[o.w2 + (int64_t)tt * kH + j]);
+  }
+  for (int t = threadIdx.x; t < kH; t += blockDim.x) w3s[t] = h16(P[o.w3 + t]);
+  __syncthreads();
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= ws.B) return;
+  const float dz = ws.dz[b];
+  float da2[kH];
+  const float *a2 = ws.a2 + (int64_t)b * kH;
+#pragma unroll
+  for (int t = 0; t < kH; ++t) {
+    da2[t] = dz * w3s[t] * gelu_grad_f(a2[t]);
+    ws.da2[(int64_t)b * kH + t] = da2[t];
+  }
+#pragma unroll 1
+  for (int j = 0; j < kH; ++j) {
+    const float *wr = w2t + j * kH;
+    float s = 0.f;
+#pragma unroll
+    for (int t = 0; t < kH; ++t) s = fmaf(wr[t], da2[t], s);
+    ws.da1[(int64_t)b * kH + j] = s * gelu_grad_f(ws.a1[(int64_t)b * kH + j]);
+  }
+}
+
+// out[m][c] += sum_b A[b][m] * f(Bm[b][c]) over a slice of the batch
+// (A: B x M, Bm: B x N, both row-major; f = identity or gelu).  32x32 output
+// tile per block, 8 x 32 threads, batch staged through shared memory.
+__global__ void __launch_bounds__(256) outer_sum_kernel(const float *A, int lda, int M,
+                                                        const float *Bm, int ldb, int N,
+                                                        int apply_gelu, int B, int chunk,
+                                                        float *out, int ldo) {
+  __shared__ float As[32][33];
+  __shared__ float Bs[32][33];
+  const int m0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int b_begin = blockIdx.z * chunk, b_end = min(B, b_begin + chunk);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty 0..7
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int b0 = b_begin; b0 < b_end; b0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int b = b0 + r;
+      As[r][tx] = (b < b_end && m0 + tx < M) ? A[(int64_t)b * lda + m0 + tx] : 0.f;
+      float v = (b < b_end && c0 + tx < N) ? Bm[(int64_t)b * ldb + c0 + tx] : 0.f;
+      Bs[r][tx] = apply_gelu ? gelu_f(v) : v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const float bv = Bs[r][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(As[r][ty + 8 * q], bv, acc[q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int mm = m0 + ty + 8 * q, cc = c0 + tx;
+    if (mm < M && cc < N) atomicAdd(out + (int64_t)mm * ldo + cc, acc[q]);
+  }
+}
+
+// out[c] += sum_b f(Bm[b][c]) * (A ? A[b] : 1)
+__global__ void col_sum_kernel(const float *Bm, int ldb, int N, const float *A, int B,
+                               float *out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += Bm[(int64_t)b * ldb + c] * (A ? A[b] : 1.f);
+  atomicAdd(out + c, s);
+}
+
+__global__ void adam_kernel(float *P, const float *g, float *m, float *v, int64_t count,
+                            float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// column mean / std of x (n x d) in FP64 partial sums
+__global__ void col_moments_kernel(const float *x, int64_t n, int d, double *acc) {
+  const int k = threadIdx.x;
+  if (k >= d) return;
+  double s = 0.0, s2 = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double v = x[i * d + k];
+    s += v;
+    s2 += v * v;
+  }
+  atomicAdd(acc + k, s);
+  atomicAdd(acc + d + k, s2);
+}
+
+__global__ void col_finish_kernel(const double *acc, int64_t n, int d, float *mean, float *stdv) {
+  const int k = threadIdx.x;
+  if (k >= d) return;
+  const double mu = acc[k] / (double)n;
+  double var = acc[d + k] / (double)n - mu * mu;
+  if (var < 0) var = 0;
+  double sd = sqrt(var);
+  if (!(sd > 1e-12)) sd = 1.0;
+  mean[k] = (float)mu;
+  stdv[k] = (float)sd;
+}
+
+// ------------------------------------------------------------- dispatch
+
+template <int DMAX>
+static cudaError_t smem_optin(const void *fn) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Smem<DMAX>::bytes);
+}
+
+static int dmax_for(int d) { return d <= 8 ? 8 : d <= 32 ? 32 : 64; }
+
+static cudaError_t launch_gate(const GateArgs &a, cudaStream_t st) {
+  const int sms = device_sms();
+  const int64_t need = (a.n + 127) / 128;
+  const int grid = (int)std::min<int64_t>(need, (int64_t)sms * 2);
+  switch (dmax_for(a.d)) {
+    case 8:
+      smem_optin<8>((const void *)mlp_gate_kernel<8>);
+      mlp_gate_kernel<8><<<grid, 128, Smem<8>::bytes, st>>>(a);
+      break;
+    case 32:
+      smem_optin<32>((const void *)mlp_gate_kernel<32>);
+      mlp_gate_kernel<32><<<grid, 128, Smem<32>::bytes, st>>>(a);
+      break;
+    default:
+      smem_optin<64>((const void *)mlp_gate_kernel<64>);
+      mlp_gate_kernel<64><<<grid, 128, Smem<64>::bytes, st>>>(a);
+      break;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_train_fwd(const FwdArgs &a, cudaStream_t st) {
+  const int grid = (a.ws.B + 127) / 128;
+  switch (dmax_for(a.d)) {
+    case 8:
+      smem_optin<8>((const void *)mlp_train_fwd<8>);
+      mlp_train_fwd<8><<<grid, 128, Smem<8>::bytes, st>>>(a);
+      break;
+    case 32:
+      smem_optin<32>((const void *)mlp_train_fwd<32>);
+      mlp_train_fwd<32><<<grid, 128, Smem<32>::bytes, st>>>(a);
+      break;
+    default:
+      smem_optin<64>((const void *)mlp_train_fwd<64>);
+      mlp_train_fwd<64><<<grid, 128, Smem<64>::bytes, st>>>(a);
+      break;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Gradient of the batch loss into ws.grad (zeroed here).
+static cudaError_t launch_loss_grad(const FwdArgs &a, cudaStream_t st) {
+  const MlpOff o = mlp_off(a.d);
+  const TrainWs &w = a.ws;
+  cudaMemsetAsync(w.grad, 0, sizeof(float) * o.train, st);
+  cudaError_t e = launch_train_fwd(a, st);
+  if (e != cudaSuccess) return e;
+  cudaFuncSetAttribute((const void *)mlp_train_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kBwdSmem);
+  mlp_train_bwd<<<(w.B + 127) / 128, 128, kBwdSmem, st>>>(a.P, a.d, w);
+  const int chunk = 256;
+  const int splits = (w.B + chunk - 1) / chunk;
+  // dW2[t][j] = sum_b da2[b][t] gelu(a1[b][j])
+  outer_sum_kernel<<<dim3(kH / 32, kH / 32, splits), 256, 0, st>>>(
+      w.da2, kH, kH, w.a1, kH, kH, 1, w.B, chunk, w.grad + o.w2, kH);
+  // dW1[j][k] = sum_b da1[b][j] u[b][k]
+  outer_sum_kernel<<<dim3(kH / 32, (a.d + 31) / 32, splits), 256, 0, st>>>(
+      w.da1, kH, kH, w.u, a.d, a.d, 0, w.B, chunk, w.grad + o.w1, a.d);
+  // dw3[t] = sum_b dz[b] gelu(a2[b][t])
+  outer_sum_kernel<<<dim3(1, kH / 32, splits), 256, 0, st>>>(
+      w.dz, 1, 1, w.a2, kH, kH, 1, w.B, chunk, w.grad + o.w3, kH);
+  col_sum_kernel<<<1, kH, 0, st>>>(w.da1, kH, kH, nullptr, w.B, w.grad + o.b1);
+  col_sum_kernel<<<1, kH, 0, st>>>(w.da2, kH, kH, nullptr, w.B, w.grad + o.b2);
+  col_sum_kernel<<<1, 32, 0, st>>>(w.dz, 1, 1, nullptr, w.B, w.grad + o.b3);
+  note_launch(7);
+  return cudaGetLastError();
+}
+
+static sng_status alloc_ws(Scratch &s, int B, int d, int steps, TrainWs *w) {
+  const MlpOff o = mlp_off(d);
+  sng_status rc;
+  w->B = B;
+  if ((rc = s.alloc((void **)&w->u, sizeof(float) * B * d, "mlp u")) ||
+      (rc = s.alloc((void **)&w->a1, sizeof(float) * B * kH, "mlp a1")) ||
+      (rc = s.alloc((void **)&w->a2, sizeof(float) * B * kH, "mlp a2")) ||
+      (rc = s.alloc((void **)&w->dz, sizeof(float) * B, "mlp dz")) ||
+      (rc = s.alloc((void **)&w->da1, sizeof(float) * B * kH, "mlp da1")) ||
+      (rc = s.alloc((void **)&w->da2, sizeof(float) * B * kH, "mlp da2")) ||
+      (rc = s.alloc((void **)&w->grad, sizeof(float) * o.train, "mlp grad")) ||
+      (rc = s.alloc((void **)&w->loss, sizeof(double) * (steps > 0 ? steps : 1), "mlp loss")))
+    return rc;
+  cudaMemsetAsync(w->loss, 0, sizeof(double) * (steps > 0 ? steps : 1), s.stream);
+  return SNG_OK;
+}
+
+static sng_status check_cfg(const sng_mlp_config *c) {
+  if (!c) return fail(SNG_EINVAL, "mlp config is NULL");
+  if (c->d < 1 || c->d > 64) return fail(SNG_EINVAL, "mlp d must be in [1, 64]");
+  if (c->hidden != kH) return fail(SNG_EINVAL, "mlp hidden width must be %d", kH);
+  return SNG_OK;
+}
+
+__global__ void loss_to_float(const double *l, int steps, int B, float *out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < steps) out[s] = (float)(l[s] / (double)B);
+}
+
+}  // namespace sng
+
+using namespace sng;
+
+extern "C" {
+
+int64_t sng_mlp_param_count(int32_t d, int32_t hidden) {
+  if (d < 1 || d > 64 || hidden != kH) return -1;
+  return mlp_off(d).total;
+}
+
+sng_status sng_mlp_standardize(const float *x, int64_t n, int32_t d, float *params,
+                               void *stream) {
+  if (!x || !params) return fail(SNG_EINVAL, "NULL argument");
+  if (n < 1 || d < 1 || d > 64) return fail(SNG_EINVAL, "bad n or d");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch s(st);
+  double *acc;
+  sng_status rc = s.alloc((void **)&acc, sizeof(double) * 2 * d, "moments");
+  if (rc) return rc;
+  cudaMemsetAsync(acc, 0, sizeof(double) * 2 * d, st);
+  const MlpOff o = mlp_off(d);
+  col_moments_kernel<<<device_sms() * 4, 64, 0, st>>>(x, n, d, acc);
+  col_finish_kernel<<<1, 64, 0, st>>>(acc, n, d, params + o.mean, params + o.std);
+  note_launch(2);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SNG_OK : cuda_fail(e, "standardize");
+}
+
+sng_status sng_mlp_loss_grad(const float *x, const uint8_t *y, int64_t n,
+                             const sng_mlp_config *cfg, const float *params, float *grad,
+                             double *loss, void *stream) {
+  sng_status rc = check_cfg(cfg);
+  if (rc) return rc;
+  if (!x || !y || !params || !grad) return fail(SNG_EINVAL, "NULL argument");
+  if (n < 1 || n > (1 << 24)) return fail(SNG_EINVAL, "n must be in [1, 2^24]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch s(st);
+  TrainWs w;
+  if ((rc = alloc_ws(s, (int)n, cfg->d, 1, &w))) return rc;
+  FwdArgs a{x, y, n, cfg->d, params, w, 0, 0, 0, make_fastmod(n + 1), 0};
+  cudaError_t e = launch_loss_grad(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "loss_grad");
+  const MlpOff o = mlp_off(cfg->d);
+  cudaMemcpyAsync(grad, w.grad, sizeof(float) * o.train, cudaMemcpyDeviceToDevice, st);
+  double l = 0;
+  e = cudaMemcpyAsync(&l, w.loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "loss_grad read-back");
+  if (loss) *loss = l / (double)n;
+  return SNG_OK;
+}
+
+sng_status sng_mlp_train(const float *x, const uint8_t *y, int64_t n, const sng_mlp_config *cfg,
+                         float *params, float *adam_m, float *adam_v, int64_t step0,
+                         int64_t steps, float *loss_trace, void *stream) {
+  sng_status rc = check_cfg(cfg);
+  if (rc) return rc;
+  if (!x || !y || !params || !adam_m || !adam_v) return fail(SNG_EINVAL, "NULL argument");
+  if (n < 1 || n > 0x7fffffffLL) return fail(SNG_EINVAL, "n out of range");
+  if (cfg->batch < 1 || cfg->batch > (1 << 20)) return fail(SNG_EINVAL, "bad batch size");
+  if (steps < 0 || steps > (1 << 24) || step0 < 0) return fail(SNG_EINVAL, "bad step range");
+  if (!(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
+      !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->adam_eps > 0.f))
+    return fail(SNG_EINVAL, "bad optimiser settings");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch s(st);
+  TrainWs w;
+  if ((rc = alloc_ws(s, cfg->batch, cfg->d, (int)steps, &w))) return rc;
+  const MlpOff o = mlp_off(cfg->d);
+  const FastMod fm = make_fastmod(n + 1);  // divisor n
+  for (int64_t k = 0; k < steps; ++k) {
+    const int64_t t = step0 + k + 1;  // Adam step count
+    FwdArgs a{x, y, n, cfg->d, params, w, cfg->sequential ? 2 : 1, cfg->seed, step0 + k, fm,
+              (int32_t)k};
+    cudaError_t e = launch_loss_grad(a, st);
+    if (e != cudaSuccess) return cuda_fail(e, "train step");
+    const float c1 = (float)(1.0 - std::pow((double)cfg->beta1, (double)t));
+    const float c2 = (float)(1.0 - std::pow((double)cfg->beta2, (double)t));
+    adam_kernel<<<64, 256, 0, st>>>(params, w.grad, adam_m, adam_v, o.train, cfg->lr,
+                                    cfg->beta1, cfg->beta2, cfg->adam_eps, c1, c2);
+    note_launch();
+  }
+  if (loss_trace && steps > 0) {
+    loss_to_float<<<(int)((steps + 255) / 256), 256, 0, st>>>(w.loss, (int)steps, cfg->batch,
+                                                                loss_trace);
+    note_launch();
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "train");
+  return SNG_OK;
+}
+
+sng_status sng_mlp_predict(const float *x, int64_t n, const sng_mlp_config *cfg,
+                           const float *params, float *prob, void *stream) {
+  sng_status rc = check_cfg(cfg);
+  if (rc) return rc;
+  if (!x || !params || !prob) return fail(SNG_EINVAL, "NULL argument");
+  if (n < 1) return fail(SNG_EINVAL, "n must be >= 1");
+  GateArgs a{x, cfg->d, n, cfg->d, params, prob, 0.f, 1.f, 0, 0, nullptr, nullptr, nullptr};
+  cudaError_t e = launch_gate(a, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SNG_OK : cuda_fail(e, "predict");
+}
+
+sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
+                                 const sng_mlp_config *cfg, const float *mlp_params,
+                                 float p_noise, float p_core, float core_draw_frac,
+                                 int32_t *labels, uint8_t *core, sng_stats *stats,
+                                 void *stream) {
+  Resolved r;
+  sng_status rc = validate(x, params, &r);
+  if (rc) return rc;
+  if ((rc = check_cfg(cfg))) return rc;
+  if (!labels || !mlp_params) return fail(SNG_EINVAL, "NULL argument");
+  if (params->dtype != SNG_F32) return fail(SNG_EINVAL, "surrogate form takes FP32 points");
+  if (params->sample_mode != SNG_SAMPLE_HASH) return fail(SNG_EINVAL, "surrogate form needs hashed draws");
+  if (cfg->d != params->d) return fail(SNG_EINVAL, "mlp d differs from the points' d");
+  if (!(p_noise >= 0.f && p_noise <= p_core && p_core <= 1.f))
+    return fail(SNG_EINVAL, "need 0 <= p_noise <= p_core <= 1");
+  if (!(core_draw_frac >= 0.f && core_draw_frac <= 1.f))
+    return fail(SNG_EINVAL, "core_draw_frac must be in [0, 1]");
+  device_sms();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch s(st);
+  Timer tm((params->flags & SNG_FLAG_TIMING) != 0);
+  uint8_t *forced;
+  int32_t *m_row;
+  unsigned long long *gcnt;
+  if ((rc = s.alloc((void **)&forced, (size_t)r.n, "forced")) ||
+      (rc = s.alloc((void **)&m_row, (size_t)r.n * 4, "draws per row")) ||
+      (rc = s.alloc((void **)&gcnt, 4 * 8, "gate counters")))
+    return rc;
+  cudaMemsetAsync(gcnt, 0, 4 * 8, st);
+  const int32_t m_core = (int32_t)std::ceil((double)core_draw_frac * (double)r.m);
+  GateArgs ga{static_cast<const float *>(x), params->ld, r.n, params->d, mlp_params, nullptr,
+              p_noise, p_core, (int32_t)r.m, m_core, forced, m_row, gcnt};
+  cudaError_t e = launch_gate(ga, st);
+  if (e != cudaSuccess) return cuda_fail(e, "surrogate gate");
+  GraphBufs gb;
+  if ((rc = run_graph(x, params, r, s, &gb, m_row, &tm))) return rc;
+  uint8_t *core_buf = core;
+  int32_t *parent = nullptr;
+  if (!core_buf && (rc = s.alloc((void **)&core_buf, (size_t)r.n, "core"))) return rc;
+  if ((rc = s.alloc((void **)&parent, (size_t)r.n * 4, "parent"))) return rc;
+  const int sms = device_sms();
+  CoreArgs ca{r.n, params->min_pts, gb.deg, forced, core_buf, parent, labels};
+  launch_core_init(ca, sms, st);
+  tm.mark(st, 4);
+  UnionArgs ua{r.n, gb.row_ptr, gb.col, core_buf, parent, labels, gb.counters};
+  launch_union(ua, sms, st);
+  tm.mark(st, 5);
+  launch_label(ua, sms, st);
+  tm.mark(st, 6);
+  FinalizeArgs fa{r.n, core_buf, gb.band_flag, labels, gb.counters};
+  launch_finalize(fa, sms, st);
+  tm.mark(st, 7);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "surrogate cluster launches");
+  rc = read_stats(gb.counters, r, stats, st, &tm);
+  if (stats && rc == SNG_OK) {
+    unsigned long long g[4];
+    e = cudaMemcpyAsync(g, gcnt, sizeof(g), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "gate counters");
+    stats->queries = (int64_t)g[0];
+    stats->surrogate_core = (int64_t)g[1];
+    stats->surrogate_noise = (int64_t)g[2];
+  }
+  s.release();
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+"""Core-point surrogate: training and gated clustering through libsng.so.
+
+A d -> 128 -> 128 -> 1 perceptron (exact GELU, FP16-rounded weights, FP32
+accumulation) learns, from coordinates alone, the core mask that Algorithm 1
+(Jiang, Jang & Lacki 2020, Section 3, step 3) produces on sibling datasets
+drawn from the same distribution.  At clustering time the network gates each
+point: confidently non-core points draw no partners, confidently core points
+draw a prefix of their partner stream, and the rest run the full sampled
+queries.  Every arithmetic step runs in the library's CUDA kernels; this
+module packs parameters and drives the calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import (SNG_F32, Params, _check, _rows, _stream_ptr, lib, sng_mlp_config, sng_stats)
+
+HIDDEN = 128
+
+
+def param_count(d: int) -> int:
+    return int(lib().sng_mlp_param_count(d, HIDDEN))
+
+
+def trained_count(d: int) -> int:
+    return param_count(d) - 2 * d
+
+
+def pack(p: dict, mean=None, std=None) -> np.ndarray:
+    """Flat FP32 parameter vector in the library's layout."""
+    d = p["w1"].shape[1]
+    mean = np.zeros(d, np.float32) if mean is None else np.asarray(mean, np.float32)
+    std = np.ones(d, np.float32) if std is None else np.asarray(std, np.float32)
+    v = np.concatenate([np.asarray(p[k], np.float32).ravel()
+                        for k in ("w1", "b1", "w2", "b2", "w3", "b3")] + [mean, std])
+    assert v.size == param_count(d)
+    return v
+
+
+def unpack(v, d: int) -> tuple[dict, np.ndarray, np.ndarray]:
+    v = np.asarray(v, np.float32)
+    H = HIDDEN
+    o = 0
+    out = {}
+    for k, shape in (("w1", (H, d)), ("b1", (H,)), ("w2", (H, H)), ("b2", (H,)),
+                     ("w3", (H,)), ("b3", (1,))):
+        size = int(np.prod(shape))
+        out[k] = v[o:o + size].reshape(shape)
+        o += size
+    return out, v[o:o + d], v[o + d:o + 2 * d]
+
+
+@dataclass
+class TrainConfig:
+    batch: int = 4096
+    lr: float = 1e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    adam_eps: float = 1e-8
+    seed: int = 0
+    sequential: bool = False
+
+    def to_c(self, d: int) -> sng_mlp_config:
+        c = sng_mlp_config()
+        c.d, c.hidden, c.batch = d, HIDDEN, self.batch
+        c.lr, c.beta1, c.beta2, c.adam_eps = self.lr, self.beta1, self.beta2, self.adam_eps
+        c.seed = self.seed & (2**64 - 1)
+        c.sequential = int(self.sequential)
+        return c
+
+
+class Surrogate:
+    """Device-resident network state (parameters and Adam moments)."""
+
+    def __init__(self, init: dict, device="cuda", cfg: TrainConfig | None = None):
+        import torch
+        self.d = init["w1"].shape[1]
+        self.cfg = cfg or TrainConfig()
+        self.params = torch.from_numpy(pack(init)).to(device)
+        nt = trained_count(self.d)
+        self.m = torch.zeros(nt, dtype=torch.float32, device=device)
+        self.v = torch.zeros(nt, dtype=torch.float32, device=device)
+        self.step = 0
+
+    def standardize(self, x):
+        _rows(x, SNG_F32)
+        _check(lib().sng_mlp_standardize(x.data_ptr(), x.shape[0], self.d,
+                                         self.params.data_ptr(), _stream_ptr()))
+
+    def train(self, x, y, steps: int):
+        """``steps`` Adam steps on hash-sampled batches of (x, y); returns the
+        per-step batch losses (float32 numpy)."""
+        import torch
+        assert x.is_contiguous() and y.dtype == torch.uint8
+        trace = torch.empty(max(1, steps), dtype=torch.float32, device=x.device)
+        c = self.cfg.to_c(self.d)
+        _check(lib().sng_mlp_train(x.data_ptr(), y.data_ptr(), x.shape[0], ctypes.byref(c),
+                                   self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                   self.step, steps, trace.data_ptr(), _stream_ptr()))
+        self.step += steps
+        return trace[:steps].cpu().numpy()
+
+    def loss_grad(self, x, y):
+        import torch
+        g = torch.empty(trained_count(self.d), dtype=torch.float32, device=x.device)
+        loss = ctypes.c_double()
+        c = self.cfg.to_c(self.d)
+        _check(lib().sng_mlp_loss_grad(x.data_ptr(), y.data_ptr(), x.shape[0], ctypes.byref(c),
+                                       self.params.data_ptr(), g.data_ptr(), ctypes.byref(loss),
+                                       _stream_ptr()))
+        return float(loss.value), g
+
+    def predict(self, x):
+        import torch
+        prob = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        c = self.cfg.to_c(self.d)
+        _check(lib().sng_mlp_predict(x.data_ptr(), x.shape[0], ctypes.byref(c),
+                                     self.params.data_ptr(), prob.data_ptr(), _stream_ptr()))
+        return prob
+
+    def cluster(self, x, p: Params, p_noise: float = 0.1, p_core: float = 0.9,
+                core_draw_frac: float = 0.25, want_core: bool = False):
+        """Algorithm 1 gated by this network; returns (labels[, core], stats)."""
+        import torch
+        n, d, ld = _rows(x, SNG_F32)
+        labels = torch.empty(n, dtype=torch.int32, device=x.device)
+        core = torch.empty(n, dtype=torch.uint8, device=x.device) if want_core else None
+        st = sng_stats()
+        c = self.cfg.to_c(self.d)
+        _check(lib().sng_cluster_surrogate(
+            x.data_ptr(), ctypes.byref(p.to_c(n, d, ld, SNG_F32)), ctypes.byref(c),
+            self.params.data_ptr(), p_noise, p_core, core_draw_frac, labels.data_ptr(),
+            core.data_ptr() if core is not None else None, ctypes.byref(st), _stream_ptr()))
+        out = st.as_dict()
+        return (labels, core, out) if want_core else (labels, out)
+
+
+def gate_decisions(prob, m: int, p_noise: float, p_core: float, core_draw_frac: float):
+    """The gate's rule on given probabilities (host mirror, for checking):
+    forced (0 uncertain, 1 core, 2 noise) and draws per point."""
+    prob = np.asarray(prob, np.float32)
+    forced = np.zeros(prob.size, np.uint8)
+    forced[prob > np.float32(p_core)] = 1
+    forced[prob < np.float32(p_noise)] = 2
+    m_core = int(math.ceil(np.float64(np.float32(core_draw_frac)) * m))
+    m_row = np.full(prob.size, m, np.int32)
+    m_row[forced == 1] = m_core
+    m_row[forced == 2] = 0
+    return forced, m_row

@@ -196,3 +196,21 @@ def test_ari_kernel_matches_oracle(orc):
         b = np.where(rng.uniform(size=n) < 0.8, a, rng.integers(-1, n, size=n)).astype(np.int32)
         got = sng.ari(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
         assert abs(got - orc.ari(a, b)) < 1e-9
+
+
+@pytest.mark.parametrize("passes", [2, 3, 7])
+@pytest.mark.parametrize("n,d,group", [(3000, 64, 0), (2000, 128, 0), (2500, 32, 0),
+                                       (1800, 100, 16), (4000, 24, 8)])
+def test_l2_blocked_gather_matches_oracle(orc, passes, n, d, group):
+    """The multi-pass (L2-blocked) gather gives the single-pass graph and the
+    oracle's, in both degree modes."""
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=passes * 100 + d)
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    for deg_mode in (0, 1):
+        p = sng.Params(eps=eps, min_pts=4, m=300, seed=passes, map_passes=passes,
+                       map_group=group, degree_mode=deg_mode)
+        _compare_graph(orc, x, torch.from_numpy(x).cuda(), p, sng)
+    labels, st = _compare_cluster(orc, x, torch.from_numpy(x).cuda(),
+                                  sng.Params(eps=eps, min_pts=4, m=300, seed=passes,
+                                             map_passes=passes, map_group=group), sng)

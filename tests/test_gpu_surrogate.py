@@ -1,0 +1,166 @@
+"""The learned surrogate: its kernels against the FP64 network oracle
+(forward, loss, every gradient), training that reduces the loss, the gated
+clustering against the oracle's gated form of Algorithm 1, and what the
+trained network gains over the plain method on a sibling dataset."""
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu
+from oracle import mlp as omlp
+from paper_2006_06743_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+def _fp16(p: dict) -> dict:
+    return {k: np.asarray(v, np.float32).astype(np.float16).astype(np.float64)
+            for k, v in p.items()}
+
+
+def _setup(d, n, seed):
+    torch, sng = need_gpu()
+    from paper_2006_06743_gb300 import surrogate as sg
+    init = datagen.mlp_init(d, 128, seed)
+    net = sg.Surrogate(init)
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal((n, d)) * 2 + 1).astype(np.float32)
+    y = (rng.uniform(size=n) < 0.4).astype(np.uint8)
+    xg = torch.from_numpy(x).cuda()
+    yg = torch.from_numpy(y).cuda()
+    net.standardize(xg)
+    _, mean, std = sg.unpack(net.params.cpu().numpy(), d)
+    return torch, sng, sg, net, init, x, y, xg, yg, mean, std
+
+
+@pytest.mark.parametrize("d,n", [(5, 37), (32, 200), (64, 130), (2, 64)])
+def test_standardize_and_forward_match_oracle(d, n):
+    torch, sng, sg, net, init, x, y, xg, yg, mean, std = _setup(d, n, d)
+    np.testing.assert_allclose(mean, x.astype(np.float64).mean(0), rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(std, x.astype(np.float64).std(0), rtol=1e-5, atol=1e-5)
+    prob = net.predict(xg).cpu().numpy()
+    f = omlp.forward(_fp16(init), x, mean.astype(np.float64), std.astype(np.float64))
+    want = 1.0 / (1.0 + np.exp(-f["z"]))
+    np.testing.assert_allclose(prob, want, atol=2e-5)
+
+
+@pytest.mark.parametrize("d,n", [(5, 37), (32, 256), (64, 100)])
+def test_loss_and_gradients_match_oracle(d, n):
+    """Analytic FP64 backprop of the oracle (itself pinned by finite
+    differences) against the FP32 kernels, on the same FP16-rounded weights.
+    Tolerance: FP32 sums of at most ~300 terms per layer, three layers deep."""
+    torch, sng, sg, net, init, x, y, xg, yg, mean, std = _setup(d, n, 100 + d)
+    loss, g = net.loss_grad(xg, yg)
+    L, G = omlp.backward(_fp16(init), x, y.astype(np.float64), mean.astype(np.float64),
+                         std.astype(np.float64))
+    assert abs(loss - L) < 1e-5 * max(1.0, abs(L))
+    got, _, _ = sg.unpack(np.concatenate([g.cpu().numpy(), np.zeros(2 * d, np.float32)]), d)
+    for k in omlp.PARAM_NAMES:
+        want = np.asarray(G[k]).reshape(got[k].shape)
+        scale = np.abs(want).max() + 1e-12
+        np.testing.assert_allclose(got[k], want, rtol=2e-3, atol=2e-4 * scale, err_msg=k)
+
+
+def test_training_reduces_loss_and_learns_a_rule():
+    torch, sng = need_gpu()
+    from paper_2006_06743_gb300 import surrogate as sg
+    d, n = 8, 50_000
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    y = ((x[:, 0] ** 2 + x[:, 1] ** 2) < 1.0).astype(np.uint8)
+    xg, yg = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    net = sg.Surrogate(datagen.mlp_init(d, 128, 1), cfg=sg.TrainConfig(batch=512, lr=3e-3))
+    net.standardize(xg)
+    trace = net.train(xg, yg, 600)
+    assert trace[-50:].mean() < 0.5 * trace[:10].mean()
+    acc = ((net.predict(xg).cpu().numpy() > 0.5) == y.astype(bool)).mean()
+    assert acc > 0.95
+
+
+def test_training_steps_match_oracle_adam():
+    """Three full-batch steps through sng_mlp_train (rows taken in order)
+    equal the oracle's Adam (Kingma & Ba 2015) applied to the gradients that
+    sng_mlp_loss_grad reports at each step's parameters."""
+    torch, sng = need_gpu()
+    from paper_2006_06743_gb300 import surrogate as sg
+    d, n = 6, 300
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    y = (rng.uniform(size=n) < 0.5).astype(np.uint8)
+    init = datagen.mlp_init(d, 128, 9)
+    xg, yg = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    net = sg.Surrogate(init, cfg=sg.TrainConfig(batch=n, lr=1e-3, sequential=True))
+    net.standardize(xg)
+    nt = sg.trained_count(d)
+    state = {}
+    for _ in range(3):
+        p0 = net.params.clone()
+        _, g = net.loss_grad(xg, yg)
+        net.train(xg, yg, 1)
+        q = omlp.adam_step({"w": p0[:nt].double().cpu().numpy()},
+                           {"w": g.double().cpu().numpy()}, state, lr=1e-3)
+        np.testing.assert_allclose(net.params[:nt].cpu().numpy(), q["w"], rtol=1e-5, atol=1e-7)
+        assert torch.equal(net.params[nt:], p0[nt:])
+
+
+def test_gated_cluster_matches_oracle_gated_form(orc):
+    """Given the gate's decisions (from the network's probabilities), the
+    surrogate path is exactly the oracle's gated form of Algorithm 1."""
+    torch, sng = need_gpu()
+    from paper_2006_06743_gb300 import surrogate as sg
+    n, d, m = 6000, 8, 120
+    x = datagen.gaussian_mixture(n, d, 8, 0.05, seed=2, centre_std=1.0, sigma_lo=0.05,
+                                 sigma_hi=0.1)
+    eps = datagen.eps_quantile(x, 0.05, 200_000, seed=2)
+    xg = torch.from_numpy(x).cuda()
+    p = sng.Params(eps=eps, min_pts=5, m=m, seed=4)
+    plain, plain_core, _ = sng.cluster(xg, p, want_core=True)
+    net = sg.Surrogate(datagen.mlp_init(d, 128, 2), cfg=sg.TrainConfig(batch=1024, lr=3e-3))
+    net.standardize(xg)
+    net.train(xg, plain_core, 300)
+    prob = net.predict(xg).cpu().numpy()
+    for pn, pc, frac in ((0.1, 0.9, 0.25), (0.3, 0.6, 0.5), (0.0, 1.0, 0.25)):
+        labels, core, st = net.cluster(xg, p, pn, pc, frac, want_core=True)
+        forced, m_row = sg.gate_decisions(prob, m, pn, pc, frac)
+        r = orc.cluster_gated(x, eps, p.seed, m, p.min_pts, forced, m_row)
+        np.testing.assert_array_equal(core.cpu().numpy(), r["core"])
+        np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
+        assert st["queries"] == r["queries"]
+        assert st["surrogate_core"] == int((forced == 1).sum())
+        assert st["surrogate_noise"] == int((forced == 2).sum())
+    # nothing gated: the plain method exactly
+    labels, _ = net.cluster(xg, p, 0.0, 1.0, 0.25)
+    assert torch.equal(labels, plain)
+
+
+def test_surrogate_gain_on_sibling_dataset():
+    """Trained on core masks of sibling datasets (same mixture, new samples),
+    the gate removes most queries on a fresh sibling while its clustering
+    stays within ARI >= 0.99 of the plain method's."""
+    torch, sng = need_gpu()
+    from paper_2006_06743_gb300 import surrogate as sg
+    n, d, m = 200_000, 32, 500
+    master = 77
+    xs, ys = [], []
+    eps = None
+    for k in range(4):
+        x = datagen.gaussian_mixture(n, d, 40, 0.03, seed=1000 + k, master_seed=master)
+        if eps is None:
+            eps = datagen.eps_quantile(x, 0.01, 1_000_000, seed=0)
+        xg = torch.from_numpy(x).cuda()
+        _, core, _ = sng.cluster(xg, sng.Params(eps=eps, min_pts=8, m=m, seed=k), want_core=True)
+        xs.append(xg)
+        ys.append(core)
+    xtr = torch.cat(xs[:3]).contiguous()
+    ytr = torch.cat(ys[:3]).contiguous()
+    net = sg.Surrogate(datagen.mlp_init(d, 128, 5), cfg=sg.TrainConfig(batch=4096, lr=1e-3))
+    net.standardize(xtr)
+    net.train(xtr, ytr, 1500)
+    x_test = xs[3]
+    p = sng.Params(eps=eps, min_pts=8, m=m, seed=3)
+    plain, plain_core, pst = sng.cluster(x_test, p, want_core=True)
+    labels, core, st = net.cluster(x_test, p, 0.1, 0.9, 0.25, want_core=True)
+    ari = sng.ari(labels, plain)
+    agree = (core == plain_core).float().mean().item()
+    assert st["queries"] < 0.6 * pst["queries"], (st["queries"], pst["queries"])
+    assert ari >= 0.99, ari
+    assert agree >= 0.97, agree

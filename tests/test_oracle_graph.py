@@ -238,3 +238,43 @@ def test_out_hits_follow_ball_mass(orc):
     assert abs(mean - m * p) < 5 * se + 0.01 * m * p, (mean, m * p, se)
     # variance close to binomial (points' own ball masses are all equal here)
     assert 0.7 < out.var() / (m * p * (1 - p)) < 1.3
+
+
+# ------------------------------------------------- surrogate-gated form
+
+def test_gated_form_reduces_to_plain_and_prefix(orc):
+    """With every point ungated the gated form is Algorithm 1 itself; a point
+    limited to m_row[i] draws keeps exactly the kept draws among its first
+    m_row[i] (prefix of the same stream)."""
+    n, m = 1500, 80
+    x = datagen.random_points(n, 2, seed=31)
+    plain = orc.cluster(x, 0.05, seed=3, m=m, min_pts=4)
+    full = orc.cluster_gated(x, 0.05, 3, m, 4, forced=np.zeros(n, np.uint8),
+                             m_row=np.full(n, m, np.int32))
+    np.testing.assert_array_equal(full["labels"], plain["labels"])
+    assert full["queries"] == n * m
+    rng = np.random.default_rng(0)
+    m_row = rng.integers(0, m + 1, size=n).astype(np.int32)
+    rp, col, _, _ = orc.build_rows(x, 0.05, 3, m, m_row=m_row)
+    p = orc.partners(3, n, 0, n, m)
+    xx = x.astype(np.float64)
+    for i in rng.choice(n, 40, replace=False):
+        cand = p[i, :m_row[i]]
+        d2 = ((xx[i] - xx[cand]) ** 2).sum(1)
+        want = cand[d2 <= float(np.float32(0.05)) ** 2]
+        np.testing.assert_array_equal(col[rp[i]:rp[i + 1]], want)
+
+
+def test_gated_forced_core_and_noise(orc):
+    # path 0-1-2-3 drawn by 0,1,2 only: degrees 1,2,2,1 (multigraph)
+    rp, col = _csr(4, [(0, 1), (1, 2), (2, 3)])
+    r = orc.cluster_graph(4, rp, col, min_pts=2)
+    np.testing.assert_array_equal(r["labels"], [1, 1, 1, 1])
+    # forcing 3 to core makes it a core of the same component
+    r = orc.cluster_graph(4, rp, col, min_pts=2, forced=np.array([0, 0, 0, 1], np.uint8))
+    np.testing.assert_array_equal(r["core"], [0, 1, 1, 1])
+    np.testing.assert_array_equal(r["labels"], [1, 1, 1, 1])
+    # forcing 2 to non-core cuts the path: 3 becomes noise, 2 a border of 1
+    r = orc.cluster_graph(4, rp, col, min_pts=2, forced=np.array([0, 0, 2, 0], np.uint8))
+    np.testing.assert_array_equal(r["core"], [0, 1, 0, 0])
+    np.testing.assert_array_equal(r["labels"], [1, 1, 1, -1])
