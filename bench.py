@@ -275,6 +275,180 @@ def bench_sng(args, w):
     return out if rank == 0 else None
 
 
+def _timed(fn, reps: int):
+    """Median wall time of fn() in ms with a device sync on both sides."""
+    import torch
+    out = None
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return statistics.median(ts), out
+
+
+def bench_bf16(args):
+    """BF16 form: n = 5,000,000 unit-norm vectors in d = 128 (1000 centres on
+    the sphere, per-coordinate noise sigma, renormalised); s = 0.0002 (m =
+    1000); eps = 0.6; MinPts = 8.  Plain FP32 on the same points beside it."""
+    import torch
+
+    import paper_2006_06743_gb300 as sng
+    from paper_2006_06743_gb300 import datagen
+    n, d, m = args.bf16_n, 128, 1000
+    x = datagen.sphere_embeddings(n, d, 1000, args.bf16_sigma, seed=args.seed)
+    xf = torch.from_numpy(x).cuda()
+    del x
+    xb = xf.to(torch.bfloat16)
+    p = sng.Params(eps=0.6, min_pts=8, s=0.0002, seed=args.seed, flags=sng.SNG_FLAG_TIMING)
+    for _ in range(args.warmup):
+        sng.cluster(xf, p)
+        sng.cluster(xb, p, x_master=xf)
+    f_ms, (lf, sf) = _timed(lambda: sng.cluster(xf, p), args.steps)
+    b_ms, (lb, sb) = _timed(lambda: sng.cluster(xb, p, x_master=xf), args.steps)
+    Q = n * m
+    peak, kind = peaks()
+    alg_b = gather_algorithmic_bytes(n, d, m, 2, sb["kept_edges"])
+    alg_f = gather_algorithmic_bytes(n, d, m, 4, sf["kept_edges"])
+    return {"form": "bf16", "metric": "sampled eps-queries/s, BF16 vs FP32 form",
+            "value": Q / (b_ms * 1e-3), "unit": "queries/s", "fp32_value": Q / (f_ms * 1e-3),
+            "speedup_vs_fp32": f_ms / b_ms, "ms_bf16": b_ms, "ms_fp32": f_ms,
+            "ari_bf16_vs_fp32": sng.ari(lb, lf),
+            "roofline_bf16": {"achieved": alg_b / (sb["ms"]["gather"] * 1e-3) / 1e9, "peak": peak,
+                              "frac": alg_b / (sb["ms"]["gather"] * 1e-3) / 1e9 / peak,
+                              "kernel_ms": sb["ms"]["gather"], "peak_kind": kind},
+            "roofline_fp32": {"achieved": alg_f / (sf["ms"]["gather"] * 1e-3) / 1e9, "peak": peak,
+                              "frac": alg_f / (sf["ms"]["gather"] * 1e-3) / 1e9 / peak,
+                              "kernel_ms": sf["ms"]["gather"]},
+            "stats_bf16": {k: sb[k] for k in ("kept_edges", "band_pairs", "recheck_pairs",
+                                              "clusters", "noise")},
+            "stats_fp32": {k: sf[k] for k in ("kept_edges", "band_pairs", "clusters", "noise")},
+            "config": {"workload": f"sphere-n{n}-d{d}-sigma{args.bf16_sigma}", "m": m,
+                       "eps": 0.6, "min_pts": 8}, "dtype": "bf16", "steps": args.steps}
+
+
+def bench_batched(args):
+    """Batched form: 4096 3-D clouds of 2,000..130,000 points (Gaussian blobs
+    plus a 30% ground layer), m = 200, eps = 0.3 m, MinPts = 4; one
+    persistent launch replayed as a CUDA graph against one sng_cluster call
+    per cloud."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_2006_06743_gb300 as sng
+    from paper_2006_06743_gb300 import datagen
+    x, off = datagen.point_clouds(args.clouds, seed=args.seed)
+    xg = torch.from_numpy(x).cuda()
+    total = x.shape[0]
+    del x
+    labels = torch.empty(total, dtype=torch.int32, device="cuda")
+    p = sng.Params(eps=0.3, min_pts=4, m=200, seed=args.seed)
+    cp = p.to_c(0, 3, 4, sng.SNG_F32)
+    L = sng.lib()
+    plan = ctypes.c_void_p()
+    offs = np.ascontiguousarray(off, dtype=np.int64)
+    sng._check(L.sng_batch_plan_create(offs.ctypes.data, len(off) - 1, ctypes.byref(cp), None,
+                                       ctypes.byref(plan)))
+    st = sng.sng_stats()
+    strm = torch.cuda.current_stream().cuda_stream
+
+    def run():
+        sng._check(L.sng_batch_run(plan, xg.data_ptr(), labels.data_ptr(), None, strm))
+    for _ in range(args.warmup):
+        run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(args.steps):
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    b_ms = statistics.median(ms)
+    sng._check(L.sng_batch_run(plan, xg.data_ptr(), labels.data_ptr(), ctypes.byref(st), strm))
+    stats = st.as_dict()
+    L.sng_batch_plan_destroy(plan)
+    # per-cloud sequential calls (each cloud its own sng_cluster)
+    seq_labels = torch.empty_like(labels)
+    ncl = min(args.clouds, args.seq_clouds)
+
+    def seq():
+        for b in range(ncl):
+            xb = xg[off[b]:off[b + 1], :3]
+            q = sng.Params(eps=0.3, min_pts=4, m=200, seed=args.seed + b)
+            lb, _ = sng.cluster(xb, q)
+            seq_labels[off[b]:off[b + 1]] = lb
+    s_ms, _ = _timed(seq, 1)
+    frac = float(off[ncl]) / float(off[-1])
+    same = bool(torch.equal(seq_labels[:off[ncl]], labels[:off[ncl]]))
+    Q = int(stats["queries"])
+    return {"form": "batched", "metric": "sampled eps-queries/s, 4096 clouds in one launch",
+            "value": Q / (b_ms * 1e-3), "unit": "queries/s", "ms_batched": b_ms,
+            "ms_sequential_est": s_ms / frac, "sequential_clouds_timed": ncl,
+            "speedup_vs_sequential": (s_ms / frac) / b_ms, "labels_equal_sequential": same,
+            "stats": {k: stats[k] for k in ("queries", "kept_edges", "cores", "clusters",
+                                            "noise")},
+            "config": {"workload": f"clouds-{args.clouds}-2k..130k-d3", "points": total,
+                       "m": 200, "eps": 0.3, "min_pts": 4, "graph": "CUDA graph replay"},
+            "dtype": "f32", "steps": args.steps}
+
+
+def bench_surrogate(args):
+    """Learned-surrogate form: n = 2,000,000 points in d = 32 from a
+    200-Gaussian mixture with 3% noise; s = 0.0005 (m = 1000); eps = 1%
+    pair-distance quantile; MinPts = 8.  The network is trained on core masks
+    of 10 sibling datasets (same mixture, new samples) labelled by the plain
+    GPU method, then gates a fresh sibling."""
+    import torch
+
+    import paper_2006_06743_gb300 as sng
+    from paper_2006_06743_gb300 import datagen, surrogate as sg
+    n, d, m = args.surr_n, 32, 1000
+    master = 2020
+    xs, ys, eps = [], [], None
+    t0 = time.perf_counter()
+    for k in range(args.siblings + 1):
+        x = datagen.gaussian_mixture(n, d, 200, 0.03, seed=10 + k, master_seed=master)
+        if eps is None:
+            eps = datagen.eps_quantile(x, 0.01, 1_000_000, seed=0)
+        xg = torch.from_numpy(x).cuda()
+        _, core, _ = sng.cluster(xg, sng.Params(eps=eps, min_pts=8, s=0.0005, seed=k),
+                                 want_core=True)
+        xs.append(xg)
+        ys.append(core)
+    t_label = time.perf_counter() - t0
+    xt = xs.pop()
+    ys.pop()
+    xtr, ytr = torch.cat(xs).contiguous(), torch.cat(ys).contiguous()
+    del xs, ys
+    net = sg.Surrogate(datagen.mlp_init(d, 128, args.seed), cfg=sg.TrainConfig(batch=4096))
+    net.standardize(xtr)
+    t_train, trace = _timed(lambda: net.train(xtr, ytr, args.train_steps), 1)
+    p = sng.Params(eps=eps, min_pts=8, s=0.0005, seed=99, flags=sng.SNG_FLAG_TIMING)
+    g = dict(p_noise=args.p_noise, p_core=args.p_core, core_draw_frac=args.core_frac)
+    for _ in range(args.warmup):
+        sng.cluster(xt, p)
+        net.cluster(xt, p, **g)
+    p_ms, (plain, pcore, pst) = _timed(lambda: sng.cluster(xt, p, want_core=True), args.steps)
+    s_ms, (lab, core, sst) = _timed(lambda: net.cluster(xt, p, want_core=True, **g), args.steps)
+    return {"form": "surrogate", "metric": "e2e cluster time, surrogate vs plain",
+            "value": n * m / (s_ms * 1e-3), "unit": "queries/s (nominal n*m)",
+            "ms_surrogate": s_ms, "ms_plain": p_ms, "speedup_vs_plain": p_ms / s_ms,
+            "ari_vs_plain": sng.ari(lab, plain),
+            "core_mask_agreement": float((core == pcore).float().mean().item()),
+            "queries_issued_frac": sst["queries"] / pst["queries"],
+            "gated_core": sst["surrogate_core"], "gated_noise": sst["surrogate_noise"],
+            "train": {"steps": args.train_steps, "seconds": t_train * 1e-3,
+                      "loss_first": float(trace[:50].mean()), "loss_last": float(trace[-200:].mean()),
+                      "label_seconds": t_label},
+            "config": {"workload": f"mixture-n{n}-d{d}-k200", "m": m, "eps": eps, "min_pts": 8,
+                       **g}, "dtype": "f32", "steps": args.steps}
+
+
 def bench_reference(args, w):
     """The reference arm: the FP64 CPU oracle, timed as it stands on the host."""
     rank, world, _ = dist_env()
@@ -315,12 +489,29 @@ def main():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tune-budget", type=float, default=40.0)
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--form", default="plain", choices=["plain", "bf16", "batched", "surrogate"])
+    ap.add_argument("--bf16-n", type=int, default=5_000_000)
+    ap.add_argument("--bf16-sigma", type=float, default=0.15)
+    ap.add_argument("--clouds", type=int, default=4096)
+    ap.add_argument("--seq-clouds", type=int, default=512)
+    ap.add_argument("--surr-n", type=int, default=2_000_000)
+    ap.add_argument("--siblings", type=int, default=10)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--p-noise", type=float, default=0.1)
+    ap.add_argument("--p-core", type=float, default=0.9)
+    ap.add_argument("--core-frac", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
     args = ap.parse_args()
     rank, world, _ = dist_env()
     if args.impl == "reference" and rank != 0:
+        return
+    if args.form != "plain":
+        import __graft_entry__
+        __graft_entry__.build()
+        fn = {"bf16": bench_bf16, "batched": bench_batched, "surrogate": bench_surrogate}
+        print(json.dumps(fn[args.form](args)), flush=True)
         return
     w = make_workload(args.workload, seed=args.seed)
     if args.impl == "reference":

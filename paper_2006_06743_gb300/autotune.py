@@ -55,17 +55,17 @@ def candidates(x, p: Params) -> list[dict]:
     if x.stride(0) % vec:
         vec = 1
     g0 = _default_group(d, vec)
-    groups = sorted({g for g in (g0, g0 // 2, g0 * 2) if 1 <= g <= 32})
+    groups = sorted({g for g in (g0 // 8, g0 // 4, g0 // 2, g0, g0 * 2) if 1 <= g <= 32})
     x_bytes = n * x.stride(0) * esize
     passes = [1]
     if x_bytes > (48 << 20):
         base = max(2, int(math.ceil(x_bytes / (48 << 20))))
         passes += sorted({2, base, base + 2, 2 * base} - {1})
     out = []
-    for g in groups:
-        for u in (2, 4, 8):
-            for b in (128, 256):
-                for ps in passes:
+    for ps in passes:
+        for g in groups:
+            for u in (1, 2, 4, 8):
+                for b in (256, 128):
                     out.append(dict(map_group=g, map_unroll=u, map_block=b, map_passes=ps))
     return out
 

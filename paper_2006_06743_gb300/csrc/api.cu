@@ -152,11 +152,14 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
     group = p->map_group;
     if (group > 32 || (group & (group - 1))) return fail(SNG_EINVAL, "map_group must be 1..32, pow2");
     nch = pow2ceil((chunks + group - 1) / group);
-  } else if (chunks <= 4 && vec <= 2) {
+  } else if (chunks <= 4) {
+    // thread per pair: the whole row in one lane
     group = 1;
     nch = pow2ceil(chunks);
   } else {
-    group = pow2ceil(chunks);
+    // about four 16-byte chunks per lane: enough pairs per warp step to
+    // amortise the group reduction and the ballot (measured best at d = 64)
+    group = pow2ceil((chunks + 3) / 4);
     if (group > 32) group = 32;
     nch = pow2ceil((chunks + group - 1) / group);
   }
@@ -166,7 +169,7 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   r->map.vec = vec;
   r->map.group = group;
   r->map.nch = nch;
-  r->map.unroll = p->map_unroll > 0 ? p->map_unroll : 4;
+  r->map.unroll = p->map_unroll > 0 ? p->map_unroll : (vec == vmax && nch >= 4 ? 2 : 4);
   if (p->map_passes < 0 || p->map_passes > 64) return fail(SNG_EINVAL, "map_passes must be in [0, 64]");
   r->map.passes = p->map_passes > 0 ? p->map_passes : 1;
   if (r->map.passes > p->n) r->map.passes = (int)p->n;

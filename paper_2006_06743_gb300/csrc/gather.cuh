@@ -155,14 +155,14 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
           }
           if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, 1);
         }
-        const uint32_t b = __ballot_sync(kFullMask, keep);
+        // R keep flags (held by the group leaders, lanes g*G) -> R low bits
         uint32_t bits;
         if (G == 1) {
-          bits = b;
+          bits = __ballot_sync(kFullMask, keep);
         } else {
-          bits = 0;
-#pragma unroll
-          for (int g = 0; g < R; ++g) bits |= ((b >> (g * G)) & 1u) << g;
+          const int src = (lane < R ? lane : 0) * G;
+          const bool kg = __shfl_sync(kFullMask, keep ? 1 : 0, src) != 0;
+          bits = __ballot_sync(kFullMask, lane < R && kg);
         }
         const int first = t * R;  // draw index within the stage
         if (lane == (first >> 5)) myword |= bits << (first & 31);

@@ -1,0 +1,32 @@
+// gather_bf16_c.cu -- compiled BF16 (values widened to FP32) gather mappings: vec 4 x unroll 4, vec 2 x unroll 4, vec 1 x unroll 4.
+// (Split across translation units so the library builds in parallel.)
+#include "gather_inst.cuh"
+
+namespace sng {
+
+bool launch_bf16_c(const GatherMap &map, const GatherArgs &args, int grid, cudaStream_t stream) {
+  SNG_SHAPES_U(uint16_t, 4, 4, SNG_TRY)
+  SNG_SHAPES_U(uint16_t, 2, 4, SNG_TRY)
+  SNG_SHAPES_U(uint16_t, 1, 4, SNG_TRY)
+  return false;
+}
+
+int occ_bf16_c(const GatherMap &map) {
+  SNG_SHAPES_U(uint16_t, 4, 4, SNG_OCC)
+  SNG_SHAPES_U(uint16_t, 2, 4, SNG_OCC)
+  SNG_SHAPES_U(uint16_t, 1, 4, SNG_OCC)
+  return -1;
+}
+
+bool launch_gather_blocked_bf16(const GatherMap &map, const GatherArgs &args, int grid,
+                               int32_t lo, int32_t hi, cudaStream_t stream) {
+  SNG_BLOCKED_SHAPES(uint16_t, 8, SNG_TRY_B)
+  return false;
+}
+
+int occ_gather_blocked_bf16(const GatherMap &map) {
+  SNG_BLOCKED_SHAPES(uint16_t, 8, SNG_OCC_B)
+  return 0;
+}
+
+}  // namespace sng

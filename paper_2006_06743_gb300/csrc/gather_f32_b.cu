@@ -1,0 +1,19 @@
+// gather_f32_b.cu -- compiled FP32 gather mappings: vec 4 x unroll 4, vec 4 x unroll 8.
+// (Split across translation units so the library builds in parallel.)
+#include "gather_inst.cuh"
+
+namespace sng {
+
+bool launch_f32_b(const GatherMap &map, const GatherArgs &args, int grid, cudaStream_t stream) {
+  SNG_SHAPES_U(float, 4, 4, SNG_TRY)
+  SNG_SHAPES_U(float, 4, 8, SNG_TRY)
+  return false;
+}
+
+int occ_f32_b(const GatherMap &map) {
+  SNG_SHAPES_U(float, 4, 4, SNG_OCC)
+  SNG_SHAPES_U(float, 4, 8, SNG_OCC)
+  return -1;
+}
+
+}  // namespace sng

@@ -64,7 +64,9 @@ static int occ_blocks_blocked(const GatherMap &m) {
 #define SNG_SHAPES_U(T, V, U, X)                                                         \
   X(T, V, 1, 1, U) X(T, V, 2, 1, U) X(T, V, 4, 1, U) X(T, V, 8, 1, U) X(T, V, 16, 1, U) \
   X(T, V, 32, 1, U) X(T, V, 16, 2, U) X(T, V, 32, 2, U) X(T, V, 32, 4, U)                \
-  X(T, V, 32, 8, U) X(T, V, 1, 2, U) X(T, V, 1, 4, U)
+  X(T, V, 32, 8, U) X(T, V, 1, 2, U) X(T, V, 1, 4, U) X(T, V, 8, 2, U) X(T, V, 4, 4, U)  \
+  X(T, V, 2, 8, U) X(T, V, 4, 2, U) X(T, V, 8, 4, U) X(T, V, 16, 4, U) X(T, V, 4, 8, U)  \
+  X(T, V, 2, 4, U)
 
 #define SNG_TRY(T, V, G, N, U) \
   if (try_launch<T, V, G, N, U>(map, args, grid, stream)) return true;

@@ -3,16 +3,38 @@
 
 namespace sng {
 
-bool launch_gather_f32(const GatherMap &, const GatherArgs &, int, cudaStream_t);
-bool launch_gather_bf16(const GatherMap &, const GatherArgs &, int, cudaStream_t);
-int occ_gather_f32(const GatherMap &);
-int occ_gather_bf16(const GatherMap &);
+#define SNG_UNIT(tag)                                                      \
+  bool launch_##tag(const GatherMap &, const GatherArgs &, int, cudaStream_t); \
+  int occ_##tag(const GatherMap &);
+SNG_UNIT(f32_a) SNG_UNIT(f32_b) SNG_UNIT(f32_c) SNG_UNIT(bf16_a) SNG_UNIT(bf16_b) SNG_UNIT(bf16_c)
+#undef SNG_UNIT
 bool launch_gather_blocked_f32(const GatherMap &, const GatherArgs &, int, int32_t, int32_t,
                                cudaStream_t);
 bool launch_gather_blocked_bf16(const GatherMap &, const GatherArgs &, int, int32_t, int32_t,
                                 cudaStream_t);
 int occ_gather_blocked_f32(const GatherMap &);
 int occ_gather_blocked_bf16(const GatherMap &);
+
+bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
+                   cudaStream_t stream) {
+  if (dtype == SNG_F32)
+    return launch_f32_a(map, args, grid, stream) || launch_f32_b(map, args, grid, stream) ||
+           launch_f32_c(map, args, grid, stream);
+  return launch_bf16_a(map, args, grid, stream) || launch_bf16_b(map, args, grid, stream) ||
+         launch_bf16_c(map, args, grid, stream);
+}
+
+int gather_max_blocks_per_sm(int dtype, const GatherMap &map) {
+  int b;
+  if (dtype == SNG_F32) {
+    if ((b = occ_f32_a(map)) >= 0 || (b = occ_f32_b(map)) >= 0 || (b = occ_f32_c(map)) >= 0)
+      return b;
+  } else {
+    if ((b = occ_bf16_a(map)) >= 0 || (b = occ_bf16_b(map)) >= 0 || (b = occ_bf16_c(map)) >= 0)
+      return b;
+  }
+  return 0;
+}
 
 bool launch_gather_blocked(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
                            int32_t lo, int32_t hi, cudaStream_t stream) {
@@ -22,16 +44,6 @@ bool launch_gather_blocked(int dtype, const GatherMap &map, const GatherArgs &ar
 
 int gather_blocked_max_blocks_per_sm(int dtype, const GatherMap &map) {
   return dtype == SNG_F32 ? occ_gather_blocked_f32(map) : occ_gather_blocked_bf16(map);
-}
-
-bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
-                   cudaStream_t stream) {
-  return dtype == SNG_F32 ? launch_gather_f32(map, args, grid, stream)
-                          : launch_gather_bf16(map, args, grid, stream);
-}
-
-int gather_max_blocks_per_sm(int dtype, const GatherMap &map) {
-  return dtype == SNG_F32 ? occ_gather_f32(map) : occ_gather_bf16(map);
 }
 
 size_t gather_smem_bytes(const GatherMap &map) {

@@ -73,19 +73,21 @@ def test_graph_padded_rows(orc, n, d, ld):
 
 
 COMPILED_SHAPES = [(1, 1), (2, 1), (4, 1), (8, 1), (16, 1), (32, 1), (16, 2), (32, 2), (32, 4),
-                   (32, 8), (1, 2), (1, 4)]
+                   (32, 8), (1, 2), (1, 4), (8, 2), (4, 4), (2, 8), (4, 2), (8, 4), (16, 4),
+                   (4, 8), (2, 4)]
 
 
 @pytest.mark.parametrize("group,nch", COMPILED_SHAPES)
-@pytest.mark.parametrize("unroll", [2, 4, 8])
+@pytest.mark.parametrize("unroll", [1, 2, 4, 8])
 def test_mapping_overrides_agree(orc, group, nch, unroll):
     """Every compiled lanes-per-pair / chunks / batches-in-flight mapping gives
-    the oracle's graph (rows one element short of the mapping's width)."""
+    the oracle's graph (rows one element short of the mapping's width, and
+    the full width)."""
     torch, sng = need_gpu()
-    d = group * nch * 4 - 1
+    d = group * nch * 4 - (1 if unroll % 2 else 0)
     n = 600
     x = datagen.random_points(n, d, seed=group * 10 + nch)
-    xg, _buf = padded(torch, x, d + 1)
+    xg, _buf = padded(torch, x, ((d + 4) // 4) * 4)   # padded, rows stay 16-byte aligned
     p = sng.Params(eps=float(np.float32(0.12 * math.sqrt(d))), min_pts=4, m=150, seed=9,
                    map_group=group, map_unroll=unroll)
     _compare_graph(orc, x, xg, p, sng)
