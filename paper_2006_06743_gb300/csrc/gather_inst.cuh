@@ -47,9 +47,10 @@ static int occ_blocks_blocked(const GatherMap &m) {
 }
 
 // L2-blocked mappings: the row widths of the large workloads
-#define SNG_BLOCKED_SHAPES(T, V, X) \
+#define SNG_BLOCKED_SHAPES(T, V, X)                                                         \
   X(T, V, 8, 1, 4) X(T, V, 16, 1, 4) X(T, V, 16, 1, 8) X(T, V, 32, 1, 4) X(T, V, 16, 2, 4) \
-  X(T, V, 32, 2, 4)
+  X(T, V, 32, 2, 4) X(T, V, 2, 4, 2) X(T, V, 4, 4, 2) X(T, V, 8, 4, 2) X(T, V, 16, 4, 2)   \
+  X(T, V, 32, 4, 2) X(T, V, 4, 4, 4) X(T, V, 1, 4, 4) X(T, V, 1, 2, 4) X(T, V, 1, 1, 4)
 
 #define SNG_TRY_B(T, V, G, N, U) \
   if (try_launch_blocked<T, V, G, N, U>(map, args, grid, lo, hi, stream)) return true;
