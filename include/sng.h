@@ -246,6 +246,27 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
                                  float p_noise, float p_core, float core_draw_frac,
                                  int32_t *labels, uint8_t *core, sng_stats *stats, void *stream);
 
+/*
+ * Clustering that allocates no memory (the paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory at call time,
+ * e.g. a plugin whose host application reserved all device memory up front,
+ * or a real-time loop that cannot afford cudaMalloc's device synchronisation
+ * or its failure under memory pressure).  Same result as sng_cluster on the
+ * same arguments (Algorithm 1), computed by the persistent kernel of the
+ * batched form with all scratch in a fixed 16 MiB device array built into
+ * the library (resident on every GPU that loads it, until exit).
+ * x: device FP32, n x ld (row shapes of the batched form: d <= 64 with ld a
+ * multiple of 4, or d <= 4).  labels: device int32[n].  Requires
+ * n * (4 * ceil(m/32) + 10) bytes plus a few KiB of scratch to fit in 16 MiB,
+ * otherwise SNG_EINVAL.  No cudaMalloc / cudaFree or other allocation.  The
+ * first call on a device looks up the array's device address (call it once
+ * before any stream capture).  All calls share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller.  Synchronises
+ * `stream` (to read the status word and fill stats, which may be NULL).
+ */
+sng_status sng_cluster_noalloc(const float *x, const sng_params *params, int32_t *labels,
+                               sng_stats *stats, void *stream);
+
 /* Number of kernels this library has launched in this process. */
 int64_t sng_launch_count(void);
 

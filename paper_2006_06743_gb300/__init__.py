@@ -110,6 +110,8 @@ SIGNATURES = {
                                                ctypes.POINTER(sng_mlp_config), _P, ctypes.c_float,
                                                ctypes.c_float, ctypes.c_float, _P, _P,
                                                ctypes.POINTER(sng_stats), _P]),
+    "sng_cluster_noalloc": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P,
+                                             ctypes.POINTER(sng_stats), _P]),
     "sng_launch_count": (ctypes.c_int64, []),
     "sng_last_error": (ctypes.c_char_p, []),
     "sng_strerror": (ctypes.c_char_p, [ctypes.c_int32]),

@@ -21,38 +21,9 @@
 #include <vector>
 
 #include "api_common.cuh"
+#include "batched.cuh"
 
 namespace sng {
-
-struct CloudInfo {
-  int64_t off;      // first row of the cloud in x_concat / labels
-  int64_t bm_off;   // first keep-bit word of the cloud
-  uint64_t seed;    // base seed + cloud index
-  FastMod fm;       // remainder constants for n - 1
-  int32_t n, m, W, ntiles;
-};
-
-struct BatchArgs {
-  const float *x;
-  int64_t ld;
-  int32_t d;
-  int32_t n_items;
-  int32_t tile_rows;
-  int32_t min_pts, deg_mode, sample_all;
-  float lo_thr, hi_thr;
-  double eps2, band;
-  const CloudInfo *clouds;
-  const int2 *items;  // (cloud, tile)
-  uint32_t *bitmask;
-  int32_t *deg;
-  int32_t *parent;
-  uint8_t *core;
-  uint8_t *band_flag;
-  int32_t *labels;
-  unsigned int *next_item;
-  unsigned int *done;
-  unsigned long long *counters;
-};
 
 // Steps 3-5 for one cloud, by one CTA, after all of its tiles are complete.
 __device__ void cloud_components(const BatchArgs &a, const CloudInfo &c) {
@@ -199,9 +170,6 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchArgs a) {
   }
 }
 
-struct BatchMap {
-  int vec, group, nch, unroll;
-};
 
 template <int VEC, int G, int NCH, int U>
 static bool try_batched(const BatchMap &m, const BatchArgs &a, int grid, int block,
@@ -230,6 +198,11 @@ static bool dispatch_batched(const BatchMap &m, const BatchArgs &a, int grid, in
   SNG_B(1, 1, 1, 4) SNG_B(1, 1, 2, 4) SNG_B(1, 1, 4, 2) SNG_B(1, 1, 4, 4)
 #undef SNG_B
   return false;
+}
+
+bool launch_batched_kernel(const BatchMap &m, const BatchArgs &a, int grid, int block,
+                           cudaStream_t st, int *occ) {
+  return dispatch_batched(m, a, grid, block, st, occ);
 }
 
 }  // namespace sng
