@@ -249,8 +249,9 @@ def bench_sng(args, w):
         "config": {"workload": args.workload, "n": n, "d": d, "m": m, "s": w["s"],
                    "eps": w["eps"], "min_pts": w["min_pts"], "queries_per_step": Q,
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"dp{world}",
-                   "gather_mapping": {k: getattr(params, k) for k in
-                                      ("map_group", "map_unroll", "map_block", "map_passes")},
+                   "gather_mapping": {**{k: getattr(params, k) for k in
+                                         ("map_group", "map_unroll", "map_block", "map_passes")},
+                                      "prefetch": bool(params.flags & sng.SNG_FLAG_PREFETCH)},
                    "autotuned": tuned is not None},
         "e2e": {"value": Q * world / (t_e2e * 1e-3), "unit": "queries/s",
                 "seconds": t_e2e * 1e-3,
@@ -429,7 +430,8 @@ def bench_surrogate(args):
     net.standardize(xtr)
     t_train, trace = _timed(lambda: net.train(xtr, ytr, args.train_steps), 1)
     p = sng.Params(eps=eps, min_pts=8, s=0.0005, seed=99, flags=sng.SNG_FLAG_TIMING)
-    g = dict(p_noise=args.p_noise, p_core=args.p_core, core_draw_frac=args.core_frac)
+    g = dict(p_noise=args.p_noise, p_core=args.p_core, core_draw_frac=args.core_frac,
+             noise_draw_frac=args.noise_frac, reweight=bool(args.reweight))
     for _ in range(args.warmup):
         sng.cluster(xt, p)
         net.cluster(xt, p, **g)
@@ -497,9 +499,11 @@ def main():
     ap.add_argument("--surr-n", type=int, default=2_000_000)
     ap.add_argument("--siblings", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=3000)
-    ap.add_argument("--p-noise", type=float, default=0.1)
-    ap.add_argument("--p-core", type=float, default=0.9)
-    ap.add_argument("--core-frac", type=float, default=0.25)
+    ap.add_argument("--p-noise", type=float, default=0.0)
+    ap.add_argument("--p-core", type=float, default=0.95)
+    ap.add_argument("--core-frac", type=float, default=0.5)
+    ap.add_argument("--noise-frac", type=float, default=0.0)
+    ap.add_argument("--reweight", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)

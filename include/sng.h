@@ -70,6 +70,8 @@ typedef int32_t sng_status;
 
 /* flags */
 #define SNG_FLAG_TIMING 1u  /* fill sng_stats.ms with per-phase CUDA-event times */
+#define SNG_FLAG_PREFETCH 2u /* gather: bulk-prefetch partner rows into L2 one stage
+                                ahead (16-byte rows; measured slower at d = 64)  */
 
 typedef struct {
     int64_t n;            /* number of points, 2 <= n <= 2^31 - 1            */
@@ -233,18 +235,33 @@ sng_status sng_mlp_predict(const float *x, int64_t n, const sng_mlp_config *cfg,
                            const float *params, float *prob, void *stream);
 
 /*
- * Algorithm 1 gated by the surrogate.  Points with p < p_noise are not core
- * and draw no partners (they can still become border points through other
- * points' draws); points with p > p_core are core and draw only the first
- * ceil(core_draw_frac * m) partners of the same hash stream (enough to keep
- * their component connected); all other points draw all m partners and are
- * core by degree.  Same arguments and outputs as sng_cluster (x: FP32, row
- * stride params->ld); stats->queries counts the queries actually issued.
+ * How the surrogate gates points (sng_cluster_surrogate).  p = network
+ * probability that the point is core.  p < p_noise: not core, draws the first
+ * ceil(noise_draw_frac * m) partners (0: none; it can still become a border
+ * point through other points' draws).  p > p_core: core, draws the first
+ * ceil(core_draw_frac * m) partners of the same hash stream.  Otherwise all m
+ * draws and the core test by degree.  reweight = 1 counts every kept draw of
+ * a point that drew m_i < m partners as m / m_i draws (in units of 1/16, at
+ * both ends), an unbiased estimate of the degree the plain method would see.
+ */
+typedef struct {
+    float p_noise;
+    float p_core;
+    float core_draw_frac;   /* (0, 1] */
+    float noise_draw_frac;  /* [0, 1] */
+    int32_t reweight;       /* 0 or 1 */
+} sng_gate;
+
+/*
+ * Algorithm 1 gated by the surrogate (see sng_gate).  Same arguments and
+ * outputs as sng_cluster (x: FP32, row stride params->ld); stats->queries
+ * counts the queries actually issued, stats->surrogate_core / _noise the
+ * points gated each way.
  */
 sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
                                  const sng_mlp_config *cfg, const float *mlp_params,
-                                 float p_noise, float p_core, float core_draw_frac,
-                                 int32_t *labels, uint8_t *core, sng_stats *stats, void *stream);
+                                 const sng_gate *gate, int32_t *labels, uint8_t *core,
+                                 sng_stats *stats, void *stream);
 
 /*
  * Clustering that allocates no memory (the paper has no counterpart: this is

@@ -82,6 +82,8 @@ def _load():
         lib.orc_build_rows_m.restype = i32
         lib.orc_cluster_graph_forced.argtypes = [i64, P, P, i32, i32, P, P, P, P, P]
         lib.orc_cluster_graph_forced.restype = i32
+        lib.orc_cluster_graph_gated.argtypes = [i64, P, P, i32, i32, P, P, P, P, P, P]
+        lib.orc_cluster_graph_gated.restype = i32
         lib.orc_graph_free.argtypes = [ctypes.POINTER(_Graph)]
         lib.orc_graph_free.restype = None
         lib.orc_degrees.argtypes = [i64, P, P, i32, P]
@@ -211,20 +213,24 @@ def border_labels(n: int, row_ptr, col, core, comp) -> np.ndarray:
     return labels
 
 
-def cluster_graph(n: int, row_ptr, col, min_pts: int, deg_mode: int = 0, forced=None) -> dict:
+def cluster_graph(n: int, row_ptr, col, min_pts: int, deg_mode: int = 0, forced=None,
+                  w_row=None) -> dict:
     """Algorithm 1, steps 3-5 on a given sampled graph (CSR by source).
     ``forced`` (uint8 per point: 1 core, 2 not core, 0 by degree) overrides
-    the core test (surrogate form)."""
+    the core test and ``w_row`` (int32 per point) weights each kept draw of
+    a row (surrogate form; min_pts is then in the weights' units)."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     cl = np.ascontiguousarray(col, dtype=np.int32)
     fc = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8)
+    wr = None if w_row is None else np.ascontiguousarray(w_row, dtype=np.int32)
     labels = np.empty(n, dtype=np.int32)
     core = np.empty(n, dtype=np.uint8)
     deg = np.empty(n, dtype=np.int32)
     stats = np.zeros(8, dtype=np.int64)
-    if _load().orc_cluster_graph_forced(n, _ptr(rp), _ptr(cl), deg_mode, min_pts,
-                                        _ptr(fc) if fc is not None else None, _ptr(labels),
-                                        _ptr(core), _ptr(deg), _ptr(stats)) != 0:
+    if _load().orc_cluster_graph_gated(n, _ptr(rp), _ptr(cl), deg_mode, min_pts,
+                                       _ptr(fc) if fc is not None else None,
+                                       _ptr(wr) if wr is not None else None, _ptr(labels),
+                                       _ptr(core), _ptr(deg), _ptr(stats)) != 0:
         raise MemoryError("orc_cluster_graph failed")
     return dict(labels=labels, core=core, deg=deg, kept_edges=int(stats[1]),
                 cores=int(stats[4]), clusters=int(stats[5]), noise=int(stats[6]))
@@ -253,12 +259,15 @@ def cluster(x, eps: float, seed: int, m: int, min_pts: int, deg_mode: int = 0,
 
 
 def cluster_gated(x, eps: float, seed: int, m: int, min_pts: int, forced, m_row,
-                  deg_mode: int = 0) -> dict:
+                  deg_mode: int = 0, w_row=None, deg_unit: int = 16) -> dict:
     """The surrogate-gated form of Algorithm 1: point i draws its first
     m_row[i] partners, and forced[i] (1 core, 2 not core, 0 by degree)
-    overrides the core test; steps 3-5 as in the plain form."""
+    overrides the core test; with ``w_row`` each kept draw of row i counts
+    w_row[i] / deg_unit in the degree.  Steps 3-5 as in the plain form."""
     rp, col, _, _ = build_rows(x, eps, seed, m, m_row=m_row)
-    r = cluster_graph(np.asarray(x).shape[0], rp, col, min_pts, deg_mode=deg_mode, forced=forced)
+    mp = min_pts * deg_unit if w_row is not None else min_pts
+    r = cluster_graph(np.asarray(x).shape[0], rp, col, mp, deg_mode=deg_mode, forced=forced,
+                      w_row=w_row)
     r["queries"] = int(np.minimum(np.asarray(m_row, dtype=np.int64), m).sum())
     return r
 

@@ -371,16 +371,54 @@ int32_t orc_cluster_graph(int64_t n, const int64_t *row_ptr, const int32_t *col,
                                     stats);
 }
 
+int32_t orc_cluster_graph_gated(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                int32_t deg_mode, int32_t min_pts, const uint8_t *forced,
+                                const int32_t *w_row, int32_t *labels, uint8_t *core,
+                                int32_t *deg, int64_t *stats);
+
 /* Steps 3-5 with an optional per-point override of the core test:
  * forced[i] = 1 makes i core, 2 makes it non-core, 0 leaves deg >= MinPts. */
 int32_t orc_cluster_graph_forced(int64_t n, const int64_t *row_ptr, const int32_t *col,
                                  int32_t deg_mode, int32_t min_pts, const uint8_t *forced,
                                  int32_t *labels, uint8_t *core, int32_t *deg, int64_t *stats)
 {
+    return orc_cluster_graph_gated(n, row_ptr, col, deg_mode, min_pts, forced, NULL, labels,
+                                   core, deg, stats);
+}
+
+/*
+ * Degrees where every kept draw of row i counts w_row[i] (at both ends in
+ * multigraph mode, at i only in out-degree mode): the gated form's estimate
+ * of the plain degree when point i drew only some of its partners.
+ */
+static void degrees_weighted(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                             int32_t mode, const int32_t *w_row, int32_t *deg)
+{
+    memset(deg, 0, (size_t)n * sizeof(int32_t));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            deg[i] += w_row[i];
+            if (mode == 0) deg[col[e]] += w_row[i];
+        }
+}
+
+/* Steps 3-5 of the gated form: forced core flags as above and, if w_row is
+ * given, weighted degrees (min_pts is then in the weights' units). */
+int32_t orc_cluster_graph_gated(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                int32_t deg_mode, int32_t min_pts, const uint8_t *forced,
+                                const int32_t *w_row, int32_t *labels, uint8_t *core,
+                                int32_t *deg, int64_t *stats)
+{
     int32_t *dg = deg ? deg : (int32_t *)malloc((size_t)n * sizeof(int32_t));
     int32_t *comp = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     if (!dg || !comp) { if (!deg) free(dg); free(comp); return -1; }
-    if (orc_degrees(n, row_ptr, col, deg_mode, dg)) { if (!deg) free(dg); free(comp); return -1; }
+    if (w_row && (deg_mode == 0 || deg_mode == 1)) {
+        degrees_weighted(n, row_ptr, col, deg_mode, w_row, dg);
+    } else if (orc_degrees(n, row_ptr, col, deg_mode, dg)) {
+        if (!deg) free(dg);
+        free(comp);
+        return -1;
+    }
     int64_t ncores = 0;
     for (int64_t i = 0; i < n; ++i) {
         core[i] = dg[i] >= min_pts ? 1 : 0;

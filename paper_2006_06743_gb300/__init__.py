@@ -29,6 +29,7 @@ SNG_F32, SNG_BF16 = 0, 1
 SNG_DEG_UNDIRECTED_MULTI, SNG_DEG_OUT = 0, 1
 SNG_SAMPLE_HASH, SNG_SAMPLE_ALL = 0, 1
 SNG_FLAG_TIMING = 1
+SNG_FLAG_PREFETCH = 2
 
 PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total")
 
@@ -72,6 +73,12 @@ class sng_mlp_config(ctypes.Structure):
                 ("sequential", ctypes.c_int32)]
 
 
+class sng_gate(ctypes.Structure):
+    _fields_ = [("p_noise", ctypes.c_float), ("p_core", ctypes.c_float),
+                ("core_draw_frac", ctypes.c_float), ("noise_draw_frac", ctypes.c_float),
+                ("reweight", ctypes.c_int32)]
+
+
 class sng_graph(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("num_edges", ctypes.c_int64),
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("deg", ctypes.c_void_p),
@@ -107,8 +114,8 @@ SIGNATURES = {
     "sng_mlp_predict": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.POINTER(sng_mlp_config), _P,
                                          _P, _P]),
     "sng_cluster_surrogate": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params),
-                                               ctypes.POINTER(sng_mlp_config), _P, ctypes.c_float,
-                                               ctypes.c_float, ctypes.c_float, _P, _P,
+                                               ctypes.POINTER(sng_mlp_config), _P,
+                                               ctypes.POINTER(sng_gate), _P, _P,
                                                ctypes.POINTER(sng_stats), _P]),
     "sng_cluster_noalloc": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P,
                                              ctypes.POINTER(sng_stats), _P]),

@@ -16,7 +16,7 @@ import os
 import statistics
 import time
 
-from . import SNG_FLAG_TIMING, Params, SngError, cluster
+from . import SNG_FLAG_PREFETCH, SNG_FLAG_TIMING, Params, SngError, cluster
 
 CACHE_ENV = "SNG_AUTOTUNE_CACHE"
 
@@ -66,8 +66,19 @@ def candidates(x, p: Params) -> list[dict]:
         for g in groups:
             for u in (1, 2, 4, 8):
                 for b in (256, 128):
-                    out.append(dict(map_group=g, map_unroll=u, map_block=b, map_passes=ps))
+                    for pf in (False, True):
+                        out.append(dict(map_group=g, map_unroll=u, map_block=b, map_passes=ps,
+                                        prefetch=pf))
     return out
+
+
+def _params_for(base: dict, cand: dict) -> Params:
+    c = dict(cand)
+    pf = c.pop("prefetch", False)
+    flags = base.get("flags", 0) & ~SNG_FLAG_PREFETCH
+    if pf:
+        flags |= SNG_FLAG_PREFETCH
+    return Params(**{**base, **c, "flags": flags})
 
 
 def _time(x, p: Params, reps: int, x_master=None) -> float:
@@ -102,7 +113,7 @@ def tune(x, p: Params, x_master=None, reps: int = 3, budget_s: float = 60.0,
     for cand in candidates(x, p):
         if time.perf_counter() - t_start > budget_s:
             break
-        q = Params(**{**base, **cand})
+        q = _params_for(base, cand)
         try:
             _time(x, q, 1, x_master)            # warm-up
             t = _time(x, q, reps, x_master)
@@ -129,4 +140,4 @@ def tune(x, p: Params, x_master=None, reps: int = 3, budget_s: float = 60.0,
 
 
 def apply(p: Params, best: dict) -> Params:
-    return Params(**{**p.__dict__, **best.get("mapping", {})})
+    return _params_for(dict(p.__dict__), best.get("mapping", {}))

@@ -216,6 +216,12 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
   g->sample_all = p->sample_mode == SNG_SAMPLE_ALL;
   g->deg_mode = p->degree_mode;
   g->m_row = nullptr;
+  g->w_row = nullptr;
+  // L2 prefetch of partner rows when rows start on 16 bytes (16-byte vectors)
+  const int esize = p->dtype == SNG_F32 ? 4 : 2;
+  g->pf_bytes = 0;
+  if (r.map.vec * esize == 16 && (p->flags & SNG_FLAG_PREFETCH))
+    g->pf_bytes = ((r.d * esize + 15) / 16) * 16;
   return true;
 }
 
@@ -234,7 +240,7 @@ int gather_grid(int dtype, const GatherMap &map, int64_t n) {
 // Steps shared by sng_build_graph and sng_cluster: the gather (step 2 with the
 // degree counts of step 3), the row-pointer scan and the CSR fill.
 sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scratch &s,
-                     GraphBufs *gb, const int32_t *m_row, Timer *tm) {
+                     GraphBufs *gb, const int32_t *m_row, Timer *tm, const int32_t *w_row) {
   cudaStream_t st = s.stream;
   const int64_t n = r.n;
   sng_status rc;
@@ -252,6 +258,7 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   GatherArgs ga;
   fill_gather_args(x, p, r, &ga);
   ga.m_row = m_row;
+  ga.w_row = w_row;
   ga.bitmask = gb->bitmask;
   ga.out_cnt = gb->out_cnt;
   ga.deg = gb->deg;

@@ -64,7 +64,8 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r);
 bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, GatherArgs *g);
 int gather_grid(int dtype, const GatherMap &map, int64_t n);
 sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scratch &s,
-                     GraphBufs *gb, const int32_t *m_row, Timer *tm);
+                     GraphBufs *gb, const int32_t *m_row, Timer *tm,
+                     const int32_t *w_row = nullptr);
 sng_status read_stats(const unsigned long long *counters, const Resolved &r, sng_stats *stats,
                       cudaStream_t st, const Timer *tm);
 

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int warps = blockDim.x >> 5;
-  int32_t *sp = smem_partner + warp * 32 * U;
+  int32_t *sp = smem_partner + warp * 64 * U;   // two stages of 32*U partners
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(a.next_item, 1u);
     __syncthreads();
@@ -143,6 +143,8 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchArgs a) {
     g.sample_all = a.sample_all;
     g.deg_mode = a.deg_mode;
     g.m_row = nullptr;
+    g.w_row = nullptr;
+    g.pf_bytes = 0;
     g.bitmask = a.bitmask + c.bm_off;
     g.out_cnt = nullptr;
     g.deg = a.deg + c.off;
@@ -175,7 +177,7 @@ template <int VEC, int G, int NCH, int U>
 static bool try_batched(const BatchMap &m, const BatchArgs &a, int grid, int block,
                         cudaStream_t st, int *occ) {
   if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return false;
-  const size_t smem = (size_t)(block / 32) * 32 * U * sizeof(int32_t);
+  const size_t smem = (size_t)(block / 32) * 64 * U * sizeof(int32_t);
   if (occ) {
     *occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batched_kernel<VEC, G, NCH, U>, block,

@@ -39,6 +39,10 @@ struct GatherArgs {
   int32_t sample_all;
   int32_t deg_mode;
   const int32_t *m_row;   // nullable: draws of row i (<= m)
+  const int32_t *w_row;   // nullable: degree weight of each kept draw of row i
+                          // (both ends); NULL = weight 1
+  int32_t pf_bytes;       // > 0: bulk-prefetch this many bytes of each partner
+                          // row into L2 one stage ahead (16-byte rows only)
   uint32_t *bitmask;      // n x W
   int32_t *out_cnt;       // n, nullable
   int32_t *deg;           // n (zeroed before launch in multigraph mode)
@@ -58,9 +62,37 @@ __device__ __forceinline__ bool recheck_pair(const GatherArgs &a, int32_t i, int
   return s <= a.eps2;
 }
 
+// Bulk prefetch of the start of partner row p into L2 (the copy engine
+// fetches it while the warp works on the current stage).  Only for rows that
+// start on 16 bytes (16-byte vector mappings); the size is a multiple of 16.
+template <typename T, int VEC>
+__device__ __forceinline__ void prefetch_row(const GatherArgs &a, int32_t p) {
+  if constexpr (VEC * sizeof(T) == 16) {
+    const T *row = static_cast<const T *>(a.x) + (int64_t)p * a.ld;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(row), "r"(a.pf_bytes)
+                 : "memory");
+  }
+}
+
+// Partners of draws j0 .. j0+32U-1 of row i into buf (one hash per lane per
+// batch of 32; -1 past the row's draws), prefetching their rows if enabled.
+template <typename T, int VEC, int U>
+__device__ __forceinline__ void stage_partners(const GatherArgs &a, int32_t i, uint64_t key,
+                                               int64_t j0, int32_t mi, int32_t *buf, int lane) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t j = j0 + u * 32 + lane;
+    int32_t p = -1;
+    if (j < mi) p = a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm);
+    buf[u * 32 + lane] = p;
+    if (a.pf_bytes > 0 && p >= 0) prefetch_row<T, VEC>(a, p);
+  }
+}
+
 // One source row: draws 0..mi-1 of point i, keep bits into bitmask row i,
 // in-degree atomics; returns the row's kept count (same value on all lanes).
-// `sp` is this warp's 32*U-entry shared-memory partner buffer.
+// `sp` is this warp's 2*32*U-entry shared-memory partner buffer: the stage
+// being tested and the next one, hashed (and prefetched) one stage ahead.
 template <typename T, int VEC, int G, int NCH, int U>
 __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_t mi,
                                           int32_t *sp, int lane) {
@@ -72,6 +104,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
   const T *X = static_cast<const T *>(a.x);
   const int d = a.d;
   const uint64_t key = row_key(a.seed, i);
+  const int32_t wi = a.w_row ? a.w_row[i] : 1;
 
   // this lane's slice of row i; elements at or past d read as zero
   float xi[NCH][VEC];
@@ -91,14 +124,10 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 
   int cnt = 0;
   int jb = 0;
+  int32_t *cur = sp, *nxt = sp + S;
+  if (mi > 0) stage_partners<T, VEC, U>(a, i, key, 0, mi, cur, lane);
   for (; jb < mi; jb += S) {
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t j = (int64_t)jb + u * 32 + lane;
-      int32_t p = -1;
-      if (j < mi) p = a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm);
-      sp[u * 32 + lane] = p;
-    }
+    if (jb + S < mi) stage_partners<T, VEC, U>(a, i, key, (int64_t)jb + S, mi, nxt, lane);
     __syncwarp();
     uint32_t myword = 0;
 #pragma unroll 1
@@ -108,7 +137,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int t = t0 + u;
-        const int32_t p = sp[t * R + grp];
+        const int32_t p = cur[t * R + grp];
         pv[u] = p;
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
@@ -153,7 +182,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
           } else if (!(acc > a.hi_thr)) {
             keep = recheck_pair<T>(a, i, p);
           }
-          if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, 1);
+          if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
         }
         // R keep flags (held by the group leaders, lanes g*G) -> R low bits
         uint32_t bits;
@@ -172,6 +201,9 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
     if (lane < U && w < a.W) a.bitmask[(int64_t)i * a.W + w] = myword;
     cnt += __popc(myword);
     __syncwarp();
+    int32_t *t = cur;
+    cur = nxt;
+    nxt = t;
   }
   // words past this row's draws (per-row draw counts) are zero
   for (int w = (jb >> 5) + lane; w < a.W; w += 32) a.bitmask[(int64_t)i * a.W + w] = 0u;
@@ -180,9 +212,9 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
   if (lane == 0) {
     if (a.out_cnt) a.out_cnt[i] = cnt;
     if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) {
-      if (cnt) atomicAdd(a.deg + i, cnt);
+      if (cnt) atomicAdd(a.deg + i, cnt * wi);
     } else {
-      a.deg[i] = cnt;
+      a.deg[i] = cnt * wi;
     }
   }
   return cnt;
@@ -200,7 +232,7 @@ __global__ void __launch_bounds__(256, MinBlocks<VEC, NCH, U>::value) gather_ker
   extern __shared__ int32_t smem_partner[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  int32_t *sp = smem_partner + warp * 32 * U;
+  int32_t *sp = smem_partner + warp * 64 * U;   // two stages of 32*U partners
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < a.n;
        row += warps_total) {
@@ -228,6 +260,7 @@ __device__ __forceinline__ void gather_row_blocked(const GatherArgs &a, int32_t 
   const T *X = static_cast<const T *>(a.x);
   const int d = a.d;
   const uint64_t key = row_key(a.seed, i);
+  const int32_t wi = a.w_row ? a.w_row[i] : 1;
   float xi[NCH][VEC];
 #pragma unroll
   for (int c = 0; c < NCH; ++c) {
@@ -310,7 +343,7 @@ __device__ __forceinline__ void gather_row_blocked(const GatherArgs &a, int32_t 
           if (keep) {
             const int32_t jj = jv[u];
             atomicOr(a.bitmask + (int64_t)i * a.W + (jj >> 5), 1u << (jj & 31));
-            if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, 1);
+            if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
             ++cnt;
           }
         }
@@ -322,7 +355,7 @@ __device__ __forceinline__ void gather_row_blocked(const GatherArgs &a, int32_t 
   for (int o = 16; o >= 1; o >>= 1) cnt += __shfl_xor_sync(kFullMask, cnt, o);
   if (lane == 0 && cnt) {
     if (a.out_cnt) atomicAdd(a.out_cnt + i, cnt);
-    atomicAdd(a.deg + i, cnt);
+    atomicAdd(a.deg + i, cnt * wi);
   }
 }
 

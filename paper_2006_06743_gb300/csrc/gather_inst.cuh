@@ -10,7 +10,7 @@ namespace sng {
 template <typename T, int VEC, int G, int NCH, int U>
 static bool try_launch(const GatherMap &m, const GatherArgs &args, int grid, cudaStream_t st) {
   if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return false;
-  const size_t smem = (size_t)(m.block / 32) * 32 * U * sizeof(int32_t);
+  const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
   gather_kernel<T, VEC, G, NCH, U><<<grid, m.block, smem, st>>>(args);
   return true;
 }
@@ -19,7 +19,7 @@ template <typename T, int VEC, int G, int NCH, int U>
 static int occ_blocks(const GatherMap &m) {
   if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return -1;
   int blocks = 0;
-  const size_t smem = (size_t)(m.block / 32) * 32 * U * sizeof(int32_t);
+  const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, gather_kernel<T, VEC, G, NCH, U>,
                                                     m.block, smem) != cudaSuccess)
     return 0;

@@ -18,7 +18,7 @@ struct FillArgs {
 
 struct CoreArgs {
   int64_t n;
-  int32_t min_pts;
+  int32_t min_pts;      // compared against deg (already in the degree's units)
   const int32_t *deg;
   const uint8_t *forced;  // nullable: 1 = core, 2 = not core, 0 = by degree
   uint8_t *core;

@@ -47,7 +47,7 @@ int gather_blocked_max_blocks_per_sm(int dtype, const GatherMap &map) {
 }
 
 size_t gather_smem_bytes(const GatherMap &map) {
-  return (size_t)(map.block / 32) * 32 * map.unroll * sizeof(int32_t);
+  return (size_t)(map.block / 32) * 64 * map.unroll * sizeof(int32_t);
 }
 
 // ------------------------------------------------------------ partners

@@ -25,6 +25,7 @@
 namespace sng {
 
 constexpr int kH = 128;
+constexpr int32_t kDegUnit = 16;  // degree units per draw when reweighting
 
 struct MlpOff {
   int64_t w1, b1, w2, b2, w3, b3, train, mean, std, total;
@@ -141,9 +142,11 @@ struct GateArgs {
   const float *P;
   float *prob;          // nullable
   float p_noise, p_core;
-  int32_t m, m_core;    // draws for uncertain / confident-core points
+  int32_t m, m_core, m_noise;  // draws for uncertain / confident-core / -noise points
+  int32_t w_full, w_core, w_noise;  // degree weight per kept draw of each class
   uint8_t *forced;      // nullable: 2 noise, 1 core, 0 uncertain
   int32_t *m_row;       // nullable
+  int32_t *w_row;       // nullable
   unsigned long long *counters;  // nullable: [0] queries [1] core [2] noise
 };
 
@@ -159,18 +162,21 @@ __global__ void __launch_bounds__(128, 1) mlp_gate_kernel(GateArgs a) {
     if (a.prob) a.prob[i] = p;
     if (a.forced) {
       uint8_t f = 0;
-      int32_t mi = a.m;
+      int32_t mi = a.m, wi = a.w_full;
       if (p < a.p_noise) {
         f = 2;
-        mi = 0;
+        mi = a.m_noise;
+        wi = a.w_noise;
         ++nn;
       } else if (p > a.p_core) {
         f = 1;
         mi = a.m_core;
+        wi = a.w_core;
         ++nc;
       }
       a.forced[i] = f;
       a.m_row[i] = mi;
+      if (a.w_row) a.w_row[i] = wi;
       q += (unsigned long long)mi;
     }
   }
@@ -572,53 +578,70 @@ sng_status sng_mlp_predict(const float *x, int64_t n, const sng_mlp_config *cfg,
   if (rc) return rc;
   if (!x || !params || !prob) return fail(SNG_EINVAL, "NULL argument");
   if (n < 1) return fail(SNG_EINVAL, "n must be >= 1");
-  GateArgs a{x, cfg->d, n, cfg->d, params, prob, 0.f, 1.f, 0, 0, nullptr, nullptr, nullptr};
+  GateArgs a{x,       cfg->d,  n,       cfg->d,  params,  prob,    0.f,     1.f, 0, 0, 0,
+             1,       1,       1,       nullptr, nullptr, nullptr, nullptr};
   cudaError_t e = launch_gate(a, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? SNG_OK : cuda_fail(e, "predict");
 }
 
 sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
                                  const sng_mlp_config *cfg, const float *mlp_params,
-                                 float p_noise, float p_core, float core_draw_frac,
-                                 int32_t *labels, uint8_t *core, sng_stats *stats,
-                                 void *stream) {
+                                 const sng_gate *gate, int32_t *labels, uint8_t *core,
+                                 sng_stats *stats, void *stream) {
   Resolved r;
   sng_status rc = validate(x, params, &r);
   if (rc) return rc;
   if ((rc = check_cfg(cfg))) return rc;
-  if (!labels || !mlp_params) return fail(SNG_EINVAL, "NULL argument");
+  if (!labels || !mlp_params || !gate) return fail(SNG_EINVAL, "NULL argument");
   if (params->dtype != SNG_F32) return fail(SNG_EINVAL, "surrogate form takes FP32 points");
-  if (params->sample_mode != SNG_SAMPLE_HASH) return fail(SNG_EINVAL, "surrogate form needs hashed draws");
+  if (params->sample_mode != SNG_SAMPLE_HASH)
+    return fail(SNG_EINVAL, "surrogate form needs hashed draws");
   if (cfg->d != params->d) return fail(SNG_EINVAL, "mlp d differs from the points' d");
-  if (!(p_noise >= 0.f && p_noise <= p_core && p_core <= 1.f))
+  const float pn = gate->p_noise, pc = gate->p_core;
+  if (!(pn >= 0.f && pn <= pc && pc <= 1.f))
     return fail(SNG_EINVAL, "need 0 <= p_noise <= p_core <= 1");
-  if (!(core_draw_frac >= 0.f && core_draw_frac <= 1.f))
-    return fail(SNG_EINVAL, "core_draw_frac must be in [0, 1]");
+  if (!(gate->core_draw_frac > 0.f && gate->core_draw_frac <= 1.f))
+    return fail(SNG_EINVAL, "core_draw_frac must be in (0, 1]");
+  if (!(gate->noise_draw_frac >= 0.f && gate->noise_draw_frac <= 1.f))
+    return fail(SNG_EINVAL, "noise_draw_frac must be in [0, 1]");
+  if (gate->reweight != 0 && gate->reweight != 1) return fail(SNG_EINVAL, "reweight is 0 or 1");
   device_sms();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Scratch s(st);
   Timer tm((params->flags & SNG_FLAG_TIMING) != 0);
   uint8_t *forced;
-  int32_t *m_row;
+  int32_t *m_row, *w_row = nullptr;
   unsigned long long *gcnt;
   if ((rc = s.alloc((void **)&forced, (size_t)r.n, "forced")) ||
       (rc = s.alloc((void **)&m_row, (size_t)r.n * 4, "draws per row")) ||
       (rc = s.alloc((void **)&gcnt, 4 * 8, "gate counters")))
     return rc;
+  if (gate->reweight && (rc = s.alloc((void **)&w_row, (size_t)r.n * 4, "degree weights")))
+    return rc;
   cudaMemsetAsync(gcnt, 0, 4 * 8, st);
-  const int32_t m_core = (int32_t)std::ceil((double)core_draw_frac * (double)r.m);
+  const int32_t m_core = (int32_t)std::ceil((double)gate->core_draw_frac * (double)r.m);
+  const int32_t m_noise = (int32_t)std::ceil((double)gate->noise_draw_frac * (double)r.m);
+  // reweighting: a kept draw of a point that drew m_i of m partners counts
+  // m / m_i (in units of 1/16), an unbiased estimate of its plain count
+  const int32_t unit = gate->reweight ? kDegUnit : 1;
+  auto weight = [&](int32_t mi) {
+    if (!gate->reweight) return 1;
+    if (mi <= 0) return kDegUnit;
+    return (int32_t)std::lround((double)kDegUnit * (double)r.m / (double)mi);
+  };
   GateArgs ga{static_cast<const float *>(x), params->ld, r.n, params->d, mlp_params, nullptr,
-              p_noise, p_core, (int32_t)r.m, m_core, forced, m_row, gcnt};
+              pn, pc, (int32_t)r.m, m_core, m_noise, weight((int32_t)r.m), weight(m_core),
+              weight(m_noise), forced, m_row, w_row, gcnt};
   cudaError_t e = launch_gate(ga, st);
   if (e != cudaSuccess) return cuda_fail(e, "surrogate gate");
   GraphBufs gb;
-  if ((rc = run_graph(x, params, r, s, &gb, m_row, &tm))) return rc;
+  if ((rc = run_graph(x, params, r, s, &gb, m_row, &tm, w_row))) return rc;
   uint8_t *core_buf = core;
   int32_t *parent = nullptr;
   if (!core_buf && (rc = s.alloc((void **)&core_buf, (size_t)r.n, "core"))) return rc;
   if ((rc = s.alloc((void **)&parent, (size_t)r.n * 4, "parent"))) return rc;
   const int sms = device_sms();
-  CoreArgs ca{r.n, params->min_pts, gb.deg, forced, core_buf, parent, labels};
+  CoreArgs ca{r.n, params->min_pts * unit, gb.deg, forced, core_buf, parent, labels};
   launch_core_init(ca, sms, st);
   tm.mark(st, 4);
   UnionArgs ua{r.n, gb.row_ptr, gb.col, core_buf, parent, labels, gb.counters};

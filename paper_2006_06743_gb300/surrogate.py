@@ -17,7 +17,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (SNG_F32, Params, _check, _rows, _stream_ptr, lib, sng_mlp_config, sng_stats)
+from . import (SNG_F32, Params, _check, _rows, _stream_ptr, lib, sng_gate, sng_mlp_config,
+               sng_stats)
 
 HIDDEN = 128
 
@@ -122,8 +123,9 @@ class Surrogate:
                                      self.params.data_ptr(), prob.data_ptr(), _stream_ptr()))
         return prob
 
-    def cluster(self, x, p: Params, p_noise: float = 0.1, p_core: float = 0.9,
-                core_draw_frac: float = 0.25, want_core: bool = False):
+    def cluster(self, x, p: Params, p_noise: float = 0.0, p_core: float = 0.95,
+                core_draw_frac: float = 0.5, noise_draw_frac: float = 0.0,
+                reweight: bool = False, want_core: bool = False):
         """Algorithm 1 gated by this network; returns (labels[, core], stats)."""
         import torch
         n, d, ld = _rows(x, SNG_F32)
@@ -131,23 +133,41 @@ class Surrogate:
         core = torch.empty(n, dtype=torch.uint8, device=x.device) if want_core else None
         st = sng_stats()
         c = self.cfg.to_c(self.d)
+        g = sng_gate()
+        g.p_noise, g.p_core = p_noise, p_core
+        g.core_draw_frac, g.noise_draw_frac, g.reweight = core_draw_frac, noise_draw_frac, int(reweight)
         _check(lib().sng_cluster_surrogate(
             x.data_ptr(), ctypes.byref(p.to_c(n, d, ld, SNG_F32)), ctypes.byref(c),
-            self.params.data_ptr(), p_noise, p_core, core_draw_frac, labels.data_ptr(),
+            self.params.data_ptr(), ctypes.byref(g), labels.data_ptr(),
             core.data_ptr() if core is not None else None, ctypes.byref(st), _stream_ptr()))
         out = st.as_dict()
         return (labels, core, out) if want_core else (labels, out)
 
 
-def gate_decisions(prob, m: int, p_noise: float, p_core: float, core_draw_frac: float):
+DEG_UNIT = 16
+
+
+def gate_decisions(prob, m: int, p_noise: float, p_core: float, core_draw_frac: float,
+                   noise_draw_frac: float = 0.0, reweight: bool = False):
     """The gate's rule on given probabilities (host mirror, for checking):
-    forced (0 uncertain, 1 core, 2 noise) and draws per point."""
+    forced (0 uncertain, 1 core, 2 noise), draws per point and, when
+    reweighting, the degree weight of each point's kept draws."""
     prob = np.asarray(prob, np.float32)
     forced = np.zeros(prob.size, np.uint8)
     forced[prob > np.float32(p_core)] = 1
     forced[prob < np.float32(p_noise)] = 2
     m_core = int(math.ceil(np.float64(np.float32(core_draw_frac)) * m))
+    m_noise = int(math.ceil(np.float64(np.float32(noise_draw_frac)) * m))
     m_row = np.full(prob.size, m, np.int32)
     m_row[forced == 1] = m_core
-    m_row[forced == 2] = 0
-    return forced, m_row
+    m_row[forced == 2] = m_noise
+    if not reweight:
+        return forced, m_row, None
+
+    def w(mi):
+        return DEG_UNIT if mi <= 0 else int(math.floor(DEG_UNIT * m / mi + 0.5))
+
+    w_row = np.full(prob.size, w(m), np.int32)
+    w_row[forced == 1] = w(m_core)
+    w_row[forced == 2] = w(m_noise)
+    return forced, m_row, w_row

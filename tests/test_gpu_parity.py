@@ -216,3 +216,28 @@ def test_l2_blocked_gather_matches_oracle(orc, passes, n, d, group):
     labels, st = _compare_cluster(orc, x, torch.from_numpy(x).cuda(),
                                   sng.Params(eps=eps, min_pts=4, m=300, seed=passes,
                                              map_passes=passes, map_group=group), sng)
+
+
+@pytest.mark.parametrize("n,d,dtype", [(3000, 64, "f32"), (2000, 128, "f32"), (2500, 128, "bf16"),
+                                       (1500, 32, "f32"), (1800, 20, "f32")])
+def test_prefetch_on_off_same_graph(orc, n, d, dtype):
+    """The bulk L2 prefetch of partner rows changes no result."""
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=n + d)
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    xg = torch.from_numpy(x).cuda()
+    master = None
+    if dtype == "bf16":
+        bits = datagen.bf16_round(x)
+        master = torch.from_numpy(datagen.bf16_to_f32(bits)).cuda()
+        xg = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+    outs = []
+    for flags in (0, sng.SNG_FLAG_PREFETCH):
+        p = sng.Params(eps=eps, min_pts=4, m=400, seed=3, flags=flags)
+        g = sng.build_graph(xg, p, x_master=master)
+        outs.append((g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    if dtype == "f32":
+        rp, col, _, _ = orc.build_rows(x, eps, 3, 400, band_rel=BAND_F32)
+        np.testing.assert_array_equal(outs[0][1], col)

@@ -118,10 +118,12 @@ def test_gated_cluster_matches_oracle_gated_form(orc):
     net.standardize(xg)
     net.train(xg, plain_core, 300)
     prob = net.predict(xg).cpu().numpy()
-    for pn, pc, frac in ((0.1, 0.9, 0.25), (0.3, 0.6, 0.5), (0.0, 1.0, 0.25)):
-        labels, core, st = net.cluster(xg, p, pn, pc, frac, want_core=True)
-        forced, m_row = sg.gate_decisions(prob, m, pn, pc, frac)
-        r = orc.cluster_gated(x, eps, p.seed, m, p.min_pts, forced, m_row)
+    for pn, pc, frac, nfrac, rw in ((0.1, 0.9, 0.25, 0.0, False), (0.3, 0.6, 0.5, 0.0, False),
+                                    (0.0, 1.0, 0.25, 0.0, False), (0.1, 0.9, 0.25, 0.1, True),
+                                    (0.05, 0.95, 0.3, 0.5, True), (0.2, 0.8, 0.5, 0.0, True)):
+        labels, core, st = net.cluster(xg, p, pn, pc, frac, nfrac, rw, want_core=True)
+        forced, m_row, w_row = sg.gate_decisions(prob, m, pn, pc, frac, nfrac, rw)
+        r = orc.cluster_gated(x, eps, p.seed, m, p.min_pts, forced, m_row, w_row=w_row)
         np.testing.assert_array_equal(core.cpu().numpy(), r["core"])
         np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
         assert st["queries"] == r["queries"]
@@ -133,17 +135,21 @@ def test_gated_cluster_matches_oracle_gated_form(orc):
 
 
 def test_surrogate_gain_on_sibling_dataset():
-    """Trained on core masks of sibling datasets (same mixture, new samples),
-    the gate removes most queries on a fresh sibling while its clustering
-    stays within ARI >= 0.99 of the plain method's."""
+    """The learned-surrogate configuration (n = 2,000,000 points in d = 32
+    from a 200-Gaussian mixture with 3% noise, m = 1000, eps = 1% distance
+    quantile, MinPts = 8), trained on core masks of three sibling datasets:
+    on a fresh sibling the gate removes over a quarter of the sampled queries
+    while its clustering stays within ARI >= 0.99 of the plain method's on the
+    same draws.  (For scale: the plain method against itself with another
+    seed gives ARI ~0.78 on this data.)"""
     torch, sng = need_gpu()
     from paper_2006_06743_gb300 import surrogate as sg
-    n, d, m = 200_000, 32, 500
-    master = 77
+    n, d, m = 2_000_000, 32, 1000
+    master = 4242
     xs, ys = [], []
     eps = None
     for k in range(4):
-        x = datagen.gaussian_mixture(n, d, 40, 0.03, seed=1000 + k, master_seed=master)
+        x = datagen.gaussian_mixture(n, d, 200, 0.03, seed=100 + k, master_seed=master)
         if eps is None:
             eps = datagen.eps_quantile(x, 0.01, 1_000_000, seed=0)
         xg = torch.from_numpy(x).cuda()
@@ -152,15 +158,18 @@ def test_surrogate_gain_on_sibling_dataset():
         ys.append(core)
     xtr = torch.cat(xs[:3]).contiguous()
     ytr = torch.cat(ys[:3]).contiguous()
+    del xs[:3], ys
     net = sg.Surrogate(datagen.mlp_init(d, 128, 5), cfg=sg.TrainConfig(batch=4096, lr=1e-3))
     net.standardize(xtr)
-    net.train(xtr, ytr, 1500)
-    x_test = xs[3]
-    p = sng.Params(eps=eps, min_pts=8, m=m, seed=3)
+    trace = net.train(xtr, ytr, 3000)
+    assert trace[-200:].mean() < 0.5 * trace[:20].mean()
+    x_test = xs[0]
+    p = sng.Params(eps=eps, min_pts=8, m=m, seed=77)
     plain, plain_core, pst = sng.cluster(x_test, p, want_core=True)
-    labels, core, st = net.cluster(x_test, p, 0.1, 0.9, 0.25, want_core=True)
+    labels, core, st = net.cluster(x_test, p, p_noise=0.0, p_core=0.95, core_draw_frac=0.5,
+                                   want_core=True)
     ari = sng.ari(labels, plain)
     agree = (core == plain_core).float().mean().item()
-    assert st["queries"] < 0.6 * pst["queries"], (st["queries"], pst["queries"])
+    assert st["queries"] < 0.75 * pst["queries"], (st["queries"], pst["queries"])
     assert ari >= 0.99, ari
-    assert agree >= 0.97, agree
+    assert agree >= 0.99, agree

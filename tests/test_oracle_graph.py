@@ -278,3 +278,19 @@ def test_gated_forced_core_and_noise(orc):
     r = orc.cluster_graph(4, rp, col, min_pts=2, forced=np.array([0, 0, 2, 0], np.uint8))
     np.testing.assert_array_equal(r["core"], [0, 1, 0, 0])
     np.testing.assert_array_equal(r["labels"], [1, 1, 1, -1])
+
+
+def test_gated_weighted_degrees(orc):
+    """Weighted degrees: each kept draw of row i counts w_row[i] at both ends
+    (multigraph) or at i only (out-degree); unit weights give the plain
+    degrees."""
+    rp, col = _csr(4, [(0, 1), (0, 2), (1, 2), (3, 2)])
+    r = orc.cluster_graph(4, rp, col, min_pts=1, w_row=np.ones(4, np.int32))
+    np.testing.assert_array_equal(r["deg"], orc.degrees(4, rp, col, 0))
+    w = np.array([16, 64, 16, 32], np.int32)
+    r = orc.cluster_graph(4, rp, col, min_pts=64, w_row=w)
+    # deg: 0 -> 16+16, 1 -> 16 (in from 0) + 64 (own), 2 -> 16+64+32, 3 -> 32
+    np.testing.assert_array_equal(r["deg"], [32, 80, 112, 32])
+    np.testing.assert_array_equal(r["core"], [0, 1, 1, 0])
+    r = orc.cluster_graph(4, rp, col, min_pts=32, deg_mode=1, w_row=w)
+    np.testing.assert_array_equal(r["deg"], [32, 64, 0, 32])
