@@ -304,11 +304,21 @@ def bench_bf16(args):
     del x
     xb = xf.to(torch.bfloat16)
     p = sng.Params(eps=0.6, min_pts=8, s=0.0002, seed=args.seed, flags=sng.SNG_FLAG_TIMING)
+    pf, pb = p, p
+    tuned = {}
+    if args.autotune:
+        from paper_2006_06743_gb300 import autotune
+        tf = autotune.tune(xf, p, reps=1, budget_s=args.tune_budget, force=args.retune,
+                           verbose=args.verbose)
+        tb = autotune.tune(xb, p, x_master=xf, reps=1, budget_s=args.tune_budget,
+                           force=args.retune, verbose=args.verbose)
+        pf, pb = autotune.apply(p, tf), autotune.apply(p, tb)
+        tuned = {"fp32": tf.get("mapping"), "bf16": tb.get("mapping")}
     for _ in range(args.warmup):
-        sng.cluster(xf, p)
-        sng.cluster(xb, p, x_master=xf)
-    f_ms, (lf, sf) = _timed(lambda: sng.cluster(xf, p), args.steps)
-    b_ms, (lb, sb) = _timed(lambda: sng.cluster(xb, p, x_master=xf), args.steps)
+        sng.cluster(xf, pf)
+        sng.cluster(xb, pb, x_master=xf)
+    f_ms, (lf, sf) = _timed(lambda: sng.cluster(xf, pf), args.steps)
+    b_ms, (lb, sb) = _timed(lambda: sng.cluster(xb, pb, x_master=xf), args.steps)
     Q = n * m
     peak, kind = peaks()
     alg_b = gather_algorithmic_bytes(n, d, m, 2, sb["kept_edges"])
@@ -327,7 +337,8 @@ def bench_bf16(args):
                                               "clusters", "noise")},
             "stats_fp32": {k: sf[k] for k in ("kept_edges", "band_pairs", "clusters", "noise")},
             "config": {"workload": f"sphere-n{n}-d{d}-sigma{args.bf16_sigma}", "m": m,
-                       "eps": 0.6, "min_pts": 8}, "dtype": "bf16", "steps": args.steps}
+                       "eps": 0.6, "min_pts": 8, "mappings": tuned}, "dtype": "bf16",
+            "steps": args.steps}
 
 
 def bench_batched(args):
@@ -348,6 +359,12 @@ def bench_batched(args):
     del x
     labels = torch.empty(total, dtype=torch.int32, device="cuda")
     p = sng.Params(eps=0.3, min_pts=4, m=200, seed=args.seed)
+    tuned = None
+    if args.autotune:
+        from paper_2006_06743_gb300 import autotune
+        tuned = autotune.tune_batched(xg, off, p, sample_clouds=256, budget_s=args.tune_budget,
+                                      force=args.retune, verbose=args.verbose)
+        p = sng.Params(**{**p.__dict__, **tuned.get("mapping", {})})
     cp = p.to_c(0, 3, 4, sng.SNG_F32)
     L = sng.lib()
     plan = ctypes.c_void_p()
@@ -394,7 +411,10 @@ def bench_batched(args):
             "stats": {k: stats[k] for k in ("queries", "kept_edges", "cores", "clusters",
                                             "noise")},
             "config": {"workload": f"clouds-{args.clouds}-2k..130k-d3", "points": total,
-                       "m": 200, "eps": 0.3, "min_pts": 4, "graph": "CUDA graph replay"},
+                       "m": 200, "eps": 0.3, "min_pts": 4, "graph": "CUDA graph replay",
+                       "mapping": {k: getattr(p, k) for k in ("map_unroll", "map_block",
+                                                              "map_tile")},
+                       "autotuned": tuned is not None},
             "dtype": "f32", "steps": args.steps}
 
 

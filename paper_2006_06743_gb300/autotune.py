@@ -141,3 +141,78 @@ def tune(x, p: Params, x_master=None, reps: int = 3, budget_s: float = 60.0,
 
 def apply(p: Params, best: dict) -> Params:
     return _params_for(dict(p.__dict__), best.get("mapping", {}))
+
+
+def tune_batched(x_concat, offsets, p: Params, sample_clouds: int = 256, reps: int = 2,
+                 budget_s: float = 60.0, cache: str | None = None, force: bool = False,
+                 verbose: bool = False) -> dict:
+    """Fastest persistent-kernel mapping (partner batches in flight, block
+    size, rows per work item) for a batch of clouds, timed with CUDA events
+    on the first ``sample_clouds`` clouds through sng_cluster_batched."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from . import SNG_F32, _check, lib
+    path = _cache_path(cache)
+    off = np.asarray(offsets, dtype=np.int64)
+    k = min(sample_clouds, off.size - 1)
+    sizes = np.diff(off[:k + 1])
+    key = (f"batched-d{p.__dict__.get('d', x_concat.shape[1])}-ld{x_concat.stride(0)}"
+           f"-mean{_bucket(int(sizes.mean()))}-m{_bucket(p.m or 1)}")
+    table = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    if not force and key in table:
+        return table[key]
+    sub = off[:k + 1].copy()
+    labels = torch.empty(int(sub[-1]), dtype=torch.int32, device=x_concat.device)
+    stream = torch.cuda.current_stream().cuda_stream
+    results = []
+    t0 = time.perf_counter()
+    for u in (1, 2, 4, 8):
+        for b in (256, 128):
+            for tile in (256, 1024, 4096):
+                if time.perf_counter() - t0 > budget_s:
+                    break
+                q = Params(**{**p.__dict__, "map_unroll": u, "map_block": b, "map_tile": tile})
+                cp = q.to_c(0, x_concat.shape[1], x_concat.stride(0), SNG_F32)
+                ms = []
+                try:
+                    for r in range(reps + 1):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        _check(lib().sng_cluster_batched(x_concat.data_ptr(), sub.ctypes.data, k,
+                                                         ctypes.byref(cp), None, labels.data_ptr(),
+                                                         None, stream))
+                        e1.record()
+                        e1.synchronize()
+                        if r:
+                            ms.append(e0.elapsed_time(e1))
+                except SngError as e:
+                    if verbose:
+                        print("skip", u, b, tile, e)
+                    continue
+                t = statistics.median(ms)
+                results.append((t, {"map_unroll": u, "map_block": b, "map_tile": tile}))
+                if verbose:
+                    print(f"{t:9.3f} ms  unroll={u} block={b} tile={tile}")
+    if not results:
+        return {"mapping": {}, "ms": None, "tried": 0}
+    results.sort(key=lambda r: r[0])
+    best = {"mapping": results[0][1], "ms": results[0][0], "tried": len(results),
+            "table": [[t, c] for t, c in results[:8]]}
+    table[key] = best
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(table, f, indent=1)
+    except OSError:
+        pass
+    return best

@@ -157,9 +157,12 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
     group = 1;
     nch = pow2ceil(chunks);
   } else {
-    // about four 16-byte chunks per lane: enough pairs per warp step to
-    // amortise the group reduction and the ballot (measured best at d = 64)
-    group = pow2ceil((chunks + 3) / 4);
+    // about 16 elements of the row per lane (4 float4 or 2 x 8 bf16 chunks):
+    // enough pairs per warp step to amortise the group reduction and the
+    // ballot, few enough registers for 3-4 blocks per SM (the autotuner's
+    // winners at d = 64 FP32 and d = 128 BF16)
+    const int per_lane = vec >= 16 ? 1 : 16 / vec;
+    group = pow2ceil((chunks + per_lane - 1) / per_lane);
     if (group > 32) group = 32;
     nch = pow2ceil((chunks + group - 1) / group);
   }
@@ -169,7 +172,7 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   r->map.vec = vec;
   r->map.group = group;
   r->map.nch = nch;
-  r->map.unroll = p->map_unroll > 0 ? p->map_unroll : (vec == vmax && nch >= 4 ? 2 : 4);
+  r->map.unroll = p->map_unroll > 0 ? p->map_unroll : (vec == vmax && nch * vec >= 16 ? 2 : 4);
   if (p->map_passes < 0 || p->map_passes > 64) return fail(SNG_EINVAL, "map_passes must be in [0, 64]");
   r->map.passes = p->map_passes > 0 ? p->map_passes : 1;
   if (r->map.passes > p->n) r->map.passes = (int)p->n;

@@ -132,7 +132,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
     uint32_t myword = 0;
 #pragma unroll 1
     for (int t0 = 0; t0 < STEPS; t0 += U) {
-      float v[U][NCH][VEC];
+      typename Raw<T, VEC>::type v[U][NCH];
       int32_t pv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -142,12 +142,8 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
-          if (p >= 0 && off < d) {
-            Chunk<T, VEC>::load(X + (int64_t)p * a.ld + off, v[u][c]);
-          } else {
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) v[u][c][k] = 0.f;
-          }
+          v[u][c] = (p >= 0 && off < d) ? Raw<T, VEC>::load(X + (int64_t)p * a.ld + off)
+                                        : Raw<T, VEC>::zero();
         }
       }
 #pragma unroll
@@ -160,13 +156,13 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
           if (off + VEC <= d) {
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
-              const float diff = xi[c][k] - v[u][c][k];
+              const float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
               acc = fmaf(diff, diff, acc);
             }
           } else {
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
-              float diff = xi[c][k] - v[u][c][k];
+              float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
               if (off + k >= d) diff = 0.f;
               acc = fmaf(diff, diff, acc);
             }
@@ -197,8 +193,10 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
         if (lane == (first >> 5)) myword |= bits << (first & 31);
       }
     }
+    // keep-bit words are written once and read back only by later kernels:
+    // streaming (evict-first) stores leave L2 to the partner rows
     const int w = (jb >> 5) + lane;
-    if (lane < U && w < a.W) a.bitmask[(int64_t)i * a.W + w] = myword;
+    if (lane < U && w < a.W) __stcs(a.bitmask + (int64_t)i * a.W + w, myword);
     cnt += __popc(myword);
     __syncwarp();
     int32_t *t = cur;
@@ -206,7 +204,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
     nxt = t;
   }
   // words past this row's draws (per-row draw counts) are zero
-  for (int w = (jb >> 5) + lane; w < a.W; w += 32) a.bitmask[(int64_t)i * a.W + w] = 0u;
+  for (int w = (jb >> 5) + lane; w < a.W; w += 32) __stcs(a.bitmask + (int64_t)i * a.W + w, 0u);
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) cnt += __shfl_xor_sync(kFullMask, cnt, o);
   if (lane == 0) {
@@ -222,13 +220,16 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 
 // Resident 256-thread blocks per SM the compiler must allow for: mappings
 // with few registers of row data get 4 (32 warps), wider ones 3 or 2.
-template <int VEC, int NCH, int U>
+template <typename T, int VEC, int NCH, int U>
 struct MinBlocks {
-  static constexpr int value = (VEC * NCH * U <= 16) ? 4 : (VEC * NCH * U <= 32 ? 3 : 2);
+  // 32-bit registers per lane of row data: partner chunks in flight (raw
+  // bits) plus this lane's slice of the source row (FP32)
+  static constexpr int words = U * NCH * (VEC * (int)sizeof(T) / 4 > 0 ? VEC * (int)sizeof(T) / 4 : 1) + NCH * VEC;
+  static constexpr int value = words <= 32 ? 4 : (words <= 56 ? 3 : 2);
 };
 
 template <typename T, int VEC, int G, int NCH, int U>
-__global__ void __launch_bounds__(256, MinBlocks<VEC, NCH, U>::value) gather_kernel(GatherArgs a) {
+__global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value) gather_kernel(GatherArgs a) {
   extern __shared__ int32_t smem_partner[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -298,7 +299,7 @@ __device__ __forceinline__ void gather_row_blocked(const GatherArgs &a, int32_t 
     const int steps = (nlist + R - 1) / R;
 #pragma unroll 1
     for (int t0 = 0; t0 < steps; t0 += U) {
-      float v[U][NCH][VEC];
+      typename Raw<T, VEC>::type v[U][NCH];
       int32_t pv[U], jv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -309,12 +310,8 @@ __device__ __forceinline__ void gather_row_blocked(const GatherArgs &a, int32_t 
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
-          if (p >= 0 && off < d) {
-            Chunk<T, VEC>::load(X + (int64_t)p * a.ld + off, v[u][c]);
-          } else {
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) v[u][c][k] = 0.f;
-          }
+          v[u][c] = (p >= 0 && off < d) ? Raw<T, VEC>::load(X + (int64_t)p * a.ld + off)
+                                        : Raw<T, VEC>::zero();
         }
       }
 #pragma unroll
@@ -325,7 +322,7 @@ __device__ __forceinline__ void gather_row_blocked(const GatherArgs &a, int32_t 
           const int off = (c * G + gl) * VEC;
 #pragma unroll
           for (int k = 0; k < VEC; ++k) {
-            float diff = xi[c][k] - v[u][c][k];
+            float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
             if (off + VEC > d && off + k >= d) diff = 0.f;
             acc = fmaf(diff, diff, acc);
           }
@@ -360,7 +357,7 @@ __device__ __forceinline__ void gather_row_blocked(const GatherArgs &a, int32_t 
 }
 
 template <typename T, int VEC, int G, int NCH, int U>
-__global__ void __launch_bounds__(256, MinBlocks<VEC, NCH, U>::value)
+__global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
     gather_blocked_kernel(GatherArgs a, int32_t lo, int32_t hi) {
   extern __shared__ int32_t smem_list[];
   const int lane = threadIdx.x & 31;

@@ -165,6 +165,86 @@ struct Chunk<uint16_t, 1> {
   }
 };
 
+// Raw vector registers of one chunk (the loaded bits, widened to FP32 only
+// where an element is used): float4/float2/float for FP32, uint4/uint2/uint
+// of packed bfloat16 pairs for BF16.
+template <typename T, int VEC>
+struct Raw;
+
+template <>
+struct Raw<float, 4> {
+  using type = float4;
+  static __device__ __forceinline__ type load(const float *p) {
+    return __ldg(reinterpret_cast<const float4 *>(p));
+  }
+  static __device__ __forceinline__ float get(const type &v, int k) {
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+  }
+  static __device__ __forceinline__ type zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct Raw<float, 2> {
+  using type = float2;
+  static __device__ __forceinline__ type load(const float *p) {
+    return __ldg(reinterpret_cast<const float2 *>(p));
+  }
+  static __device__ __forceinline__ float get(const type &v, int k) { return k == 0 ? v.x : v.y; }
+  static __device__ __forceinline__ type zero() { return make_float2(0.f, 0.f); }
+};
+template <>
+struct Raw<float, 1> {
+  using type = float;
+  static __device__ __forceinline__ type load(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ float get(const type &v, int) { return v; }
+  static __device__ __forceinline__ type zero() { return 0.f; }
+};
+template <>
+struct Raw<uint16_t, 8> {
+  using type = uint4;
+  static __device__ __forceinline__ type load(const uint16_t *p) {
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+  }
+  static __device__ __forceinline__ float get(const type &v, int k) {
+    const uint32_t w = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
+    return __uint_as_float((k & 1) ? (w & 0xffff0000u) : (w << 16));
+  }
+  static __device__ __forceinline__ type zero() { return make_uint4(0u, 0u, 0u, 0u); }
+};
+template <>
+struct Raw<uint16_t, 4> {
+  using type = uint2;
+  static __device__ __forceinline__ type load(const uint16_t *p) {
+    return __ldg(reinterpret_cast<const uint2 *>(p));
+  }
+  static __device__ __forceinline__ float get(const type &v, int k) {
+    const uint32_t w = (k >> 1) == 0 ? v.x : v.y;
+    return __uint_as_float((k & 1) ? (w & 0xffff0000u) : (w << 16));
+  }
+  static __device__ __forceinline__ type zero() { return make_uint2(0u, 0u); }
+};
+template <>
+struct Raw<uint16_t, 2> {
+  using type = uint32_t;
+  static __device__ __forceinline__ type load(const uint16_t *p) {
+    return __ldg(reinterpret_cast<const unsigned int *>(p));
+  }
+  static __device__ __forceinline__ float get(const type &v, int k) {
+    return __uint_as_float(k ? (v & 0xffff0000u) : (v << 16));
+  }
+  static __device__ __forceinline__ type zero() { return 0u; }
+};
+template <>
+struct Raw<uint16_t, 1> {
+  using type = uint32_t;
+  static __device__ __forceinline__ type load(const uint16_t *p) {
+    return (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(p));
+  }
+  static __device__ __forceinline__ float get(const type &v, int) {
+    return __uint_as_float(v << 16);
+  }
+  static __device__ __forceinline__ type zero() { return 0u; }
+};
+
 // FP64 squared distance in the oracle's order: left to right, each operation
 // rounded on its own (explicit _rn intrinsics forbid contraction into FMA).
 __device__ __forceinline__ double dist2_fp64(const float *a, const float *b, int d) {

@@ -1,0 +1,145 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+The oracle cannot redo 1e9-5e9 FP64 queries in a test, so: (1) the edge lists
+of a seeded sample of source rows must equal the oracle's exactly (step 2 is
+row-independent); (2) the oracle's steps 3-5 run on the GPU's complete edge
+list must reproduce the GPU's degrees, core mask and every label (steps 3-5
+are exact integer work)."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import BAND_BF16, BAND_F32, need_gpu
+from paper_2006_06743_gb300 import datagen
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _check_rows(orc, x_np, g, p, m, rows, band, master=None):
+    rp, col, _, _ = orc.build_rows(x_np if master is None else master, p.eps, p.seed, m,
+                                   band_rel=band, rows=rows)
+    grp = g["row_ptr"].cpu().numpy()
+    gcol = g["col"].cpu().numpy()
+    mism = 0
+    for k, i in enumerate(rows):
+        a = gcol[grp[i]:grp[i + 1]]
+        b = col[rp[k]:rp[k + 1]]
+        if not np.array_equal(a, b):
+            mism += 1
+    return mism
+
+
+def _check_cc(orc, g, labels, core, min_pts):
+    n = labels.numel()
+    r = orc.cluster_graph(n, g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy(), min_pts)
+    np.testing.assert_array_equal(g["deg"].cpu().numpy(), r["deg"])
+    np.testing.assert_array_equal(core.cpu().numpy(), r["core"])
+    np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
+    return r
+
+
+def test_headline_config_n1M_d64(orc):
+    """n = 1,000,000 in d = 64, 100-Gaussian mixture, s = 0.001 (m = 1000),
+    eps = 1% distance quantile, MinPts = 10: the benchmark's workload."""
+    torch, sng = need_gpu()
+    n, d = 1_000_000, 64
+    x = datagen.gaussian_mixture(n, d, 100, 0.02, seed=0)
+    eps = datagen.eps_quantile(x, 0.01, 1_000_000, seed=0)
+    p = sng.Params(eps=eps, min_pts=10, s=0.001, seed=0)
+    m = p.draws(n)
+    assert m == 1000
+    xg = torch.from_numpy(x).cuda()
+    g = sng.build_graph(xg, p)
+    rows = np.sort(np.random.default_rng(1).choice(n, 3000, replace=False))
+    assert _check_rows(orc, x, g, p, m, rows, BAND_F32) == 0
+    labels, core, st = sng.cluster(xg, p, want_core=True)
+    assert st["kept_edges"] == g["col"].numel()
+    r = _check_cc(orc, g, labels, core, 10)
+    assert st["clusters"] == r["clusters"] and st["noise"] == r["noise"]
+
+
+@pytest.mark.parametrize("sigma", [0.15, 0.0375])
+def test_bf16_config_n5M_d128(orc, sigma):
+    """n = 5,000,000 unit vectors in d = 128 stored as BF16, s = 0.0002 (m =
+    1000), eps = 0.6, MinPts = 8.  Sampled rows: decisions equal the FP64
+    oracle on the FP32 master except where BF16 rounding moves d^2 across
+    eps^2 outside the band (counted); steps 3-5 exact on the GPU's graph."""
+    torch, sng = need_gpu()
+    n, d = 5_000_000, 128
+    x = datagen.sphere_embeddings(n, d, 1000, sigma, seed=0)
+    xf = torch.from_numpy(x).cuda()
+    xb = xf.to(torch.bfloat16)
+    p = sng.Params(eps=0.6, min_pts=8, s=0.0002, seed=0)
+    m = p.draws(n)
+    assert m == 1000
+    g = sng.build_graph(xb, p, x_master=xf)
+    rows = np.sort(np.random.default_rng(2).choice(n, 600, replace=False))
+    # every sampled draw, decided the way the kernel must: far outside the
+    # band by the BF16 values (certified FP32 screen), inside it by the FP64
+    # recheck on the FP32 master, and either way only in a thin guard zone
+    # where the FP32 screen may fall on either side of its boundary
+    xq = xb[torch.from_numpy(rows).cuda()].float().cpu().numpy().astype(np.float64)
+    eps2 = float(np.float32(p.eps)) ** 2
+    grp, gcol = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    band = BAND_BF16
+    checked = either = 0
+    for k, i in enumerate(rows):
+        pr = orc.partners(p.seed, n, int(i), 1, m)[0]
+        q = xb[torch.from_numpy(pr).cuda()].float().cpu().numpy().astype(np.float64)
+        d2q = ((xq[k] - q) ** 2).sum(1)
+        d2m = ((x[i].astype(np.float64) - x[pr].astype(np.float64)) ** 2).sum(1)
+        gap = np.abs(d2q - eps2) / eps2
+        keep_far = d2q <= eps2
+        keep_band = d2m <= eps2
+        want_sure = np.where(gap < band * 0.999, keep_band, keep_far)
+        unsure = (gap >= band * 0.999) & (gap <= band + 2e-5)
+        # the kept list is in draw order and repeated draws of one partner
+        # share one decision, so matching it greedily recovers each draw's bit
+        got = np.zeros(m, bool)
+        it = iter(gcol[grp[i]:grp[i + 1]].tolist())
+        nxt = next(it, None)
+        for j in range(m):
+            if nxt is not None and pr[j] == nxt:
+                got[j] = True
+                nxt = next(it, None)
+        assert nxt is None, f"row {i}: kept draws not explained"
+        assert ((got == want_sure) | unsure).all(), f"row {i}"
+        checked += m
+        either += int(unsure.sum())
+    assert either < 0.001 * checked
+    labels, core, st = sng.cluster(xb, p, x_master=xf, want_core=True)
+    _check_cc(orc, g, labels, core, 8)
+    lf, sf = sng.cluster(xf, p)
+    assert sng.ari(labels, lf) >= 0.99
+
+
+def test_batched_config_4096_clouds(orc):
+    """4096 clouds of 2,000..130,000 points, m = 200, eps = 0.3, MinPts = 4,
+    in one persistent launch: sampled clouds equal the oracle; totals equal
+    per-cloud single calls on a further sample."""
+    import ctypes
+    torch, sng = need_gpu()
+    x, off = datagen.point_clouds(4096, seed=0)
+    xg = torch.from_numpy(x).cuda()
+    labels = torch.empty(x.shape[0], dtype=torch.int32, device="cuda")
+    p = sng.Params(eps=0.3, min_pts=4, m=200, seed=0)
+    cp = p.to_c(0, 3, 4, sng.SNG_F32)
+    offs = np.ascontiguousarray(off, dtype=np.int64)
+    st = sng.sng_stats()
+    sng._check(sng.lib().sng_cluster_batched(xg.data_ptr(), offs.ctypes.data, 4096,
+                                             ctypes.byref(cp), None, labels.data_ptr(),
+                                             ctypes.byref(st),
+                                             torch.cuda.current_stream().cuda_stream))
+    lab = labels.cpu().numpy()
+    sizes = np.diff(off)
+    picks = [int(np.argmin(sizes)), int(np.argmax(sizes)), 1234]
+    for b in picks:
+        xb = np.ascontiguousarray(x[off[b]:off[b + 1], :3])
+        r = orc.cluster(xb, p.eps, p.seed + b, 200, 4, band_rel=BAND_F32)
+        np.testing.assert_array_equal(lab[off[b]:off[b + 1]], r["labels"], err_msg=f"cloud {b}")
+    for b in (7, 2048, 4095):
+        lb, _ = sng.cluster(xg[off[b]:off[b + 1], :3],
+                            sng.Params(eps=p.eps, min_pts=4, m=200, seed=p.seed + b))
+        np.testing.assert_array_equal(lb.cpu().numpy(), lab[off[b]:off[b + 1]])
+    assert st.queries == int((sizes * 200).sum())
