@@ -112,6 +112,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM traffic (read + write bytes) of one gather launch, from one ncu
+# capture of this workload and kernel (profiles/gather_f32_mixture-n1M-d64.md).
+# Reported only while the timed launch uses that same kernel and mapping.
+CAPTURED_TRAFFIC = {
+    ("mixture-n1M-d64", "gather_kernel<float, 4, 4, 4, 2>"): 168_506_367_744 + 454_598_144,
+}
+
+
 def gather_algorithmic_bytes(n: int, d: int, m: int, esize: int, kept: int) -> int:
     """Bytes the gather must move per launch: one partner row per query, each
     point's own row once, its keep-bit words and row count once, and a 4-byte
@@ -233,6 +241,11 @@ def bench_sng(args, w):
     g_ms = statistics.mean(gather_ms)
     alg = gather_algorithmic_bytes(n, d, m, 4, stats["kept_edges"])
     achieved = alg / (g_ms * 1e-3) / 1e9
+    kname = (f"gather_kernel<float, {stats['map_vec']}, {stats['map_group']}, "
+             f"{stats['map_nch']}, {stats['map_unroll']}>")
+    traffic = None
+    if params.map_passes <= 1 and not (params.flags & sng.SNG_FLAG_PREFETCH):
+        traffic = CAPTURED_TRAFFIC.get((args.workload, kname))
     truth = w["truth"].astype(np.int32)
     ari_truth = sng.ari(labels, torch.from_numpy(truth).to(dev))
     out = {
@@ -259,8 +272,8 @@ def bench_sng(args, w):
                 "d2h_bytes_per_step": int(n * 4)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "gather_kernel", "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": kname, "peak_kind": peak_kind,
                      "algorithmic_bytes": alg, "kernel_ms": g_ms},
         "phases_ms": {k: v for k, v in stats["ms"].items()},
         "stats": {k: stats[k] for k in ("kept_edges", "band_pairs", "band_points", "cores",

@@ -113,6 +113,7 @@ typedef struct {
     int64_t surrogate_noise; /* surrogate form: points gated as confident noise */
     float ms[8];          /* SNG_FLAG_TIMING: [0] gather [1] scan [2] fill
                              [3] core+union [4] labels [5] finalize [6] total */
+    int32_t map_vec, map_group, map_nch, map_unroll; /* gather mapping used     */
 } sng_stats;
 
 typedef struct {

@@ -58,7 +58,9 @@ class sng_stats(ctypes.Structure):
                 ("cores", ctypes.c_int64), ("clusters", ctypes.c_int64),
                 ("noise", ctypes.c_int64), ("recheck_pairs", ctypes.c_int64),
                 ("surrogate_core", ctypes.c_int64), ("surrogate_noise", ctypes.c_int64),
-                ("ms", ctypes.c_float * 8)]
+                ("ms", ctypes.c_float * 8), ("map_vec", ctypes.c_int32),
+                ("map_group", ctypes.c_int32), ("map_nch", ctypes.c_int32),
+                ("map_unroll", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "ms"}

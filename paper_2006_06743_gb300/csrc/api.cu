@@ -344,6 +344,10 @@ sng_status read_stats(const unsigned long long *counters, const Resolved &r, sng
     stats->noise = (int64_t)c[kCntNoise];
     stats->recheck_pairs = (int64_t)c[kCntRecheck];
     if (tm) tm->fill(stats->ms);
+    stats->map_vec = r.map.vec;
+    stats->map_group = r.map.group;
+    stats->map_nch = r.map.nch;
+    stats->map_unroll = r.map.unroll;
   }
   if (status & (kErrUnionLimit | kErrFindLimit | kErrBatchLimit))
     return fail(SNG_ETIMEOUT, "a bounded device loop gave up (status 0x%x)", status);
