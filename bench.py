@@ -484,6 +484,34 @@ def bench_surrogate(args):
                        **g}, "dtype": "f32", "steps": args.steps}
 
 
+def bench_balls(args):
+    """The simulation of the paper's Figure 1: a uniform mixture of three unit
+    balls in R^3 (centres 3 apart, so 1 apart at the closest), m =
+    ceil(20 ln n) draws per point, eps = 0.5, MinPts = 2 (the caption fixes
+    only the sampling rate; eps below the gap and the smallest MinPts are this
+    reading).  ARI against the generating ball, for growing n."""
+    import numpy as np
+    import torch
+
+    import paper_2006_06743_gb300 as sng
+    from paper_2006_06743_gb300 import datagen
+    rows = []
+    for n in args.balls_n:
+        x, truth = datagen.uniform_balls(n, seed=args.seed)
+        m = int(math.ceil(20.0 * math.log(n)))
+        xg = torch.from_numpy(x).cuda()
+        p = sng.Params(eps=0.5, min_pts=2, m=m, seed=args.seed, flags=sng.SNG_FLAG_TIMING)
+        sng.cluster(xg, p)
+        t_ms, (lab, st) = _timed(lambda: sng.cluster(xg, p), 3)
+        ari = sng.ari(lab, torch.from_numpy(truth.astype(np.int32)).cuda())
+        rows.append({"n": n, "m": m, "ari_vs_truth": ari, "clusters": st["clusters"],
+                     "noise": st["noise"], "ms": t_ms})
+    return {"form": "balls", "metric": "ARI vs generating ball (Figure 1 simulation)",
+            "value": rows[-1]["ari_vs_truth"], "unit": "ARI", "rows": rows,
+            "config": {"workload": "3 uniform unit balls in R^3", "eps": 0.5, "min_pts": 2,
+                       "m": "ceil(20 ln n)"}, "dtype": "f32"}
+
+
 def bench_reference(args, w):
     """The reference arm: the FP64 CPU oracle, timed as it stands on the host."""
     rank, world, _ = dist_env()
@@ -498,10 +526,15 @@ def bench_reference(args, w):
     v = statistics.mean(steps)
     return {"impl": "reference",
             "metric": "sampled eps-queries/s (whole SNG-DBSCAN pass), n=1M d=64",
-            "value": v, "unit": "queries/s", "n_gpus": 0, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload},
+            "value": v, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / v * w["n"] * w["m"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Gaussian mixture, no dataset)",
+            "config": {"workload": args.workload, "n": w["n"], "d": w["d"], "m": w["m"],
+                       "eps": w["eps"], "min_pts": w["min_pts"],
+                       "note": "FP64 CPU oracle (single-threaded C) on a bounded sample of "
+                               "source rows per step; ms_per_step extrapolates to the full "
+                               "workload"},
             "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
                              "sample": base["sample"]},
             "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
@@ -524,7 +557,10 @@ def main():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tune-budget", type=float, default=40.0)
     ap.add_argument("--verbose", action="store_true")
-    ap.add_argument("--form", default="plain", choices=["plain", "bf16", "batched", "surrogate"])
+    ap.add_argument("--form", default="plain",
+                    choices=["plain", "bf16", "batched", "surrogate", "balls"])
+    ap.add_argument("--balls-n", type=int, nargs="+",
+                    default=[100, 300, 1000, 3000, 10_000, 100_000, 1_000_000, 10_000_000])
     ap.add_argument("--bf16-n", type=int, default=5_000_000)
     ap.add_argument("--bf16-sigma", type=float, default=0.15)
     ap.add_argument("--clouds", type=int, default=4096)
@@ -539,7 +575,7 @@ def main():
     ap.add_argument("--reweight", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--ref-budget", type=float, default=8.0)
+    ap.add_argument("--ref-budget", type=float, default=5.0)
     args = ap.parse_args()
     rank, world, _ = dist_env()
     if args.impl == "reference" and rank != 0:
@@ -547,7 +583,8 @@ def main():
     if args.form != "plain":
         import __graft_entry__
         __graft_entry__.build()
-        fn = {"bf16": bench_bf16, "batched": bench_batched, "surrogate": bench_surrogate}
+        fn = {"bf16": bench_bf16, "batched": bench_batched, "surrogate": bench_surrogate,
+              "balls": bench_balls}
         print(json.dumps(fn[args.form](args)), flush=True)
         return
     w = make_workload(args.workload, seed=args.seed)

@@ -285,6 +285,15 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
 sng_status sng_cluster_noalloc(const float *x, const sng_params *params, int32_t *labels,
                                sng_stats *stats, void *stream);
 
+/*
+ * The gather mapping sng_cluster / sng_build_graph would use for these
+ * arguments (x is only inspected for its alignment; no CUDA call is made):
+ * mapping[0..6] = vector width, lanes per pair, chunks per lane, batches in
+ * flight, block size, L2 slices, and 1 if that mapping is compiled (0: the
+ * call would fail with SNG_EINVAL).
+ */
+sng_status sng_gather_mapping(const void *x, const sng_params *params, int32_t *mapping);
+
 /* Number of kernels this library has launched in this process. */
 int64_t sng_launch_count(void);
 

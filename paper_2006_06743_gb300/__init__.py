@@ -121,6 +121,7 @@ SIGNATURES = {
                                                ctypes.POINTER(sng_stats), _P]),
     "sng_cluster_noalloc": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P,
                                              ctypes.POINTER(sng_stats), _P]),
+    "sng_gather_mapping": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P]),
     "sng_launch_count": (ctypes.c_int64, []),
     "sng_last_error": (ctypes.c_char_p, []),
     "sng_strerror": (ctypes.c_char_p, [ctypes.c_int32]),

@@ -156,13 +156,18 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
     // thread per pair: the whole row in one lane
     group = 1;
     nch = pow2ceil(chunks);
-  } else {
+  } else if (vec == vmax) {
     // about 16 elements of the row per lane (4 float4 or 2 x 8 bf16 chunks):
     // enough pairs per warp step to amortise the group reduction and the
     // ballot, few enough registers for 3-4 blocks per SM (the autotuner's
     // winners at d = 64 FP32 and d = 128 BF16)
-    const int per_lane = vec >= 16 ? 1 : 16 / vec;
+    const int per_lane = 16 / vec;
     group = pow2ceil((chunks + per_lane - 1) / per_lane);
+    if (group > 32) group = 32;
+    nch = pow2ceil((chunks + group - 1) / group);
+  } else {
+    // rows that cannot use 16-byte vectors: widest groups first
+    group = pow2ceil(chunks);
     if (group > 32) group = 32;
     nch = pow2ceil((chunks + group - 1) / group);
   }
@@ -319,6 +324,11 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   fa.bitmask = gb->bitmask;
   fa.row_ptr = gb->row_ptr;
   fa.col = gb->col;
+  fa.src = nullptr;
+  if (gb->want_src) {
+    if ((rc = s.alloc((void **)&gb->src, (size_t)E * 4, "edge sources"))) return rc;
+    fa.src = gb->src;
+  }
   launch_fill(fa, device_sms(), st);
   tm->mark(st, 3);
   e = cudaGetLastError();
@@ -407,6 +417,22 @@ const char *sng_strerror(sng_status s) {
   }
 }
 
+sng_status sng_gather_mapping(const void *x, const sng_params *params, int32_t *mapping) {
+  if (!mapping) return fail(SNG_EINVAL, "mapping is NULL");
+  Resolved r;
+  sng_status rc = validate(x, params, &r);
+  if (rc) return rc;
+  mapping[0] = r.map.vec;
+  mapping[1] = r.map.group;
+  mapping[2] = r.map.nch;
+  mapping[3] = r.map.unroll;
+  mapping[4] = r.map.block;
+  mapping[5] = r.map.passes;
+  mapping[6] = r.map.passes > 1 ? gather_blocked_is_compiled(params->dtype, r.map)
+                                : gather_is_compiled(params->dtype, r.map);
+  return SNG_OK;
+}
+
 sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels, uint8_t *core,
                        sng_stats *stats, void *stream) {
   Resolved r;
@@ -418,6 +444,7 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
   Scratch s(st);
   Timer tm((params->flags & SNG_FLAG_TIMING) != 0);
   GraphBufs gb;
+  gb.want_src = true;
   if ((rc = run_graph(x, params, r, s, &gb, nullptr, &tm))) return rc;
   uint8_t *core_buf = core;
   int32_t *parent = nullptr;
@@ -427,12 +454,13 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
   CoreArgs ca{r.n, params->min_pts, gb.deg, nullptr, core_buf, parent, labels};
   launch_core_init(ca, sms, st);
   tm.mark(st, 4);
-  UnionArgs ua{r.n, gb.row_ptr, gb.col, core_buf, parent, labels, gb.counters};
+  UnionArgs ua{r.n,      gb.row_ptr, gb.col,      gb.src,      gb.num_edges,
+               core_buf, parent,     labels,      gb.counters, loop_limit()};
   launch_union(ua, sms, st);
   tm.mark(st, 5);
   launch_label(ua, sms, st);
   tm.mark(st, 6);
-  FinalizeArgs fa{r.n, core_buf, gb.band_flag, labels, gb.counters};
+  FinalizeArgs fa{r.n, core_buf, gb.band_flag, labels, gb.counters, parent, loop_limit()};
   launch_finalize(fa, sms, st);
   tm.mark(st, 7);
   cudaError_t e = cudaGetLastError();

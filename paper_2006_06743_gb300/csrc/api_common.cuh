@@ -53,7 +53,9 @@ struct GraphBufs {
   int64_t *tile_tmp = nullptr;
   int64_t *row_ptr = nullptr;
   int32_t *col = nullptr;
+  int32_t *src = nullptr;   // source row per edge (clustering only)
   int64_t num_edges = 0;
+  bool want_src = false;
   bool col_owned_by_caller = false;  // true: col from cudaMalloc, not scratch
 };
 

@@ -22,6 +22,7 @@
 
 #include "api_common.cuh"
 #include "batched.cuh"
+#include "graph.cuh"
 
 namespace sng {
 
@@ -52,7 +53,7 @@ __device__ void cloud_components(const BatchArgs &a, const CloudInfo &c) {
         word &= word - 1;
         const int64_t j = (int64_t)w * 32 + bit;
         const int32_t p = a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, c.fm);
-        if (core[p]) uf_unite(parent, i, p, status);
+        if (core[p]) uf_unite(parent, i, p, status, a.loop_limit);
       }
     }
   }
@@ -60,7 +61,7 @@ __device__ void cloud_components(const BatchArgs &a, const CloudInfo &c) {
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
     const uint64_t key = row_key(c.seed, i);
     const bool ci = core[i] != 0;
-    int32_t r = ci ? uf_root(parent, i, status) : kNoLabel;
+    int32_t r = ci ? uf_root(parent, i, status, a.loop_limit) : kNoLabel;
     if (ci) labels[i] = r;
     int32_t best = kNoLabel;
     for (int w = 0; w < c.W; ++w) {
@@ -73,7 +74,7 @@ __device__ void cloud_components(const BatchArgs &a, const CloudInfo &c) {
         const bool cp = core[p] != 0;
         if (ci && !cp) atomicMin(labels + p, r);
         if (!ci && cp) {
-          const int32_t rp = uf_root(parent, p, status);
+          const int32_t rp = uf_root(parent, p, status, a.loop_limit);
           best = rp < best ? rp : best;
         }
       }
@@ -287,6 +288,7 @@ static sng_status plan_enqueue(sng_batch_plan *p, const void *x, int32_t *labels
   a.next_item = p->next_item;
   a.done = p->done;
   a.counters = p->counters;
+  a.loop_limit = loop_limit();
   if (!dispatch_batched(p->map, a, p->grid, p->block, st, nullptr))
     return fail(SNG_EINVAL, "no compiled batched mapping vec=%d group=%d nch=%d unroll=%d",
                 p->map.vec, p->map.group, p->map.nch, p->map.unroll);

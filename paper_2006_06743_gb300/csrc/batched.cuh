@@ -33,6 +33,7 @@ struct BatchArgs {
   unsigned int *next_item;
   unsigned int *done;
   unsigned long long *counters;
+  int32_t loop_limit;   // union-find loop bound
 };
 
 struct BatchMap {

@@ -386,6 +386,9 @@ bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int 
 bool launch_gather_blocked(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
                            int32_t lo, int32_t hi, cudaStream_t stream);
 int gather_blocked_max_blocks_per_sm(int dtype, const GatherMap &map);
+// Whether a mapping has a compiled kernel (host-only check, no CUDA call).
+bool gather_is_compiled(int dtype, const GatherMap &map);
+bool gather_blocked_is_compiled(int dtype, const GatherMap &map);
 size_t gather_smem_bytes(const GatherMap &map);
 int gather_max_blocks_per_sm(int dtype, const GatherMap &map);
 

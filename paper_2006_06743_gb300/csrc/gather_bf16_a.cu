@@ -16,4 +16,10 @@ int occ_bf16_a(const GatherMap &map) {
   return -1;
 }
 
+bool has_bf16_a(const GatherMap &map) {
+  SNG_SHAPES_U(uint16_t, 8, 1, SNG_HAS)
+  SNG_SHAPES_U(uint16_t, 8, 2, SNG_HAS)
+  return false;
+}
+
 }  // namespace sng

@@ -16,4 +16,10 @@ int occ_bf16_b(const GatherMap &map) {
   return -1;
 }
 
+bool has_bf16_b(const GatherMap &map) {
+  SNG_SHAPES_U(uint16_t, 8, 4, SNG_HAS)
+  SNG_SHAPES_U(uint16_t, 8, 8, SNG_HAS)
+  return false;
+}
+
 }  // namespace sng

@@ -29,4 +29,16 @@ int occ_gather_blocked_bf16(const GatherMap &map) {
   return 0;
 }
 
+bool has_bf16_c(const GatherMap &map) {
+  SNG_SHAPES_U(uint16_t, 4, 4, SNG_HAS)
+  SNG_SHAPES_U(uint16_t, 2, 4, SNG_HAS)
+  SNG_SHAPES_U(uint16_t, 1, 4, SNG_HAS)
+  return false;
+}
+
+bool has_gather_blocked_bf16(const GatherMap &map) {
+  SNG_BLOCKED_SHAPES(uint16_t, 8, SNG_HAS)
+  return false;
+}
+
 }  // namespace sng

@@ -16,4 +16,10 @@ int occ_f32_b(const GatherMap &map) {
   return -1;
 }
 
+bool has_f32_b(const GatherMap &map) {
+  SNG_SHAPES_U(float, 4, 4, SNG_HAS)
+  SNG_SHAPES_U(float, 4, 8, SNG_HAS)
+  return false;
+}
+
 }  // namespace sng

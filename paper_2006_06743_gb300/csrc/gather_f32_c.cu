@@ -27,4 +27,15 @@ int occ_gather_blocked_f32(const GatherMap &map) {
   return 0;
 }
 
+bool has_f32_c(const GatherMap &map) {
+  SNG_SHAPES_U(float, 2, 4, SNG_HAS)
+  SNG_SHAPES_U(float, 1, 4, SNG_HAS)
+  return false;
+}
+
+bool has_gather_blocked_f32(const GatherMap &map) {
+  SNG_BLOCKED_SHAPES(float, 4, SNG_HAS)
+  return false;
+}
+
 }  // namespace sng

@@ -69,6 +69,13 @@ static int occ_blocks_blocked(const GatherMap &m) {
   X(T, V, 2, 8, U) X(T, V, 4, 2, U) X(T, V, 8, 4, U) X(T, V, 16, 4, U) X(T, V, 4, 8, U)  \
   X(T, V, 2, 4, U)
 
+template <int VEC, int G, int NCH, int U>
+static bool matches(const GatherMap &m) {
+  return m.vec == VEC && m.group == G && m.nch == NCH && m.unroll == U;
+}
+#define SNG_HAS(T, V, G, N, U) \
+  if (matches<V, G, N, U>(map)) return true;
+
 #define SNG_TRY(T, V, G, N, U) \
   if (try_launch<T, V, G, N, U>(map, args, grid, stream)) return true;
 #define SNG_OCC(T, V, G, N, U)                 \

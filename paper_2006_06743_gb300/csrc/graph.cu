@@ -11,6 +11,8 @@
 //  label     cores take their root; a non-core point adjacent (either
 //            direction) to a core takes the smallest adjacent root (step 4)
 //  finalize  untouched points become noise, -1 (step 5); counters for stats
+#include <cstdlib>
+
 #include "graph.cuh"
 
 namespace sng {
@@ -138,7 +140,9 @@ __global__ void __launch_bounds__(256) fill_kernel(FillArgs a) {
         const int bit = __ffs(word) - 1;
         word &= word - 1;
         const int64_t j = (int64_t)w * 32 + bit;
-        a.col[at++] = a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm);
+        a.col[at] = a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm);
+        if (a.src) a.src[at] = i;
+        ++at;
       }
       pos += total;
     }
@@ -162,56 +166,52 @@ __global__ void core_init_kernel(CoreArgs a) {
   }
 }
 
-// Thread per row: join i with every core partner it kept.
+// Thread per edge: join the components of both ends of every core-core
+// edge (edges are independent, so the work is balanced however the kept
+// draws are spread over rows).
 __global__ void union_kernel(UnionArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    if (!a.core[i]) continue;
-    const int64_t e1 = a.row_ptr[i + 1];
-    for (int64_t e = a.row_ptr[i]; e < e1; ++e) {
-      const int32_t p = a.col[e];
-      if (a.core[p]) uf_unite(a.parent, (int32_t)i, p, status);
-    }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.num_edges;
+       e += stride) {
+    const int32_t i = a.src[e], p = a.col[e];
+    if (a.core[i] && a.core[p]) uf_unite(a.parent, i, p, status, a.loop_limit);
   }
 }
 
+// Thread per edge: an edge with exactly one core end offers that core's
+// component label to the other end (step 4; the smallest offer wins).  Core
+// labels are written by finalize_kernel.
 __global__ void label_kernel(UnionArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const int64_t e0 = a.row_ptr[i], e1 = a.row_ptr[i + 1];
-    if (a.core[i]) {
-      const int32_t r = uf_root(a.parent, (int32_t)i, status);
-      a.labels[i] = r;
-      for (int64_t e = e0; e < e1; ++e) {
-        const int32_t p = a.col[e];
-        if (!a.core[p]) atomicMin(a.labels + p, r);
-      }
-    } else {
-      int32_t best = kNoLabel;
-      for (int64_t e = e0; e < e1; ++e) {
-        const int32_t p = a.col[e];
-        if (a.core[p]) {
-          const int32_t r = uf_root(a.parent, p, status);
-          best = r < best ? r : best;
-        }
-      }
-      if (best != kNoLabel) atomicMin(a.labels + i, best);
-    }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.num_edges;
+       e += stride) {
+    const int32_t i = a.src[e], p = a.col[e];
+    const bool ci = a.core[i] != 0, cp = a.core[p] != 0;
+    if (ci == cp) continue;
+    const int32_t c = ci ? i : p, b = ci ? p : i;
+    atomicMin(a.labels + b, uf_root(a.parent, c, status, a.loop_limit));
   }
 }
 
 __global__ void finalize_kernel(FinalizeArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
   unsigned long long cores = 0, clusters = 0, noise = 0, band = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    int32_t l = a.labels[i];
-    if (l == kNoLabel) {
-      l = -1;
-      a.labels[i] = -1;
-    }
     const bool c = a.core[i] != 0;
+    int32_t l;
+    if (c) {
+      l = uf_root(a.parent, (int32_t)i, status, a.loop_limit);
+      a.labels[i] = l;
+    } else {
+      l = a.labels[i];
+      if (l == kNoLabel) {
+        l = -1;
+        a.labels[i] = -1;
+      }
+    }
     cores += c;
     clusters += (c && l == (int32_t)i);
     noise += (l < 0);
@@ -232,6 +232,15 @@ __global__ void finalize_kernel(FinalizeArgs a) {
   }
 }
 
+int32_t loop_limit() {
+  const char *v = std::getenv("SNG_LOOP_LIMIT");
+  if (v && *v) {
+    const long long k = std::atoll(v);
+    if (k >= 1 && k < kLoopLimit) return (int32_t)k;
+  }
+  return kLoopLimit;
+}
+
 static int grid_for(int64_t n, int threads, int max_blocks) {
   int64_t b = (n + threads - 1) / threads;
   if (b > max_blocks) b = max_blocks;
@@ -249,12 +258,12 @@ void launch_core_init(const CoreArgs &a, int sms, cudaStream_t st) {
 }
 
 void launch_union(const UnionArgs &a, int sms, cudaStream_t st) {
-  union_kernel<<<grid_for(a.n, 256, sms * 16), 256, 0, st>>>(a);
+  union_kernel<<<grid_for(a.num_edges, 256, sms * 16), 256, 0, st>>>(a);
   note_launch();
 }
 
 void launch_label(const UnionArgs &a, int sms, cudaStream_t st) {
-  label_kernel<<<grid_for(a.n, 256, sms * 16), 256, 0, st>>>(a);
+  label_kernel<<<grid_for(a.num_edges, 256, sms * 16), 256, 0, st>>>(a);
   note_launch();
 }
 

@@ -14,6 +14,7 @@ struct FillArgs {
   const uint32_t *bitmask;
   const int64_t *row_ptr;
   int32_t *col;
+  int32_t *src;   // nullable: source row of every edge (edge-parallel steps 3-4)
 };
 
 struct CoreArgs {
@@ -30,11 +31,18 @@ struct UnionArgs {
   int64_t n;
   const int64_t *row_ptr;
   const int32_t *col;
+  const int32_t *src;     // source row of each edge
+  int64_t num_edges;
   const uint8_t *core;
   int32_t *parent;
   int32_t *labels;
   unsigned long long *counters;
+  int32_t loop_limit;   // bound of every union-find loop (see sng_internal.cuh)
 };
+
+// Loop bound for union-find: kLoopLimit, or SNG_LOOP_LIMIT from the
+// environment (host-side fault injection for tests).
+int32_t loop_limit();
 
 struct FinalizeArgs {
   int64_t n;
@@ -42,6 +50,8 @@ struct FinalizeArgs {
   const uint8_t *band_flag;  // nullable
   int32_t *labels;
   unsigned long long *counters;
+  const int32_t *parent;     // union-find forest: cores take their root
+  int32_t loop_limit;
 };
 
 int64_t scan_tiles(int64_t n);

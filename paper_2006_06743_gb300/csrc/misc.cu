@@ -8,6 +8,23 @@ namespace sng {
   int occ_##tag(const GatherMap &);
 SNG_UNIT(f32_a) SNG_UNIT(f32_b) SNG_UNIT(f32_c) SNG_UNIT(bf16_a) SNG_UNIT(bf16_b) SNG_UNIT(bf16_c)
 #undef SNG_UNIT
+bool has_f32_a(const GatherMap &);
+bool has_f32_b(const GatherMap &);
+bool has_f32_c(const GatherMap &);
+bool has_bf16_a(const GatherMap &);
+bool has_bf16_b(const GatherMap &);
+bool has_bf16_c(const GatherMap &);
+bool has_gather_blocked_f32(const GatherMap &);
+bool has_gather_blocked_bf16(const GatherMap &);
+
+bool gather_is_compiled(int dtype, const GatherMap &map) {
+  if (dtype == SNG_F32) return has_f32_a(map) || has_f32_b(map) || has_f32_c(map);
+  return has_bf16_a(map) || has_bf16_b(map) || has_bf16_c(map);
+}
+
+bool gather_blocked_is_compiled(int dtype, const GatherMap &map) {
+  return dtype == SNG_F32 ? has_gather_blocked_f32(map) : has_gather_blocked_bf16(map);
+}
 bool launch_gather_blocked_f32(const GatherMap &, const GatherArgs &, int, int32_t, int32_t,
                                cudaStream_t);
 bool launch_gather_blocked_bf16(const GatherMap &, const GatherArgs &, int, int32_t, int32_t,

@@ -635,6 +635,7 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
   cudaError_t e = launch_gate(ga, st);
   if (e != cudaSuccess) return cuda_fail(e, "surrogate gate");
   GraphBufs gb;
+  gb.want_src = true;
   if ((rc = run_graph(x, params, r, s, &gb, m_row, &tm, w_row))) return rc;
   uint8_t *core_buf = core;
   int32_t *parent = nullptr;
@@ -644,12 +645,13 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
   CoreArgs ca{r.n, params->min_pts * unit, gb.deg, forced, core_buf, parent, labels};
   launch_core_init(ca, sms, st);
   tm.mark(st, 4);
-  UnionArgs ua{r.n, gb.row_ptr, gb.col, core_buf, parent, labels, gb.counters};
+  UnionArgs ua{r.n,      gb.row_ptr, gb.col,      gb.src,      gb.num_edges,
+               core_buf, parent,     labels,      gb.counters, loop_limit()};
   launch_union(ua, sms, st);
   tm.mark(st, 5);
   launch_label(ua, sms, st);
   tm.mark(st, 6);
-  FinalizeArgs fa{r.n, core_buf, gb.band_flag, labels, gb.counters};
+  FinalizeArgs fa{r.n, core_buf, gb.band_flag, labels, gb.counters, parent, loop_limit()};
   launch_finalize(fa, sms, st);
   tm.mark(st, 7);
   e = cudaGetLastError();

@@ -169,6 +169,7 @@ sng_status sng_cluster_noalloc(const float *x, const sng_params *params, int32_t
   a.next_item = reinterpret_cast<unsigned int *>(base + o_next);
   a.done = a.next_item + 1;
   a.counters = reinterpret_cast<unsigned long long *>(base + o_counters);
+  a.loop_limit = kLoopLimit;
   const int grid = (int)std::min<int64_t>((int64_t)sms * (occ > 0 ? occ : 1), ntiles);
   launch_batched_kernel(map, a, grid, block, st, nullptr);
   note_launch();

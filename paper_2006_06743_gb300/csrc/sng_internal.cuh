@@ -258,11 +258,17 @@ __device__ __forceinline__ double dist2_fp64(const float *a, const float *b, int
 
 // ------------------------------------------------------------ union-find
 
+// Every union-find loop below stops after `limit` steps, records the
+// overrun in the status word and returns, so a corrupted forest can never
+// spin; with the default limit (2^30, above any tree depth for n < 2^31) it
+// is never reached.
+
 // Root of x with path halving.  Parent links only ever point to smaller
 // indices and only ever move towards the root, so concurrent halving writes
 // keep every link an ancestor.  Loads bypass L1 (cg) to see other SMs' links.
-__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x, uint32_t *status) {
-  for (int it = 0; it < (1 << 30); ++it) {
+__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x, uint32_t *status,
+                                           int32_t limit) {
+  for (int32_t it = 0; it < limit; ++it) {
     const int32_t p = __ldcg(parent + x);
     if (p == x) return x;
     const int32_t gp = __ldcg(parent + p);
@@ -274,8 +280,9 @@ __device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x, uint32_t 
 }
 
 // Read-only root lookup (no writes), used once components are final.
-__device__ __forceinline__ int32_t uf_root(const int32_t *parent, int32_t x, uint32_t *status) {
-  for (int it = 0; it < (1 << 30); ++it) {
+__device__ __forceinline__ int32_t uf_root(const int32_t *parent, int32_t x, uint32_t *status,
+                                           int32_t limit) {
+  for (int32_t it = 0; it < limit; ++it) {
     const int32_t p = __ldcg(parent + x);
     if (p == x) return x;
     x = p;
@@ -288,10 +295,11 @@ __device__ __forceinline__ int32_t uf_root(const int32_t *parent, int32_t x, uin
 // smaller with a compare-and-swap, so the surviving root of every component
 // is its smallest index.  A failed swap means another thread linked that
 // root first; retry from the new parent (bounded).
-__device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b, uint32_t *status) {
-  for (int it = 0; it < (1 << 24); ++it) {
-    a = uf_find(parent, a, status);
-    b = uf_find(parent, b, status);
+__device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b, uint32_t *status,
+                                         int32_t limit) {
+  for (int32_t it = 0; it < limit; ++it) {
+    a = uf_find(parent, a, status, limit);
+    b = uf_find(parent, b, status, limit);
     if (a == b) return;
     const int32_t hi = a > b ? a : b;
     const int32_t lo = a > b ? b : a;
@@ -302,6 +310,8 @@ __device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b, 
   }
   atomicOr(status, kErrUnionLimit);
 }
+
+constexpr int32_t kLoopLimit = 1 << 30;
 
 // ---------------------------------------------------------- launch count
 

@@ -58,3 +58,25 @@ def test_injected_alloc_failure_no_leak():
     torch.cuda.synchronize()
     # the stream-ordered pool keeps its blocks; nothing beyond it is retained
     assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+
+
+def test_bounded_loops_report_timeout_and_context_survives():
+    """Every union-find loop is bounded; forcing the bound down to one step
+    (host-side, through SNG_LOOP_LIMIT) makes the device give up, record it in
+    the status word and return.  The call reports SNG_ETIMEOUT, nothing
+    faults, and the next call with the normal bound is exact again."""
+    torch, sng = need_gpu()
+    x = torch.from_numpy(datagen.random_points(20_000, 3, seed=9)).cuda()
+    p = sng.Params(eps=0.2, min_pts=4, m=64, seed=3)
+    ref, st = sng.cluster(x, p)
+    assert st["clusters"] >= 1 and st["cores"] > 1000
+    os.environ["SNG_LOOP_LIMIT"] = "1"
+    try:
+        with pytest.raises(sng.SngError) as e:
+            sng.cluster(x, p)
+        assert e.value.status == sng.SNG_ETIMEOUT
+        assert "bounded" in sng.last_error()
+    finally:
+        del os.environ["SNG_LOOP_LIMIT"]
+    again, _ = sng.cluster(x, p)
+    assert torch.equal(again, ref)

@@ -294,3 +294,17 @@ def test_gated_weighted_degrees(orc):
     np.testing.assert_array_equal(r["core"], [0, 1, 1, 0])
     r = orc.cluster_graph(4, rp, col, min_pts=32, deg_mode=1, w_row=w)
     np.testing.assert_array_equal(r["deg"], [32, 64, 0, 32])
+
+
+def test_uniform_balls_recovery_improves_with_n(orc):
+    """Theorem 1 / Figure 1: with s ~ 20 ln n / n the sampled graph recovers
+    well-separated clusters once n is large enough; on three uniform balls the
+    oracle's ARI against the generating ball rises to 1."""
+    aris = []
+    for n in (200, 3000):
+        x, truth = datagen.uniform_balls(n, seed=1)
+        m = int(math.ceil(20 * math.log(n)))
+        r = orc.cluster(x, 0.5, seed=1, m=m, min_pts=2)
+        aris.append(orc.ari(r["labels"], truth))
+    assert aris[-1] > 0.99
+    assert aris[-1] >= aris[0]
