@@ -512,6 +512,45 @@ def bench_balls(args):
                        "m": "ceil(20 ln n)"}, "dtype": "f32"}
 
 
+def bench_sweep(args):
+    """Quality and time against the sampling rate s (the synthetic analogue of
+    the paper's Figure 10): a Gaussian mixture (as the headline workload,
+    smaller n), full DBSCAN computed on the GPU with every pair queried
+    (s = 1, multigraph degree, MinPts = 2 (min_samples - 1)), and
+    SNG-DBSCAN at decreasing s with MinPts scaled by s; ARI of each against
+    full DBSCAN and against the generating mixture."""
+    import numpy as np
+    import torch
+
+    import paper_2006_06743_gb300 as sng
+    from paper_2006_06743_gb300 import datagen
+    n, d = args.sweep_n, 16
+    x, truth = datagen.gaussian_mixture(n, d, 20, 0.02, seed=args.seed, return_truth=True)
+    eps = datagen.eps_quantile(x, 0.01, 1_000_000, seed=args.seed)
+    xg = torch.from_numpy(x).cuda()
+    tg = torch.from_numpy(truth.astype(np.int32)).cuda()
+    k_db = 10                                  # textbook min_samples (self included)
+    full_p = sng.Params(eps=eps, min_pts=2 * (k_db - 1), sample_mode=sng.SNG_SAMPLE_ALL,
+                        flags=sng.SNG_FLAG_TIMING)
+    sng.cluster(xg, full_p)
+    full_ms, (full, fst) = _timed(lambda: sng.cluster(xg, full_p), 1)
+    rows = [{"s": 1.0, "ms": full_ms, "ari_vs_full": 1.0, "ari_vs_truth": sng.ari(full, tg),
+             "clusters": fst["clusters"]}]
+    for s in args.sweep_s:
+        mp = max(2, int(round(2 * (k_db - 1) * s)))
+        p = sng.Params(eps=eps, min_pts=mp, s=s, seed=args.seed)
+        sng.cluster(xg, p)
+        ms, (lab, st) = _timed(lambda: sng.cluster(xg, p), 3)
+        rows.append({"s": s, "m": p.draws(n), "min_pts": mp, "ms": ms,
+                     "speedup_vs_full": full_ms / ms, "ari_vs_full": sng.ari(lab, full),
+                     "ari_vs_truth": sng.ari(lab, tg), "clusters": st["clusters"]})
+    return {"form": "sweep", "metric": "ARI vs full DBSCAN against sampling rate",
+            "value": rows[-1]["ari_vs_full"], "unit": "ARI", "rows": rows,
+            "config": {"workload": f"mixture-n{n}-d{d}-k20", "eps": eps, "min_samples": k_db,
+                       "min_pts_rule": "round(2 (min_samples - 1) s), at least 2"},
+            "dtype": "f32"}
+
+
 def bench_reference(args, w):
     """The reference arm: the FP64 CPU oracle, timed as it stands on the host."""
     rank, world, _ = dist_env()
@@ -558,7 +597,10 @@ def main():
     ap.add_argument("--tune-budget", type=float, default=40.0)
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--form", default="plain",
-                    choices=["plain", "bf16", "batched", "surrogate", "balls"])
+                    choices=["plain", "bf16", "batched", "surrogate", "balls", "sweep"])
+    ap.add_argument("--sweep-n", type=int, default=100_000)
+    ap.add_argument("--sweep-s", type=float, nargs="+",
+                    default=[0.3, 0.1, 0.03, 0.01, 0.003, 0.001])
     ap.add_argument("--balls-n", type=int, nargs="+",
                     default=[100, 300, 1000, 3000, 10_000, 100_000, 1_000_000, 10_000_000])
     ap.add_argument("--bf16-n", type=int, default=5_000_000)
@@ -584,7 +626,7 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         fn = {"bf16": bench_bf16, "batched": bench_batched, "surrogate": bench_surrogate,
-              "balls": bench_balls}
+              "balls": bench_balls, "sweep": bench_sweep}
         print(json.dumps(fn[args.form](args)), flush=True)
         return
     w = make_workload(args.workload, seed=args.seed)
