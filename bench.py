@@ -332,6 +332,25 @@ def bench_bf16(args):
         sng.cluster(xb, pb, x_master=xf)
     f_ms, (lf, sf) = _timed(lambda: sng.cluster(xf, pf), args.steps)
     b_ms, (lb, sb) = _timed(lambda: sng.cluster(xb, pb, x_master=xf), args.steps)
+    # edge-decision error of the BF16 form against FP64: the FP32 form's
+    # decisions equal the FP64 ones on every pair (guard band + FP64
+    # recheck), so the difference of the two edge sets is that error
+    gf = sng.build_graph(xf, pf)
+    gb = sng.build_graph(xb, pb, x_master=xf)
+
+    def keys(g):
+        src = torch.repeat_interleave(torch.arange(n, device="cuda", dtype=torch.int64),
+                                      torch.diff(g["row_ptr"]))
+        return torch.sort(src * n + g["col"].to(torch.int64)).values
+
+    kf, kb = keys(gf), keys(gb)
+    common = int(torch.isin(kb, kf).sum().item())
+    edge_error = {"kept_fp64": int(kf.numel()), "kept_bf16": int(kb.numel()),
+                  "false_keep": int(kb.numel()) - common,
+                  "false_drop": int(kf.numel()) - common,
+                  "rate_of_fp64_edges": (int(kb.numel()) + int(kf.numel()) - 2 * common)
+                  / max(1, int(kf.numel()))}
+    del gf, gb, kf, kb
     Q = n * m
     peak, kind = peaks()
     alg_b = gather_algorithmic_bytes(n, d, m, 2, sb["kept_edges"])
@@ -339,7 +358,7 @@ def bench_bf16(args):
     return {"form": "bf16", "metric": "sampled eps-queries/s, BF16 vs FP32 form",
             "value": Q / (b_ms * 1e-3), "unit": "queries/s", "fp32_value": Q / (f_ms * 1e-3),
             "speedup_vs_fp32": f_ms / b_ms, "ms_bf16": b_ms, "ms_fp32": f_ms,
-            "ari_bf16_vs_fp32": sng.ari(lb, lf),
+            "ari_bf16_vs_fp32": sng.ari(lb, lf), "edge_decision_error_vs_fp64": edge_error,
             "roofline_bf16": {"achieved": alg_b / (sb["ms"]["gather"] * 1e-3) / 1e9, "peak": peak,
                               "frac": alg_b / (sb["ms"]["gather"] * 1e-3) / 1e9 / peak,
                               "kernel_ms": sb["ms"]["gather"], "peak_kind": kind},
@@ -477,6 +496,7 @@ def bench_surrogate(args):
             "core_mask_agreement": float((core == pcore).float().mean().item()),
             "queries_issued_frac": sst["queries"] / pst["queries"],
             "gated_core": sst["surrogate_core"], "gated_noise": sst["surrogate_noise"],
+            "phases_ms_surrogate": sst["ms"], "phases_ms_plain": pst["ms"],
             "train": {"steps": args.train_steps, "seconds": t_train * 1e-3,
                       "loss_first": float(trace[:50].mean()), "loss_last": float(trace[-200:].mean()),
                       "label_seconds": t_label},

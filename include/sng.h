@@ -112,7 +112,8 @@ typedef struct {
     int64_t surrogate_core;  /* surrogate form: points gated as confident core */
     int64_t surrogate_noise; /* surrogate form: points gated as confident noise */
     float ms[8];          /* SNG_FLAG_TIMING: [0] gather [1] scan [2] fill
-                             [3] core+union [4] labels [5] finalize [6] total */
+                             [3] core+union [4] labels [5] finalize [6] total
+                             (gather to finalize) [7] surrogate gate        */
     int32_t map_vec, map_group, map_nch, map_unroll; /* gather mapping used     */
 } sng_stats;
 

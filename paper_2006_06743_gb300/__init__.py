@@ -31,7 +31,7 @@ SNG_SAMPLE_HASH, SNG_SAMPLE_ALL = 0, 1
 SNG_FLAG_TIMING = 1
 SNG_FLAG_PREFETCH = 2
 
-PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total")
+PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total", "gate")
 
 
 class SngError(RuntimeError):

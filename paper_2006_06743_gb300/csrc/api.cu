@@ -62,8 +62,6 @@ int device_sms() {
 
 // ------------------------------------------------------------- scratch
 
-static std::atomic<int64_t> g_alloc_seq{0};
-
 Scratch::~Scratch() { release(); }
 
 void Scratch::release() {
@@ -74,14 +72,18 @@ void Scratch::release() {
 sng_status Scratch::alloc(void **out, size_t bytes, const char *what) {
   *out = nullptr;
   const char *fault = std::getenv("SNG_FAULT_ALLOC");
-  const int64_t seq = g_alloc_seq.fetch_add(1) + 1;
   if (fault && *fault) {
-    // SNG_FAULT_ALLOC=k: the k-th allocation counted from the moment the
-    // variable was first seen fails (host-side fault injection for tests).
-    static std::atomic<int64_t> base{-1};
-    int64_t expect = -1;
-    base.compare_exchange_strong(expect, seq - 1);
-    if (seq - base.load() == std::atoll(fault))
+    // SNG_FAULT_ALLOC=k: host-side fault injection for tests.  The k-th
+    // scratch allocation counted from the moment this value was set fails.
+    static std::mutex mu;
+    static std::string seen;
+    static int64_t count = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (seen != fault) {
+      seen = fault;
+      count = 0;
+    }
+    if (++count == std::atoll(fault))
       return fail(SNG_ENOMEM, "injected allocation failure (%s)", what);
   }
   void *p = nullptr;
@@ -386,8 +388,9 @@ void Timer::fill(float *ms) const {
   // ms[0] gather (0->1), [1] scan (1->2), [2] fill (2->3 after the host
   // read-back: 3 is recorded after the fill launch), [3] core+union (4->5),
   // [4] labels (5->6), [5] finalize (6->7), [6] total (0->7)
-  const int pairs[7][2] = {{0, 1}, {1, 2}, {8, 3}, {3, 5}, {5, 6}, {6, 7}, {0, 7}};
-  for (int q = 0; q < 7; ++q) {
+  // [7] surrogate gate (9 -> 0), when the gated form recorded mark 9
+  const int pairs[8][2] = {{0, 1}, {1, 2}, {8, 3}, {3, 5}, {5, 6}, {6, 7}, {0, 7}, {9, 0}};
+  for (int q = 0; q < 8; ++q) {
     const int a = pairs[q][0], b = pairs[q][1];
     float v = 0.f;
     if (used_[a] && used_[b]) cudaEventElapsedTime(&v, ev_[a], ev_[b]);

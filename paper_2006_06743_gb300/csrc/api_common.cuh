@@ -32,7 +32,7 @@ struct Scratch {
 // Per-phase CUDA-event marks for sng_stats.ms (SNG_FLAG_TIMING).
 class Timer {
  public:
-  static constexpr int kMarks = 9;
+  static constexpr int kMarks = 10;
   explicit Timer(bool on);
   ~Timer();
   void mark(cudaStream_t st, int k);

@@ -632,6 +632,7 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
   GateArgs ga{static_cast<const float *>(x), params->ld, r.n, params->d, mlp_params, nullptr,
               pn, pc, (int32_t)r.m, m_core, m_noise, weight((int32_t)r.m), weight(m_core),
               weight(m_noise), forced, m_row, w_row, gcnt};
+  tm.mark(st, 9);
   cudaError_t e = launch_gate(ga, st);
   if (e != cudaSuccess) return cuda_fail(e, "surrogate gate");
   GraphBufs gb;
