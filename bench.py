@@ -164,9 +164,11 @@ def bench_sng(args, w):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    # weak scaling: every rank clusters its own independent dataset (no
-    # collective on the data path); rank r uses seed base + r
-    if rank > 0:
+    # default (weak scaling): every rank clusters its own independent dataset
+    # (no collective on the data path); rank r uses seed base + r.
+    # --sharded (strong scaling): one dataset, step 2 split by source rows,
+    # degrees all-reduced and edges all-gathered over NCCL.
+    if rank > 0 and not args.sharded:
         w = make_workload(args.workload, seed=args.seed + rank)
     x_host = torch.from_numpy(w["x"]).pin_memory()
     x = x_host.to(dev)
@@ -185,6 +187,8 @@ def bench_sng(args, w):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    if args.sharded and world > 1:
+        return bench_sharded(args, w, x, params, rank, world, dev)
     for _ in range(args.warmup):
         labels, st = sng.cluster(x, params)
     torch.cuda.synchronize(dev)
@@ -286,6 +290,39 @@ def bench_sng(args, w):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def bench_sharded(args, w, x, params, rank, world, dev):
+    """One dataset across all ranks (strong scaling): each step is the whole
+    pass, step 2 split by source rows, one all-reduce of the degrees and one
+    all-gather of the kept edges."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2006_06743_gb300.distributed import GpuCompute, cluster_sharded
+    comp = GpuCompute(x, params)
+    n = w["n"]
+    for _ in range(args.warmup):
+        cluster_sharded(comp, n)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        labels, core, _ = cluster_sharded(comp, n)
+    torch.cuda.synchronize(dev)
+    dt = torch.tensor([(time.perf_counter() - t0) / args.steps], device=dev)
+    dist.all_reduce(dt, op=dist.ReduceOp.MAX)
+    t_step = float(dt.item()) * 1e3
+    Q = n * w["m"]
+    out = {"metric": "sampled eps-queries/s (whole SNG-DBSCAN pass), n=1M d=64",
+           "value": Q / (t_step * 1e-3), "unit": "queries/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+           "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded Gaussian mixture, no dataset)",
+           "config": {"workload": args.workload, "n": n, "d": w["d"], "m": w["m"],
+                      "parallelism": f"rows-sharded x{world}, NCCL all-reduce + all-gather"}}
+    dist.destroy_process_group()
     return out if rank == 0 else None
 
 
@@ -616,6 +653,8 @@ def main():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tune-budget", type=float, default=40.0)
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--sharded", action="store_true",
+                    help="N > 1: split one dataset's rows across ranks (strong scaling)")
     ap.add_argument("--form", default="plain",
                     choices=["plain", "bf16", "batched", "surrogate", "balls", "sweep"])
     ap.add_argument("--sweep-n", type=int, default=100_000)

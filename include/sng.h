@@ -98,6 +98,13 @@ typedef struct {
     int32_t map_passes;   /* gather: 0/1 = one pass over all partners; k > 1 = k
                              launches, each testing only the draws whose partner
                              lies in one of k equal slices of X (L2-resident) */
+    int32_t reserved0;
+    /* Source rows [row_begin, row_end) draw partners; 0, 0 = all rows.  Other
+     * rows draw nothing (their CSR rows are empty) but still receive
+     * in-degree from the rows that do: a shard of step 2 for multi-GPU runs
+     * (sng_build_graph only; the other calls reject a partial range).      */
+    int64_t row_begin;
+    int64_t row_end;
 } sng_params;
 
 typedef struct {
@@ -139,6 +146,19 @@ sng_status sng_build_graph(const void *x, const sng_params *params, sng_graph *o
 
 /* Frees the arrays of a graph from sng_build_graph (device-synchronising). */
 void sng_graph_free(sng_graph *g);
+
+/*
+ * Algorithm 1, steps 3-5 on a given sampled graph: src/col (device int32[E])
+ * list its kept draws (src[e] drew col[e]), deg (device int32[n]) the degree
+ * of every point in params->degree_mode (e.g. summed over the ranks that
+ * built parts of the graph).  Core = deg >= params->min_pts; labels
+ * (device int32[n]) and core (device uint8[n] or NULL) as in sng_cluster.
+ * Only n, min_pts and degree_mode of params are read.  Synchronises `stream`
+ * when stats != NULL.
+ */
+sng_status sng_cluster_edges(int64_t n, const int32_t *src, const int32_t *col, int64_t num_edges,
+                             const int32_t *deg, const sng_params *params, int32_t *labels,
+                             uint8_t *core, sng_stats *stats, void *stream);
 
 /*
  * The whole of Algorithm 1: graph (step 2), degrees and core mask, core
@@ -207,6 +227,9 @@ typedef struct {
     uint64_t seed;        /* batch rows drawn with replacement by the hash    */
     int32_t sequential;   /* 1: batch b of step t takes rows (t*batch + b) mod n
                              in order instead of hashed draws                 */
+    int32_t fp32_activations; /* inference: 0 = tensor cores (FP16 activations at
+                             the MMA inputs, FP32 accumulation); 1 = CUDA cores
+                             with FP32 activations                           */
 } sng_mlp_config;
 
 /* Entries of the parameter vector, or -1 for an unsupported shape. */

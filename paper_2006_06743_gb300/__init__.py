@@ -49,7 +49,8 @@ class sng_params(ctypes.Structure):
                 ("x_f32_master", ctypes.c_void_p), ("flags", ctypes.c_uint32),
                 ("map_group", ctypes.c_int32), ("map_unroll", ctypes.c_int32),
                 ("map_block", ctypes.c_int32), ("map_tile", ctypes.c_int32),
-                ("map_passes", ctypes.c_int32)]
+                ("map_passes", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64)]
 
 
 class sng_stats(ctypes.Structure):
@@ -72,7 +73,7 @@ class sng_mlp_config(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("hidden", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("adam_eps", ctypes.c_float), ("seed", ctypes.c_uint64),
-                ("sequential", ctypes.c_int32)]
+                ("sequential", ctypes.c_int32), ("fp32_activations", ctypes.c_int32)]
 
 
 class sng_gate(ctypes.Structure):
@@ -98,6 +99,9 @@ SIGNATURES = {
     "sng_graph_free": (None, [ctypes.POINTER(sng_graph)]),
     "sng_cluster": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P, _P,
                                      ctypes.POINTER(sng_stats), _P]),
+    "sng_cluster_edges": (ctypes.c_int32, [ctypes.c_int64, _P, _P, ctypes.c_int64, _P,
+                                           ctypes.POINTER(sng_params), _P, _P,
+                                           ctypes.POINTER(sng_stats), _P]),
     "sng_cluster_batched": (ctypes.c_int32, [_P, _P, ctypes.c_int32, ctypes.POINTER(sng_params),
                                              _P, _P, ctypes.POINTER(sng_stats), _P]),
     "sng_batch_plan_create": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(sng_params),
@@ -184,6 +188,8 @@ class Params:
     map_block: int = 0
     map_tile: int = 0
     map_passes: int = 0
+    row_begin: int = 0
+    row_end: int = 0
 
     def to_c(self, n: int, d: int, ld: int, dtype: int, master_ptr: int = 0) -> sng_params:
         p = sng_params()
@@ -196,6 +202,7 @@ class Params:
         p.map_group, p.map_unroll, p.map_block = self.map_group, self.map_unroll, self.map_block
         p.map_tile = self.map_tile
         p.map_passes = self.map_passes
+        p.row_begin, p.row_end = self.row_begin, self.row_end
         return p
 
     def draws(self, n: int) -> int:
@@ -299,6 +306,24 @@ def _copy_out(ptr: int, count: int, typestr: str, dtype, device):
     if count == 0 or not ptr:
         return torch.empty(count, dtype=dtype, device=device)
     return torch.as_tensor(_DeviceArray(ptr, count, typestr), device=device).clone()
+
+
+def cluster_edges(n: int, src, col, deg, params: Params, want_core: bool = False, stream=None):
+    """Algorithm 1, steps 3-5 on a given graph: kept draws src[e] -> col[e]
+    (int32 CUDA tensors) and degrees deg (int32, n).  Returns (labels[, core],
+    stats)."""
+    import torch
+    labels = torch.empty(n, dtype=torch.int32, device=deg.device)
+    core = torch.empty(n, dtype=torch.uint8, device=deg.device) if want_core else None
+    st = sng_stats()
+    E = int(src.numel())
+    _check(lib().sng_cluster_edges(n, src.data_ptr() if E else None,
+                                   col.data_ptr() if E else None, E, deg.data_ptr(),
+                                   ctypes.byref(params.to_c(n, 1, 1, SNG_F32)), labels.data_ptr(),
+                                   core.data_ptr() if core is not None else None,
+                                   ctypes.byref(st), _stream_ptr(stream)))
+    d = st.as_dict()
+    return (labels, core, d) if want_core else (labels, d)
 
 
 def sample_partners(n: int, seed: int, i0: int, rows: int, m: int, sample_all: bool = False,

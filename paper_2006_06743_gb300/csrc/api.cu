@@ -187,6 +187,15 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   if (r->map.block % 32 || r->map.block < 32 || r->map.block > 256)
     return fail(SNG_EINVAL, "map_block must be a multiple of 32 in [32, 256]");
   if (p->map_tile < 0) return fail(SNG_EINVAL, "map_tile must be >= 0");
+  if (p->row_begin == 0 && p->row_end == 0) {
+    r->row_begin = 0;
+    r->row_end = p->n;
+  } else {
+    if (p->row_begin < 0 || p->row_begin > p->row_end || p->row_end > p->n)
+      return fail(SNG_EINVAL, "need 0 <= row_begin <= row_end <= n");
+    r->row_begin = p->row_begin;
+    r->row_end = p->row_end;
+  }
 
   // eps^2 in FP64 exactly as the oracle forms it; the FP32 screen is widened
   // by twice a bound on the FP32 relative error of the kernel's sum: one
@@ -214,6 +223,8 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
   g->xm = p->dtype == SNG_F32 ? static_cast<const float *>(x) : p->x_f32_master;
   g->ldm = p->ld;
   g->n = (int32_t)r.n;
+  g->row_begin = (int32_t)r.row_begin;
+  g->row_end = (int32_t)r.row_end;
   g->d = r.d;
   g->m = (int32_t)r.m;
   g->W = r.W;
@@ -274,8 +285,9 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   ga.deg = gb->deg;
   ga.band_flag = gb->band_flag;
   ga.counters = gb->counters;
-  const int grid = gather_grid(p->dtype, r.map, n);
-  if (r.map.passes > 1) {
+  const int grid = gather_grid(p->dtype, r.map, r.row_end - r.row_begin);
+  if (r.map.passes > 1 || r.row_begin > 0 || r.row_end < n) {
+    // rows outside the processed range (or filled slice by slice) start empty
     cudaMemsetAsync(gb->bitmask, 0, (size_t)n * r.W * 4, st);
     cudaMemsetAsync(gb->out_cnt, 0, (size_t)n * 4, st);
   }
@@ -436,11 +448,56 @@ sng_status sng_gather_mapping(const void *x, const sng_params *params, int32_t *
   return SNG_OK;
 }
 
+sng_status sng_cluster_edges(int64_t n, const int32_t *src, const int32_t *col, int64_t num_edges,
+                             const int32_t *deg, const sng_params *params, int32_t *labels,
+                             uint8_t *core, sng_stats *stats, void *stream) {
+  if (!params || !deg || !labels) return fail(SNG_EINVAL, "NULL argument");
+  if (n < 1 || n > 0x7fffffffLL) return fail(SNG_EINVAL, "n must be in [1, 2^31-1]");
+  if (num_edges < 0) return fail(SNG_EINVAL, "num_edges must be >= 0");
+  if (num_edges > 0 && (!src || !col)) return fail(SNG_EINVAL, "src / col is NULL");
+  if (params->min_pts < 1) return fail(SNG_EINVAL, "min_pts must be >= 1");
+  device_sms();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch s(st);
+  Resolved r;
+  r.n = n;
+  r.m = 0;
+  uint8_t *core_buf = core;
+  int32_t *parent = nullptr;
+  unsigned long long *counters = nullptr;
+  sng_status rc;
+  if (!core_buf && (rc = s.alloc((void **)&core_buf, (size_t)n, "core"))) return rc;
+  if ((rc = s.alloc((void **)&parent, (size_t)n * 4, "parent"))) return rc;
+  if ((rc = s.alloc((void **)&counters, kCntSlots * 8, "counters"))) return rc;
+  cudaMemsetAsync(counters, 0, kCntSlots * 8, st);
+  cudaMemcpyAsync(counters + kCntEdges, &num_edges, 8, cudaMemcpyHostToDevice, st);
+  const int sms = device_sms();
+  CoreArgs ca{n, params->min_pts, deg, nullptr, core_buf, parent, labels};
+  launch_core_init(ca, sms, st);
+  UnionArgs ua{n, nullptr, col, src, num_edges, core_buf, parent, labels, counters, loop_limit()};
+  launch_union(ua, sms, st);
+  launch_label(ua, sms, st);
+  FinalizeArgs fa{n, core_buf, nullptr, labels, counters, parent, loop_limit()};
+  launch_finalize(fa, sms, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "cluster_edges launches");
+  if (stats) {
+    rc = read_stats(counters, r, stats, st, nullptr);
+  } else {
+    // still surface device-side status (bounded loops, out-of-range edges)
+    rc = read_stats(counters, r, nullptr, st, nullptr);
+  }
+  s.release();
+  return rc;
+}
+
 sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels, uint8_t *core,
                        sng_stats *stats, void *stream) {
   Resolved r;
   sng_status rc = validate(x, params, &r);
   if (rc) return rc;
+  if (r.row_begin != 0 || r.row_end != r.n)
+    return fail(SNG_EINVAL, "a source-row range is for sng_build_graph only");
   if (!labels) return fail(SNG_EINVAL, "labels is NULL");
   device_sms();
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -12,6 +12,7 @@ struct Resolved {
   int64_t n = 0;
   int32_t d = 0;
   int64_t m = 0;        // draws per point
+  int64_t row_begin = 0, row_end = 0;  // source rows processed
   int32_t W = 0;        // keep-bit words per row
   float band_rel = 0.f;
   double eps2 = 0.0, band = 0.0;

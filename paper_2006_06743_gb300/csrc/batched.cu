@@ -132,6 +132,8 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchArgs a) {
     g.xm = static_cast<const float *>(g.x);
     g.ldm = a.ld;
     g.n = c.n;
+    g.row_begin = 0;
+    g.row_end = c.n;
     g.d = a.d;
     g.m = c.m;
     g.W = c.W;
@@ -315,6 +317,8 @@ sng_status sng_batch_plan_create(const int64_t *offsets, int32_t n_clouds, const
   if (!offsets || !base) return fail(SNG_EINVAL, "offsets / base is NULL");
   if (n_clouds < 1) return fail(SNG_EINVAL, "n_clouds must be >= 1");
   if (base->dtype != SNG_F32) return fail(SNG_EINVAL, "batched form takes FP32 points");
+  if (base->row_begin != 0 || base->row_end != 0)
+    return fail(SNG_EINVAL, "a source-row range is for sng_build_graph only");
   if (offsets[0] != 0) return fail(SNG_EINVAL, "offsets[0] must be 0");
   int64_t nmax = 0;
   for (int32_t b = 0; b < n_clouds; ++b) {

@@ -31,6 +31,7 @@ struct GatherArgs {
   const float *xm;        // FP32 values for the FP64 recheck (x itself for F32)
   int64_t ldm;
   int32_t n, d, m, W;     // W = ceil(m/32) words per bitmask row
+  int32_t row_begin, row_end;  // source rows this launch processes
   uint64_t seed;
   FastMod fm;
   float lo_thr, hi_thr;   // d2 < lo_thr: keep; d2 > hi_thr: drop; else FP64
@@ -235,8 +236,8 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value) gather_
   const int warp = threadIdx.x >> 5;
   int32_t *sp = smem_partner + warp * 64 * U;   // two stages of 32*U partners
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < a.n;
-       row += warps_total) {
+  for (int64_t row = a.row_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+       row < a.row_end; row += warps_total) {
     const int32_t i = (int32_t)row;
     const int32_t mi = a.m_row ? a.m_row[i] : a.m;
     gather_row<T, VEC, G, NCH, U>(a, i, mi, sp, lane);
@@ -365,8 +366,8 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
   int32_t *sp = smem_list + warp * 64 * U;
   int32_t *sj = sp + 32 * U;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < a.n;
-       row += warps_total) {
+  for (int64_t row = a.row_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+       row < a.row_end; row += warps_total) {
     const int32_t i = (int32_t)row;
     const int32_t mi = a.m_row ? a.m_row[i] : a.m;
     gather_row_blocked<T, VEC, G, NCH, U>(a, i, mi, lo, hi, sp, sj, lane);

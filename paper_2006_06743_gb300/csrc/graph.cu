@@ -175,6 +175,10 @@ __global__ void union_kernel(UnionArgs a) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.num_edges;
        e += stride) {
     const int32_t i = a.src[e], p = a.col[e];
+    if ((uint32_t)i >= (uint32_t)a.n || (uint32_t)p >= (uint32_t)a.n) {
+      atomicOr(status, kErrIndex);   // caller-supplied edge out of range: skipped
+      continue;
+    }
     if (a.core[i] && a.core[p]) uf_unite(a.parent, i, p, status, a.loop_limit);
   }
 }
@@ -188,6 +192,7 @@ __global__ void label_kernel(UnionArgs a) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.num_edges;
        e += stride) {
     const int32_t i = a.src[e], p = a.col[e];
+    if ((uint32_t)i >= (uint32_t)a.n || (uint32_t)p >= (uint32_t)a.n) continue;
     const bool ci = a.core[i] != 0, cp = a.core[p] != 0;
     if (ci == cp) continue;
     const int32_t c = ci ? i : p, b = ci ? p : i;

@@ -135,6 +135,7 @@ __device__ __forceinline__ float forward_point(const float *s, const float *xrow
 // --------------------------------------------------------------- inference
 
 struct GateArgs {
+  int32_t fp32_activations;   // 1: CUDA-core path with FP32 activations
   const float *x;
   int64_t ld;
   int64_t n;
@@ -189,6 +190,196 @@ __global__ void __launch_bounds__(128, 1) mlp_gate_kernel(GateArgs a) {
     }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(a.counters + 0, q);
+      atomicAdd(a.counters + 1, nc);
+      atomicAdd(a.counters + 2, nn);
+    }
+  }
+}
+
+// ------------------------------------------------ inference on tensor cores
+//
+// The gate's two dense layers run on the tensor cores with warp-level
+// mma.sync.m16n8k16 (FP16 operands, FP32 accumulation): one warp pushes 16
+// points through the network.  Layer-1 accumulators (16 x 128) become,
+// after bias + GELU and rounding to FP16, exactly the A fragments of layer 2
+// in registers (the m16n8 accumulator layout of two adjacent n-tiles is the
+// m16k16 A layout), so hidden activations never touch memory.  Weights are
+// staged once per block in shared memory as FP16, rows padded so the
+// fragment loads are free of bank conflicts.  Activations are FP16 at the MMA
+// inputs (standardised inputs and layer-1 outputs).
+//
+// Fragment layouts (PTX ISA, mma.m16n8k16, g = lane / 4, q = lane % 4):
+//   A (16x16, row): a0 = (g, 2q..2q+1), a1 = (g+8, 2q..), a2 = (g, 2q+8..),
+//                   a3 = (g+8, 2q+8..)
+//   B (16x8, col):  b0 = (k = 2q..2q+1, n = g), b1 = (k = 2q+8.., n = g)
+//   C (16x8):       c0,c1 = (g, 2q..2q+1), c2,c3 = (g+8, 2q..2q+1)
+
+constexpr int kW1Pad = 8;                 // halves of padding per W1 row
+constexpr int kW2Stride = kH + 8;         // halves per W2 row (136)
+
+template <int KT1>
+struct MmaSmem {
+  static constexpr int k1 = 16 * KT1;                    // padded input width
+  static constexpr int w1_stride = k1 + kW1Pad;          // halves per W1 row
+  static constexpr size_t w1 = 0;                        // half [H][w1_stride]
+  static constexpr size_t w2 = w1 + sizeof(__half) * kH * w1_stride;   // half [H][136]
+  static constexpr size_t fp = w2 + sizeof(__half) * kH * kW2Stride;   // float params
+  // float params: b1[H] b2[H] w3[H] b3 pad[3] mean[k1] istd[k1]
+  static constexpr size_t fp_count = 3 * kH + 4 + 2 * k1;
+  static constexpr size_t xs = fp + sizeof(float) * fp_count;          // float [warps][16][k1]
+  static constexpr size_t bytes(int warps) { return xs + sizeof(float) * warps * 16 * k1; }
+};
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int KT1>
+__global__ void __launch_bounds__(128) mlp_gate_mma_kernel(GateArgs a) {
+  using L = MmaSmem<KT1>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __half *w1s = reinterpret_cast<__half *>(smem_raw + L::w1);
+  __half *w2s = reinterpret_cast<__half *>(smem_raw + L::w2);
+  float *fp = reinterpret_cast<float *>(smem_raw + L::fp);
+  float *b1s = fp, *b2s = fp + kH, *w3s = fp + 2 * kH, *b3s = fp + 3 * kH;
+  float *means = fp + 3 * kH + 4, *istd = means + L::k1;
+  const int d = a.d;
+  const MlpOff o = mlp_off(d);
+  for (int t = threadIdx.x; t < kH * L::w1_stride; t += blockDim.x) {
+    const int j = t / L::w1_stride, k = t % L::w1_stride;
+    w1s[t] = __float2half_rn(k < d ? a.P[o.w1 + (int64_t)j * d + k] : 0.f);
+  }
+  for (int t = threadIdx.x; t < kH * kW2Stride; t += blockDim.x) {
+    const int j = t / kW2Stride, k = t % kW2Stride;   // W2s[j][k] = W2[j][k]
+    w2s[t] = __float2half_rn(k < kH ? a.P[o.w2 + (int64_t)j * kH + k] : 0.f);
+  }
+  for (int t = threadIdx.x; t < kH; t += blockDim.x) {
+    b1s[t] = h16(a.P[o.b1 + t]);
+    b2s[t] = h16(a.P[o.b2 + t]);
+    w3s[t] = h16(a.P[o.w3 + t]);
+  }
+  for (int k = threadIdx.x; k < L::k1; k += blockDim.x) {
+    means[k] = k < d ? a.P[o.mean + k] : 0.f;
+    istd[k] = k < d ? 1.f / a.P[o.std + k] : 0.f;
+  }
+  if (threadIdx.x == 0) b3s[0] = h16(a.P[o.b3]);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  float *xs = reinterpret_cast<float *>(smem_raw + L::xs) + warp * 16 * L::k1;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long nq = 0, nc = 0, nn = 0;
+  for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 16; base < a.n;
+       base += warps_total * 16) {
+    // stage 16 standardised rows (zero past n and past d)
+    for (int t = lane; t < 16 * L::k1; t += 32) {
+      const int r = t / L::k1, k = t % L::k1;
+      const int64_t i = base + r;
+      xs[t] = (i < a.n && k < d) ? (a.x[i * a.ld + k] - means[k]) * istd[k] : 0.f;
+    }
+    __syncwarp();
+    // layer 1: acc1[nt] = U (16 x k1) * W1^T (k1 x 128)
+    float acc1[kH / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < kH / 8; ++nt) acc1[nt][0] = acc1[nt][1] = acc1[nt][2] = acc1[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < KT1; ++kt) {
+      uint32_t af[4];
+      const float *r0 = xs + g * L::k1 + kt * 16 + 2 * q;
+      const float *r1 = xs + (g + 8) * L::k1 + kt * 16 + 2 * q;
+      af[0] = pack_h2(r0[0], r0[1]);
+      af[1] = pack_h2(r1[0], r1[1]);
+      af[2] = pack_h2(r0[8], r0[9]);
+      af[3] = pack_h2(r1[8], r1[9]);
+#pragma unroll
+      for (int nt = 0; nt < kH / 8; ++nt) {
+        const __half *wr = w1s + (nt * 8 + g) * L::w1_stride + kt * 16 + 2 * q;
+        mma16816(acc1[nt], af, *reinterpret_cast<const uint32_t *>(wr),
+                 *reinterpret_cast<const uint32_t *>(wr + 8));
+      }
+    }
+    __syncwarp();
+    // bias + GELU -> FP16 A fragments of layer 2 (k-tile kt2 = n-tiles 2kt2, 2kt2+1)
+    uint32_t hf[kH / 16][4];
+#pragma unroll
+    for (int kt2 = 0; kt2 < kH / 16; ++kt2) {
+      const int c0 = kt2 * 16 + 2 * q, c1 = c0 + 8;
+      const float *lo = acc1[2 * kt2], *hi = acc1[2 * kt2 + 1];
+      hf[kt2][0] = pack_h2(gelu_f(lo[0] + b1s[c0]), gelu_f(lo[1] + b1s[c0 + 1]));
+      hf[kt2][1] = pack_h2(gelu_f(lo[2] + b1s[c0]), gelu_f(lo[3] + b1s[c0 + 1]));
+      hf[kt2][2] = pack_h2(gelu_f(hi[0] + b1s[c1]), gelu_f(hi[1] + b1s[c1 + 1]));
+      hf[kt2][3] = pack_h2(gelu_f(hi[2] + b1s[c1]), gelu_f(hi[3] + b1s[c1 + 1]));
+    }
+    // layer 2 and the output unit, one n-tile of hidden units at a time
+    float z0 = 0.f, z1 = 0.f;   // rows g and g + 8
+#pragma unroll 2
+    for (int nt = 0; nt < kH / 8; ++nt) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kt2 = 0; kt2 < kH / 16; ++kt2) {
+        const __half *wr = w2s + (nt * 8 + g) * kW2Stride + kt2 * 16 + 2 * q;
+        mma16816(c, hf[kt2], *reinterpret_cast<const uint32_t *>(wr),
+                 *reinterpret_cast<const uint32_t *>(wr + 8));
+      }
+      const int col = nt * 8 + 2 * q;
+      z0 = fmaf(w3s[col], gelu_f(c[0] + b2s[col]), z0);
+      z0 = fmaf(w3s[col + 1], gelu_f(c[1] + b2s[col + 1]), z0);
+      z1 = fmaf(w3s[col], gelu_f(c[2] + b2s[col]), z1);
+      z1 = fmaf(w3s[col + 1], gelu_f(c[3] + b2s[col + 1]), z1);
+    }
+    z0 += __shfl_xor_sync(kFullMask, z0, 1);
+    z0 += __shfl_xor_sync(kFullMask, z0, 2);
+    z1 += __shfl_xor_sync(kFullMask, z1, 1);
+    z1 += __shfl_xor_sync(kFullMask, z1, 2);
+    if (q < 2) {
+      const int64_t i = base + g + 8 * q;
+      const float z = (q == 0 ? z0 : z1) + b3s[0];
+      if (i < a.n) {
+        const float p = 1.f / (1.f + expf(-z));
+        if (a.prob) a.prob[i] = p;
+        if (a.forced) {
+          uint8_t f = 0;
+          int32_t mi = a.m, wi = a.w_full;
+          if (p < a.p_noise) {
+            f = 2;
+            mi = a.m_noise;
+            wi = a.w_noise;
+            ++nn;
+          } else if (p > a.p_core) {
+            f = 1;
+            mi = a.m_core;
+            wi = a.w_core;
+            ++nc;
+          }
+          a.forced[i] = f;
+          a.m_row[i] = mi;
+          if (a.w_row) a.w_row[i] = wi;
+          nq += (unsigned long long)mi;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (a.counters) {
+#pragma unroll
+    for (int o2 = 16; o2 >= 1; o2 >>= 1) {
+      nq += __shfl_xor_sync(kFullMask, nq, o2);
+      nc += __shfl_xor_sync(kFullMask, nc, o2);
+      nn += __shfl_xor_sync(kFullMask, nn, o2);
+    }
+    if (lane == 0) {
+      atomicAdd(a.counters + 0, nq);
       atomicAdd(a.counters + 1, nc);
       atomicAdd(a.counters + 2, nn);
     }
@@ -380,7 +571,37 @@ static cudaError_t smem_optin(const void *fn) {
 
 static int dmax_for(int d) { return d <= 8 ? 8 : d <= 32 ? 32 : 64; }
 
+template <int KT1>
+static cudaError_t launch_gate_mma(const GateArgs &a, cudaStream_t st) {
+  const size_t smem = MmaSmem<KT1>::bytes(4);
+  cudaError_t e = cudaFuncSetAttribute((const void *)mlp_gate_mma_kernel<KT1>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_gate_mma_kernel<KT1>, 128, smem);
+  const int64_t need = (a.n + 63) / 64;
+  const int grid = (int)std::min<int64_t>(need, (int64_t)device_sms() * (occ > 0 ? occ : 1));
+  mlp_gate_mma_kernel<KT1><<<grid, 128, smem, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_gate_simt(const GateArgs &a, cudaStream_t st);
+
+// Gate / prediction: tensor-core kernel (FP16 activations at the MMA inputs)
+// unless FP32 activations are asked for.
 static cudaError_t launch_gate(const GateArgs &a, cudaStream_t st) {
+  if (a.fp32_activations) return launch_gate_simt(a, st);
+  switch ((a.d + 15) / 16) {
+    case 1: return launch_gate_mma<1>(a, st);
+    case 2: return launch_gate_mma<2>(a, st);
+    case 3: return launch_gate_mma<3>(a, st);
+    default: return launch_gate_mma<4>(a, st);
+  }
+}
+
+// FP32-activation reference path on CUDA cores (kept for checking).
+static cudaError_t launch_gate_simt(const GateArgs &a, cudaStream_t st) {
   const int sms = device_sms();
   const int64_t need = (a.n + 127) / 128;
   const int grid = (int)std::min<int64_t>(need, (int64_t)sms * 2);
@@ -578,8 +799,25 @@ sng_status sng_mlp_predict(const float *x, int64_t n, const sng_mlp_config *cfg,
   if (rc) return rc;
   if (!x || !params || !prob) return fail(SNG_EINVAL, "NULL argument");
   if (n < 1) return fail(SNG_EINVAL, "n must be >= 1");
-  GateArgs a{x,       cfg->d,  n,       cfg->d,  params,  prob,    0.f,     1.f, 0, 0, 0,
-             1,       1,       1,       nullptr, nullptr, nullptr, nullptr};
+  GateArgs a{cfg->fp32_activations != 0,
+             x,
+             cfg->d,
+             n,
+             cfg->d,
+             params,
+             prob,
+             0.f,
+             1.f,
+             0,
+             0,
+             0,
+             1,
+             1,
+             1,
+             nullptr,
+             nullptr,
+             nullptr,
+             nullptr};
   cudaError_t e = launch_gate(a, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? SNG_OK : cuda_fail(e, "predict");
 }
@@ -594,6 +832,8 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
   if ((rc = check_cfg(cfg))) return rc;
   if (!labels || !mlp_params || !gate) return fail(SNG_EINVAL, "NULL argument");
   if (params->dtype != SNG_F32) return fail(SNG_EINVAL, "surrogate form takes FP32 points");
+  if (r.row_begin != 0 || r.row_end != r.n)
+    return fail(SNG_EINVAL, "a source-row range is for sng_build_graph only");
   if (params->sample_mode != SNG_SAMPLE_HASH)
     return fail(SNG_EINVAL, "surrogate form needs hashed draws");
   if (cfg->d != params->d) return fail(SNG_EINVAL, "mlp d differs from the points' d");
@@ -629,9 +869,25 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
     if (mi <= 0) return kDegUnit;
     return (int32_t)std::lround((double)kDegUnit * (double)r.m / (double)mi);
   };
-  GateArgs ga{static_cast<const float *>(x), params->ld, r.n, params->d, mlp_params, nullptr,
-              pn, pc, (int32_t)r.m, m_core, m_noise, weight((int32_t)r.m), weight(m_core),
-              weight(m_noise), forced, m_row, w_row, gcnt};
+  GateArgs ga{cfg->fp32_activations != 0,
+              static_cast<const float *>(x),
+              params->ld,
+              r.n,
+              params->d,
+              mlp_params,
+              nullptr,
+              pn,
+              pc,
+              (int32_t)r.m,
+              m_core,
+              m_noise,
+              weight((int32_t)r.m),
+              weight(m_core),
+              weight(m_noise),
+              forced,
+              m_row,
+              w_row,
+              gcnt};
   tm.mark(st, 9);
   cudaError_t e = launch_gate(ga, st);
   if (e != cudaSuccess) return cuda_fail(e, "surrogate gate");

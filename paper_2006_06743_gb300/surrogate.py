@@ -64,6 +64,7 @@ class TrainConfig:
     adam_eps: float = 1e-8
     seed: int = 0
     sequential: bool = False
+    fp32_activations: bool = False
 
     def to_c(self, d: int) -> sng_mlp_config:
         c = sng_mlp_config()
@@ -71,6 +72,7 @@ class TrainConfig:
         c.lr, c.beta1, c.beta2, c.adam_eps = self.lr, self.beta1, self.beta2, self.adam_eps
         c.seed = self.seed & (2**64 - 1)
         c.sequential = int(self.sequential)
+        c.fp32_activations = int(self.fp32_activations)
         return c
 
 

@@ -32,15 +32,23 @@ def _setup(d, n, seed):
     return torch, sng, sg, net, init, x, y, xg, yg, mean, std
 
 
-@pytest.mark.parametrize("d,n", [(5, 37), (32, 200), (64, 130), (2, 64)])
+@pytest.mark.parametrize("d,n", [(5, 37), (32, 200), (64, 130), (2, 64), (17, 1000),
+                                 (48, 3001)])
 def test_standardize_and_forward_match_oracle(d, n):
+    """Inference against the FP64 network on the same FP16-rounded weights.
+    CUDA-core path (FP32 activations): |dp| <= 2e-5.  Tensor-core path: the
+    standardised inputs and the layer-1 outputs are rounded to FP16 at the MMA
+    inputs (relative 2^-11 each), which moves the logit by ~5e-4 on sums of
+    <= 128 terms of weights ~0.1 (|dp| <= |dz| / 4); bound used: 2e-3."""
     torch, sng, sg, net, init, x, y, xg, yg, mean, std = _setup(d, n, d)
     np.testing.assert_allclose(mean, x.astype(np.float64).mean(0), rtol=1e-5, atol=1e-5)
     np.testing.assert_allclose(std, x.astype(np.float64).std(0), rtol=1e-5, atol=1e-5)
-    prob = net.predict(xg).cpu().numpy()
     f = omlp.forward(_fp16(init), x, mean.astype(np.float64), std.astype(np.float64))
     want = 1.0 / (1.0 + np.exp(-f["z"]))
-    np.testing.assert_allclose(prob, want, atol=2e-5)
+    net.cfg.fp32_activations = True
+    np.testing.assert_allclose(net.predict(xg).cpu().numpy(), want, atol=2e-5)
+    net.cfg.fp32_activations = False
+    np.testing.assert_allclose(net.predict(xg).cpu().numpy(), want, atol=2e-3)
 
 
 @pytest.mark.parametrize("d,n", [(5, 37), (32, 256), (64, 100)])
