@@ -143,3 +143,36 @@ def test_batched_config_4096_clouds(orc):
                             sng.Params(eps=p.eps, min_pts=4, m=200, seed=p.seed + b))
         np.testing.assert_array_equal(lb.cpu().numpy(), lab[off[b]:off[b + 1]])
     assert st.queries == int((sizes * 200).sum())
+
+
+def test_maximum_point_count(orc):
+    """n = 2^31 - 1 points (the largest the ABI accepts) in d = 1 with
+    integer coordinates x_i = i mod 1000, eps = 0.5, m = 2: a draw is kept
+    exactly when the partner has the same value.  Every index path (64-bit
+    row offsets, the 96-bit remainder at n - 1 = 2^31 - 2, the scan, the
+    union-find) runs at the limit; sampled rows are checked exactly against
+    the oracle's draws and the closed form, totals for consistency."""
+    torch, sng = need_gpu()
+    n = 2**31 - 1
+    free, _ = torch.cuda.mem_get_info()
+    if free < (120 << 30):
+        pytest.skip("needs ~120 GB of free device memory")
+    x = (torch.arange(n, device="cuda", dtype=torch.int64) % 1000).to(torch.float32)
+    x = x.view(n, 1)
+    p = sng.Params(eps=0.5, min_pts=2, m=2, seed=11)
+    g = sng.build_graph(x, p)
+    rows = np.array([0, 1, 2, 999, 1000, n // 2, n - 3, n - 2, n - 1], dtype=np.int64)
+    rows = np.concatenate([rows, np.random.default_rng(5).integers(0, n, 200)])
+    rp = g["row_ptr"]
+    for i in rows.tolist():
+        pr = orc.partners(11, n, i, 1, 2)[0]
+        want = [int(q) for q in pr if q % 1000 == i % 1000]
+        got = g["col"][int(rp[i]):int(rp[i + 1])].cpu().tolist()
+        assert got == want, i
+    assert int(rp[-1]) == g["col"].numel() == g["stats"]["kept_edges"]
+    assert int(g["deg"].sum().item()) == 2 * g["col"].numel()
+    del g
+    labels, st = sng.cluster(x, p)
+    lab = labels[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert ((lab == -1) | ((lab >= 0) & (lab < n))).all()
+    assert st["queries"] == 2 * n
