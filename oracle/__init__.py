@@ -14,6 +14,9 @@ Contents
     union-find), border labels -- plus textbook brute-force DBSCAN.
   * ``ari``: the adjusted Rand index of Hubert & Arabie (1985), the score the
     paper's Section 5 evaluates clusterings with.
+  * ``ami``: the adjusted mutual information of Vinh, Epps & Bailey (2010),
+    the paper's second score, with its expected mutual information summed
+    over every term of the hypergeometric model.
   * ``mlp``: FP64 forward/backward/Adam for the core-point surrogate network.
 
 Parity status per function is listed in each docstring; every function here is
@@ -332,3 +335,82 @@ def canonical(labels) -> np.ndarray:
                 first[l] = i
         out[mask] = np.array([first[l] for l in lab.tolist()], dtype=np.int64)
     return out
+
+
+def _contingency(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    if a.shape != b.shape:
+        raise ValueError("label arrays differ in length")
+    _, ia = np.unique(a, return_inverse=True)
+    _, ib = np.unique(b, return_inverse=True)
+    table = np.zeros((int(ia.max()) + 1, int(ib.max()) + 1), dtype=np.int64)
+    np.add.at(table, (ia, ib), 1)
+    return table
+
+
+def entropy(counts, n: int) -> float:
+    """H = -sum_i (a_i/n) log(a_i/n) over the clusters of one labelling."""
+    c = np.asarray(counts, dtype=np.float64)
+    c = c[c > 0]
+    return float(-np.sum(c / n * np.log(c / n)))
+
+
+def mutual_info(table) -> float:
+    """MI = sum_ij (n_ij/n) log(n n_ij / (a_i b_j)) over the non-empty cells of
+    the contingency table (natural logarithm)."""
+    t = np.asarray(table, dtype=np.int64)
+    n = float(t.sum())
+    a = t.sum(axis=1).astype(np.float64)
+    b = t.sum(axis=0).astype(np.float64)
+    i, j = np.nonzero(t)
+    c = t[i, j].astype(np.float64)
+    return float(np.sum(c / n * np.log(n * c / (a[i] * b[j]))))
+
+
+def expected_mutual_info(a_counts, b_counts, n: int) -> float:
+    """E[MI] when the labels of one side are permuted uniformly at random (the
+    hypergeometric model of Vinh, Epps & Bailey 2010): for every pair of
+    cluster sizes (a, b), sum over every feasible cell count k >= 1 of
+    (k/n) log(n k / (a b)) times the hypergeometric probability of k, the
+    latter from log-gamma values."""
+    from scipy.special import gammaln
+    total = 0.0
+    lg_n = gammaln(n + 1.0)
+    for a in np.asarray(a_counts, dtype=np.int64):
+        for b in np.asarray(b_counts, dtype=np.int64):
+            lo, hi = max(1, a + b - n), min(a, b)
+            if lo > hi:
+                continue
+            k = np.arange(lo, hi + 1, dtype=np.float64)
+            logp = (gammaln(a + 1.0) + gammaln(b + 1.0) + gammaln(n - a + 1.0)
+                    + gammaln(n - b + 1.0) - lg_n - gammaln(k + 1.0) - gammaln(a - k + 1.0)
+                    - gammaln(b - k + 1.0) - gammaln(n - a - b + k + 1.0))
+            total += float(np.sum(k / n * np.log(n * k / (float(a) * float(b))) * np.exp(logp)))
+    return total
+
+
+AMI_AVERAGES = ("min", "geometric", "arithmetic", "max")
+
+
+def ami(a, b, average: str = "arithmetic") -> dict:
+    """Adjusted mutual information (MI - E[MI]) / (avg(H_a, H_b) - E[MI]),
+    avg one of min / geometric / arithmetic / max (Vinh, Epps & Bailey 2010).
+    Two trivial labellings of the same kind (both one cluster, or both all
+    singletons) score 1; a vanishing normaliser otherwise scores 0.  Noise
+    (-1) is one label.  Returns the score and its terms."""
+    t = _contingency(a, b)
+    n = int(t.sum())
+    ra, rb = t.sum(axis=1), t.sum(axis=0)
+    ha, hb = entropy(ra, n), entropy(rb, n)
+    mi = mutual_info(t)
+    emi = expected_mutual_info(ra, rb, n)
+    out = dict(mi=mi, emi=emi, h_a=ha, h_b=hb)
+    if (ra.size == 1 and rb.size == 1) or (ra.size == n and rb.size == n):
+        return dict(out, ami=1.0)
+    norm = {"min": min(ha, hb), "geometric": float(np.sqrt(ha * hb)),
+            "arithmetic": 0.5 * (ha + hb), "max": max(ha, hb)}[average]
+    den = norm - emi
+    if den <= 0.0:
+        return dict(out, ami=0.0)
+    return dict(out, ami=(mi - emi) / den)

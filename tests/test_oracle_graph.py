@@ -144,12 +144,34 @@ def test_sample_all_equals_textbook_dbscan(orc, seed, n, d, m_db):
     # out-degree mode: MinPts = min_samples - 1
     r1 = orc.cluster(x, eps, seed=0, m=n - 1, min_pts=m_db - 1, deg_mode=1, sample_all=True)
     np.testing.assert_array_equal(r1["labels"], bl)
+    # simple-graph degree: distinct neighbours = |N_eps(x)| - 1 as well
+    r2 = orc.cluster(x, eps, seed=0, m=n - 1, min_pts=m_db - 1, deg_mode=2, sample_all=True)
+    np.testing.assert_array_equal(r2["labels"], bl)
+    np.testing.assert_array_equal(r2["deg"], r1["deg"])
     # scikit-learn: same cores; same partition of cores; borders valid
     sl, sc = _sk_dbscan(x, eps, m_db)
     np.testing.assert_array_equal(sc, bc)
     cores = bc.astype(bool)
     assert orc.ari(sl[cores], bl[cores]) == 1.0
     np.testing.assert_array_equal(sl < 0, bl < 0)
+
+
+def test_simple_degree_counts_distinct_pairs(orc):
+    """Distinct-neighbour degree against a set of unordered pairs built in
+    Python from hashed draws with many repeats (n = 40, m = 60)."""
+    x = datagen.random_points(40, 2, seed=3)
+    rp, col, _, _ = orc.build_rows(x, 0.4, 5, 60)
+    pairs = set()
+    for i in range(40):
+        for p in col[rp[i]:rp[i + 1]]:
+            pairs.add((min(i, int(p)), max(i, int(p))))
+    want = np.zeros(40, dtype=np.int32)
+    for a, b in pairs:
+        want[a] += 1
+        want[b] += 1
+    got = orc.degrees(40, rp, col, mode=2)
+    np.testing.assert_array_equal(got, want)
+    assert (orc.degrees(40, rp, col, mode=0) > got).any()   # repeats were present
 
 
 # ------------------------------------------------ components cross-checks
