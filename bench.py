@@ -176,7 +176,7 @@ def bench_sng(args, w):
     params = sng.Params(eps=w["eps"], min_pts=w["min_pts"], s=w["s"], seed=w["seed"],
                         flags=sng.SNG_FLAG_TIMING, map_group=args.map_group,
                         map_unroll=args.map_unroll, map_block=args.map_block,
-                        map_passes=args.map_passes)
+                        map_passes=args.map_passes, degree_mode=args.degree_mode)
     tuned = None
     if args.autotune and not (args.map_group or args.map_unroll or args.map_block
                               or args.map_passes):
@@ -265,6 +265,8 @@ def bench_sng(args, w):
         "data": "synthetic (seeded Gaussian mixture, no dataset)",
         "config": {"workload": args.workload, "n": n, "d": d, "m": m, "s": w["s"],
                    "eps": w["eps"], "min_pts": w["min_pts"], "queries_per_step": Q,
+                   "degree": ["undirected multigraph", "out-degree",
+                              "distinct neighbours"][args.degree_mode],
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"dp{world}",
                    "gather_mapping": {**{k: getattr(params, k) for k in
                                          ("map_group", "map_unroll", "map_block", "map_passes")},
@@ -283,6 +285,7 @@ def bench_sng(args, w):
         "stats": {k: stats[k] for k in ("kept_edges", "band_pairs", "band_points", "cores",
                                         "clusters", "noise", "recheck_pairs")},
         "ari_vs_generating_mixture": ari_truth,
+        "ami_vs_generating_mixture": sng.ami(labels, torch.from_numpy(truth).to(dev))["ami"],
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -546,7 +549,7 @@ def bench_balls(args):
     balls in R^3 (centres 3 apart, so 1 apart at the closest), m =
     ceil(20 ln n) draws per point, eps = 0.5, MinPts = 2 (the caption fixes
     only the sampling rate; eps below the gap and the smallest MinPts are this
-    reading).  ARI against the generating ball, for growing n."""
+    reading).  ARI and AMI against the generating ball, for growing n."""
     import numpy as np
     import torch
 
@@ -560,8 +563,9 @@ def bench_balls(args):
         p = sng.Params(eps=0.5, min_pts=2, m=m, seed=args.seed, flags=sng.SNG_FLAG_TIMING)
         sng.cluster(xg, p)
         t_ms, (lab, st) = _timed(lambda: sng.cluster(xg, p), 3)
-        ari = sng.ari(lab, torch.from_numpy(truth.astype(np.int32)).cuda())
-        rows.append({"n": n, "m": m, "ari_vs_truth": ari, "clusters": st["clusters"],
+        tg = torch.from_numpy(truth.astype(np.int32)).cuda()
+        rows.append({"n": n, "m": m, "ari_vs_truth": sng.ari(lab, tg),
+                     "ami_vs_truth": sng.ami(lab, tg)["ami"], "clusters": st["clusters"],
                      "noise": st["noise"], "ms": t_ms})
     return {"form": "balls", "metric": "ARI vs generating ball (Figure 1 simulation)",
             "value": rows[-1]["ari_vs_truth"], "unit": "ARI", "rows": rows,
@@ -574,8 +578,8 @@ def bench_sweep(args):
     the paper's Figure 10): a Gaussian mixture (as the headline workload,
     smaller n), full DBSCAN computed on the GPU with every pair queried
     (s = 1, multigraph degree, MinPts = 2 (min_samples - 1)), and
-    SNG-DBSCAN at decreasing s with MinPts scaled by s; ARI of each against
-    full DBSCAN and against the generating mixture."""
+    SNG-DBSCAN at decreasing s with MinPts scaled by s; ARI and AMI of each
+    against full DBSCAN and against the generating mixture."""
     import numpy as np
     import torch
 
@@ -592,6 +596,7 @@ def bench_sweep(args):
     sng.cluster(xg, full_p)
     full_ms, (full, fst) = _timed(lambda: sng.cluster(xg, full_p), 1)
     rows = [{"s": 1.0, "ms": full_ms, "ari_vs_full": 1.0, "ari_vs_truth": sng.ari(full, tg),
+             "ami_vs_full": 1.0, "ami_vs_truth": sng.ami(full, tg)["ami"],
              "clusters": fst["clusters"]}]
     for s in args.sweep_s:
         mp = max(2, int(round(2 * (k_db - 1) * s)))
@@ -600,7 +605,8 @@ def bench_sweep(args):
         ms, (lab, st) = _timed(lambda: sng.cluster(xg, p), 3)
         rows.append({"s": s, "m": p.draws(n), "min_pts": mp, "ms": ms,
                      "speedup_vs_full": full_ms / ms, "ari_vs_full": sng.ari(lab, full),
-                     "ari_vs_truth": sng.ari(lab, tg), "clusters": st["clusters"]})
+                     "ari_vs_truth": sng.ari(lab, tg), "ami_vs_full": sng.ami(lab, full)["ami"],
+                     "ami_vs_truth": sng.ami(lab, tg)["ami"], "clusters": st["clusters"]})
     return {"form": "sweep", "metric": "ARI vs full DBSCAN against sampling rate",
             "value": rows[-1]["ari_vs_full"], "unit": "ARI", "rows": rows,
             "config": {"workload": f"mixture-n{n}-d{d}-k20", "eps": eps, "min_samples": k_db,
@@ -650,6 +656,8 @@ def main():
     ap.add_argument("--map-block", type=int, default=0)
     ap.add_argument("--map-passes", type=int, default=0)
     ap.add_argument("--autotune", type=int, default=1, help="1: tune the gather mapping first")
+    ap.add_argument("--degree-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="0 undirected multigraph, 1 out-degree, 2 distinct neighbours")
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tune-budget", type=float, default=40.0)
     ap.add_argument("--verbose", action="store_true")

@@ -62,6 +62,12 @@ typedef int32_t sng_status;
 #define SNG_DEG_UNDIRECTED_MULTI 0 /* each kept draw (i,p) adds 1 to i and to p */
 #define SNG_DEG_OUT 1              /* kept draws of i only (the count thresholded in
                                       the proof of Lemma 2)                      */
+#define SNG_DEG_SIMPLE 2           /* distinct neighbours of i in the simple
+                                      undirected graph G (repeated draws and both
+                                      directions of a pair count once); costs a
+                                      pair set of 2E..4E 8-byte slots.  Not in the
+                                      batched or no-allocation forms, nor with the
+                                      surrogate's reweighted degrees             */
 
 /* how partners are drawn (Algorithm 1, step 2) */
 #define SNG_SAMPLE_HASH 0   /* m hashed draws with replacement, never i itself */
@@ -151,7 +157,9 @@ void sng_graph_free(sng_graph *g);
  * Algorithm 1, steps 3-5 on a given sampled graph: src/col (device int32[E])
  * list its kept draws (src[e] drew col[e]), deg (device int32[n]) the degree
  * of every point in params->degree_mode (e.g. summed over the ranks that
- * built parts of the graph).  Core = deg >= params->min_pts; labels
+ * built parts of the graph).  With SNG_DEG_SIMPLE the degrees are computed
+ * from src/col here and deg is not read (may be NULL).  Core = deg >=
+ * params->min_pts; labels
  * (device int32[n]) and core (device uint8[n] or NULL) as in sng_cluster.
  * Only n, min_pts and degree_mode of params are read.  Synchronises `stream`
  * when stats != NULL.
@@ -201,10 +209,38 @@ void sng_batch_plan_destroy(sng_batch_plan *plan);
 sng_status sng_sample_partners(int64_t n, uint64_t seed, int64_t i0, int64_t rows, int64_t m,
                                int32_t sample_mode, int32_t *out, void *stream);
 
-/* Adjusted Rand index (Hubert & Arabie 1985; the score of the paper's
- * Section 5) of two labelings a, b (device int32[n], values in [-1, 2^31)),
- * noise as one label.  Synchronises `stream`; result in *ari (host). */
+/* Adjusted Rand index (Hubert & Arabie 1985; the first score of the paper's
+ * Section 5) of two labelings a, b (device int32[n], values in [-1, n)),
+ * noise as one label.  Synchronises `stream`; result in *ari (host).
+ * Labels outside [-1, n) -> SNG_EINVAL. */
 sng_status sng_ari(const int32_t *a, const int32_t *b, int64_t n, double *ari, void *stream);
+
+/* normaliser of the adjusted mutual information */
+#define SNG_AMI_MIN 0
+#define SNG_AMI_GEOMETRIC 1
+#define SNG_AMI_ARITHMETIC 2  /* mean of the two entropies (the usual default) */
+#define SNG_AMI_MAX 3
+
+typedef struct {
+    double ami;           /* (mi - emi) / (avg(h_a, h_b) - emi)               */
+    double mi;            /* mutual information (natural log)                 */
+    double emi;           /* its expectation under random relabelling         */
+    double h_a, h_b;      /* entropies of the two labelings                   */
+    int64_t clusters_a;   /* distinct labels (noise counts as one)            */
+    int64_t clusters_b;
+} sng_mi_terms;
+
+/* Adjusted mutual information (Vinh, Epps & Bailey 2010; the second score
+ * of the paper's Section 5) of two labelings a, b (device int32[n], values in
+ * [-1, n)), noise as one label, with normaliser `average` (SNG_AMI_*).  The
+ * expectation sums every term of the hypergeometric model (terms below the
+ * FP64 underflow threshold are zero).  Two trivial labelings of the same
+ * kind (both one cluster, or both all singletons) score 1; a normaliser that
+ * does not exceed the expectation scores 0.  Synchronises `stream` three
+ * times; result and terms in *out (host).  Labels outside [-1, n) or an
+ * unknown normaliser -> SNG_EINVAL. */
+sng_status sng_ami(const int32_t *a, const int32_t *b, int64_t n, int32_t average,
+                   sng_mi_terms *out, void *stream);
 
 /*
  * Core-point surrogate (no counterpart in the paper): a d -> 128 -> 128 -> 1

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libsng.so")
 
 SNG_OK, SNG_EINVAL, SNG_ENOMEM, SNG_ECUDA, SNG_ETIMEOUT, SNG_EINTERNAL = 0, -1, -2, -3, -4, -5
 SNG_F32, SNG_BF16 = 0, 1
-SNG_DEG_UNDIRECTED_MULTI, SNG_DEG_OUT = 0, 1
+SNG_DEG_UNDIRECTED_MULTI, SNG_DEG_OUT, SNG_DEG_SIMPLE = 0, 1, 2
 SNG_SAMPLE_HASH, SNG_SAMPLE_ALL = 0, 1
 SNG_FLAG_TIMING = 1
 SNG_FLAG_PREFETCH = 2
@@ -51,6 +51,15 @@ class sng_params(ctypes.Structure):
                 ("map_block", ctypes.c_int32), ("map_tile", ctypes.c_int32),
                 ("map_passes", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64)]
+
+
+class sng_mi_terms(ctypes.Structure):
+    _fields_ = [("ami", ctypes.c_double), ("mi", ctypes.c_double), ("emi", ctypes.c_double),
+                ("h_a", ctypes.c_double), ("h_b", ctypes.c_double),
+                ("clusters_a", ctypes.c_int64), ("clusters_b", ctypes.c_int64)]
+
+
+AMI_AVERAGES = {"min": 0, "geometric": 1, "arithmetic": 2, "max": 3}
 
 
 class sng_stats(ctypes.Structure):
@@ -111,6 +120,8 @@ SIGNATURES = {
     "sng_sample_partners": (ctypes.c_int32, [ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64,
                                              ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _P, _P]),
     "sng_ari": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _P]),
+    "sng_ami": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.c_int32,
+                                 ctypes.POINTER(sng_mi_terms), _P]),
     "sng_mlp_param_count": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32]),
     "sng_mlp_standardize": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
     "sng_mlp_loss_grad": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(sng_mlp_config),
@@ -310,15 +321,18 @@ def _copy_out(ptr: int, count: int, typestr: str, dtype, device):
 
 def cluster_edges(n: int, src, col, deg, params: Params, want_core: bool = False, stream=None):
     """Algorithm 1, steps 3-5 on a given graph: kept draws src[e] -> col[e]
-    (int32 CUDA tensors) and degrees deg (int32, n).  Returns (labels[, core],
+    (int32 CUDA tensors) and degrees deg (int32, n; None with the simple-graph
+    degree, which is computed from the edges).  Returns (labels[, core],
     stats)."""
     import torch
-    labels = torch.empty(n, dtype=torch.int32, device=deg.device)
-    core = torch.empty(n, dtype=torch.uint8, device=deg.device) if want_core else None
+    dev = src.device
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    core = torch.empty(n, dtype=torch.uint8, device=dev) if want_core else None
     st = sng_stats()
     E = int(src.numel())
     _check(lib().sng_cluster_edges(n, src.data_ptr() if E else None,
-                                   col.data_ptr() if E else None, E, deg.data_ptr(),
+                                   col.data_ptr() if E else None, E,
+                                   deg.data_ptr() if deg is not None else None,
                                    ctypes.byref(params.to_c(n, 1, 1, SNG_F32)), labels.data_ptr(),
                                    core.data_ptr() if core is not None else None,
                                    ctypes.byref(st), _stream_ptr(stream)))
@@ -334,6 +348,15 @@ def sample_partners(n: int, seed: int, i0: int, rows: int, m: int, sample_all: b
     _check(lib().sng_sample_partners(n, seed & (2**64 - 1), i0, rows, m, int(sample_all),
                                      out.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+def ami(a, b, average: str = "arithmetic", stream=None) -> dict:
+    """Adjusted mutual information of two int32 CUDA label tensors (values in
+    [-1, n)) with its terms: ami, mi, emi, h_a, h_b, clusters_a, clusters_b."""
+    t = sng_mi_terms()
+    _check(lib().sng_ami(a.data_ptr(), b.data_ptr(), a.numel(), AMI_AVERAGES[average],
+                         ctypes.byref(t), _stream_ptr(stream)))
+    return {k: getattr(t, k) for k, _ in t._fields_}
 
 
 def ari(a, b, stream=None) -> float:

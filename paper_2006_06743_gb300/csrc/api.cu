@@ -108,7 +108,8 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   if (p->d < 1) return fail(SNG_EINVAL, "d must be >= 1");
   if (p->ld < p->d) return fail(SNG_EINVAL, "ld must be >= d");
   if (p->dtype != SNG_F32 && p->dtype != SNG_BF16) return fail(SNG_EINVAL, "unknown dtype");
-  if (p->degree_mode != SNG_DEG_UNDIRECTED_MULTI && p->degree_mode != SNG_DEG_OUT)
+  if (p->degree_mode != SNG_DEG_UNDIRECTED_MULTI && p->degree_mode != SNG_DEG_OUT &&
+      p->degree_mode != SNG_DEG_SIMPLE)
     return fail(SNG_EINVAL, "unknown degree_mode");
   if (p->sample_mode != SNG_SAMPLE_HASH && p->sample_mode != SNG_SAMPLE_ALL)
     return fail(SNG_EINVAL, "unknown sample_mode");
@@ -260,6 +261,24 @@ int gather_grid(int dtype, const GatherMap &map, int64_t n) {
 
 // Steps shared by sng_build_graph and sng_cluster: the gather (step 2 with the
 // degree counts of step 3), the row-pointer scan and the CSR fill.
+// Degrees of the simple undirected graph of an edge list (deg is
+// overwritten; counters receives device status bits).
+sng_status simple_degrees(int64_t n, const int32_t *src, const int32_t *col, int64_t num_edges,
+                          int32_t *deg, unsigned long long *counters, Scratch &s) {
+  cudaStream_t st = s.stream;
+  cudaMemsetAsync(deg, 0, (size_t)n * 4, st);
+  if (num_edges == 0) return SNG_OK;
+  const uint64_t cap = simple_table_slots(num_edges);
+  unsigned long long *table = nullptr;
+  sng_status rc;
+  if ((rc = s.alloc((void **)&table, (size_t)cap * 8, "pair set"))) return rc;
+  cudaMemsetAsync(table, 0xff, (size_t)cap * 8, st);
+  SimpleDegArgs a{n, src, col, num_edges, table, cap - 1, deg, counters};
+  launch_simple_degree(a, device_sms(), st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SNG_OK : cuda_fail(e, "simple-degree launch");
+}
+
 sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scratch &s,
                      GraphBufs *gb, const int32_t *m_row, Timer *tm, const int32_t *w_row) {
   cudaStream_t st = s.stream;
@@ -339,7 +358,8 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   fa.row_ptr = gb->row_ptr;
   fa.col = gb->col;
   fa.src = nullptr;
-  if (gb->want_src) {
+  const bool simple = p->degree_mode == SNG_DEG_SIMPLE;
+  if (gb->want_src || simple) {
     if ((rc = s.alloc((void **)&gb->src, (size_t)E * 4, "edge sources"))) return rc;
     fa.src = gb->src;
   }
@@ -347,6 +367,9 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   tm->mark(st, 3);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fill launch");
+  // the gather left out-degrees; the simple-graph degree replaces them
+  if (simple && (rc = simple_degrees(n, gb->src, gb->col, gb->num_edges, gb->deg, gb->counters, s)))
+    return rc;
   return SNG_OK;
 }
 
@@ -451,7 +474,9 @@ sng_status sng_gather_mapping(const void *x, const sng_params *params, int32_t *
 sng_status sng_cluster_edges(int64_t n, const int32_t *src, const int32_t *col, int64_t num_edges,
                              const int32_t *deg, const sng_params *params, int32_t *labels,
                              uint8_t *core, sng_stats *stats, void *stream) {
-  if (!params || !deg || !labels) return fail(SNG_EINVAL, "NULL argument");
+  if (!params || !labels) return fail(SNG_EINVAL, "NULL argument");
+  const bool simple = params->degree_mode == SNG_DEG_SIMPLE;
+  if (!deg && !simple) return fail(SNG_EINVAL, "deg is NULL");
   if (n < 1 || n > 0x7fffffffLL) return fail(SNG_EINVAL, "n must be in [1, 2^31-1]");
   if (num_edges < 0) return fail(SNG_EINVAL, "num_edges must be >= 0");
   if (num_edges > 0 && (!src || !col)) return fail(SNG_EINVAL, "src / col is NULL");
@@ -471,6 +496,14 @@ sng_status sng_cluster_edges(int64_t n, const int32_t *src, const int32_t *col, 
   if ((rc = s.alloc((void **)&counters, kCntSlots * 8, "counters"))) return rc;
   cudaMemsetAsync(counters, 0, kCntSlots * 8, st);
   cudaMemcpyAsync(counters + kCntEdges, &num_edges, 8, cudaMemcpyHostToDevice, st);
+  if (simple) {
+    // degrees of the simple graph come from the edge list itself (the
+    // caller's deg, if any, is not read)
+    int32_t *sdeg = nullptr;
+    if ((rc = s.alloc((void **)&sdeg, (size_t)n * 4, "degrees"))) return rc;
+    if ((rc = simple_degrees(n, src, col, num_edges, sdeg, counters, s))) return rc;
+    deg = sdeg;
+  }
   const int sms = device_sms();
   CoreArgs ca{n, params->min_pts, deg, nullptr, core_buf, parent, labels};
   launch_core_init(ca, sms, st);

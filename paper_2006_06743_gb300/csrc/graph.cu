@@ -237,6 +237,50 @@ __global__ void finalize_kernel(FinalizeArgs a) {
   }
 }
 
+// Thread per edge: degree in the simple undirected graph.  Every kept draw
+// names the unordered pair {i, p}; the thread whose insertion puts the pair
+// into the set first adds one to both ends, so repeated draws and draws in
+// both directions count once (a pair {i, i}, possible only in caller-supplied
+// edge lists, adds one to i).  The set has at least twice as many slots as
+// edges, so linear probing meets a free slot or the key within cap probes.
+__global__ void simple_degree_kernel(SimpleDegArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.num_edges;
+       e += stride) {
+    const int32_t i = a.src[e], p = a.col[e];
+    if ((uint32_t)i >= (uint32_t)a.n || (uint32_t)p >= (uint32_t)a.n) {
+      atomicOr(status, kErrIndex);
+      continue;
+    }
+    const uint32_t lo = (uint32_t)min(i, p), hi = (uint32_t)max(i, p);
+    const unsigned long long key = ((unsigned long long)lo << 32) | hi;
+    uint64_t h = mix64(key) & a.cap_mask;
+    bool done = false;
+    for (uint64_t probe = 0; probe <= a.cap_mask; ++probe) {
+      const unsigned long long old = atomicCAS(a.table + h, ~0ull, key);
+      if (old == ~0ull) {
+        atomicAdd(a.deg + lo, 1);
+        if (hi != lo) atomicAdd(a.deg + hi, 1);
+        done = true;
+        break;
+      }
+      if (old == key) {
+        done = true;
+        break;
+      }
+      h = (h + 1) & a.cap_mask;
+    }
+    if (!done) atomicOr(status, kErrIndex);
+  }
+}
+
+uint64_t simple_table_slots(int64_t num_edges) {
+  uint64_t cap = 64;
+  while (cap < (uint64_t)(2 * num_edges)) cap <<= 1;
+  return cap;
+}
+
 int32_t loop_limit() {
   const char *v = std::getenv("SNG_LOOP_LIMIT");
   if (v && *v) {
@@ -274,6 +318,11 @@ void launch_label(const UnionArgs &a, int sms, cudaStream_t st) {
 
 void launch_finalize(const FinalizeArgs &a, int sms, cudaStream_t st) {
   finalize_kernel<<<grid_for(a.n, 256, sms * 8), 256, 0, st>>>(a);
+  note_launch();
+}
+
+void launch_simple_degree(const SimpleDegArgs &a, int sms, cudaStream_t st) {
+  simple_degree_kernel<<<grid_for(a.num_edges, 256, sms * 16), 256, 0, st>>>(a);
   note_launch();
 }
 

@@ -54,6 +54,21 @@ struct FinalizeArgs {
   int32_t loop_limit;
 };
 
+// Simple-graph degree (distinct neighbours in either direction): an
+// open-addressing set of unordered pairs {i, p}, keyed (min << 32) | max,
+// all-ones = empty slot.
+struct SimpleDegArgs {
+  int64_t n;
+  const int32_t *src;
+  const int32_t *col;
+  int64_t num_edges;
+  unsigned long long *table;  // simple_table_slots(num_edges) slots, set to all ones
+  uint64_t cap_mask;
+  int32_t *deg;               // zeroed by the caller
+  unsigned long long *counters;
+};
+uint64_t simple_table_slots(int64_t num_edges);
+
 int64_t scan_tiles(int64_t n);
 void launch_scan(const int32_t *cnt, int64_t n, int64_t *tile_tmp, int64_t *row_ptr,
                  unsigned long long *counters, cudaStream_t st);
@@ -62,5 +77,6 @@ void launch_core_init(const CoreArgs &a, int sms, cudaStream_t st);
 void launch_union(const UnionArgs &a, int sms, cudaStream_t st);
 void launch_label(const UnionArgs &a, int sms, cudaStream_t st);
 void launch_finalize(const FinalizeArgs &a, int sms, cudaStream_t st);
+void launch_simple_degree(const SimpleDegArgs &a, int sms, cudaStream_t st);
 
 }  // namespace sng

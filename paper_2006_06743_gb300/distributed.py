@@ -11,7 +11,10 @@ every point's degree and the whole core subgraph, so the ranks exchange
     ranges in rank order make the concatenation the graph's CSR order;
 
 after which every rank runs steps 3-5 on the full edge list and holds the
-same labels.  The exchange is written once against a small compute
+same labels.  With the simple-graph degree (distinct neighbours) partial
+degrees do not add up across ranks (two ranks may draw the same pair), so
+the all-reduce is skipped and each rank counts degrees from the gathered
+edge list.  The exchange is written once against a small compute
 interface, so the CPU test (gloo, oracle as compute) runs the same code as
 GPU ranks (NCCL, libsng.so as compute).
 """
@@ -37,6 +40,7 @@ class GpuCompute:
 
     def __init__(self, x, params, x_master=None):
         self.x, self.params, self.x_master = x, params, x_master
+        self.simple_degree = params.degree_mode == 2
 
     def local_graph(self, lo: int, hi: int) -> LocalGraph:
         import torch
@@ -71,15 +75,18 @@ def cluster_sharded(compute, n: int, group=None):
     world = dist.get_world_size(group)
     lo, hi = row_range(n, rank, world)
     g = compute.local_graph(lo, hi)
-    deg = g.deg.clone()
-    dist.all_reduce(deg, op=dist.ReduceOp.SUM, group=group)
+    dev = g.deg.device
+    deg = None
+    if not getattr(compute, "simple_degree", False):
+        deg = g.deg.clone()
+        dist.all_reduce(deg, op=dist.ReduceOp.SUM, group=group)
     # all-gather the edge lists (padded to the longest; sizes first)
-    e = torch.tensor([g.src.numel()], dtype=torch.int64, device=deg.device)
+    e = torch.tensor([g.src.numel()], dtype=torch.int64, device=dev)
     sizes = [torch.zeros_like(e) for _ in range(world)]
     dist.all_gather(sizes, e, group=group)
     sizes = [int(s.item()) for s in sizes]
     emax = max(sizes)
-    pair = torch.full((2, emax), -1, dtype=torch.int32, device=deg.device)
+    pair = torch.full((2, emax), -1, dtype=torch.int32, device=dev)
     pair[0, :g.src.numel()] = g.src
     pair[1, :g.col.numel()] = g.col
     parts = [torch.empty_like(pair) for _ in range(world)]

@@ -113,3 +113,8 @@ def test_batched_rejects_bad_tables():
         with pytest.raises(sng.SngError) as e:
             _run_batched(sng, torch, x, np.array(off), p)
         assert e.value.status == sng.SNG_EINVAL
+    # the simple-graph degree needs a pair set per cloud: not in this form
+    with pytest.raises(sng.SngError) as e:
+        _run_batched(sng, torch, x, np.array([0, 5, 10]),
+                     sng.Params(eps=0.3, min_pts=4, m=8, degree_mode=2))
+    assert e.value.status == sng.SNG_EINVAL

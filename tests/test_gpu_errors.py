@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", float("nan")), ("min_pts", 0),
                                          ("s", 0.0), ("s", 1.5), ("band_rel", -1.0),
-                                         ("map_group", 3), ("map_block", 48)])
+                                         ("map_group", 3), ("map_block", 48),
+                                         ("degree_mode", 3)])
 def test_invalid_params_rejected(field, value):
     torch, sng = need_gpu()
     x = torch.from_numpy(datagen.random_points(100, 3, seed=0)).cuda()

@@ -110,13 +110,49 @@ def _compare_cluster(orc, x_np, xg, p, sng):
 @pytest.mark.parametrize("n,d,m,mp", [(2, 1, 1, 1), (50, 2, 49, 2), (3000, 2, 60, 3),
                                       (5000, 3, 100, 4), (4000, 8, 200, 6), (3000, 64, 300, 10),
                                       (2500, 128, 128, 8)])
-@pytest.mark.parametrize("deg_mode", [0, 1])
+@pytest.mark.parametrize("deg_mode", [0, 1, 2])
 def test_cluster_matches_oracle(orc, n, d, m, mp, deg_mode):
     torch, sng = need_gpu()
     x = datagen.random_points(n, d, seed=n + d)
     eps = float(np.float32(0.1 * math.sqrt(d)))
     p = sng.Params(eps=eps, min_pts=mp, m=m, seed=n, degree_mode=deg_mode)
     _compare_cluster(orc, x, torch.from_numpy(x).cuda(), p, sng)
+
+
+@pytest.mark.parametrize("n,d,m", [(2, 1, 5), (40, 2, 200), (1000, 3, 300), (3000, 16, 100)])
+def test_simple_degree_graph(orc, n, d, m):
+    """Distinct-neighbour degrees (repeated draws and both directions of a
+    pair count once) equal the oracle's; m > n forces many repeats."""
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=n + 3 * d)
+    eps = float(np.float32(0.3 * math.sqrt(d)))
+    p = sng.Params(eps=eps, min_pts=3, m=m, seed=n, degree_mode=2)
+    _compare_graph(orc, x, torch.from_numpy(x).cuda(), p, sng)
+
+
+def test_simple_degree_cluster_edges(orc):
+    """Steps 3-5 from an edge list with the simple-graph degree: degrees come
+    from the edges (deg not passed), including repeats, both directions and a
+    self pair, which the oracle counts once."""
+    torch, sng = need_gpu()
+    n = 500
+    rng = np.random.default_rng(4)
+    src = rng.integers(0, n, size=4000).astype(np.int32)
+    col = rng.integers(0, n, size=4000).astype(np.int32)
+    src = np.concatenate([src, src[:300], col[:200], [7]]).astype(np.int32)
+    col = np.concatenate([col, col[:300], src[:200], [7]]).astype(np.int32)
+    order = np.argsort(src, kind="stable")
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, src + 1, 1)
+    rp = np.cumsum(rp)
+    p = sng.Params(eps=1.0, min_pts=17, m=1, degree_mode=2)
+    labels, core, st = sng.cluster_edges(n, torch.from_numpy(src[order]).cuda(),
+                                         torch.from_numpy(col[order]).cuda(), None, p,
+                                         want_core=True)
+    r = orc.cluster_graph(n, rp, col[order], 17, deg_mode=2)
+    np.testing.assert_array_equal(core.cpu().numpy(), r["core"])
+    np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
+    assert 0 < r["core"].sum() < n
 
 
 def test_config_small_2d_mixture(orc):
@@ -139,6 +175,10 @@ def test_sample_all_equals_textbook_dbscan(orc, seed, n, d, m_db):
     labels, st = sng.cluster(torch.from_numpy(x).cuda(), p)
     bl, _ = orc.dbscan_bruteforce(x, eps, m_db)
     np.testing.assert_array_equal(labels.cpu().numpy(), bl)
+    # simple-graph degree counts each neighbour once: MinPts = min_samples - 1
+    p2 = sng.Params(eps=eps, min_pts=m_db - 1, sample_mode=1, degree_mode=2)
+    labels2, _ = sng.cluster(torch.from_numpy(x).cuda(), p2)
+    np.testing.assert_array_equal(labels2.cpu().numpy(), bl)
 
 
 def test_integer_grid_ties_at_eps(orc):

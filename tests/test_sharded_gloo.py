@@ -19,8 +19,10 @@ N, D, M, EPS, MINPTS, SEED = 3000, 3, 60, 0.05, 4, 7
 class OracleCompute:
     """Oracle-backed stand-in for GpuCompute (CPU tensors)."""
 
-    def __init__(self, x):
+    def __init__(self, x, deg_mode=0):
         self.x = x
+        self.deg_mode = deg_mode
+        self.simple_degree = deg_mode == 2
 
     def local_graph(self, lo, hi):
         import torch
@@ -41,8 +43,11 @@ class OracleCompute:
         rp = np.zeros(n + 1, dtype=np.int64)
         np.add.at(rp, s + 1, 1)
         rp = np.cumsum(rp)
-        r = oracle.cluster_graph(n, rp, c[order], MINPTS)
-        np.testing.assert_array_equal(r["deg"], deg.numpy())   # all-reduced degrees
+        r = oracle.cluster_graph(n, rp, c[order], MINPTS, deg_mode=self.deg_mode)
+        if deg is None:
+            assert self.simple_degree     # simple degrees come from the edges
+        else:
+            np.testing.assert_array_equal(r["deg"], deg.numpy())   # all-reduced degrees
         return r["labels"], r["core"]
 
 
@@ -54,13 +59,13 @@ def _free_port():
     return p
 
 
-def _worker(rank, world, port, out):
+def _worker(rank, world, port, out, deg_mode=0):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     x = datagen.random_points(N, D, seed=SEED)
-    labels, core, (src, col) = cluster_sharded(OracleCompute(x), N)
+    labels, core, (src, col) = cluster_sharded(OracleCompute(x, deg_mode), N)
     np.savez(f"{out}.{rank}.npz", labels=labels, core=core, src=src.numpy(), col=col.numpy())
     dist.barrier()
     dist.destroy_process_group()
@@ -74,14 +79,16 @@ def test_row_ranges_cover_rows():
             assert all(a[1] == b[0] for a, b in zip(r, r[1:]))
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_sharded_ranks_match_single_process(tmp_path, orc, world):
+@pytest.mark.parametrize("world,deg_mode", [(2, 0), (3, 0), (2, 2)])
+def test_sharded_ranks_match_single_process(tmp_path, orc, world, deg_mode):
+    """deg_mode 2 (distinct neighbours) skips the degree all-reduce: every rank
+    counts degrees from the gathered edge list."""
     mp = pytest.importorskip("torch.multiprocessing")
     out = str(tmp_path / "res")
-    mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world,
+    mp.start_processes(_worker, args=(world, _free_port(), out, deg_mode), nprocs=world,
                        start_method="spawn")
     x = datagen.random_points(N, D, seed=SEED)
-    want = orc.cluster(x, EPS, SEED, M, MINPTS)
+    want = orc.cluster(x, EPS, SEED, M, MINPTS, deg_mode=deg_mode)
     rp, col, _, _ = orc.build_rows(x, EPS, SEED, M)
     for r in range(world):
         got = np.load(f"{out}.{r}.npz")

@@ -53,3 +53,10 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     rc, _, _ = _noalloc(sng, torch, x, sng.Params(eps=0.3, min_pts=4, m=512, seed=1))
     assert rc == sng.SNG_EINVAL
     assert "scratch" in sng.last_error()
+
+
+def test_noalloc_rejects_simple_degree():
+    torch, sng = need_gpu()
+    x = torch.zeros((1000, 3), device="cuda")
+    rc, _, _ = _noalloc(sng, torch, x, sng.Params(eps=0.3, min_pts=4, m=16, degree_mode=2))
+    assert rc == sng.SNG_EINVAL
