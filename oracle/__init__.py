@@ -48,7 +48,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, _SRC]
+           "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -83,6 +83,13 @@ def _load():
         lib.orc_build_rows_m.argtypes = [i64, i32, i64, P, f32, u64, i64, i32, f64, P, i64,
                                          ctypes.POINTER(_Graph), P, P]
         lib.orc_build_rows_m.restype = i32
+        lib.orc_build_rows_metric.argtypes = [i64, i32, i64, P, f32, u64, i64, i32, f64, P, i64,
+                                              ctypes.POINTER(_Graph), P, P, i32]
+        lib.orc_build_rows_metric.restype = i32
+        lib.orc_dot.argtypes = [P, P, i32]
+        lib.orc_dot.restype = f64
+        lib.orc_cosine.argtypes = [P, P, i32]
+        lib.orc_cosine.restype = f64
         lib.orc_cluster_graph_forced.argtypes = [i64, P, P, i32, i32, P, P, P, P, P]
         lib.orc_cluster_graph_forced.restype = i32
         lib.orc_cluster_graph_gated.argtypes = [i64, P, P, i32, i32, P, P, P, P, P, P]
@@ -102,6 +109,9 @@ def _load():
         lib.orc_cluster.argtypes = [i64, i32, i64, P, f32, u64, i64, i32, i32, i32, f64, P, P,
                                     P, P, P]
         lib.orc_cluster.restype = i32
+        lib.orc_cluster_metric.argtypes = [i64, i32, i64, P, f32, u64, i64, i32, i32, i32, f64,
+                                           P, P, P, P, P, i32]
+        lib.orc_cluster_metric.restype = i32
         lib.orc_dbscan_bruteforce.argtypes = [i64, i32, i64, P, f32, i32, P, P]
         lib.orc_dbscan_bruteforce.restype = i32
         _lib = lib
@@ -146,12 +156,33 @@ def dist2(a, b) -> float:
     return float(_load().orc_dist2(_ptr(a), _ptr(b), a.size))
 
 
+# neighbourhood tests: Euclidean ball, inner product, cosine similarity
+METRIC_L2, METRIC_DOT, METRIC_COSINE = 0, 1, 2
+
+
+def dot(a, b) -> float:
+    """FP64 inner product, products and sums left to right, unfused."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    return float(_load().orc_dot(_ptr(a), _ptr(b), a.size))
+
+
+def cosine(a, b) -> float:
+    """FP64 cosine similarity <a,b> / (sqrt(<a,a>) sqrt(<b,b>)); NaN when
+    either vector is zero."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    return float(_load().orc_cosine(_ptr(a), _ptr(b), a.size))
+
+
 # ------------------------------------------------------------ graph build
 
 def build_rows(x, eps: float, seed: int, m: int, sample_all: bool = False,
-               band_rel: float = 1e-5, rows=None, m_row=None):
+               band_rel: float = 1e-5, rows=None, m_row=None, metric: int = METRIC_L2):
     """Algorithm 1, step 2 for the given rows (default all).  ``m_row`` (int32
     per point) limits point i to its first m_row[i] draws (surrogate form).
+    ``metric``: METRIC_L2 (edge iff d2 <= eps^2), METRIC_DOT / METRIC_COSINE
+    (edge iff similarity >= eps).
 
     Returns ``(row_ptr int64[nr+1], col int32[E], band_pairs, band_point uint8[n])``.
     """
@@ -165,9 +196,9 @@ def build_rows(x, eps: float, seed: int, m: int, sample_all: bool = False,
         rows_arr = np.ascontiguousarray(rows, dtype=np.int64)
         nr, rp = rows_arr.size, _ptr(rows_arr)
     mr = None if m_row is None else np.ascontiguousarray(m_row, dtype=np.int32)
-    rc = lib.orc_build_rows_m(n, d, ld, _ptr(x), ctypes.c_float(eps), seed & (2**64 - 1), m,
-                              int(sample_all), band_rel, rp, nr, ctypes.byref(g), _ptr(bp),
-                              _ptr(mr) if mr is not None else None)
+    rc = lib.orc_build_rows_metric(n, d, ld, _ptr(x), ctypes.c_float(eps), seed & (2**64 - 1),
+                                   m, int(sample_all), band_rel, rp, nr, ctypes.byref(g),
+                                   _ptr(bp), _ptr(mr) if mr is not None else None, metric)
     if rc != 0:
         raise ValueError("orc_build_rows failed (bad arguments or out of memory)")
     try:
@@ -240,7 +271,7 @@ def cluster_graph(n: int, row_ptr, col, min_pts: int, deg_mode: int = 0, forced=
 
 
 def cluster(x, eps: float, seed: int, m: int, min_pts: int, deg_mode: int = 0,
-            sample_all: bool = False, band_rel: float = 1e-5) -> dict:
+            sample_all: bool = False, band_rel: float = 1e-5, metric: int = METRIC_L2) -> dict:
     """The whole of Algorithm 1 in FP64.  Returns labels (int32, -1 noise, else
     the smallest core index of the cluster), core mask, degrees, band points
     and the counters (queries, kept edges, band pairs/points, cores, clusters,
@@ -251,9 +282,10 @@ def cluster(x, eps: float, seed: int, m: int, min_pts: int, deg_mode: int = 0,
     deg = np.empty(n, dtype=np.int32)
     bp = np.zeros(n, dtype=np.uint8)
     stats = np.zeros(8, dtype=np.int64)
-    rc = _load().orc_cluster(n, d, ld, _ptr(x), ctypes.c_float(eps), seed & (2**64 - 1), m,
-                             int(sample_all), deg_mode, min_pts, band_rel, _ptr(labels),
-                             _ptr(core), _ptr(deg), _ptr(bp), _ptr(stats))
+    rc = _load().orc_cluster_metric(n, d, ld, _ptr(x), ctypes.c_float(eps), seed & (2**64 - 1),
+                                    m, int(sample_all), deg_mode, min_pts, band_rel,
+                                    _ptr(labels), _ptr(core), _ptr(deg), _ptr(bp), _ptr(stats),
+                                    metric)
     if rc != 0:
         raise ValueError("orc_cluster failed (bad arguments or out of memory)")
     return dict(labels=labels, core=core, deg=deg, band_point=bp, queries=int(stats[0]),

@@ -38,6 +38,7 @@
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math -fPIC -shared.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -119,6 +120,10 @@ int32_t orc_build_rows_m(int64_t n, int32_t d, int64_t ld, const float *x, float
                          uint64_t seed, int64_t m, int32_t sample_all, double band_rel,
                          const int64_t *rows, int64_t n_rows, orc_graph *out,
                          uint8_t *band_point, const int32_t *m_row);
+int32_t orc_build_rows_metric(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
+                              uint64_t seed, int64_t m, int32_t sample_all, double band_rel,
+                              const int64_t *rows, int64_t n_rows, orc_graph *out,
+                              uint8_t *band_point, const int32_t *m_row, int32_t metric);
 
 int32_t orc_build_rows(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
                        uint64_t seed, int64_t m, int32_t sample_all, double band_rel,
@@ -140,11 +145,51 @@ int32_t orc_build_rows_m(int64_t n, int32_t d, int64_t ld, const float *x, float
                          const int64_t *rows, int64_t n_rows, orc_graph *out,
                          uint8_t *band_point, const int32_t *m_row)
 {
+    return orc_build_rows_metric(n, d, ld, x, eps, seed, m, sample_all, band_rel, rows, n_rows,
+                                 out, band_point, m_row, 0);
+}
+
+/* Inner product <a, b> in FP64: products and sums left to right, each
+ * operation rounded on its own. */
+double orc_dot(const float *a, const float *b, int32_t d)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < d; ++k) {
+        double t = (double)a[k] * (double)b[k];
+        s = s + t;
+    }
+    return s;
+}
+
+/* Cosine similarity <a, b> / (|a| |b|): the inner product and both squared
+ * norms as in orc_dot, then sqrt(|a|^2) * sqrt(|b|^2), the quotient last; a
+ * zero vector gives NaN, which is never similar to anything. */
+double orc_cosine(const float *a, const float *b, int32_t d)
+{
+    double ab = orc_dot(a, b, d);
+    double aa = orc_dot(a, a, d);
+    double bb = orc_dot(b, b, d);
+    double den = sqrt(aa) * sqrt(bb);
+    return ab / den;
+}
+
+/* Algorithm 1, step 2 with the neighbourhood test of `metric`: 0 = Euclidean
+ * ball (d2 <= eps^2, band |d2 - eps^2| <= band_rel eps^2); 1 = inner product,
+ * 2 = cosine similarity (edge iff sim >= eps, band |sim - eps| <= band_rel
+ * |eps|). */
+int32_t orc_build_rows_metric(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
+                              uint64_t seed, int64_t m, int32_t sample_all, double band_rel,
+                              const int64_t *rows, int64_t n_rows, orc_graph *out,
+                              uint8_t *band_point, const int32_t *m_row, int32_t metric)
+{
     if (n < 2 || d < 1 || ld < d || m < 0 || !out) return -1;
     if (sample_all && m != n - 1) return -1;
+    if (metric < 0 || metric > 2) return -1;
     if (!rows) n_rows = n;
     double eps2 = (double)eps * (double)eps;
     double band = band_rel * eps2;
+    double tau = (double)eps;
+    if (metric != 0) band = band_rel * fabs(tau);
     int64_t cap = 1024, e = 0;
     int32_t *col = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
     int64_t *row_ptr = (int64_t *)malloc((size_t)(n_rows + 1) * sizeof(int64_t));
@@ -158,14 +203,23 @@ int32_t orc_build_rows_m(int64_t n, int32_t d, int64_t ld, const float *x, float
         if (mi > m) mi = m;
         for (int64_t j = 0; j < mi; ++j) {
             int64_t p = orc_partner(seed, i, j, n, sample_all);
-            double d2 = orc_dist2(xi, x + p * ld, d);
-            double gap = d2 - eps2;
+            double v, gap;
+            int keep;
+            if (metric == 0) {
+                v = orc_dist2(xi, x + p * ld, d);
+                gap = v - eps2;
+                keep = v <= eps2;
+            } else {
+                v = metric == 1 ? orc_dot(xi, x + p * ld, d) : orc_cosine(xi, x + p * ld, d);
+                gap = v - tau;
+                keep = v >= tau;
+            }
             if (gap < 0) gap = -gap;
             if (gap <= band) {
                 ++band_pairs;
                 if (band_point) { band_point[i] = 1; band_point[p] = 1; }
             }
-            if (d2 <= eps2) {
+            if (keep) {
                 if (e == cap) {
                     cap *= 2;
                     int32_t *nc = (int32_t *)realloc(col, (size_t)cap * sizeof(int32_t));
@@ -447,16 +501,33 @@ int32_t orc_cluster_graph_gated(int64_t n, const int64_t *row_ptr, const int32_t
  * components (step 3), borders and noise (steps 4-5).  labels, core (length n)
  * are outputs; deg may be NULL; band_point (length n) may be NULL.
  */
+int32_t orc_cluster_metric(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
+                           uint64_t seed, int64_t m, int32_t sample_all, int32_t deg_mode,
+                           int32_t min_pts, double band_rel, int32_t *labels, uint8_t *core,
+                           int32_t *deg, uint8_t *band_point, int64_t *stats, int32_t metric);
+
 int32_t orc_cluster(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
                     uint64_t seed, int64_t m, int32_t sample_all, int32_t deg_mode,
                     int32_t min_pts, double band_rel, int32_t *labels, uint8_t *core,
                     int32_t *deg, uint8_t *band_point, int64_t *stats)
 {
+    return orc_cluster_metric(n, d, ld, x, eps, seed, m, sample_all, deg_mode, min_pts,
+                              band_rel, labels, core, deg, band_point, stats, 0);
+}
+
+/* The whole of Algorithm 1 with the neighbourhood test of `metric` (see
+ * orc_build_rows_metric). */
+int32_t orc_cluster_metric(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
+                           uint64_t seed, int64_t m, int32_t sample_all, int32_t deg_mode,
+                           int32_t min_pts, double band_rel, int32_t *labels, uint8_t *core,
+                           int32_t *deg, uint8_t *band_point, int64_t *stats, int32_t metric)
+{
     orc_graph g;
     uint8_t *bp = band_point ? band_point : (uint8_t *)calloc((size_t)n, 1);
     if (!bp) return -1;
     if (band_point) memset(bp, 0, (size_t)n);
-    if (orc_build_rows(n, d, ld, x, eps, seed, m, sample_all, band_rel, NULL, 0, &g, bp)) {
+    if (orc_build_rows_metric(n, d, ld, x, eps, seed, m, sample_all, band_rel, NULL, 0, &g, bp,
+                              NULL, metric)) {
         if (!band_point) free(bp);
         return -1;
     }
