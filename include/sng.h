@@ -74,6 +74,14 @@ typedef int32_t sng_status;
 #define SNG_SAMPLE_ALL 1    /* every other point once (m = n-1): s = 1, textbook
                                DBSCAN's full eps-neighbourhood graph           */
 
+/* neighbourhood test of Algorithm 1, step 2 (the method needs only
+ * similarity queries, Section 1).  FP32 inputs: every decision equals the
+ * FP64 result computed in the stated order (unfused, left to right). */
+#define SNG_METRIC_L2 0     /* edge iff sum_k (a_k - b_k)^2 <= eps^2          */
+#define SNG_METRIC_DOT 1    /* edge iff <a, b> >= eps                          */
+#define SNG_METRIC_COSINE 2 /* edge iff <a, b> / (sqrt(<a,a>) sqrt(<b,b>)) >= eps;
+                               a zero vector is similar to nothing            */
+
 /* flags */
 #define SNG_FLAG_TIMING 1u  /* fill sng_stats.ms with per-phase CUDA-event times */
 #define SNG_FLAG_PREFETCH 2u /* gather: bulk-prefetch partner rows into L2 one stage
@@ -87,9 +95,12 @@ typedef struct {
     int32_t degree_mode;  /* SNG_DEG_*                                       */
     int32_t sample_mode;  /* SNG_SAMPLE_*                                    */
     int32_t min_pts;      /* MinPts, >= 1                                    */
-    float eps;            /* radius, finite, 1e-15 <= eps <= 1e18            */
+    float eps;            /* SNG_METRIC_L2: radius, 1e-15 <= eps <= 1e18;
+                             SNG_METRIC_DOT / _COSINE: similarity threshold,
+                             any finite value                               */
     float band_rel;       /* half-width of the reported band |d2-eps^2| <=
-                             band_rel*eps^2; 0 selects 1e-5 (F32) / 1e-3 (BF16) */
+                             band_rel*eps^2 (similarity: |sim-eps| <=
+                             band_rel*|eps|); 0 selects 1e-5 (F32) / 1e-3 (BF16) */
     double s;             /* sampling rate in (0, 1]; m = ceil(s*n)          */
     int64_t m_override;   /* > 0: use this m instead of ceil(s*n)            */
     uint64_t seed;        /* partner-hash seed                               */
@@ -104,7 +115,8 @@ typedef struct {
     int32_t map_passes;   /* gather: 0/1 = one pass over all partners; k > 1 = k
                              launches, each testing only the draws whose partner
                              lies in one of k equal slices of X (L2-resident) */
-    int32_t reserved0;
+    int32_t metric;       /* SNG_METRIC_*; similarity metrics in sng_cluster and
+                             sng_build_graph only, one pass (map_passes <= 1) */
     /* Source rows [row_begin, row_end) draw partners; 0, 0 = all rows.  Other
      * rows draw nothing (their CSR rows are empty) but still receive
      * in-degree from the rows that do: a shard of step 2 for multi-GPU runs

@@ -27,6 +27,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libsng.so")
 SNG_OK, SNG_EINVAL, SNG_ENOMEM, SNG_ECUDA, SNG_ETIMEOUT, SNG_EINTERNAL = 0, -1, -2, -3, -4, -5
 SNG_F32, SNG_BF16 = 0, 1
 SNG_DEG_UNDIRECTED_MULTI, SNG_DEG_OUT, SNG_DEG_SIMPLE = 0, 1, 2
+SNG_METRIC_L2, SNG_METRIC_DOT, SNG_METRIC_COSINE = 0, 1, 2
 SNG_SAMPLE_HASH, SNG_SAMPLE_ALL = 0, 1
 SNG_FLAG_TIMING = 1
 SNG_FLAG_PREFETCH = 2
@@ -49,7 +50,7 @@ class sng_params(ctypes.Structure):
                 ("x_f32_master", ctypes.c_void_p), ("flags", ctypes.c_uint32),
                 ("map_group", ctypes.c_int32), ("map_unroll", ctypes.c_int32),
                 ("map_block", ctypes.c_int32), ("map_tile", ctypes.c_int32),
-                ("map_passes", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("map_passes", ctypes.c_int32), ("metric", ctypes.c_int32),
                 ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64)]
 
 
@@ -201,6 +202,7 @@ class Params:
     map_passes: int = 0
     row_begin: int = 0
     row_end: int = 0
+    metric: int = 0             # SNG_METRIC_*: 0 Euclidean ball, 1 inner product, 2 cosine
 
     def to_c(self, n: int, d: int, ld: int, dtype: int, master_ptr: int = 0) -> sng_params:
         p = sng_params()
@@ -214,6 +216,7 @@ class Params:
         p.map_tile = self.map_tile
         p.map_passes = self.map_passes
         p.row_begin, p.row_end = self.row_begin, self.row_end
+        p.metric = self.metric
         return p
 
     def draws(self, n: int) -> int:

@@ -114,8 +114,14 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   if (p->sample_mode != SNG_SAMPLE_HASH && p->sample_mode != SNG_SAMPLE_ALL)
     return fail(SNG_EINVAL, "unknown sample_mode");
   if (p->min_pts < 1) return fail(SNG_EINVAL, "min_pts must be >= 1");
-  if (!std::isfinite(p->eps) || p->eps < 1e-15f || p->eps > 1e18f)
-    return fail(SNG_EINVAL, "eps must be finite and in [1e-15, 1e18]");
+  if (p->metric != SNG_METRIC_L2 && p->metric != SNG_METRIC_DOT &&
+      p->metric != SNG_METRIC_COSINE)
+    return fail(SNG_EINVAL, "unknown metric");
+  if (!std::isfinite(p->eps)) return fail(SNG_EINVAL, "eps must be finite");
+  if (p->metric == SNG_METRIC_L2 && (p->eps < 1e-15f || p->eps > 1e18f))
+    return fail(SNG_EINVAL, "eps must be in [1e-15, 1e18]");
+  if (p->metric != SNG_METRIC_L2 && p->map_passes > 1)
+    return fail(SNG_EINVAL, "the similarity form runs in one pass (map_passes <= 1)");
   if (!(p->band_rel >= 0.f) || p->band_rel > 0.25f)
     return fail(SNG_EINVAL, "band_rel must be in [0, 0.25]");
   const size_t esize = p->dtype == SNG_F32 ? 4 : 2;
@@ -180,6 +186,7 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   r->map.vec = vec;
   r->map.group = group;
   r->map.nch = nch;
+  r->map.sim = p->metric != SNG_METRIC_L2;
   r->map.unroll = p->map_unroll > 0 ? p->map_unroll : (vec == vmax && nch * vec >= 16 ? 2 : 4);
   if (p->map_passes < 0 || p->map_passes > 64) return fail(SNG_EINVAL, "map_passes must be in [0, 64]");
   r->map.passes = p->map_passes > 0 ? p->map_passes : 1;
@@ -215,6 +222,32 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   if ((double)hif < hi) hif = std::nextafter(hif, INFINITY);
   r->lo_thr = lof;
   r->hi_thr = hif;
+
+  // similarity form: |dot32 - dot| <= (K + 1) u sum|a_k b_k| with K roundings
+  // per term (nch*vec fused multiply-adds, log2 group shuffle levels); the
+  // FP32 sum S of |a_k b_k| carries the same relative error, so c1 S with c1
+  // doubled (plus slack for the FP64 result's own rounding) bounds it.  For
+  // cosine each FP32 inverse norm (a warp sum of ceil(d/32) + 5 roundings,
+  // a square root and a quotient) is within e_inv relative, so the two norms
+  // and two products add c2 |dot32|.  Underflowing products add at most
+  // K 2^-150 in absolute terms: sim_abs.  All constants are rounded up.
+  r->metric = p->metric;
+  if (p->metric != SNG_METRIC_L2) {
+    const double tau = (double)p->eps;
+    r->band = (double)r->band_rel * std::fabs(tau);
+    const double c1 = 2.0 * (double)(nch * vec + lg + 3) * u + std::ldexp(1.0, -22);
+    const double e_inv = (double)((p->d + 31) / 32 + 8) * u;
+    const double c2 = p->metric == SNG_METRIC_COSINE ? 2.0 * (2.0 * e_inv + 3.0 * u) : 0.0;
+    auto up = [](double v) {
+      float f = (float)v;
+      if ((double)f < v) f = std::nextafter(f, INFINITY);
+      return f;
+    };
+    r->sim_c1 = up(c1);
+    r->sim_c2 = up(c2);
+    r->sim_abs = std::ldexp(1.0f, -120);
+    r->band_f = up(r->band);
+  }
   return SNG_OK;
 }
 
@@ -239,6 +272,14 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
   g->deg_mode = p->degree_mode;
   g->m_row = nullptr;
   g->w_row = nullptr;
+  g->cosine = p->metric == SNG_METRIC_COSINE;
+  g->tau = p->eps;
+  g->tau64 = (double)p->eps;
+  g->sim_c1 = r.sim_c1;
+  g->sim_c2 = r.sim_c2;
+  g->sim_abs = r.sim_abs;
+  g->band_f = r.band_f;
+  g->inv_norm = nullptr;   // set by run_graph for cosine
   // L2 prefetch of partner rows when rows start on 16 bytes (16-byte vectors)
   const int esize = p->dtype == SNG_F32 ? 4 : 2;
   g->pf_bytes = 0;
@@ -299,6 +340,12 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   fill_gather_args(x, p, r, &ga);
   ga.m_row = m_row;
   ga.w_row = w_row;
+  if (p->metric == SNG_METRIC_COSINE) {
+    float *inv = nullptr;
+    if ((rc = s.alloc((void **)&inv, (size_t)n * 4, "inverse norms"))) return rc;
+    launch_inv_norm(p->dtype, x, p->ld, n, p->d, inv, st);
+    ga.inv_norm = inv;
+  }
   ga.bitmask = gb->bitmask;
   ga.out_cnt = gb->out_cnt;
   ga.deg = gb->deg;

@@ -17,6 +17,9 @@ struct Resolved {
   float band_rel = 0.f;
   double eps2 = 0.0, band = 0.0;
   float lo_thr = 0.f, hi_thr = 0.f;
+  // similarity form (metric != SNG_METRIC_L2): constants of the FP32 screen
+  int32_t metric = 0;
+  float sim_c1 = 0.f, sim_c2 = 0.f, sim_abs = 0.f, band_f = 0.f;
   GatherMap map{};
 };
 

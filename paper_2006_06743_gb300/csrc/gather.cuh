@@ -19,6 +19,12 @@
 // the FP64 decision on every pair.  For BF16 inputs the band is a heuristic
 // (quantisation error is not bounded by it) and the recheck reads the FP32
 // master copy.
+//
+// Similarity form (SIM = true; inner product or cosine, edge iff sim >= tau):
+// the lanes also accumulate sum |a_k b_k|, which bounds the FP32 error of the
+// inner product (one rounding per fused multiply-add and per shuffle level),
+// so each pair gets its own certified band; cosine scales both by the FP32
+// inverse norms of the two rows, whose own error enters through |<a,b>|.
 #pragma once
 
 #include "sng_internal.cuh"
@@ -36,7 +42,15 @@ struct GatherArgs {
   FastMod fm;
   float lo_thr, hi_thr;   // d2 < lo_thr: keep; d2 > hi_thr: drop; else FP64
   double eps2;            // (double)eps * (double)eps
-  double band;            // band_rel * eps2 (reported band half-width)
+  double band;            // band_rel * eps2 (reported band half-width;
+                          // band_rel * |tau| in the similarity form)
+  // similarity form: keep iff sim >= tau.  Certified outside
+  // |sim32 - tau| <= sim_c1 * S + sim_c2 * |dot32| (cosine: both times
+  // inv_i * inv_p) + sim_abs + band_f, S = FP32 sum of |a_k b_k|.
+  int32_t cosine;         // 1: cosine (needs inv_norm), 0: inner product
+  float tau, sim_c1, sim_c2, sim_abs, band_f;
+  double tau64;
+  const float *inv_norm;  // cosine: FP32 1/|x_i| per row
   int32_t sample_all;
   int32_t deg_mode;
   const int32_t *m_row;   // nullable: draws of row i (<= m)
@@ -50,6 +64,29 @@ struct GatherArgs {
   uint8_t *band_flag;     // n
   unsigned long long *counters;
 };
+
+// Similarity in FP64 in the oracle's order: inner product and squared norms
+// left to right, unfused; cosine = <a,b> / (sqrt(<a,a>) * sqrt(<b,b>)).
+__device__ __forceinline__ bool recheck_sim(const GatherArgs &a, int32_t i, int32_t p) {
+  const float *xa = a.xm + (int64_t)i * a.ldm, *xb = a.xm + (int64_t)p * a.ldm;
+  double ab = 0.0, aa = 0.0, bb = 0.0;
+  for (int k = 0; k < a.d; ++k) {
+    const double u = (double)xa[k], v = (double)xb[k];
+    ab = __dadd_rn(ab, __dmul_rn(u, v));
+    if (a.cosine) {
+      aa = __dadd_rn(aa, __dmul_rn(u, u));
+      bb = __dadd_rn(bb, __dmul_rn(v, v));
+    }
+  }
+  const double s = a.cosine ? __ddiv_rn(ab, __dmul_rn(__dsqrt_rn(aa), __dsqrt_rn(bb))) : ab;
+  atomicAdd(a.counters + kCntRecheck, 1ull);
+  if (fabs(__dsub_rn(s, a.tau64)) <= a.band) {
+    atomicAdd(a.counters + kCntBandPairs, 1ull);
+    a.band_flag[i] = 1;
+    a.band_flag[p] = 1;
+  }
+  return s >= a.tau64;
+}
 
 template <typename T>
 __device__ __forceinline__ bool recheck_pair(const GatherArgs &a, int32_t i, int32_t p) {
@@ -94,7 +131,7 @@ __device__ __forceinline__ void stage_partners(const GatherArgs &a, int32_t i, u
 // in-degree atomics; returns the row's kept count (same value on all lanes).
 // `sp` is this warp's 2*32*U-entry shared-memory partner buffer: the stage
 // being tested and the next one, hashed (and prefetched) one stage ahead.
-template <typename T, int VEC, int G, int NCH, int U>
+template <typename T, int VEC, int G, int NCH, int U, bool SIM = false>
 __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_t mi,
                                           int32_t *sp, int lane) {
   constexpr int R = 32 / G;      // pairs per warp step
@@ -123,6 +160,8 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
     }
   }
 
+  const float inv_i = (SIM && a.cosine) ? a.inv_norm[i] : 1.f;
+
   int cnt = 0;
   int jb = 0;
   int32_t *cur = sp, *nxt = sp + S;
@@ -135,11 +174,13 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
     for (int t0 = 0; t0 < STEPS; t0 += U) {
       typename Raw<T, VEC>::type v[U][NCH];
       int32_t pv[U];
+      float ipv[U];   // similarity form, cosine: partner's inverse norm
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int t = t0 + u;
         const int32_t p = cur[t * R + grp];
         pv[u] = p;
+        if constexpr (SIM) ipv[u] = (a.cosine && gl == 0 && p >= 0) ? __ldg(a.inv_norm + p) : 1.f;
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
@@ -151,33 +192,67 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
       for (int u = 0; u < U; ++u) {
         const int t = t0 + u;
         float acc = 0.f;
+        float sacc = 0.f;   // similarity form: sum of |a_k b_k|
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
           if (off + VEC <= d) {
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
-              const float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
-              acc = fmaf(diff, diff, acc);
+              if constexpr (SIM) {
+                const float b = Raw<T, VEC>::get(v[u][c], k);
+                acc = fmaf(xi[c][k], b, acc);
+                sacc = fmaf(fabsf(xi[c][k]), fabsf(b), sacc);
+              } else {
+                const float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
+                acc = fmaf(diff, diff, acc);
+              }
             }
           } else {
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
-              float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
-              if (off + k >= d) diff = 0.f;
-              acc = fmaf(diff, diff, acc);
+              if constexpr (SIM) {
+                float b = Raw<T, VEC>::get(v[u][c], k);
+                if (off + k >= d) b = 0.f;   // row padding may hold anything
+                acc = fmaf(xi[c][k], b, acc);
+                sacc = fmaf(fabsf(xi[c][k]), fabsf(b), sacc);
+              } else {
+                float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
+                if (off + k >= d) diff = 0.f;
+                acc = fmaf(diff, diff, acc);
+              }
             }
           }
         }
 #pragma unroll
-        for (int o = G / 2; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+        for (int o = G / 2; o >= 1; o >>= 1) {
+          acc += __shfl_xor_sync(kFullMask, acc, o);
+          if constexpr (SIM) sacc += __shfl_xor_sync(kFullMask, sacc, o);
+        }
         bool keep = false;
         const int32_t p = pv[u];
         if (gl == 0 && p >= 0) {
-          if (acc < a.lo_thr) {
-            keep = true;
-          } else if (!(acc > a.hi_thr)) {
-            keep = recheck_pair<T>(a, i, p);
+          if constexpr (SIM) {
+            float sim = acc;
+            float err = a.sim_c1 * sacc + a.sim_c2 * fabsf(acc);
+            if (a.cosine) {
+              const float w = inv_i * ipv[u];
+              sim = (acc * inv_i) * ipv[u];
+              err = err * w;
+            }
+            err = err + a.sim_abs + a.band_f;
+            // NaN (zero or non-finite rows) certifies nothing: FP64 decides
+            if (sim - err >= a.tau) {
+              keep = true;
+            } else if (!(sim + err < a.tau)) {
+              keep = recheck_sim(a, i, p);
+            }
+          } else {
+            if (acc < a.lo_thr) {
+              keep = true;
+            } else if (!(acc > a.hi_thr)) {
+              keep = recheck_pair<T>(a, i, p);
+            }
           }
           if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
         }
@@ -229,7 +304,7 @@ struct MinBlocks {
   static constexpr int value = words <= 32 ? 4 : (words <= 56 ? 3 : 2);
 };
 
-template <typename T, int VEC, int G, int NCH, int U>
+template <typename T, int VEC, int G, int NCH, int U, bool SIM = false>
 __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value) gather_kernel(GatherArgs a) {
   extern __shared__ int32_t smem_partner[];
   const int lane = threadIdx.x & 31;
@@ -240,7 +315,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value) gather_
        row < a.row_end; row += warps_total) {
     const int32_t i = (int32_t)row;
     const int32_t mi = a.m_row ? a.m_row[i] : a.m;
-    gather_row<T, VEC, G, NCH, U>(a, i, mi, sp, lane);
+    gather_row<T, VEC, G, NCH, U, SIM>(a, i, mi, sp, lane);
   }
 }
 
@@ -379,9 +454,14 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
 struct GatherMap {
   int vec, group, nch, unroll, block;
   int passes;   // 1: single pass; > 1: L2-blocked slices of the partner range
+  int sim;      // 1: similarity form (inner product / cosine) of the kernel
 };
 
 // Host-side launcher; returns false if no compiled variant matches `map`.
+// Cosine form: out[i] = 1 / sqrt(sum_k x_ik^2) in FP32 (correctly rounded
+// square root and quotient), one warp per row; a zero row gives +inf.
+void launch_inv_norm(int dtype, const void *x, int64_t ld, int64_t n, int32_t d, float *out,
+                     cudaStream_t stream);
 bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
                    cudaStream_t stream);
 bool launch_gather_blocked(int dtype, const GatherMap &map, const GatherArgs &args, int grid,

@@ -7,21 +7,23 @@
 
 namespace sng {
 
-template <typename T, int VEC, int G, int NCH, int U>
+template <typename T, int VEC, int G, int NCH, int U, bool SIM = false>
 static bool try_launch(const GatherMap &m, const GatherArgs &args, int grid, cudaStream_t st) {
-  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return false;
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || (m.sim != 0) != SIM)
+    return false;
   const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
-  gather_kernel<T, VEC, G, NCH, U><<<grid, m.block, smem, st>>>(args);
+  gather_kernel<T, VEC, G, NCH, U, SIM><<<grid, m.block, smem, st>>>(args);
   return true;
 }
 
-template <typename T, int VEC, int G, int NCH, int U>
+template <typename T, int VEC, int G, int NCH, int U, bool SIM = false>
 static int occ_blocks(const GatherMap &m) {
-  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return -1;
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || (m.sim != 0) != SIM)
+    return -1;
   int blocks = 0;
   const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, gather_kernel<T, VEC, G, NCH, U>,
-                                                    m.block, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &blocks, gather_kernel<T, VEC, G, NCH, U, SIM>, m.block, smem) != cudaSuccess)
     return 0;
   return blocks;
 }
@@ -29,7 +31,7 @@ static int occ_blocks(const GatherMap &m) {
 template <typename T, int VEC, int G, int NCH, int U>
 static bool try_launch_blocked(const GatherMap &m, const GatherArgs &args, int grid, int32_t lo,
                                int32_t hi, cudaStream_t st) {
-  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return false;
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || m.sim) return false;
   const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
   gather_blocked_kernel<T, VEC, G, NCH, U><<<grid, m.block, smem, st>>>(args, lo, hi);
   return true;
@@ -37,7 +39,7 @@ static bool try_launch_blocked(const GatherMap &m, const GatherArgs &args, int g
 
 template <typename T, int VEC, int G, int NCH, int U>
 static int occ_blocks_blocked(const GatherMap &m) {
-  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return -1;
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || m.sim) return -1;
   int blocks = 0;
   const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -69,9 +71,9 @@ static int occ_blocks_blocked(const GatherMap &m) {
   X(T, V, 2, 8, U) X(T, V, 4, 2, U) X(T, V, 8, 4, U) X(T, V, 16, 4, U) X(T, V, 4, 8, U)  \
   X(T, V, 2, 4, U)
 
-template <int VEC, int G, int NCH, int U>
+template <int VEC, int G, int NCH, int U, bool SIM = false>
 static bool matches(const GatherMap &m) {
-  return m.vec == VEC && m.group == G && m.nch == NCH && m.unroll == U;
+  return m.vec == VEC && m.group == G && m.nch == NCH && m.unroll == U && (m.sim != 0) == SIM;
 }
 #define SNG_HAS(T, V, G, N, U) \
   if (matches<V, G, N, U>(map)) return true;
@@ -82,6 +84,17 @@ static bool matches(const GatherMap &m) {
   {                                            \
     int b = occ_blocks<T, V, G, N, U>(map);    \
     if (b >= 0) return b;                      \
+  }
+
+// similarity form (inner product / cosine)
+#define SNG_HAS_S(T, V, G, N, U) \
+  if (matches<V, G, N, U, true>(map)) return true;
+#define SNG_TRY_S(T, V, G, N, U) \
+  if (try_launch<T, V, G, N, U, true>(map, args, grid, stream)) return true;
+#define SNG_OCC_S(T, V, G, N, U)                    \
+  {                                                 \
+    int b = occ_blocks<T, V, G, N, U, true>(map);   \
+    if (b >= 0) return b;                           \
   }
 
 }  // namespace sng

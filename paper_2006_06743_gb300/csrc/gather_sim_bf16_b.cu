@@ -1,0 +1,29 @@
+// gather_sim_bf16_b.cu -- compiled BF16 similarity-form gather mappings: vec 4, 2, 1 x unroll 4
+// (the default mapping rule's vector widths and unrolls; split across
+// translation units so the library builds in parallel).
+#include "gather_inst.cuh"
+
+namespace sng {
+
+bool launch_sim_bf16_b(const GatherMap &map, const GatherArgs &args, int grid, cudaStream_t stream) {
+  SNG_SHAPES_U(uint16_t, 4, 4, SNG_TRY_S)
+  SNG_SHAPES_U(uint16_t, 2, 4, SNG_TRY_S)
+  SNG_SHAPES_U(uint16_t, 1, 4, SNG_TRY_S)
+  return false;
+}
+
+int occ_sim_bf16_b(const GatherMap &map) {
+  SNG_SHAPES_U(uint16_t, 4, 4, SNG_OCC_S)
+  SNG_SHAPES_U(uint16_t, 2, 4, SNG_OCC_S)
+  SNG_SHAPES_U(uint16_t, 1, 4, SNG_OCC_S)
+  return -1;
+}
+
+bool has_sim_bf16_b(const GatherMap &map) {
+  SNG_SHAPES_U(uint16_t, 4, 4, SNG_HAS_S)
+  SNG_SHAPES_U(uint16_t, 2, 4, SNG_HAS_S)
+  SNG_SHAPES_U(uint16_t, 1, 4, SNG_HAS_S)
+  return false;
+}
+
+}  // namespace sng

@@ -7,7 +7,12 @@ namespace sng {
   bool launch_##tag(const GatherMap &, const GatherArgs &, int, cudaStream_t); \
   int occ_##tag(const GatherMap &);
 SNG_UNIT(f32_a) SNG_UNIT(f32_b) SNG_UNIT(f32_c) SNG_UNIT(bf16_a) SNG_UNIT(bf16_b) SNG_UNIT(bf16_c)
+SNG_UNIT(sim_f32_a) SNG_UNIT(sim_f32_b) SNG_UNIT(sim_bf16_a) SNG_UNIT(sim_bf16_b)
 #undef SNG_UNIT
+bool has_sim_f32_a(const GatherMap &);
+bool has_sim_f32_b(const GatherMap &);
+bool has_sim_bf16_a(const GatherMap &);
+bool has_sim_bf16_b(const GatherMap &);
 bool has_f32_a(const GatherMap &);
 bool has_f32_b(const GatherMap &);
 bool has_f32_c(const GatherMap &);
@@ -18,6 +23,10 @@ bool has_gather_blocked_f32(const GatherMap &);
 bool has_gather_blocked_bf16(const GatherMap &);
 
 bool gather_is_compiled(int dtype, const GatherMap &map) {
+  if (map.sim) {
+    if (dtype == SNG_F32) return has_sim_f32_a(map) || has_sim_f32_b(map);
+    return has_sim_bf16_a(map) || has_sim_bf16_b(map);
+  }
   if (dtype == SNG_F32) return has_f32_a(map) || has_f32_b(map) || has_f32_c(map);
   return has_bf16_a(map) || has_bf16_b(map) || has_bf16_c(map);
 }
@@ -34,6 +43,11 @@ int occ_gather_blocked_bf16(const GatherMap &);
 
 bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
                    cudaStream_t stream) {
+  if (map.sim) {
+    if (dtype == SNG_F32)
+      return launch_sim_f32_a(map, args, grid, stream) || launch_sim_f32_b(map, args, grid, stream);
+    return launch_sim_bf16_a(map, args, grid, stream) || launch_sim_bf16_b(map, args, grid, stream);
+  }
   if (dtype == SNG_F32)
     return launch_f32_a(map, args, grid, stream) || launch_f32_b(map, args, grid, stream) ||
            launch_f32_c(map, args, grid, stream);
@@ -43,6 +57,14 @@ bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int 
 
 int gather_max_blocks_per_sm(int dtype, const GatherMap &map) {
   int b;
+  if (map.sim) {
+    if (dtype == SNG_F32) {
+      if ((b = occ_sim_f32_a(map)) >= 0 || (b = occ_sim_f32_b(map)) >= 0) return b;
+    } else {
+      if ((b = occ_sim_bf16_a(map)) >= 0 || (b = occ_sim_bf16_b(map)) >= 0) return b;
+    }
+    return 0;
+  }
   if (dtype == SNG_F32) {
     if ((b = occ_f32_a(map)) >= 0 || (b = occ_f32_b(map)) >= 0 || (b = occ_f32_c(map)) >= 0)
       return b;
@@ -65,6 +87,41 @@ int gather_blocked_max_blocks_per_sm(int dtype, const GatherMap &map) {
 
 size_t gather_smem_bytes(const GatherMap &map) {
   return (size_t)(map.block / 32) * 64 * map.unroll * sizeof(int32_t);
+}
+
+// --------------------------------------------------------- inverse norms
+
+template <typename T>
+__global__ void inv_norm_kernel(const T *x, int64_t ld, int64_t n, int32_t d, float *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+       i += warps) {
+    const T *row = x + i * ld;
+    float acc = 0.f;
+    for (int k = lane; k < d; k += 32) {
+      float v[1];
+      Chunk<T, 1>::load(row + k, v);
+      acc = fmaf(v[0], v[0], acc);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+    if (lane == 0) out[i] = __fdiv_rn(1.0f, __fsqrt_rn(acc));
+  }
+}
+
+void launch_inv_norm(int dtype, const void *x, int64_t ld, int64_t n, int32_t d, float *out,
+                     cudaStream_t stream) {
+  int64_t blocks = (n + 7) / 8;
+  const int64_t cap = (int64_t)device_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  if (dtype == SNG_F32)
+    inv_norm_kernel<float><<<(int)blocks, 256, 0, stream>>>(static_cast<const float *>(x), ld,
+                                                            n, d, out);
+  else
+    inv_norm_kernel<uint16_t><<<(int)blocks, 256, 0, stream>>>(
+        static_cast<const uint16_t *>(x), ld, n, d, out);
+  note_launch();
 }
 
 // ------------------------------------------------------------ partners

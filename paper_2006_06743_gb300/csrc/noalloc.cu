@@ -82,6 +82,8 @@ sng_status sng_cluster_noalloc(const float *x, const sng_params *params, int32_t
   if (rc) return rc;
   if (!labels) return fail(SNG_EINVAL, "labels is NULL");
   if (params->dtype != SNG_F32) return fail(SNG_EINVAL, "the no-allocation path takes FP32 points");
+  if (params->metric != SNG_METRIC_L2)
+    return fail(SNG_EINVAL, "the no-allocation path uses the Euclidean ball (metric 0)");
   if (params->degree_mode == SNG_DEG_SIMPLE)
     return fail(SNG_EINVAL, "simple-graph degree needs a pair set; not in the no-allocation path");
   if (r.row_begin != 0 || r.row_end != r.n)
