@@ -413,6 +413,57 @@ def bench_bf16(args):
             "steps": args.steps}
 
 
+def bench_cosine(args):
+    """Similarity form on the embedding workload: n = 5,000,000 unit vectors in
+    d = 128 (1000 centres on the sphere, per-coordinate sigma, renormalised),
+    m = 1000.  Cosine similarity >= 1 - eps^2/2 (eps = 0.6: the same graph as
+    the Euclidean ball of radius eps, up to rounding, for unit vectors) in
+    FP32 and BF16, the inner product in FP32, and the Euclidean form beside
+    them; default gather mappings."""
+    import numpy as np
+    import torch
+
+    import paper_2006_06743_gb300 as sng
+    from paper_2006_06743_gb300 import datagen
+    n, d, m = args.bf16_n, 128, 1000
+    x = datagen.sphere_embeddings(n, d, 1000, args.cos_sigma, seed=args.seed)
+    xf = torch.from_numpy(x).cuda()
+    del x
+    xb = xf.to(torch.bfloat16)
+    tau = float(np.float32(1.0 - 0.6 * 0.6 / 2.0))
+    base = dict(min_pts=8, m=m, seed=args.seed, flags=sng.SNG_FLAG_TIMING)
+    runs = {
+        "l2_fp32": (xf, None, sng.Params(eps=0.6, **base), 4, 0),
+        "cosine_fp32": (xf, None, sng.Params(eps=tau, metric=sng.SNG_METRIC_COSINE, **base), 4, 0),
+        "dot_fp32": (xf, None, sng.Params(eps=tau, metric=sng.SNG_METRIC_DOT, **base), 4, 0),
+        "cosine_bf16": (xb, xf, sng.Params(eps=tau, metric=sng.SNG_METRIC_COSINE, **base), 2, 0),
+    }
+    peak, kind = peaks()
+    out, labels = {}, {}
+    for name, (xx, master, p, esize, extra) in runs.items():
+        for _ in range(args.warmup):
+            sng.cluster(xx, p, x_master=master)
+        ms, (lab, st) = _timed(lambda: sng.cluster(xx, p, x_master=master), args.steps)
+        labels[name] = lab
+        alg = gather_algorithmic_bytes(n, d, m, esize, st["kept_edges"]) + n * m * extra
+        g_ms = st["ms"]["gather"]
+        out[name] = {"ms": ms, "queries_per_s": n * m / (ms * 1e-3), "gather_ms": g_ms,
+                     "gather_gbs": alg / (g_ms * 1e-3) / 1e9,
+                     "frac_of_hbm": alg / (g_ms * 1e-3) / 1e9 / peak,
+                     "kept_edges": st["kept_edges"], "recheck_pairs": st["recheck_pairs"],
+                     "clusters": st["clusters"], "noise": st["noise"],
+                     "mapping": [st["map_vec"], st["map_group"], st["map_nch"],
+                                 st["map_unroll"]]}
+    for name in ("cosine_fp32", "dot_fp32", "cosine_bf16"):
+        out[name]["ari_vs_l2"] = sng.ari(labels[name], labels["l2_fp32"])
+    return {"form": "cosine", "metric": "sampled similarity queries/s (cosine, FP32)",
+            "value": out["cosine_fp32"]["queries_per_s"], "unit": "queries/s", "runs": out,
+            "peak_gbs": peak, "peak_kind": kind,
+            "config": {"workload": f"sphere-n{n}-d{d}-sigma{args.cos_sigma}", "m": m,
+                       "tau": tau, "eps_l2": 0.6, "min_pts": 8}, "dtype": "f32",
+            "steps": args.steps}
+
+
 def bench_batched(args):
     """Batched form: 4096 3-D clouds of 2,000..130,000 points (Gaussian blobs
     plus a 30% ground layer), m = 200, eps = 0.3 m, MinPts = 4; one
@@ -664,7 +715,7 @@ def main():
     ap.add_argument("--sharded", action="store_true",
                     help="N > 1: split one dataset's rows across ranks (strong scaling)")
     ap.add_argument("--form", default="plain",
-                    choices=["plain", "bf16", "batched", "surrogate", "balls", "sweep"])
+                    choices=["plain", "bf16", "batched", "surrogate", "balls", "sweep", "cosine"])
     ap.add_argument("--sweep-n", type=int, default=100_000)
     ap.add_argument("--sweep-s", type=float, nargs="+",
                     default=[0.3, 0.1, 0.03, 0.01, 0.003, 0.001])
@@ -672,6 +723,7 @@ def main():
                     default=[100, 300, 1000, 3000, 10_000, 100_000, 1_000_000, 10_000_000])
     ap.add_argument("--bf16-n", type=int, default=5_000_000)
     ap.add_argument("--bf16-sigma", type=float, default=0.15)
+    ap.add_argument("--cos-sigma", type=float, default=0.0375)
     ap.add_argument("--clouds", type=int, default=4096)
     ap.add_argument("--seq-clouds", type=int, default=512)
     ap.add_argument("--surr-n", type=int, default=2_000_000)
@@ -692,7 +744,8 @@ def main():
     if args.form != "plain":
         import __graft_entry__
         __graft_entry__.build()
-        fn = {"bf16": bench_bf16, "batched": bench_batched, "surrogate": bench_surrogate,
+        fn = {"bf16": bench_bf16, "cosine": bench_cosine, "batched": bench_batched,
+              "surrogate": bench_surrogate,
               "balls": bench_balls, "sweep": bench_sweep}
         print(json.dumps(fn[args.form](args)), flush=True)
         return

@@ -227,16 +227,17 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   // per term (nch*vec fused multiply-adds, log2 group shuffle levels); the
   // FP32 sum S of |a_k b_k| carries the same relative error, so c1 S with c1
   // doubled (plus slack for the FP64 result's own rounding) bounds it.  For
-  // cosine each FP32 inverse norm (a warp sum of ceil(d/32) + 5 roundings,
-  // a square root and a quotient) is within e_inv relative, so the two norms
-  // and two products add c2 |dot32|.  Underflowing products add at most
-  // K 2^-150 in absolute terms: sim_abs.  All constants are rounded up.
+  // cosine each squared norm is summed with the same K roundings and its
+  // correctly rounded reciprocal square root is within e_inv = (K/2 + 2) u
+  // relative, so the two norms and two products add c2 |dot32|.
+  // Underflowing products add at most K 2^-150 in absolute terms: sim_abs.
+  // All constants are rounded up.
   r->metric = p->metric;
   if (p->metric != SNG_METRIC_L2) {
     const double tau = (double)p->eps;
     r->band = (double)r->band_rel * std::fabs(tau);
     const double c1 = 2.0 * (double)(nch * vec + lg + 3) * u + std::ldexp(1.0, -22);
-    const double e_inv = (double)((p->d + 31) / 32 + 8) * u;
+    const double e_inv = ((double)(nch * vec + lg) / 2.0 + 2.0) * u;
     const double c2 = p->metric == SNG_METRIC_COSINE ? 2.0 * (2.0 * e_inv + 3.0 * u) : 0.0;
     auto up = [](double v) {
       float f = (float)v;
@@ -279,7 +280,6 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
   g->sim_c2 = r.sim_c2;
   g->sim_abs = r.sim_abs;
   g->band_f = r.band_f;
-  g->inv_norm = nullptr;   // set by run_graph for cosine
   // L2 prefetch of partner rows when rows start on 16 bytes (16-byte vectors)
   const int esize = p->dtype == SNG_F32 ? 4 : 2;
   g->pf_bytes = 0;
@@ -340,12 +340,6 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   fill_gather_args(x, p, r, &ga);
   ga.m_row = m_row;
   ga.w_row = w_row;
-  if (p->metric == SNG_METRIC_COSINE) {
-    float *inv = nullptr;
-    if ((rc = s.alloc((void **)&inv, (size_t)n * 4, "inverse norms"))) return rc;
-    launch_inv_norm(p->dtype, x, p->ld, n, p->d, inv, st);
-    ga.inv_norm = inv;
-  }
   ga.bitmask = gb->bitmask;
   ga.out_cnt = gb->out_cnt;
   ga.deg = gb->deg;

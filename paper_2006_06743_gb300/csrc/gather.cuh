@@ -23,8 +23,10 @@
 // Similarity form (SIM = true; inner product or cosine, edge iff sim >= tau):
 // the lanes also accumulate sum |a_k b_k|, which bounds the FP32 error of the
 // inner product (one rounding per fused multiply-add and per shuffle level),
-// so each pair gets its own certified band; cosine scales both by the FP32
-// inverse norms of the two rows, whose own error enters through |<a,b>|.
+// so each pair gets its own certified band.  Cosine also accumulates the
+// partner's squared norm in the same pass (no extra memory traffic; the
+// source row's is summed once per row) and scales by the two correctly
+// rounded reciprocal square roots, whose error enters through |<a,b>|.
 #pragma once
 
 #include "sng_internal.cuh"
@@ -45,12 +47,13 @@ struct GatherArgs {
   double band;            // band_rel * eps2 (reported band half-width;
                           // band_rel * |tau| in the similarity form)
   // similarity form: keep iff sim >= tau.  Certified outside
-  // |sim32 - tau| <= sim_c1 * S + sim_c2 * |dot32| (cosine: both times
-  // inv_i * inv_p) + sim_abs + band_f, S = FP32 sum of |a_k b_k|.
-  int32_t cosine;         // 1: cosine (needs inv_norm), 0: inner product
+  // |sim32 - tau| <= (sim_c1 * S + sim_c2 * |dot32| + sim_abs) * w + band_f,
+  // S = FP32 sum of |a_k b_k|, w = 1 (inner product) or the product of the
+  // two FP32 reciprocal norms (cosine; certified only for w in
+  // [2^-100, 2^100], so that w itself carries a relative error).
+  int32_t cosine;         // 1: cosine, 0: inner product
   float tau, sim_c1, sim_c2, sim_abs, band_f;
   double tau64;
-  const float *inv_norm;  // cosine: FP32 1/|x_i| per row
   int32_t sample_all;
   int32_t deg_mode;
   const int32_t *m_row;   // nullable: draws of row i (<= m)
@@ -160,7 +163,20 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
     }
   }
 
-  const float inv_i = (SIM && a.cosine) ? a.inv_norm[i] : 1.f;
+  // cosine: reciprocal norm of row i, summed like a pair (group reduction)
+  float inv_i = 1.f;
+  if constexpr (SIM) {
+    if (a.cosine) {
+      float nn = 0.f;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) nn = fmaf(xi[c][k], xi[c][k], nn);
+#pragma unroll
+      for (int o = G / 2; o >= 1; o >>= 1) nn += __shfl_xor_sync(kFullMask, nn, o);
+      inv_i = __frsqrt_rn(nn);
+    }
+  }
 
   int cnt = 0;
   int jb = 0;
@@ -174,13 +190,11 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
     for (int t0 = 0; t0 < STEPS; t0 += U) {
       typename Raw<T, VEC>::type v[U][NCH];
       int32_t pv[U];
-      float ipv[U];   // similarity form, cosine: partner's inverse norm
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int t = t0 + u;
         const int32_t p = cur[t * R + grp];
         pv[u] = p;
-        if constexpr (SIM) ipv[u] = (a.cosine && gl == 0 && p >= 0) ? __ldg(a.inv_norm + p) : 1.f;
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
@@ -193,6 +207,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
         const int t = t0 + u;
         float acc = 0.f;
         float sacc = 0.f;   // similarity form: sum of |a_k b_k|
+        float bb = 0.f;     // similarity form: partner's squared norm (cosine)
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
@@ -203,6 +218,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
                 const float b = Raw<T, VEC>::get(v[u][c], k);
                 acc = fmaf(xi[c][k], b, acc);
                 sacc = fmaf(fabsf(xi[c][k]), fabsf(b), sacc);
+                bb = fmaf(b, b, bb);
               } else {
                 const float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
                 acc = fmaf(diff, diff, acc);
@@ -216,6 +232,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
                 if (off + k >= d) b = 0.f;   // row padding may hold anything
                 acc = fmaf(xi[c][k], b, acc);
                 sacc = fmaf(fabsf(xi[c][k]), fabsf(b), sacc);
+                bb = fmaf(b, b, bb);
               } else {
                 float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
                 if (off + k >= d) diff = 0.f;
@@ -227,20 +244,25 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 #pragma unroll
         for (int o = G / 2; o >= 1; o >>= 1) {
           acc += __shfl_xor_sync(kFullMask, acc, o);
-          if constexpr (SIM) sacc += __shfl_xor_sync(kFullMask, sacc, o);
+          if constexpr (SIM) {
+            sacc += __shfl_xor_sync(kFullMask, sacc, o);
+            bb += __shfl_xor_sync(kFullMask, bb, o);
+          }
         }
         bool keep = false;
         const int32_t p = pv[u];
         if (gl == 0 && p >= 0) {
           if constexpr (SIM) {
             float sim = acc;
-            float err = a.sim_c1 * sacc + a.sim_c2 * fabsf(acc);
+            float err = a.sim_c1 * sacc + a.sim_c2 * fabsf(acc) + a.sim_abs;
             if (a.cosine) {
-              const float w = inv_i * ipv[u];
-              sim = (acc * inv_i) * ipv[u];
-              err = err * w;
+              const float inv_p = __frsqrt_rn(bb);
+              const float w = inv_i * inv_p;
+              sim = (acc * inv_i) * inv_p;
+              // zero, overflowing or underflowing norms certify nothing
+              err = (w >= 0x1p-100f && w <= 0x1p100f) ? err * w : __int_as_float(0x7fc00000);
             }
-            err = err + a.sim_abs + a.band_f;
+            err = err + a.band_f;
             // NaN (zero or non-finite rows) certifies nothing: FP64 decides
             if (sim - err >= a.tau) {
               keep = true;
@@ -296,16 +318,18 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 
 // Resident 256-thread blocks per SM the compiler must allow for: mappings
 // with few registers of row data get 4 (32 warps), wider ones 3 or 2.
-template <typename T, int VEC, int NCH, int U>
+template <typename T, int VEC, int NCH, int U, bool SIM = false>
 struct MinBlocks {
   // 32-bit registers per lane of row data: partner chunks in flight (raw
-  // bits) plus this lane's slice of the source row (FP32)
-  static constexpr int words = U * NCH * (VEC * (int)sizeof(T) / 4 > 0 ? VEC * (int)sizeof(T) / 4 : 1) + NCH * VEC;
+  // bits) plus this lane's slice of the source row (FP32); the similarity
+  // form carries three accumulators and the cosine scale factors besides
+  static constexpr int words = U * NCH * (VEC * (int)sizeof(T) / 4 > 0 ? VEC * (int)sizeof(T) / 4 : 1) +
+                               NCH * VEC + (SIM ? 2 * U + 4 : 0);
   static constexpr int value = words <= 32 ? 4 : (words <= 56 ? 3 : 2);
 };
 
 template <typename T, int VEC, int G, int NCH, int U, bool SIM = false>
-__global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value) gather_kernel(GatherArgs a) {
+__global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U, SIM>::value) gather_kernel(GatherArgs a) {
   extern __shared__ int32_t smem_partner[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -458,10 +482,6 @@ struct GatherMap {
 };
 
 // Host-side launcher; returns false if no compiled variant matches `map`.
-// Cosine form: out[i] = 1 / sqrt(sum_k x_ik^2) in FP32 (correctly rounded
-// square root and quotient), one warp per row; a zero row gives +inf.
-void launch_inv_norm(int dtype, const void *x, int64_t ld, int64_t n, int32_t d, float *out,
-                     cudaStream_t stream);
 bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int grid,
                    cudaStream_t stream);
 bool launch_gather_blocked(int dtype, const GatherMap &map, const GatherArgs &args, int grid,

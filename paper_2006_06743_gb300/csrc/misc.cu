@@ -89,41 +89,6 @@ size_t gather_smem_bytes(const GatherMap &map) {
   return (size_t)(map.block / 32) * 64 * map.unroll * sizeof(int32_t);
 }
 
-// --------------------------------------------------------- inverse norms
-
-template <typename T>
-__global__ void inv_norm_kernel(const T *x, int64_t ld, int64_t n, int32_t d, float *out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
-       i += warps) {
-    const T *row = x + i * ld;
-    float acc = 0.f;
-    for (int k = lane; k < d; k += 32) {
-      float v[1];
-      Chunk<T, 1>::load(row + k, v);
-      acc = fmaf(v[0], v[0], acc);
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
-    if (lane == 0) out[i] = __fdiv_rn(1.0f, __fsqrt_rn(acc));
-  }
-}
-
-void launch_inv_norm(int dtype, const void *x, int64_t ld, int64_t n, int32_t d, float *out,
-                     cudaStream_t stream) {
-  int64_t blocks = (n + 7) / 8;
-  const int64_t cap = (int64_t)device_sms() * 16;
-  if (blocks > cap) blocks = cap;
-  if (dtype == SNG_F32)
-    inv_norm_kernel<float><<<(int)blocks, 256, 0, stream>>>(static_cast<const float *>(x), ld,
-                                                            n, d, out);
-  else
-    inv_norm_kernel<uint16_t><<<(int)blocks, 256, 0, stream>>>(
-        static_cast<const uint16_t *>(x), ld, n, d, out);
-  note_launch();
-}
-
 // ------------------------------------------------------------ partners
 
 __global__ void partners_kernel(int64_t n, uint64_t seed, int64_t i0, int64_t rows, int64_t m,

@@ -117,6 +117,21 @@ def test_cosine_zero_and_nonfinite_rows(orc):
     assert not np.isin(col, np.arange(0, n, 7)).any()
 
 
+@pytest.mark.parametrize("tau", [-0.2, 0.0, 0.3])
+def test_cosine_extreme_magnitudes(orc, tau):
+    """Rows whose FP32 squared norm overflows (entries ~1e20) or underflows
+    (~1e-25) have finite FP64 cosines; the FP32 screen must not certify them
+    (its reciprocal norms are 0 or inf there), so FP64 decides each pair."""
+    torch, sng = need_gpu()
+    n, d = 1200, 8
+    x = datagen.random_points(n, d, seed=12) - 0.5
+    x[::5] *= np.float32(1e20)
+    x[1::5] *= np.float32(1e-25)
+    p = sng.Params(eps=tau, min_pts=3, m=150, seed=4, metric=COS)
+    st = _compare(orc, sng, torch, x, torch.from_numpy(x).cuda(), p)
+    assert st["kept_edges"] > 0
+
+
 @pytest.mark.parametrize("metric", [DOT, COS])
 @pytest.mark.parametrize("deg_mode", [0, 1, 2])
 def test_similarity_degree_modes_and_sample_all(orc, metric, deg_mode):
