@@ -419,7 +419,7 @@ def bench_cosine(args):
     m = 1000.  Cosine similarity >= 1 - eps^2/2 (eps = 0.6: the same graph as
     the Euclidean ball of radius eps, up to rounding, for unit vectors) in
     FP32 and BF16, the inner product in FP32, and the Euclidean form beside
-    them; default gather mappings."""
+    them; gather mappings from the autotuner (--autotune 0: defaults)."""
     import numpy as np
     import torch
 
@@ -436,10 +436,19 @@ def bench_cosine(args):
         "l2_fp32": (xf, None, sng.Params(eps=0.6, **base), 4, 0),
         "cosine_fp32": (xf, None, sng.Params(eps=tau, metric=sng.SNG_METRIC_COSINE, **base), 4, 0),
         "dot_fp32": (xf, None, sng.Params(eps=tau, metric=sng.SNG_METRIC_DOT, **base), 4, 0),
+        "l2_bf16": (xb, xf, sng.Params(eps=0.6, **base), 2, 0),
         "cosine_bf16": (xb, xf, sng.Params(eps=tau, metric=sng.SNG_METRIC_COSINE, **base), 2, 0),
     }
     peak, kind = peaks()
-    out, labels = {}, {}
+    out, labels, tuned = {}, {}, {}
+    if args.autotune:
+        from paper_2006_06743_gb300 import autotune
+        for name in list(runs):
+            xx, master, p, esize, extra = runs[name]
+            t = autotune.tune(xx, p, x_master=master, reps=1, budget_s=args.tune_budget / 2,
+                              force=args.retune, verbose=args.verbose)
+            tuned[name] = t.get("mapping")
+            runs[name] = (xx, master, autotune.apply(p, t), esize, extra)
     for name, (xx, master, p, esize, extra) in runs.items():
         for _ in range(args.warmup):
             sng.cluster(xx, p, x_master=master)
@@ -454,13 +463,14 @@ def bench_cosine(args):
                      "clusters": st["clusters"], "noise": st["noise"],
                      "mapping": [st["map_vec"], st["map_group"], st["map_nch"],
                                  st["map_unroll"]]}
-    for name in ("cosine_fp32", "dot_fp32", "cosine_bf16"):
+    for name in ("cosine_fp32", "dot_fp32", "l2_bf16", "cosine_bf16"):
         out[name]["ari_vs_l2"] = sng.ari(labels[name], labels["l2_fp32"])
     return {"form": "cosine", "metric": "sampled similarity queries/s (cosine, FP32)",
             "value": out["cosine_fp32"]["queries_per_s"], "unit": "queries/s", "runs": out,
             "peak_gbs": peak, "peak_kind": kind,
             "config": {"workload": f"sphere-n{n}-d{d}-sigma{args.cos_sigma}", "m": m,
-                       "tau": tau, "eps_l2": 0.6, "min_pts": 8}, "dtype": "f32",
+                       "tau": tau, "eps_l2": 0.6, "min_pts": 8, "mappings": tuned},
+            "dtype": "f32",
             "steps": args.steps}
 
 

@@ -35,8 +35,9 @@ def _bucket(v: int) -> int:
 
 def key_for(x, p: Params) -> str:
     n, d = x.shape
-    return (f"{str(x.dtype).replace('torch.', '')}-d{d}-ld{x.stride(0)}-n{_bucket(n)}"
-            f"-m{_bucket(p.draws(n))}-mode{p.sample_mode}")
+    key = (f"{str(x.dtype).replace('torch.', '')}-d{d}-ld{x.stride(0)}-n{_bucket(n)}"
+           f"-m{_bucket(p.draws(n))}-mode{p.sample_mode}")
+    return key + (f"-metric{p.metric}" if p.metric else "")
 
 
 def _default_group(d: int, vec: int) -> int:
@@ -58,7 +59,7 @@ def candidates(x, p: Params) -> list[dict]:
     groups = sorted({g for g in (g0 // 8, g0 // 4, g0 // 2, g0, g0 * 2) if 1 <= g <= 32})
     x_bytes = n * x.stride(0) * esize
     passes = [1]
-    if x_bytes > (48 << 20):
+    if x_bytes > (48 << 20) and not p.metric:   # the similarity form runs in one pass
         base = max(2, int(math.ceil(x_bytes / (48 << 20))))
         passes += sorted({2, base, base + 2, 2 * base} - {1})
     out = []

@@ -223,15 +223,16 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   r->lo_thr = lof;
   r->hi_thr = hif;
 
-  // similarity form: |dot32 - dot| <= (K + 1) u sum|a_k b_k| with K roundings
-  // per term (nch*vec fused multiply-adds, log2 group shuffle levels); the
-  // FP32 sum S of |a_k b_k| carries the same relative error, so c1 S with c1
-  // doubled (plus slack for the FP64 result's own rounding) bounds it.  For
-  // cosine each squared norm is summed with the same K roundings and its
-  // correctly rounded reciprocal square root is within e_inv = (K/2 + 2) u
-  // relative, so the two norms and two products add c2 |dot32|.
-  // Underflowing products add at most K 2^-150 in absolute terms: sim_abs.
-  // All constants are rounded up.
+  // similarity form: |dot32 - dot| <= (K + 1) u sum|a_k b_k| <= (K + 1) u
+  // |a| |b| with K roundings per term (nch*vec fused multiply-adds, log2
+  // group shuffle levels).  The squared norms are summed with the same K
+  // roundings, so |a| |b| from them (and its correctly rounded square roots
+  // and products) is within a few K u relative; c1 = twice the bound plus
+  // 2^-22 covers that and the FP64 result's own rounding.  With both norms
+  // in [2^-50, 2^50] products that underflow cost at most K 2^-150 absolute,
+  // far below c1 |a| |b|.  Cosine divides by |a| |b| through two reciprocal
+  // square roots within e_inv = (K/2 + 2) u each, adding c2 |cos32|.  All
+  // constants are rounded up.
   r->metric = p->metric;
   if (p->metric != SNG_METRIC_L2) {
     const double tau = (double)p->eps;
@@ -246,7 +247,6 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
     };
     r->sim_c1 = up(c1);
     r->sim_c2 = up(c2);
-    r->sim_abs = std::ldexp(1.0f, -120);
     r->band_f = up(r->band);
   }
   return SNG_OK;
@@ -278,7 +278,6 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
   g->tau64 = (double)p->eps;
   g->sim_c1 = r.sim_c1;
   g->sim_c2 = r.sim_c2;
-  g->sim_abs = r.sim_abs;
   g->band_f = r.band_f;
   // L2 prefetch of partner rows when rows start on 16 bytes (16-byte vectors)
   const int esize = p->dtype == SNG_F32 ? 4 : 2;

@@ -19,7 +19,7 @@ struct Resolved {
   float lo_thr = 0.f, hi_thr = 0.f;
   // similarity form (metric != SNG_METRIC_L2): constants of the FP32 screen
   int32_t metric = 0;
-  float sim_c1 = 0.f, sim_c2 = 0.f, sim_abs = 0.f, band_f = 0.f;
+  float sim_c1 = 0.f, sim_c2 = 0.f, band_f = 0.f;
   GatherMap map{};
 };
 

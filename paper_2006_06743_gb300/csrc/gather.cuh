@@ -21,12 +21,14 @@
 // master copy.
 //
 // Similarity form (SIM = true; inner product or cosine, edge iff sim >= tau):
-// the lanes also accumulate sum |a_k b_k|, which bounds the FP32 error of the
-// inner product (one rounding per fused multiply-add and per shuffle level),
-// so each pair gets its own certified band.  Cosine also accumulates the
-// partner's squared norm in the same pass (no extra memory traffic; the
-// source row's is summed once per row) and scales by the two correctly
-// rounded reciprocal square roots, whose error enters through |<a,b>|.
+// the lanes also accumulate the partner's squared norm in the same pass (no
+// extra memory traffic; the source row's is summed once per row).  The FP32
+// inner product is within gamma_K sum |a_k b_k| <= gamma_K |a| |b| of the
+// exact one (K roundings per term: one per fused multiply-add and per shuffle
+// level), so each pair gets its own certified band from the two norms;
+// cosine scales by the two correctly rounded reciprocal square roots, whose
+// error enters through |cos|.  Norms outside [2^-50, 2^50] (zero, tiny,
+// huge or non-finite rows) certify nothing.
 #pragma once
 
 #include "sng_internal.cuh"
@@ -47,12 +49,10 @@ struct GatherArgs {
   double band;            // band_rel * eps2 (reported band half-width;
                           // band_rel * |tau| in the similarity form)
   // similarity form: keep iff sim >= tau.  Certified outside
-  // |sim32 - tau| <= (sim_c1 * S + sim_c2 * |dot32| + sim_abs) * w + band_f,
-  // S = FP32 sum of |a_k b_k|, w = 1 (inner product) or the product of the
-  // two FP32 reciprocal norms (cosine; certified only for w in
-  // [2^-100, 2^100], so that w itself carries a relative error).
+  // |sim32 - tau| <= sim_c1 |a| |b| + band_f (inner product) or
+  // sim_c1 + sim_c2 |cos32| + band_f (cosine), norms from the FP32 sums.
   int32_t cosine;         // 1: cosine, 0: inner product
-  float tau, sim_c1, sim_c2, sim_abs, band_f;
+  float tau, sim_c1, sim_c2, band_f;
   double tau64;
   int32_t sample_all;
   int32_t deg_mode;
@@ -163,19 +163,20 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
     }
   }
 
-  // cosine: reciprocal norm of row i, summed like a pair (group reduction)
-  float inv_i = 1.f;
+  // similarity form: norm of row i, summed like a pair (group reduction)
+  float inv_i = 1.f, nrm_i = 1.f;
+  bool row_ok = true;
   if constexpr (SIM) {
-    if (a.cosine) {
-      float nn = 0.f;
+    float nn = 0.f;
 #pragma unroll
-      for (int c = 0; c < NCH; ++c)
+    for (int c = 0; c < NCH; ++c)
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) nn = fmaf(xi[c][k], xi[c][k], nn);
+      for (int k = 0; k < VEC; ++k) nn = fmaf(xi[c][k], xi[c][k], nn);
 #pragma unroll
-      for (int o = G / 2; o >= 1; o >>= 1) nn += __shfl_xor_sync(kFullMask, nn, o);
-      inv_i = __frsqrt_rn(nn);
-    }
+    for (int o = G / 2; o >= 1; o >>= 1) nn += __shfl_xor_sync(kFullMask, nn, o);
+    row_ok = nn >= 0x1p-100f && nn <= 0x1p100f;   // false for NaN
+    inv_i = __frsqrt_rn(nn);
+    nrm_i = __fsqrt_rn(nn);
   }
 
   int cnt = 0;
@@ -206,8 +207,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
       for (int u = 0; u < U; ++u) {
         const int t = t0 + u;
         float acc = 0.f;
-        float sacc = 0.f;   // similarity form: sum of |a_k b_k|
-        float bb = 0.f;     // similarity form: partner's squared norm (cosine)
+        float bb = 0.f;     // similarity form: partner's squared norm
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
@@ -217,7 +217,6 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
               if constexpr (SIM) {
                 const float b = Raw<T, VEC>::get(v[u][c], k);
                 acc = fmaf(xi[c][k], b, acc);
-                sacc = fmaf(fabsf(xi[c][k]), fabsf(b), sacc);
                 bb = fmaf(b, b, bb);
               } else {
                 const float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
@@ -231,7 +230,6 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
                 float b = Raw<T, VEC>::get(v[u][c], k);
                 if (off + k >= d) b = 0.f;   // row padding may hold anything
                 acc = fmaf(xi[c][k], b, acc);
-                sacc = fmaf(fabsf(xi[c][k]), fabsf(b), sacc);
                 bb = fmaf(b, b, bb);
               } else {
                 float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
@@ -244,25 +242,24 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 #pragma unroll
         for (int o = G / 2; o >= 1; o >>= 1) {
           acc += __shfl_xor_sync(kFullMask, acc, o);
-          if constexpr (SIM) {
-            sacc += __shfl_xor_sync(kFullMask, sacc, o);
-            bb += __shfl_xor_sync(kFullMask, bb, o);
-          }
+          if constexpr (SIM) bb += __shfl_xor_sync(kFullMask, bb, o);
         }
         bool keep = false;
         const int32_t p = pv[u];
         if (gl == 0 && p >= 0) {
           if constexpr (SIM) {
-            float sim = acc;
-            float err = a.sim_c1 * sacc + a.sim_c2 * fabsf(acc) + a.sim_abs;
+            const float inv_p = __frsqrt_rn(bb);
+            float sim, err;
             if (a.cosine) {
-              const float inv_p = __frsqrt_rn(bb);
-              const float w = inv_i * inv_p;
               sim = (acc * inv_i) * inv_p;
-              // zero, overflowing or underflowing norms certify nothing
-              err = (w >= 0x1p-100f && w <= 0x1p100f) ? err * w : __int_as_float(0x7fc00000);
+              err = a.sim_c1 + a.sim_c2 * fabsf(sim);
+            } else {
+              sim = acc;
+              err = a.sim_c1 * (nrm_i * (bb * inv_p));   // c1 |a| |b|
             }
-            err = err + a.band_f;
+            // zero, tiny, huge or non-finite norms certify nothing
+            const bool ok = row_ok && bb >= 0x1p-100f && bb <= 0x1p100f;
+            err = ok ? err + a.band_f : __int_as_float(0x7fc00000);
             // NaN (zero or non-finite rows) certifies nothing: FP64 decides
             if (sim - err >= a.tau) {
               keep = true;
@@ -322,7 +319,7 @@ template <typename T, int VEC, int NCH, int U, bool SIM = false>
 struct MinBlocks {
   // 32-bit registers per lane of row data: partner chunks in flight (raw
   // bits) plus this lane's slice of the source row (FP32); the similarity
-  // form carries three accumulators and the cosine scale factors besides
+  // form carries a second accumulator per pair and the row's norms besides
   static constexpr int words = U * NCH * (VEC * (int)sizeof(T) / 4 > 0 ? VEC * (int)sizeof(T) / 4 : 1) +
                                NCH * VEC + (SIM ? 2 * U + 4 : 0);
   static constexpr int value = words <= 32 ? 4 : (words <= 56 ? 3 : 2);
