@@ -231,14 +231,15 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   // 2^-22 covers that and the FP64 result's own rounding.  With both norms
   // in [2^-50, 2^50] products that underflow cost at most K 2^-150 absolute,
   // far below c1 |a| |b|.  Cosine divides by |a| |b| through two reciprocal
-  // square roots within e_inv = (K/2 + 2) u each, adding c2 |cos32|.  All
+  // square roots within e_inv = (K/2 + 5) u each, adding c2 |cos32|.  All
   // constants are rounded up.
   r->metric = p->metric;
   if (p->metric != SNG_METRIC_L2) {
     const double tau = (double)p->eps;
     r->band = (double)r->band_rel * std::fabs(tau);
     const double c1 = 2.0 * (double)(nch * vec + lg + 3) * u + std::ldexp(1.0, -22);
-    const double e_inv = ((double)(nch * vec + lg) / 2.0 + 2.0) * u;
+    // rsqrtf is within 2 ulp = 4u (CUDA's documented bound)
+    const double e_inv = ((double)(nch * vec + lg) / 2.0 + 5.0) * u;
     const double c2 = p->metric == SNG_METRIC_COSINE ? 2.0 * (2.0 * e_inv + 3.0 * u) : 0.0;
     auto up = [](double v) {
       float f = (float)v;

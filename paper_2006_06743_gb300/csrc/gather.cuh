@@ -26,8 +26,8 @@
 // inner product is within gamma_K sum |a_k b_k| <= gamma_K |a| |b| of the
 // exact one (K roundings per term: one per fused multiply-add and per shuffle
 // level), so each pair gets its own certified band from the two norms;
-// cosine scales by the two correctly rounded reciprocal square roots, whose
-// error enters through |cos|.  Norms outside [2^-50, 2^50] (zero, tiny,
+// cosine scales by the two reciprocal square roots (rsqrtf, within 2 ulp by
+// CUDA's documented bound), whose error enters through |cos|.  Norms outside [2^-50, 2^50] (zero, tiny,
 // huge or non-finite rows) certify nothing.
 #pragma once
 
@@ -163,9 +163,11 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
     }
   }
 
-  // similarity form: norm of row i, summed like a pair (group reduction)
-  float inv_i = 1.f, nrm_i = 1.f;
-  bool row_ok = true;
+  // similarity form: the row's scale, from its squared norm summed like a
+  // pair (group reduction): 1/|x_i| for cosine, |x_i| for the inner
+  // product; NaN when the norm is outside [2^-50, 2^50] (zero, tiny, huge or
+  // non-finite row), which then certifies none of the row's pairs
+  float scale_i = 1.f;
   if constexpr (SIM) {
     float nn = 0.f;
 #pragma unroll
@@ -174,9 +176,9 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
       for (int k = 0; k < VEC; ++k) nn = fmaf(xi[c][k], xi[c][k], nn);
 #pragma unroll
     for (int o = G / 2; o >= 1; o >>= 1) nn += __shfl_xor_sync(kFullMask, nn, o);
-    row_ok = nn >= 0x1p-100f && nn <= 0x1p100f;   // false for NaN
-    inv_i = __frsqrt_rn(nn);
-    nrm_i = __fsqrt_rn(nn);
+    const float r = rsqrtf(nn);   // within 2 ulp (CUDA's documented bound)
+    scale_i = a.cosine ? r : nn * r;
+    if (!(nn >= 0x1p-100f && nn <= 0x1p100f)) scale_i = __int_as_float(0x7fc00000);
   }
 
   int cnt = 0;
@@ -248,17 +250,18 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
         const int32_t p = pv[u];
         if (gl == 0 && p >= 0) {
           if constexpr (SIM) {
-            const float inv_p = __frsqrt_rn(bb);
+            const float inv_p = rsqrtf(bb);
             float sim, err;
             if (a.cosine) {
-              sim = (acc * inv_i) * inv_p;
+              sim = (acc * scale_i) * inv_p;
               err = a.sim_c1 + a.sim_c2 * fabsf(sim);
             } else {
               sim = acc;
-              err = a.sim_c1 * (nrm_i * (bb * inv_p));   // c1 |a| |b|
+              err = a.sim_c1 * (scale_i * (bb * inv_p));   // c1 |a| |b|
             }
-            // zero, tiny, huge or non-finite norms certify nothing
-            const bool ok = row_ok && bb >= 0x1p-100f && bb <= 0x1p100f;
+            // zero, tiny, huge or non-finite norms certify nothing (a NaN
+            // scale_i has already made err NaN)
+            const bool ok = bb >= 0x1p-100f && bb <= 0x1p100f;
             err = ok ? err + a.band_f : __int_as_float(0x7fc00000);
             // NaN (zero or non-finite rows) certifies nothing: FP64 decides
             if (sim - err >= a.tau) {
