@@ -112,11 +112,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# DRAM traffic (read + write bytes) of one gather launch, from one ncu
-# capture of this workload and kernel (profiles/gather_f32_mixture-n1M-d64.md).
-# Reported only while the timed launch uses that same kernel and mapping.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one gather
+# launch, from one ncu capture of this workload and kernel.  Reported only
+# while the timed launch uses that same kernel and mapping.
 CAPTURED_TRAFFIC = {
-    ("mixture-n1M-d64", "gather_kernel<float, 4, 4, 4, 2>"): 168_506_367_744 + 454_598_144,
+    ("mixture-n1M-d64", "gather_kernel<float, 4, 4, 4, 2, 0>"): 168_511_908_096 + 455_208_704,
 }
 
 
@@ -226,17 +226,25 @@ def bench_sng(args, w):
         t_step = float(t.item())
 
     # end to end through the public API: pinned host points in, labels out
-    e2e_ms = []
+    e2e_ms, h2d_ms, d2h_ms = [], [], []
     labels_host = torch.empty(n, dtype=torch.int32).pin_memory()
-    for _ in range(max(2, min(args.steps, 5))):
+    for it in range(max(1, args.warmup) + max(2, min(args.steps, 5))):
         flush.fill_(1)
         torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         t0 = time.perf_counter()
+        ev[0].record(stream)
         xd = x_host.to(dev, non_blocking=True)
+        ev[1].record(stream)
         lab, _ = sng.cluster(xd, params)
+        ev[2].record(stream)
         labels_host.copy_(lab, non_blocking=True)
+        ev[3].record(stream)
         torch.cuda.synchronize(dev)
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        if it >= max(1, args.warmup):   # untimed warm-up calls first
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            h2d_ms.append(ev[0].elapsed_time(ev[1]))
+            d2h_ms.append(ev[2].elapsed_time(ev[3]))
         del xd
     t_e2e = statistics.mean(e2e_ms)
 
@@ -246,7 +254,7 @@ def bench_sng(args, w):
     alg = gather_algorithmic_bytes(n, d, m, 4, stats["kept_edges"])
     achieved = alg / (g_ms * 1e-3) / 1e9
     kname = (f"gather_kernel<float, {stats['map_vec']}, {stats['map_group']}, "
-             f"{stats['map_nch']}, {stats['map_unroll']}>")
+             f"{stats['map_nch']}, {stats['map_unroll']}, 0>")
     traffic = None
     if params.map_passes <= 1 and not (params.flags & sng.SNG_FLAG_PREFETCH):
         traffic = CAPTURED_TRAFFIC.get((args.workload, kname))
@@ -275,7 +283,9 @@ def bench_sng(args, w):
         "e2e": {"value": Q * world / (t_e2e * 1e-3), "unit": "queries/s",
                 "seconds": t_e2e * 1e-3,
                 "h2d_bytes_per_step": int(x_host.numel() * 4),
-                "d2h_bytes_per_step": int(n * 4)},
+                "d2h_bytes_per_step": int(n * 4),
+                "h2d_ms": statistics.mean(h2d_ms), "d2h_ms": statistics.mean(d2h_ms),
+                "step_ms": e2e_ms},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
