@@ -112,6 +112,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# Warp instructions per query of the batched kernel (smsp__inst_executed.sum
+# over the queries of one launch), from one ncu capture of 256 clouds of the
+# same size distribution; the 4096-cloud launch runs the same per-query code,
+# so its count scales with the queries.
+BATCHED_INST_PER_QUERY = {"batched_kernel<4, 1, 1, 4>": 19_418_482_977 / 3_518_330_800}
+
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one gather
 # launch, from one ncu capture of this workload and kernel.  Reported only
 # while the timed launch uses that same kernel and mapping.
@@ -547,8 +553,22 @@ def bench_batched(args):
     frac = float(off[ncl]) / float(off[-1])
     same = bool(torch.equal(seq_labels[:off[ncl]], labels[:off[ncl]]))
     Q = int(stats["queries"])
+    # issue-rate roofline: the kernel is bound by instruction issue and L2
+    # latency (clouds are L2-resident), not by HBM
+    kname = f"batched_kernel<4, 1, 1, {p.map_unroll or 4}>"
+    ipq = BATCHED_INST_PER_QUERY.get(kname)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    issue_peak = sms * 4 * 2070e6           # 4 warp instructions per SM per cycle
+    roof = {"bound": "alu", "unit": "warp-instr/s", "peak": issue_peak, "kernel": kname,
+            "achieved": None, "frac": None, "traffic": None,
+            "peak_basis": f"{sms} SMs x 4 issue slots x 2070 MHz"}
+    if ipq is not None and p.map_block in (0, 256):
+        roof["achieved"] = ipq * Q / (b_ms * 1e-3)
+        roof["frac"] = roof["achieved"] / issue_peak
+        roof["inst_per_query"] = ipq
     return {"form": "batched", "metric": "sampled eps-queries/s, 4096 clouds in one launch",
             "value": Q / (b_ms * 1e-3), "unit": "queries/s", "ms_batched": b_ms,
+            "roofline": roof,
             "ms_sequential_est": s_ms / frac, "sequential_clouds_timed": ncl,
             "speedup_vs_sequential": (s_ms / frac) / b_ms, "labels_equal_sequential": same,
             "stats": {k: stats[k] for k in ("queries", "kept_edges", "cores", "clusters",
