@@ -259,8 +259,9 @@ def bench_sng(args, w):
     g_ms = statistics.mean(gather_ms)
     alg = gather_algorithmic_bytes(n, d, m, 4, stats["kept_edges"])
     achieved = alg / (g_ms * 1e-3) / 1e9
+    full = stats["map_group"] * stats["map_nch"] * stats["map_vec"] == d
     kname = (f"gather_kernel<float, {stats['map_vec']}, {stats['map_group']}, "
-             f"{stats['map_nch']}, {stats['map_unroll']}, 0>")
+             f"{stats['map_nch']}, {stats['map_unroll']}, 0{', 1' if full else ''}>")
     traffic = None
     if params.map_passes <= 1 and not (params.flags & sng.SNG_FLAG_PREFETCH):
         traffic = CAPTURED_TRAFFIC.get((args.workload, kname))

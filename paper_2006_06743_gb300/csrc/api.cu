@@ -187,6 +187,7 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   r->map.group = group;
   r->map.nch = nch;
   r->map.sim = p->metric != SNG_METRIC_L2;
+  r->map.full = group * nch * vec == p->d;
   r->map.unroll = p->map_unroll > 0 ? p->map_unroll : (vec == vmax && nch * vec >= 16 ? 2 : 4);
   if (p->map_passes < 0 || p->map_passes > 64) return fail(SNG_EINVAL, "map_passes must be in [0, 64]");
   r->map.passes = p->map_passes > 0 ? p->map_passes : 1;

@@ -134,7 +134,7 @@ __device__ __forceinline__ void stage_partners(const GatherArgs &a, int32_t i, u
 // in-degree atomics; returns the row's kept count (same value on all lanes).
 // `sp` is this warp's 2*32*U-entry shared-memory partner buffer: the stage
 // being tested and the next one, hashed (and prefetched) one stage ahead.
-template <typename T, int VEC, int G, int NCH, int U, bool SIM = false>
+template <typename T, int VEC, int G, int NCH, int U, bool SIM = false, bool FULL = false>
 __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_t mi,
                                           int32_t *sp, int lane) {
   constexpr int R = 32 / G;      // pairs per warp step
@@ -152,11 +152,11 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 #pragma unroll
   for (int c = 0; c < NCH; ++c) {
     const int off = (c * G + gl) * VEC;
-    if (off < d) {
+    if (FULL || off < d) {
       Chunk<T, VEC>::load(X + (int64_t)i * a.ld + off, xi[c]);
 #pragma unroll
       for (int k = 0; k < VEC; ++k)
-        if (off + k >= d) xi[c][k] = 0.f;
+        if (!FULL && off + k >= d) xi[c][k] = 0.f;
     } else {
 #pragma unroll
       for (int k = 0; k < VEC; ++k) xi[c][k] = 0.f;
@@ -201,7 +201,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
-          v[u][c] = (p >= 0 && off < d) ? Raw<T, VEC>::load(X + (int64_t)p * a.ld + off)
+          v[u][c] = (p >= 0 && (FULL || off < d)) ? Raw<T, VEC>::load(X + (int64_t)p * a.ld + off)
                                         : Raw<T, VEC>::zero();
         }
       }
@@ -213,7 +213,7 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
-          if (off + VEC <= d) {
+          if (FULL || off + VEC <= d) {
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
               if constexpr (SIM) {
@@ -328,7 +328,9 @@ struct MinBlocks {
   static constexpr int value = words <= 32 ? 4 : (words <= 56 ? 3 : 2);
 };
 
-template <typename T, int VEC, int G, int NCH, int U, bool SIM = false>
+// FULL: every row is exactly G * NCH * VEC elements wide (no partial or
+// empty chunk), so the per-chunk bounds tests drop out of the pair loop.
+template <typename T, int VEC, int G, int NCH, int U, bool SIM = false, bool FULL = false>
 __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U, SIM>::value) gather_kernel(GatherArgs a) {
   extern __shared__ int32_t smem_partner[];
   const int lane = threadIdx.x & 31;
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U, SIM>::value) ga
        row < a.row_end; row += warps_total) {
     const int32_t i = (int32_t)row;
     const int32_t mi = a.m_row ? a.m_row[i] : a.m;
-    gather_row<T, VEC, G, NCH, U, SIM>(a, i, mi, sp, lane);
+    gather_row<T, VEC, G, NCH, U, SIM, FULL>(a, i, mi, sp, lane);
   }
 }
 
@@ -479,6 +481,7 @@ struct GatherMap {
   int vec, group, nch, unroll, block;
   int passes;   // 1: single pass; > 1: L2-blocked slices of the partner range
   int sim;      // 1: similarity form (inner product / cosine) of the kernel
+  int full;     // 1: d == group * nch * vec (a FULL instantiation may serve)
 };
 
 // Host-side launcher; returns false if no compiled variant matches `map`.

@@ -1,0 +1,21 @@
+// gather_full_bf16.cu -- BF16 gather mappings for rows exactly group * nch * vec wide
+// (16-byte vectors, unroll 2 and 4: the default rule's choices for such
+// widths), without per-chunk bounds tests.  The general instantiations serve
+// every other row width.
+#include "gather_inst.cuh"
+
+namespace sng {
+
+bool launch_full_bf16(const GatherMap &map, const GatherArgs &args, int grid, cudaStream_t stream) {
+  SNG_SHAPES_U(uint16_t, 8, 2, SNG_TRY_F)
+  SNG_SHAPES_U(uint16_t, 8, 4, SNG_TRY_F)
+  return false;
+}
+
+int occ_full_bf16(const GatherMap &map) {
+  SNG_SHAPES_U(uint16_t, 8, 2, SNG_OCC_F)
+  SNG_SHAPES_U(uint16_t, 8, 4, SNG_OCC_F)
+  return -1;
+}
+
+}  // namespace sng

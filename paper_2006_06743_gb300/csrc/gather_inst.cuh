@@ -7,23 +7,27 @@
 
 namespace sng {
 
-template <typename T, int VEC, int G, int NCH, int U, bool SIM = false>
+// A FULL instantiation serves only maps with m.full; the general one serves
+// either.
+template <typename T, int VEC, int G, int NCH, int U, bool SIM = false, bool FULL = false>
 static bool try_launch(const GatherMap &m, const GatherArgs &args, int grid, cudaStream_t st) {
-  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || (m.sim != 0) != SIM)
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || (m.sim != 0) != SIM ||
+      (FULL && !m.full))
     return false;
   const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
-  gather_kernel<T, VEC, G, NCH, U, SIM><<<grid, m.block, smem, st>>>(args);
+  gather_kernel<T, VEC, G, NCH, U, SIM, FULL><<<grid, m.block, smem, st>>>(args);
   return true;
 }
 
-template <typename T, int VEC, int G, int NCH, int U, bool SIM = false>
+template <typename T, int VEC, int G, int NCH, int U, bool SIM = false, bool FULL = false>
 static int occ_blocks(const GatherMap &m) {
-  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || (m.sim != 0) != SIM)
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || (m.sim != 0) != SIM ||
+      (FULL && !m.full))
     return -1;
   int blocks = 0;
   const size_t smem = (size_t)(m.block / 32) * 64 * U * sizeof(int32_t);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &blocks, gather_kernel<T, VEC, G, NCH, U, SIM>, m.block, smem) != cudaSuccess)
+          &blocks, gather_kernel<T, VEC, G, NCH, U, SIM, FULL>, m.block, smem) != cudaSuccess)
     return 0;
   return blocks;
 }
@@ -84,6 +88,15 @@ static bool matches(const GatherMap &m) {
   {                                            \
     int b = occ_blocks<T, V, G, N, U>(map);    \
     if (b >= 0) return b;                      \
+  }
+
+// full rows (d == group * nch * vec), Euclidean form
+#define SNG_TRY_F(T, V, G, N, U) \
+  if (try_launch<T, V, G, N, U, false, true>(map, args, grid, stream)) return true;
+#define SNG_OCC_F(T, V, G, N, U)                          \
+  {                                                       \
+    int b = occ_blocks<T, V, G, N, U, false, true>(map);  \
+    if (b >= 0) return b;                                 \
   }
 
 // similarity form (inner product / cosine)
