@@ -167,9 +167,11 @@ __global__ void size_hist_kernel(const unsigned long long *sizes, int64_t len,
 // comes from log-gamma values (at least 1/(min(a,b)+1), so it does not
 // underflow) and the other terms from the ratios
 //   P(k+1)/P(k) = (a-k)(b-k) / ((k+1)(n-a-b+k+1))
-// walking outwards, where P only decreases: a walk stops at the end of the
-// support or once P underflows to zero, past which every term is zero in
-// FP64 as well.
+// walking outwards.  P is log-concave, so along each walk the ratios only
+// shrink: once a ratio r is below 1 the terms still ahead sum to at most
+// P r / (1 - r) times the largest weight |(k/n) log(n k / (a b))| on the
+// support, and the walk stops when that bound falls below 2^-60 of the sum
+// so far (or P underflows, or the support ends).
 __device__ double emi_pair(double a, double b, double n, double lg_n1) {
   const double lo = fmax(1.0, a + b - n), hi = fmin(a, b);
   if (lo > hi) return 0.0;
@@ -181,20 +183,28 @@ __device__ double emi_pair(double a, double b, double n, double lg_n1) {
                       lgamma(n - a - b + mode + 1.0);
   const double p0 = exp(logp);
   const double ab = a * b;
+  // |weight| <= (hi/n) max(|log(n lo/(a b))|, |log(n hi/(a b))|): the log is
+  // monotone in k and k/n <= hi/n
+  const double wmax = hi / n * fmax(fabs(log(n * lo / ab)), fabs(log(n * hi / ab)));
+  const double tiny = 0x1p-60;
   double sum = mode / n * log(n * mode / ab) * p0;
   double p = p0;
   for (double k = mode; k < hi;) {
-    p *= ((a - k) * (b - k)) / ((k + 1.0) * (n - a - b + k + 1.0));
+    const double r = ((a - k) * (b - k)) / ((k + 1.0) * (n - a - b + k + 1.0));
+    p *= r;
     k += 1.0;
     if (p == 0.0) break;
     sum += k / n * log(n * k / ab) * p;
+    if (r < 1.0 && wmax * p * r / (1.0 - r) <= tiny * fabs(sum)) break;
   }
   p = p0;
   for (double k = mode; k > lo;) {
-    p *= (k * (n - a - b + k)) / ((a - k + 1.0) * (b - k + 1.0));
+    const double r = (k * (n - a - b + k)) / ((a - k + 1.0) * (b - k + 1.0));
+    p *= r;
     k -= 1.0;
     if (p == 0.0) break;
     sum += k / n * log(n * k / ab) * p;
+    if (r < 1.0 && wmax * p * r / (1.0 - r) <= tiny * fabs(sum)) break;
   }
   return sum;
 }
