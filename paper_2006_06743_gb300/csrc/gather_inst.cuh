@@ -99,6 +99,15 @@ static bool matches(const GatherMap &m) {
     if (b >= 0) return b;                                 \
   }
 
+// full rows, similarity form
+#define SNG_TRY_SF(T, V, G, N, U) \
+  if (try_launch<T, V, G, N, U, true, true>(map, args, grid, stream)) return true;
+#define SNG_OCC_SF(T, V, G, N, U)                        \
+  {                                                      \
+    int b = occ_blocks<T, V, G, N, U, true, true>(map);  \
+    if (b >= 0) return b;                                \
+  }
+
 // similarity form (inner product / cosine)
 #define SNG_HAS_S(T, V, G, N, U) \
   if (matches<V, G, N, U, true>(map)) return true;
