@@ -210,10 +210,27 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
         const int t = t0 + u;
         float acc = 0.f;
         float bb = 0.f;     // similarity form: partner's squared norm
+        // full-row instantiations: even and odd elements in the two halves of
+        // packed FP32x2 accumulators (one instruction per element pair)
+        F32x2 acc2 = f32x2_zero(), bb2 = f32x2_zero();
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           const int off = (c * G + gl) * VEC;
-          if (FULL || off + VEC <= d) {
+          if (FULL && VEC % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < VEC; k += 2) {
+              const F32x2 a2 = f32x2_pack(xi[c][k], xi[c][k + 1]);
+              const F32x2 b2 = f32x2_pack(Raw<T, VEC>::get(v[u][c], k),
+                                          Raw<T, VEC>::get(v[u][c], k + 1));
+              if constexpr (SIM) {
+                acc2 = f32x2_fma(a2, b2, acc2);
+                bb2 = f32x2_fma(b2, b2, bb2);
+              } else {
+                const F32x2 d2 = f32x2_sub(a2, b2);
+                acc2 = f32x2_fma(d2, d2, acc2);
+              }
+            }
+          } else if (FULL || off + VEC <= d) {
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
               if constexpr (SIM) {
@@ -240,6 +257,10 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
               }
             }
           }
+        }
+        if constexpr (FULL && VEC % 2 == 0) {
+          acc = f32x2_sum(acc2);
+          if constexpr (SIM) bb = f32x2_sum(bb2);
         }
 #pragma unroll
         for (int o = G / 2; o >= 1; o >>= 1) {

@@ -107,6 +107,32 @@ __device__ __forceinline__ float bf16_bits_to_f32(uint16_t b) {
 }
 
 // Read-only vector loads of one chunk of VEC elements, converted to FP32.
+// Packed FP32 pairs (Blackwell's two-wide FP32 add / fused multiply-add):
+// each half is rounded exactly as the scalar operation on that half.
+typedef unsigned long long F32x2;
+__device__ __forceinline__ F32x2 f32x2_zero() { return 0ull; }
+__device__ __forceinline__ F32x2 f32x2_pack(float lo, float hi) {
+  F32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ F32x2 f32x2_sub(F32x2 a, F32x2 b) {
+  F32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ F32x2 f32x2_fma(F32x2 a, F32x2 b, F32x2 c) {
+  F32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// lo + hi, one rounding
+__device__ __forceinline__ float f32x2_sum(F32x2 v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return lo + hi;
+}
+
 template <typename T, int VEC>
 struct Chunk;
 
