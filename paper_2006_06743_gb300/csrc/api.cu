@@ -50,7 +50,7 @@ int device_sms() {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cache[dev] = sms > 0 ? sms : 148;
-    // keep freed pool memory for reuse instead of returning it to the driver
+    // keep freed pool memory for reuse instead of releasing it to the OS
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
       uint64_t thr = UINT64_MAX;

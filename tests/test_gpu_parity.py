@@ -7,7 +7,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import BAND_F32, need_gpu, padded
+from gpu_util import BAND_BF16, BAND_F32, need_gpu, padded
 from paper_2006_06743_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
@@ -105,6 +105,49 @@ def _compare_cluster(orc, x_np, xg, p, sng):
         assert st[k] == r[k], (k, st[k], r[k])
     assert st["queries"] == n * m
     return labels, st
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("d,metric", [(16, 0), (32, 0), (64, 0), (128, 0), (64, 2), (128, 1)])
+def test_full_row_and_general_kernels_agree(orc, dtype, d, metric):
+    """Rows exactly lanes x chunks x vector wide run the full-row kernel
+    (packed FP32x2 arithmetic, no bounds tests); unroll 1 has no full-row
+    instantiation, so the same mapping then runs the general kernel.  Both
+    graphs must equal the oracle's bit for bit."""
+    torch, sng = need_gpu()
+    n = 3000
+    x = datagen.random_points(n, d, seed=d + metric) - (0.5 if metric else 0.0)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if metric:
+        xn = x.astype(np.float64)
+        s = (xn[:500] * xn[500:1000]).sum(1)
+        if metric == 2:
+            s /= np.linalg.norm(xn[:500], axis=1) * np.linalg.norm(xn[500:1000], axis=1)
+        eps = float(np.float32(np.quantile(s, 0.97)))
+    else:
+        eps = float(np.float32(0.12 * math.sqrt(d)))
+    if dtype == "bf16":
+        bits = datagen.bf16_round(x)
+        xo = datagen.bf16_to_f32(bits)
+        xg = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+        master, band = torch.from_numpy(xo).cuda(), BAND_BF16
+    else:
+        xo, xg, master, band = x, torch.from_numpy(x).cuda(), None, BAND_F32
+    rp, col, bpairs, _ = orc.build_rows(xo, eps, 5, 200, band_rel=band, metric=metric)
+    graphs = []
+    # the similarity form has no unroll-1 instantiation: there both runs
+    # are full-row kernels, checked against the oracle all the same
+    for unroll in ((1, 2, 4) if metric == 0 else (2, 4)):
+        p = sng.Params(eps=eps, min_pts=3, m=200, seed=5, metric=metric, map_unroll=unroll)
+        g = sng.build_graph(xg, p, x_master=master)
+        np.testing.assert_array_equal(g["row_ptr"].cpu().numpy(), rp)
+        np.testing.assert_array_equal(g["col"].cpu().numpy(), col)
+        assert g["stats"]["band_pairs"] == bpairs
+        graphs.append(g)
+    vec = 4 if dtype == "f32" else 8
+    st = graphs[-1]["stats"]
+    assert st["map_group"] * st["map_nch"] * st["map_vec"] == d   # a full-row mapping
+    assert st["map_vec"] == vec
 
 
 @pytest.mark.parametrize("n,d,m,mp", [(2, 1, 1, 1), (50, 2, 49, 2), (3000, 2, 60, 3),
