@@ -491,6 +491,55 @@ def bench_cosine(args):
             "steps": args.steps}
 
 
+def bench_graph(args):
+    """One whole pass launched directly (sng_cluster, host reads E mid-way)
+    against the same pass captured once as a CUDA graph
+    (SNG_FLAG_NO_SYNC, replayed): the small configuration (n = 10^4, d = 2,
+    s = 0.01) where launches and the host round trip dominate, and the
+    headline workload."""
+    import numpy as np
+    import torch
+
+    import paper_2006_06743_gb300 as sng
+    from paper_2006_06743_gb300 import datagen
+    out = {}
+    cases = {"mixture2d-n10k": (datagen.mixture_2d(10_000, seed=args.seed),
+                                sng.Params(eps=0.03, min_pts=3, s=0.01, seed=args.seed))}
+    w = make_workload("mixture-n1M-d64", seed=args.seed)
+    cases["mixture-n1M-d64"] = (w["x"], sng.Params(eps=w["eps"], min_pts=w["min_pts"],
+                                                   s=w["s"], seed=w["seed"]))
+    for name, (x, p) in cases.items():
+        xg = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        n = xg.shape[0]
+        ref, _ = sng.cluster(xg, p)
+        reps = max(args.steps, 20) if n <= 100_000 else args.steps
+        for _ in range(args.warmup):
+            sng.cluster(xg, p)
+        direct, _ = _timed(lambda: sng.cluster(xg, p), reps)
+        labels = torch.empty(n, dtype=torch.int32, device="cuda")
+        counters = torch.zeros(9, dtype=torch.int64, device="cuda")
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            sng.cluster_async(xg, p, labels, counters)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            sng.cluster_async(xg, p, labels, counters)
+        for _ in range(args.warmup):
+            graph.replay()
+        replay, _ = _timed(graph.replay, reps)
+        out[name] = {"direct_ms": direct, "graph_replay_ms": replay,
+                     "speedup": direct / replay,
+                     "labels_equal": bool(torch.equal(labels, ref)),
+                     "queries": int(n * p.draws(n))}
+        del graph, xg
+        torch.cuda.synchronize()
+    return {"form": "graph", "metric": "whole-pass time, direct call vs CUDA graph replay",
+            "value": out["mixture2d-n10k"]["speedup"], "unit": "x (small configuration)",
+            "cases": out, "dtype": "f32", "steps": args.steps}
+
+
 def bench_batched(args):
     """Batched form: 4096 3-D clouds of 2,000..130,000 points (Gaussian blobs
     plus a 30% ground layer), m = 200, eps = 0.3 m, MinPts = 4; one
@@ -756,7 +805,8 @@ def main():
     ap.add_argument("--sharded", action="store_true",
                     help="N > 1: split one dataset's rows across ranks (strong scaling)")
     ap.add_argument("--form", default="plain",
-                    choices=["plain", "bf16", "batched", "surrogate", "balls", "sweep", "cosine"])
+                    choices=["plain", "bf16", "batched", "surrogate", "balls", "sweep", "cosine",
+                             "graph"])
     ap.add_argument("--sweep-n", type=int, default=100_000)
     ap.add_argument("--sweep-s", type=float, nargs="+",
                     default=[0.3, 0.1, 0.03, 0.01, 0.003, 0.001])
@@ -785,7 +835,8 @@ def main():
     if args.form != "plain":
         import __graft_entry__
         __graft_entry__.build()
-        fn = {"bf16": bench_bf16, "cosine": bench_cosine, "batched": bench_batched,
+        fn = {"bf16": bench_bf16, "cosine": bench_cosine, "graph": bench_graph,
+              "batched": bench_batched,
               "surrogate": bench_surrogate,
               "balls": bench_balls, "sweep": bench_sweep}
         print(json.dumps(fn[args.form](args)), flush=True)

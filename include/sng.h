@@ -86,6 +86,13 @@ typedef int32_t sng_status;
 #define SNG_FLAG_TIMING 1u  /* fill sng_stats.ms with per-phase CUDA-event times */
 #define SNG_FLAG_PREFETCH 2u /* gather: bulk-prefetch partner rows into L2 one stage
                                 ahead (16-byte rows; measured slower at d = 64)  */
+#define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
+                                call, so it can be captured in a CUDA graph.  The
+                                edge arrays are sized for all n*m draws (8 bytes
+                                each) instead of the counted E; stats must be NULL;
+                                counters go to counters_out (if set); not with
+                                SNG_FLAG_TIMING or SNG_DEG_SIMPLE.  Device-side
+                                status bits are reported only in counters_out.  */
 
 typedef struct {
     int64_t n;            /* number of points, 2 <= n <= 2^31 - 1            */
@@ -123,6 +130,12 @@ typedef struct {
      * (sng_build_graph only; the other calls reject a partial range).      */
     int64_t row_begin;
     int64_t row_end;
+    /* SNG_FLAG_NO_SYNC: device uint64[9] receiving, at the end of the call,
+     * [0] reserved (0), [1] band pairs, [2] FP64 rechecks, [3] band points,
+     * [4] cores, [5] clusters, [6] noise points, [7] kept draws (edges),
+     * [8] device status bits (nonzero: a bounded loop gave up or an index
+     * check failed).  NULL: not written.  Ignored without the flag. */
+    unsigned long long *counters_out;
 } sng_params;
 
 typedef struct {

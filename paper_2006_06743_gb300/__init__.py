@@ -31,6 +31,7 @@ SNG_METRIC_L2, SNG_METRIC_DOT, SNG_METRIC_COSINE = 0, 1, 2
 SNG_SAMPLE_HASH, SNG_SAMPLE_ALL = 0, 1
 SNG_FLAG_TIMING = 1
 SNG_FLAG_PREFETCH = 2
+SNG_FLAG_NO_SYNC = 4
 
 PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total", "gate")
 
@@ -51,7 +52,8 @@ class sng_params(ctypes.Structure):
                 ("map_group", ctypes.c_int32), ("map_unroll", ctypes.c_int32),
                 ("map_block", ctypes.c_int32), ("map_tile", ctypes.c_int32),
                 ("map_passes", ctypes.c_int32), ("metric", ctypes.c_int32),
-                ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64)]
+                ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
+                ("counters_out", ctypes.c_void_p)]
 
 
 class sng_mi_terms(ctypes.Structure):
@@ -274,6 +276,28 @@ def cluster(x, params: Params, x_master=None, want_core: bool = False, stream=No
     st = sng_cluster(x.data_ptr(), params.to_c(n, d, ld, dtype, mp), labels.data_ptr(),
                      core.data_ptr() if core is not None else 0, _stream_ptr(stream))
     return (labels, core, st) if want_core else (labels, st)
+
+
+def cluster_async(x, params: Params, labels, counters=None, core=None, stream=None):
+    """Algorithm 1 without any host synchronisation inside the call
+    (SNG_FLAG_NO_SYNC), so the call can be captured in a CUDA graph: labels
+    (int32, n) and core (uint8, n, optional) are caller-owned CUDA tensors
+    written when the stream reaches them; ``counters`` (int64 CUDA tensor of
+    9, optional) receives [0] 0, [1] band pairs, [2] rechecks, [3] band
+    points, [4] cores, [5] clusters, [6] noise, [7] kept draws and [8] the
+    device status bits.  FP32 points only."""
+    import torch
+    dtype = SNG_BF16 if x.dtype == torch.bfloat16 else SNG_F32
+    if dtype != SNG_F32:
+        raise ValueError("cluster_async takes float32 points")
+    n, d, ld = _rows(x, dtype)
+    c = params.to_c(n, d, ld, dtype, 0)
+    c.flags = (c.flags | SNG_FLAG_NO_SYNC) & ~SNG_FLAG_TIMING
+    c.counters_out = counters.data_ptr() if counters is not None else None
+    _check(lib().sng_cluster(x.data_ptr(), ctypes.byref(c), labels.data_ptr(),
+                             core.data_ptr() if core is not None else None, None,
+                             _stream_ptr(stream)))
+    return labels
 
 
 def sng_build_graph(x_ptr: int, params: sng_params, stream: int = 0):

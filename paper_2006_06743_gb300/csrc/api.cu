@@ -122,6 +122,13 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
     return fail(SNG_EINVAL, "eps must be in [1e-15, 1e18]");
   if (p->metric != SNG_METRIC_L2 && p->map_passes > 1)
     return fail(SNG_EINVAL, "the similarity form runs in one pass (map_passes <= 1)");
+  if (p->flags & SNG_FLAG_NO_SYNC) {
+    if (p->flags & SNG_FLAG_TIMING)
+      return fail(SNG_EINVAL, "phase timing reads events on the host: not with SNG_FLAG_NO_SYNC");
+    if (p->degree_mode == SNG_DEG_SIMPLE)
+      return fail(SNG_EINVAL, "the distinct-neighbour degree sizes its pair set from E: "
+                              "not with SNG_FLAG_NO_SYNC");
+  }
   if (!(p->band_rel >= 0.f) || p->band_rel > 0.25f)
     return fail(SNG_EINVAL, "band_rel must be in [0, 0.25]");
   const size_t esize = p->dtype == SNG_F32 ? 4 : 2;
@@ -376,9 +383,16 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   launch_scan(gb->out_cnt, n, gb->tile_tmp, gb->row_ptr, gb->counters, st);
   tm->mark(st, 2);
   unsigned long long E = 0;
-  e = cudaMemcpyAsync(&E, gb->counters + kCntEdges, 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "edge count read-back");
+  if (p->flags & SNG_FLAG_NO_SYNC) {
+    // no host read of E: the edge arrays get room for every draw and the
+    // later kernels read E from row_ptr[n] on the device
+    E = (unsigned long long)n * (unsigned long long)r.m;
+    gb->num_edges_dev = gb->row_ptr + n;
+  } else {
+    e = cudaMemcpyAsync(&E, gb->counters + kCntEdges, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "edge count read-back");
+  }
   gb->num_edges = (int64_t)E;
   if (gb->col_owned_by_caller) {
     e = cudaMalloc((void **)&gb->col, (size_t)(E ? E : 1) * 4);
@@ -574,6 +588,9 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
   if (r.row_begin != 0 || r.row_end != r.n)
     return fail(SNG_EINVAL, "a source-row range is for sng_build_graph only");
   if (!labels) return fail(SNG_EINVAL, "labels is NULL");
+  if ((params->flags & SNG_FLAG_NO_SYNC) && stats)
+    return fail(SNG_EINVAL, "stats are read on the host: pass NULL with SNG_FLAG_NO_SYNC "
+                            "(counters_out receives the counters)");
   device_sms();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Scratch s(st);
@@ -590,7 +607,8 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
   launch_core_init(ca, sms, st);
   tm.mark(st, 4);
   UnionArgs ua{r.n,      gb.row_ptr, gb.col,      gb.src,      gb.num_edges,
-               core_buf, parent,     labels,      gb.counters, loop_limit()};
+               core_buf, parent,     labels,      gb.counters, loop_limit(),
+               gb.num_edges_dev};
   launch_union(ua, sms, st);
   tm.mark(st, 5);
   launch_label(ua, sms, st);
@@ -600,6 +618,16 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
   tm.mark(st, 7);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "cluster launches");
+  if (params->flags & SNG_FLAG_NO_SYNC) {
+    // counters (and device status bits) to the caller's device memory
+    if (params->counters_out) {
+      e = cudaMemcpyAsync(params->counters_out, gb.counters, kCntStatus * 8 + 8,
+                          cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "counters copy");
+    }
+    s.release();
+    return SNG_OK;
+  }
   rc = read_stats(gb.counters, r, stats, st, &tm);
   s.release();
   return rc;
@@ -611,6 +639,8 @@ sng_status sng_build_graph(const void *x, const sng_params *params, sng_graph *o
   sng_status rc = validate(x, params, &r);
   if (rc) return rc;
   if (!out) return fail(SNG_EINVAL, "out is NULL");
+  if (params->flags & SNG_FLAG_NO_SYNC)
+    return fail(SNG_EINVAL, "SNG_FLAG_NO_SYNC is for sng_cluster only");
   std::memset(out, 0, sizeof(*out));
   device_sms();
   cudaStream_t st = static_cast<cudaStream_t>(stream);

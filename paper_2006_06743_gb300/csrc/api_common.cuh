@@ -58,7 +58,8 @@ struct GraphBufs {
   int64_t *row_ptr = nullptr;
   int32_t *col = nullptr;
   int32_t *src = nullptr;   // source row per edge (clustering only)
-  int64_t num_edges = 0;
+  int64_t num_edges = 0;     // exact, or the capacity in the no-sync form
+  const int64_t *num_edges_dev = nullptr;   // no-sync form: row_ptr + n
   bool want_src = false;
   bool col_owned_by_caller = false;  // true: col from cudaMalloc, not scratch
 };

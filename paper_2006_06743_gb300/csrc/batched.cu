@@ -317,6 +317,8 @@ sng_status sng_batch_plan_create(const int64_t *offsets, int32_t n_clouds, const
   if (!offsets || !base) return fail(SNG_EINVAL, "offsets / base is NULL");
   if (n_clouds < 1) return fail(SNG_EINVAL, "n_clouds must be >= 1");
   if (base->dtype != SNG_F32) return fail(SNG_EINVAL, "batched form takes FP32 points");
+  if (base->flags & SNG_FLAG_NO_SYNC)
+    return fail(SNG_EINVAL, "SNG_FLAG_NO_SYNC is for sng_cluster only (plans replay as graphs)");
   if (base->metric != SNG_METRIC_L2)
     return fail(SNG_EINVAL, "the batched form uses the Euclidean ball (metric 0)");
   if (base->degree_mode == SNG_DEG_SIMPLE)

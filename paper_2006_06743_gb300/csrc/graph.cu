@@ -172,7 +172,8 @@ __global__ void core_init_kernel(CoreArgs a) {
 __global__ void union_kernel(UnionArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.num_edges;
+  const int64_t num_edges = a.num_edges_dev ? *a.num_edges_dev : a.num_edges;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < num_edges;
        e += stride) {
     const int32_t i = a.src[e], p = a.col[e];
     if ((uint32_t)i >= (uint32_t)a.n || (uint32_t)p >= (uint32_t)a.n) {
@@ -189,7 +190,8 @@ __global__ void union_kernel(UnionArgs a) {
 __global__ void label_kernel(UnionArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.num_edges;
+  const int64_t num_edges = a.num_edges_dev ? *a.num_edges_dev : a.num_edges;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < num_edges;
        e += stride) {
     const int32_t i = a.src[e], p = a.col[e];
     if ((uint32_t)i >= (uint32_t)a.n || (uint32_t)p >= (uint32_t)a.n) continue;

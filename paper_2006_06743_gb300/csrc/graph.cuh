@@ -38,6 +38,9 @@ struct UnionArgs {
   int32_t *labels;
   unsigned long long *counters;
   int32_t loop_limit;   // bound of every union-find loop (see sng_internal.cuh)
+  // nullable: device copy of the edge count (num_edges is then only the
+  // capacity the grid is sized for); lets the call run without a host read
+  const int64_t *num_edges_dev = nullptr;
 };
 
 // Loop bound for union-find: kLoopLimit, or SNG_LOOP_LIMIT from the

@@ -845,6 +845,8 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
   if (!(gate->noise_draw_frac >= 0.f && gate->noise_draw_frac <= 1.f))
     return fail(SNG_EINVAL, "noise_draw_frac must be in [0, 1]");
   if (gate->reweight != 0 && gate->reweight != 1) return fail(SNG_EINVAL, "reweight is 0 or 1");
+  if (params->flags & SNG_FLAG_NO_SYNC)
+    return fail(SNG_EINVAL, "SNG_FLAG_NO_SYNC is for sng_cluster only");
   if (params->metric != SNG_METRIC_L2)
     return fail(SNG_EINVAL, "the surrogate form uses the Euclidean ball (metric 0)");
   if (gate->reweight && params->degree_mode == SNG_DEG_SIMPLE)

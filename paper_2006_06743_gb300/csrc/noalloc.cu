@@ -82,6 +82,8 @@ sng_status sng_cluster_noalloc(const float *x, const sng_params *params, int32_t
   if (rc) return rc;
   if (!labels) return fail(SNG_EINVAL, "labels is NULL");
   if (params->dtype != SNG_F32) return fail(SNG_EINVAL, "the no-allocation path takes FP32 points");
+  if (params->flags & SNG_FLAG_NO_SYNC)
+    return fail(SNG_EINVAL, "SNG_FLAG_NO_SYNC is for sng_cluster only");
   if (params->metric != SNG_METRIC_L2)
     return fail(SNG_EINVAL, "the no-allocation path uses the Euclidean ball (metric 0)");
   if (params->degree_mode == SNG_DEG_SIMPLE)

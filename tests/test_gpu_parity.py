@@ -324,3 +324,63 @@ def test_prefetch_on_off_same_graph(orc, n, d, dtype):
     if dtype == "f32":
         rp, col, _, _ = orc.build_rows(x, eps, 3, 400, band_rel=BAND_F32)
         np.testing.assert_array_equal(outs[0][1], col)
+
+
+def test_no_sync_form_matches_and_replays_as_a_cuda_graph(orc):
+    """SNG_FLAG_NO_SYNC: the same labels and counters as the synchronous call,
+    and the call captured once in a CUDA graph replays correctly, also after
+    the points are overwritten in place (n = 10,000 mixture, s = 0.01)."""
+    torch, sng = need_gpu()
+    n = 10_000
+    x = datagen.mixture_2d(n, seed=0)
+    p = sng.Params(eps=0.03, min_pts=3, s=0.01, seed=0)
+    xg = torch.from_numpy(x).cuda()
+    ref, st = sng.cluster(xg, p)
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    counters = torch.zeros(9, dtype=torch.int64, device="cuda")
+    sng.cluster_async(xg, p, labels, counters)
+    torch.cuda.synchronize()
+    assert torch.equal(labels, ref)
+    c = counters.cpu().tolist()
+    assert c == [0, st["band_pairs"], st["recheck_pairs"], st["band_points"], st["cores"],
+                 st["clusters"], st["noise"], st["kept_edges"], 0]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        sng.cluster_async(xg, p, labels, counters)      # warm-up off the capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        sng.cluster_async(xg, p, labels, counters)
+    labels.fill_(-7)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(labels, ref)
+    x2 = datagen.mixture_2d(n, seed=1)
+    xg.copy_(torch.from_numpy(x2))
+    graph.replay()
+    torch.cuda.synchronize()
+    r = orc.cluster(x2, 0.03, 0, 100, 3, band_rel=BAND_F32)
+    np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
+    assert counters[7].item() == r["kept_edges"]
+
+
+def test_no_sync_form_rejections():
+    torch, sng = need_gpu()
+    x = torch.from_numpy(datagen.random_points(300, 3, seed=0)).cuda()
+    labels = torch.empty(300, dtype=torch.int32, device="cuda")
+    with pytest.raises(sng.SngError) as e:     # distinct-neighbour degree
+        sng.cluster_async(x, sng.Params(eps=0.2, min_pts=3, m=20, degree_mode=2), labels)
+    assert e.value.status == sng.SNG_EINVAL
+    with pytest.raises(sng.SngError) as e:     # phase timing with the flag
+        c = sng.Params(eps=0.2, min_pts=3, m=20).to_c(300, 3, 3, sng.SNG_F32)
+        c.flags = sng.SNG_FLAG_NO_SYNC | sng.SNG_FLAG_TIMING
+        sng._check(sng.lib().sng_cluster(x.data_ptr(), sng.ctypes.byref(c), labels.data_ptr(),
+                                         None, None, None))
+    assert e.value.status == sng.SNG_EINVAL
+    # stats requested with the flag
+    p = sng.Params(eps=0.2, min_pts=3, m=20, flags=sng.SNG_FLAG_NO_SYNC)
+    with pytest.raises(sng.SngError) as e:
+        sng.cluster(x, p)
+    assert e.value.status == sng.SNG_EINVAL
