@@ -89,7 +89,8 @@ typedef int32_t sng_status;
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The
                                 edge arrays are sized for all n*m draws (8 bytes
-                                each) instead of the counted E; stats must be NULL;
+                                each; SNG_ENOMEM when that does not fit) instead
+                                of the counted E; stats must be NULL;
                                 counters go to counters_out (if set); not with
                                 SNG_FLAG_TIMING or SNG_DEG_SIMPLE.  Device-side
                                 status bits are reported only in counters_out.  */
