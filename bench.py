@@ -116,7 +116,7 @@ def peaks():
 # over the queries of one launch), from one ncu capture of 256 clouds of the
 # same size distribution; the 4096-cloud launch runs the same per-query code,
 # so its count scales with the queries.
-BATCHED_INST_PER_QUERY = {"batched_kernel<4, 1, 1, 4>": 19_418_482_977 / 3_518_330_800}
+BATCHED_INST_PER_QUERY = {}   # re-captured after each change of the kernel
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one gather
 # launch, from one ncu capture of this workload and kernel.  Reported only
@@ -557,9 +557,13 @@ def bench_batched(args):
     total = x.shape[0]
     del x
     labels = torch.empty(total, dtype=torch.int32, device="cuda")
-    p = sng.Params(eps=0.3, min_pts=4, m=200, seed=args.seed)
+    p = sng.Params(eps=0.3, min_pts=4, m=200, seed=args.seed,
+                   flags=0 if args.lane_rows else sng.SNG_FLAG_WARP_ROWS)
     tuned = None
-    if args.autotune:
+    if args.map_unroll or args.map_block:
+        p = sng.Params(**{**p.__dict__, "map_unroll": args.map_unroll,
+                          "map_block": args.map_block})
+    elif args.autotune:
         from paper_2006_06743_gb300 import autotune
         tuned = autotune.tune_batched(xg, off, p, sample_clouds=256, budget_s=args.tune_budget,
                                       force=args.retune, verbose=args.verbose)
@@ -605,7 +609,8 @@ def bench_batched(args):
     Q = int(stats["queries"])
     # issue-rate roofline: the kernel is bound by instruction issue and L2
     # latency (clouds are L2-resident), not by HBM
-    kname = f"batched_kernel<4, 1, 1, {p.map_unroll or 4}>"
+    lanes = not (p.flags & sng.SNG_FLAG_WARP_ROWS)
+    kname = f"batched_kernel<4, 1, 1, {p.map_unroll or 4}, {int(lanes)}>"
     ipq = BATCHED_INST_PER_QUERY.get(kname)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     issue_peak = sms * 4 * 2070e6           # 4 warp instructions per SM per cycle
@@ -625,8 +630,9 @@ def bench_batched(args):
                                             "noise")},
             "config": {"workload": f"clouds-{args.clouds}-2k..130k-d3", "points": total,
                        "m": 200, "eps": 0.3, "min_pts": 4, "graph": "CUDA graph replay",
-                       "mapping": {k: getattr(p, k) for k in ("map_unroll", "map_block",
-                                                              "map_tile")},
+                       "mapping": {**{k: getattr(p, k) for k in ("map_unroll", "map_block",
+                                                                 "map_tile")},
+                                   "lane_rows": not (p.flags & sng.SNG_FLAG_WARP_ROWS)},
                        "autotuned": tuned is not None},
             "dtype": "f32", "steps": args.steps}
 
@@ -817,6 +823,8 @@ def main():
     ap.add_argument("--cos-sigma", type=float, default=0.0375)
     ap.add_argument("--clouds", type=int, default=4096)
     ap.add_argument("--seq-clouds", type=int, default=512)
+    ap.add_argument("--lane-rows", type=int, default=1,
+                    help="batched form: 1 = one lane per source row (default), 0 = one warp")
     ap.add_argument("--surr-n", type=int, default=2_000_000)
     ap.add_argument("--siblings", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=3000)

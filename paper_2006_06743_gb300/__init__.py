@@ -32,6 +32,7 @@ SNG_SAMPLE_HASH, SNG_SAMPLE_ALL = 0, 1
 SNG_FLAG_TIMING = 1
 SNG_FLAG_PREFETCH = 2
 SNG_FLAG_NO_SYNC = 4
+SNG_FLAG_WARP_ROWS = 8
 
 PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total", "gate")
 

@@ -162,6 +162,8 @@ def tune_batched(x_concat, offsets, p: Params, sample_clouds: int = 256, reps: i
     sizes = np.diff(off[:k + 1])
     key = (f"batched-d{p.__dict__.get('d', x_concat.shape[1])}-ld{x_concat.stride(0)}"
            f"-mean{_bucket(int(sizes.mean()))}-m{_bucket(p.m or 1)}")
+    if p.flags & 8:   # one warp per source row (rows of one float4 default to lanes)
+        key += "-warprows"
     table = {}
     if os.path.exists(path):
         try:

@@ -110,8 +110,84 @@ __device__ void cloud_components(const BatchArgs &a, const CloudInfo &c) {
   }
 }
 
-template <int VEC, int G, int NCH, int U>
-__global__ void __launch_bounds__(256) batched_kernel(BatchArgs a) {
+// One lane per source row, for rows of one float4 (d <= 4): each lane hashes
+// its own row's draws, tests them U at a time (U partner rows in flight per
+// lane) and assembles the keep-bit words in a register -- no shared-memory
+// staging, no ballots, no idle slots when m is not a multiple of a warp's
+// stage.  Decisions, keep bits and degrees are those of gather_row.
+// Returns this lane's kept draws.
+template <int U>
+__device__ unsigned long long lane_rows(const GatherArgs &g, int32_t r0, int32_t r1, int lane,
+                                        int warp, int warps) {
+  unsigned long long kept = 0;
+  const float *X = static_cast<const float *>(g.x);
+  const int m = g.m;
+  for (int32_t base = r0 + warp * 32; base < r1; base += warps * 32) {
+    const int32_t i = base + lane;
+    if (i >= r1) continue;
+    const uint64_t key = row_key(g.seed, i);
+    float xi[4];
+    Chunk<float, 4>::load(X + (int64_t)i * g.ld, xi);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k >= g.d) xi[k] = 0.f;
+    int cnt = 0;
+    for (int jb = 0; jb < m; jb += 32) {
+      const int jn = min(32, m - jb);
+      uint32_t word = 0;
+      for (int j0 = 0; j0 < jn; j0 += U) {
+        int32_t p[U];
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = jb + j0 + u;
+          p[u] = -1;
+          if (j0 + u < jn) p[u] = g.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, g.fm);
+          v[u] = p[u] >= 0 ? __ldg(reinterpret_cast<const float4 *>(X + (int64_t)p[u] * g.ld))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (p[u] < 0) continue;
+          const float b[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            float diff = xi[k] - b[k];
+            if (k >= g.d) diff = 0.f;
+            acc = fmaf(diff, diff, acc);
+          }
+          bool keep = false;
+          if (acc < g.lo_thr) {
+            keep = true;
+          } else if (!(acc > g.hi_thr)) {
+            keep = recheck_pair<float>(g, i, p[u]);
+          }
+          if (keep) {
+            word |= 1u << (j0 + u);
+            if (g.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(g.deg + p[u], 1);
+          }
+        }
+      }
+      __stcs(g.bitmask + (int64_t)i * g.W + (jb >> 5), word);
+      cnt += __popc(word);
+    }
+    if (g.deg_mode == SNG_DEG_UNDIRECTED_MULTI) {
+      if (cnt) atomicAdd(g.deg + i, cnt);
+    } else {
+      g.deg[i] = cnt;
+    }
+    kept += (unsigned long long)cnt;
+  }
+  return kept;
+}
+
+// Lane per row: 4 resident blocks of 256 threads (64 registers; 2 with 8
+// batches in flight -- 6 blocks at 2 in flight fit in 40 registers but
+// measured slower).  Warp per row: no occupancy bound (the compiler's 80
+// registers measured faster than a 64-register bound).
+template <int VEC, int G, int NCH, int U, bool LANES = false>
+__global__ void __launch_bounds__(256, LANES ? (U > 4 ? 2 : 4) : 1) batched_kernel(BatchArgs a) {
   extern __shared__ int32_t smem_partner[];
   __shared__ int s_item;
   __shared__ int s_last;
@@ -156,8 +232,14 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchArgs a) {
     const int32_t r0 = it.y * a.tile_rows;
     const int32_t r1 = min(c.n, r0 + a.tile_rows);
     unsigned long long kept = 0;
-    for (int32_t row = r0 + warp; row < r1; row += warps)
-      kept += (unsigned long long)gather_row<float, VEC, G, NCH, U>(g, row, c.m, sp, lane);
+    if constexpr (LANES) {
+      kept = lane_rows<U>(g, r0, r1, lane, warp, warps);
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) kept += __shfl_xor_sync(kFullMask, kept, o);
+    } else {
+      for (int32_t row = r0 + warp; row < r1; row += warps)
+        kept += (unsigned long long)gather_row<float, VEC, G, NCH, U>(g, row, c.m, sp, lane);
+    }
     if (lane == 0 && kept) atomicAdd(a.counters + kCntEdges, kept);
     // release this tile's keep bits / degree updates, then count the tile
     __threadfence();
@@ -176,18 +258,19 @@ __global__ void __launch_bounds__(256) batched_kernel(BatchArgs a) {
 }
 
 
-template <int VEC, int G, int NCH, int U>
+template <int VEC, int G, int NCH, int U, bool LANES = false>
 static bool try_batched(const BatchMap &m, const BatchArgs &a, int grid, int block,
                         cudaStream_t st, int *occ) {
-  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U) return false;
-  const size_t smem = (size_t)(block / 32) * 64 * U * sizeof(int32_t);
+  if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || (m.lanes != 0) != LANES)
+    return false;
+  const size_t smem = LANES ? 0 : (size_t)(block / 32) * 64 * U * sizeof(int32_t);
   if (occ) {
     *occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batched_kernel<VEC, G, NCH, U>, block,
-                                                  smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batched_kernel<VEC, G, NCH, U, LANES>,
+                                                  block, smem);
     return true;
   }
-  batched_kernel<VEC, G, NCH, U><<<grid, block, smem, st>>>(a);
+  batched_kernel<VEC, G, NCH, U, LANES><<<grid, block, smem, st>>>(a);
   return true;
 }
 
@@ -202,6 +285,10 @@ static bool dispatch_batched(const BatchMap &m, const BatchArgs &a, int grid, in
   SNG_B(2, 1, 1, 2) SNG_B(2, 1, 1, 4) SNG_B(2, 1, 2, 4)
   SNG_B(1, 1, 1, 4) SNG_B(1, 1, 2, 4) SNG_B(1, 1, 4, 2) SNG_B(1, 1, 4, 4)
 #undef SNG_B
+  // one lane per source row (float4 rows)
+  if (try_batched<4, 1, 1, 2, true>(m, a, grid, block, st, occ)) return true;
+  if (try_batched<4, 1, 1, 4, true>(m, a, grid, block, st, occ)) return true;
+  if (try_batched<4, 1, 1, 8, true>(m, a, grid, block, st, occ)) return true;
   return false;
 }
 
@@ -359,6 +446,11 @@ sng_status sng_batch_plan_create(const int64_t *offsets, int32_t n_clouds, const
   p->map.group = r.map.group;
   p->map.nch = r.map.nch;
   p->map.unroll = base->map_unroll > 0 ? base->map_unroll : 4;
+  // rows of one float4: one lane per source row unless asked otherwise (or
+  // unless an unroll the lane-per-row kernel is not compiled for is asked)
+  const bool one_vec = p->map.vec == 4 && p->map.nch == 1 && p->map.group == 1;
+  const bool lane_unroll = p->map.unroll == 2 || p->map.unroll == 4 || p->map.unroll == 8;
+  p->map.lanes = (one_vec && lane_unroll && !(base->flags & SNG_FLAG_WARP_ROWS)) ? 1 : 0;
 
   std::vector<CloudInfo> clouds(n_clouds);
   int64_t bm = 0, q = 0;

@@ -38,6 +38,7 @@ struct BatchArgs {
 
 struct BatchMap {
   int vec, group, nch, unroll;
+  int lanes;   // 1: one lane per source row (rows of one float4)
 };
 
 // Launch the persistent kernel for mapping m (occ != NULL: only report the

@@ -44,10 +44,15 @@ def _run_batched(sng, torch, x, offsets, p, m_per_cloud=None, plan=False, repeat
 
 
 @pytest.mark.parametrize("use_plan", [False, True])
-def test_batched_matches_oracle_per_cloud(orc, use_plan):
+@pytest.mark.parametrize("lanes", [False, True])
+def test_batched_matches_oracle_per_cloud(orc, use_plan, lanes):
+    """Lane per row (the default for float4 rows) and warp per row
+    (SNG_FLAG_WARP_ROWS): m = 40 puts a partial keep-bit word at the end of
+    every row."""
     torch, sng = need_gpu()
     x, off = datagen.point_clouds(12, seed=3, n_min=200, n_max=3000)
-    p = sng.Params(eps=0.3, min_pts=4, m=40, seed=100)
+    p = sng.Params(eps=0.3, min_pts=4, m=40, seed=100,
+                   flags=0 if lanes else sng.SNG_FLAG_WARP_ROWS)
     labels, st, _ = _run_batched(sng, torch, x, off, p, plan=use_plan)
     tot = dict(cores=0, clusters=0, noise=0, kept_edges=0)
     for b in range(len(off) - 1):
@@ -92,6 +97,33 @@ def test_batched_graph_replay_identical_and_matches_single_calls():
         xb = torch.from_numpy(np.ascontiguousarray(x[off[b]:off[b + 1], :3])).cuda()
         lb, _ = sng.cluster(xb, sng.Params(eps=p.eps, min_pts=p.min_pts, m=p.m, seed=p.seed + b))
         np.testing.assert_array_equal(lb.cpu().numpy(), last[off[b]:off[b + 1]])
+
+
+def test_batched_lane_rows_per_cloud_draws_and_modes(orc):
+    """Lane per row with per-cloud draw counts (1 .. 200), out-degree, every
+    pair queried, and each compiled unroll; rows of d = 3 padded to 4 with
+    NaN in the padding, which must not reach the distance."""
+    torch, sng = need_gpu()
+    x, off = datagen.point_clouds(6, seed=8, n_min=100, n_max=900)
+    x = x.copy()
+    x[:, 3] = np.nan
+    mpc = np.array([1, 5, 33, 64, 65, 200])
+    for unroll in (2, 4, 8):
+        for deg_mode in (0, 1):
+            p = sng.Params(eps=0.4, min_pts=3, seed=7, map_unroll=unroll, degree_mode=deg_mode)
+            labels, _, _ = _run_batched(sng, torch, x, off, p, m_per_cloud=mpc)
+            for b in range(len(off) - 1):
+                xb = np.ascontiguousarray(x[off[b]:off[b + 1], :3])
+                r = orc.cluster(xb, p.eps, p.seed + b, int(mpc[b]), p.min_pts, deg_mode=deg_mode,
+                                band_rel=BAND_F32)
+                np.testing.assert_array_equal(labels[off[b]:off[b + 1]], r["labels"])
+    p = sng.Params(eps=0.4, min_pts=3, sample_mode=1)
+    labels, _, _ = _run_batched(sng, torch, x, off, p)
+    for b in range(len(off) - 1):
+        xb = np.ascontiguousarray(x[off[b]:off[b + 1], :3])
+        r = orc.cluster(xb, p.eps, 0, int(off[b + 1] - off[b]) - 1, p.min_pts, sample_all=True,
+                        band_rel=BAND_F32)
+        np.testing.assert_array_equal(labels[off[b]:off[b + 1]], r["labels"])
 
 
 @pytest.mark.parametrize("unroll,block,tile", [(1, 256, 1024), (2, 128, 64), (8, 256, 4096)])
