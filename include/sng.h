@@ -90,7 +90,7 @@ typedef int32_t sng_status;
                                 rows of one float4 (d <= 4, ld = 4), where the
                                 default is one lane per source row (each lane
                                 hashes, tests and records its own row's draws;
-                                2, 4 or 8 batches in flight -- map_unroll 1
+                                2 or 4 batches in flight -- map_unroll 1 or 8
                                 selects one warp per row as well)             */
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The

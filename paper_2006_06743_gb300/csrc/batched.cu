@@ -182,12 +182,12 @@ __device__ unsigned long long lane_rows(const GatherArgs &g, int32_t r0, int32_t
   return kept;
 }
 
-// Lane per row: 4 resident blocks of 256 threads (64 registers; 2 with 8
-// batches in flight -- 6 blocks at 2 in flight fit in 40 registers but
-// measured slower).  Warp per row: no occupancy bound (the compiler's 80
-// registers measured faster than a 64-register bound).
+// Lane per row: 4 resident blocks of 256 threads (64 registers; 6 blocks at
+// 2 batches in flight fit in 40 registers but measured slower, and 8 in
+// flight would leave 2 blocks).  Warp per row: no occupancy bound (the
+// compiler's 80 registers measured faster than a 64-register bound).
 template <int VEC, int G, int NCH, int U, bool LANES = false>
-__global__ void __launch_bounds__(256, LANES ? (U > 4 ? 2 : 4) : 1) batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(256, LANES ? 4 : 1) batched_kernel(BatchArgs a) {
   extern __shared__ int32_t smem_partner[];
   __shared__ int s_item;
   __shared__ int s_last;
@@ -288,7 +288,6 @@ static bool dispatch_batched(const BatchMap &m, const BatchArgs &a, int grid, in
   // one lane per source row (float4 rows)
   if (try_batched<4, 1, 1, 2, true>(m, a, grid, block, st, occ)) return true;
   if (try_batched<4, 1, 1, 4, true>(m, a, grid, block, st, occ)) return true;
-  if (try_batched<4, 1, 1, 8, true>(m, a, grid, block, st, occ)) return true;
   return false;
 }
 
@@ -449,7 +448,7 @@ sng_status sng_batch_plan_create(const int64_t *offsets, int32_t n_clouds, const
   // rows of one float4: one lane per source row unless asked otherwise (or
   // unless an unroll the lane-per-row kernel is not compiled for is asked)
   const bool one_vec = p->map.vec == 4 && p->map.nch == 1 && p->map.group == 1;
-  const bool lane_unroll = p->map.unroll == 2 || p->map.unroll == 4 || p->map.unroll == 8;
+  const bool lane_unroll = p->map.unroll == 2 || p->map.unroll == 4;
   p->map.lanes = (one_vec && lane_unroll && !(base->flags & SNG_FLAG_WARP_ROWS)) ? 1 : 0;
 
   std::vector<CloudInfo> clouds(n_clouds);
