@@ -86,12 +86,15 @@ typedef int32_t sng_status;
 #define SNG_FLAG_TIMING 1u  /* fill sng_stats.ms with per-phase CUDA-event times */
 #define SNG_FLAG_PREFETCH 2u /* gather: bulk-prefetch partner rows into L2 one stage
                                 ahead (16-byte rows; measured slower at d = 64)  */
-#define SNG_FLAG_WARP_ROWS 8u /* batched form: one warp per source row even for
-                                rows of one float4 (d <= 4, ld = 4), where the
-                                default is one lane per source row (each lane
-                                hashes, tests and records its own row's draws;
-                                2 or 4 batches in flight -- map_unroll 1 or 8
-                                selects one warp per row as well)             */
+#define SNG_FLAG_WARP_ROWS 8u /* one warp per source row even where the default
+                                is one lane per source row: the Euclidean form
+                                with one lane per pair (rows of at most 4
+                                vectors and at least 32 x 16 rows per SM; in
+                                the batched form, rows of one float4), where
+                                each lane hashes, tests and
+                                records its own row's draws with 2 or 4
+                                batches in flight (map_unroll 1 or 8 selects
+                                one warp per row as well)                    */
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The
                                 edge arrays are sized for all n*m draws (8 bytes

@@ -196,6 +196,14 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   r->map.sim = p->metric != SNG_METRIC_L2;
   r->map.full = group * nch * vec == p->d;
   r->map.unroll = p->map_unroll > 0 ? p->map_unroll : (vec == vmax && nch * vec >= 16 ? 2 : 4);
+  // one lane per pair and short rows: one lane per source row (compiled for
+  // 2 and 4 partner rows in flight), unless one warp per row is asked for or
+  // the rows would give fewer than 16 warps per SM (32 rows per warp: small
+  // sets run faster with a warp per row)
+  const int64_t rows = (p->row_begin == 0 && p->row_end == 0) ? p->n : p->row_end - p->row_begin;
+  r->map.lanes = group == 1 && p->metric == SNG_METRIC_L2 &&
+                 (r->map.unroll == 2 || r->map.unroll == 4) &&
+                 !(p->flags & SNG_FLAG_WARP_ROWS) && rows >= 32LL * 16 * device_sms();
   if (p->map_passes < 0 || p->map_passes > 64) return fail(SNG_EINVAL, "map_passes must be in [0, 64]");
   r->map.passes = p->map_passes > 0 ? p->map_passes : 1;
   if (r->map.passes > p->n) r->map.passes = (int)p->n;
@@ -302,7 +310,8 @@ int gather_grid(int dtype, const GatherMap &map, int64_t n) {
                               : gather_max_blocks_per_sm(dtype, map);
   if (per_sm < 1) per_sm = 1;
   const int64_t warps_per_block = map.block / 32;
-  int64_t need = (n + warps_per_block - 1) / warps_per_block;
+  const int64_t rows_per_warp = map.lanes ? 32 : 1;
+  int64_t need = (n + warps_per_block * rows_per_warp - 1) / (warps_per_block * rows_per_warp);
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > need) grid = need;
   return (int)(grid < 1 ? 1 : grid);

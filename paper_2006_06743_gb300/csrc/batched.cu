@@ -110,78 +110,6 @@ __device__ void cloud_components(const BatchArgs &a, const CloudInfo &c) {
   }
 }
 
-// One lane per source row, for rows of one float4 (d <= 4): each lane hashes
-// its own row's draws, tests them U at a time (U partner rows in flight per
-// lane) and assembles the keep-bit words in a register -- no shared-memory
-// staging, no ballots, no idle slots when m is not a multiple of a warp's
-// stage.  Decisions, keep bits and degrees are those of gather_row.
-// Returns this lane's kept draws.
-template <int U>
-__device__ unsigned long long lane_rows(const GatherArgs &g, int32_t r0, int32_t r1, int lane,
-                                        int warp, int warps) {
-  unsigned long long kept = 0;
-  const float *X = static_cast<const float *>(g.x);
-  const int m = g.m;
-  for (int32_t base = r0 + warp * 32; base < r1; base += warps * 32) {
-    const int32_t i = base + lane;
-    if (i >= r1) continue;
-    const uint64_t key = row_key(g.seed, i);
-    float xi[4];
-    Chunk<float, 4>::load(X + (int64_t)i * g.ld, xi);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (k >= g.d) xi[k] = 0.f;
-    int cnt = 0;
-    for (int jb = 0; jb < m; jb += 32) {
-      const int jn = min(32, m - jb);
-      uint32_t word = 0;
-      for (int j0 = 0; j0 < jn; j0 += U) {
-        int32_t p[U];
-        float4 v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int j = jb + j0 + u;
-          p[u] = -1;
-          if (j0 + u < jn) p[u] = g.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, g.fm);
-          v[u] = p[u] >= 0 ? __ldg(reinterpret_cast<const float4 *>(X + (int64_t)p[u] * g.ld))
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (p[u] < 0) continue;
-          const float b[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-          float acc = 0.f;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            float diff = xi[k] - b[k];
-            if (k >= g.d) diff = 0.f;
-            acc = fmaf(diff, diff, acc);
-          }
-          bool keep = false;
-          if (acc < g.lo_thr) {
-            keep = true;
-          } else if (!(acc > g.hi_thr)) {
-            keep = recheck_pair<float>(g, i, p[u]);
-          }
-          if (keep) {
-            word |= 1u << (j0 + u);
-            if (g.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(g.deg + p[u], 1);
-          }
-        }
-      }
-      __stcs(g.bitmask + (int64_t)i * g.W + (jb >> 5), word);
-      cnt += __popc(word);
-    }
-    if (g.deg_mode == SNG_DEG_UNDIRECTED_MULTI) {
-      if (cnt) atomicAdd(g.deg + i, cnt);
-    } else {
-      g.deg[i] = cnt;
-    }
-    kept += (unsigned long long)cnt;
-  }
-  return kept;
-}
-
 // Lane per row: 4 resident blocks of 256 threads (64 registers; 6 blocks at
 // 2 batches in flight fit in 40 registers but measured slower, and 8 in
 // flight would leave 2 blocks).  Warp per row: no occupancy bound (the
@@ -233,7 +161,7 @@ __global__ void __launch_bounds__(256, LANES ? 4 : 1) batched_kernel(BatchArgs a
     const int32_t r1 = min(c.n, r0 + a.tile_rows);
     unsigned long long kept = 0;
     if constexpr (LANES) {
-      kept = lane_rows<U>(g, r0, r1, lane, warp, warps);
+      kept = gather_rows_lanes<float, 4, 1, U>(g, r0, r1, lane, warp, warps);
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) kept += __shfl_xor_sync(kFullMask, kept, o);
     } else {

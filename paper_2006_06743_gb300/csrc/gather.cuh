@@ -337,6 +337,102 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
   return cnt;
 }
 
+// One lane per source row, for rows of at most NCH vectors of VEC elements
+// (the mappings with one lane per pair): each lane hashes its own row's
+// draws, keeps U partner rows in flight and assembles the keep-bit words in
+// a register -- no shared-memory staging, no ballots, no idle slots in a
+// row's last stage.  Rows [r0, r1) are taken 32 at a time by warps
+// first_warp, first_warp + warp_stride, ...  Decisions, keep bits, row
+// counts and degrees are those of gather_row.  Returns this lane's kept
+// draws.
+template <typename T, int VEC, int NCH, int U>
+__device__ __forceinline__ unsigned long long gather_rows_lanes(const GatherArgs &a, int64_t r0,
+                                                                int64_t r1, int lane,
+                                                                int64_t first_warp,
+                                                                int64_t warp_stride) {
+  const T *X = static_cast<const T *>(a.x);
+  const int d = a.d;
+  unsigned long long kept = 0;
+  for (int64_t base = r0 + first_warp * 32; base < r1; base += warp_stride * 32) {
+    const int64_t row = base + lane;
+    if (row >= r1) continue;
+    const int32_t i = (int32_t)row;
+    const int32_t mi = a.m_row ? a.m_row[i] : a.m;
+    const int32_t wi = a.w_row ? a.w_row[i] : 1;
+    const uint64_t key = row_key(a.seed, i);
+    float xi[NCH][VEC];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const int off = c * VEC;
+      if (off < d) {
+        Chunk<T, VEC>::load(X + (int64_t)i * a.ld + off, xi[c]);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k)
+          if (off + k >= d) xi[c][k] = 0.f;
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) xi[c][k] = 0.f;
+      }
+    }
+    int cnt = 0;
+    for (int jb = 0; jb < mi; jb += 32) {
+      const int jn = min(32, mi - jb);
+      uint32_t word = 0;
+      for (int j0 = 0; j0 < jn; j0 += U) {
+        int32_t p[U];
+        typename Raw<T, VEC>::type v[U][NCH];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t j = (int64_t)jb + j0 + u;
+          p[u] = -1;
+          if (j0 + u < jn) p[u] = a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm);
+#pragma unroll
+          for (int c = 0; c < NCH; ++c)
+            v[u][c] = (p[u] >= 0 && c * VEC < d)
+                          ? Raw<T, VEC>::load(X + (int64_t)p[u] * a.ld + c * VEC)
+                          : Raw<T, VEC>::zero();
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (p[u] < 0) continue;
+          float acc = 0.f;
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+              float diff = xi[c][k] - Raw<T, VEC>::get(v[u][c], k);
+              if (c * VEC + k >= d) diff = 0.f;   // row padding may hold anything
+              acc = fmaf(diff, diff, acc);
+            }
+          }
+          bool keep = false;
+          if (acc < a.lo_thr) {
+            keep = true;
+          } else if (!(acc > a.hi_thr)) {
+            keep = recheck_pair<T>(a, i, p[u]);
+          }
+          if (keep) {
+            word |= 1u << (j0 + u);
+            if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p[u], wi);
+          }
+        }
+      }
+      __stcs(a.bitmask + (int64_t)i * a.W + (jb >> 5), word);
+      cnt += __popc(word);
+    }
+    // words past this row's draws (per-row draw counts) are zero
+    for (int w = (mi + 31) >> 5; w < a.W; ++w) __stcs(a.bitmask + (int64_t)i * a.W + w, 0u);
+    if (a.out_cnt) a.out_cnt[i] = cnt;
+    if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) {
+      if (cnt) atomicAdd(a.deg + i, cnt * wi);
+    } else {
+      a.deg[i] = cnt * wi;
+    }
+    kept += (unsigned long long)cnt;
+  }
+  return kept;
+}
+
 // Resident 256-thread blocks per SM the compiler must allow for: mappings
 // with few registers of row data get 4 (32 warps), wider ones 3 or 2.
 template <typename T, int VEC, int NCH, int U, bool SIM = false>
@@ -351,11 +447,21 @@ struct MinBlocks {
 
 // FULL: every row is exactly G * NCH * VEC elements wide (no partial or
 // empty chunk), so the per-chunk bounds tests drop out of the pair loop.
-template <typename T, int VEC, int G, int NCH, int U, bool SIM = false, bool FULL = false>
-__global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U, SIM>::value) gather_kernel(GatherArgs a) {
+// LANES: one lane per source row (G == 1 only; see gather_rows_lanes).
+template <typename T, int VEC, int G, int NCH, int U, bool SIM = false, bool FULL = false,
+          bool LANES = false>
+__global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U, SIM>::value)
+    gather_kernel(GatherArgs a) {
   extern __shared__ int32_t smem_partner[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  if constexpr (LANES) {
+    static_assert(G == 1 && !SIM, "one lane per row: Euclidean form, one lane per pair");
+    gather_rows_lanes<T, VEC, NCH, U>(a, a.row_begin, a.row_end, lane,
+                                      (int64_t)blockIdx.x * (blockDim.x >> 5) + warp,
+                                      (int64_t)gridDim.x * (blockDim.x >> 5));
+    return;
+  }
   int32_t *sp = smem_partner + warp * 64 * U;   // two stages of 32*U partners
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = a.row_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -503,6 +609,7 @@ struct GatherMap {
   int passes;   // 1: single pass; > 1: L2-blocked slices of the partner range
   int sim;      // 1: similarity form (inner product / cosine) of the kernel
   int full;     // 1: d == group * nch * vec (a FULL instantiation may serve)
+  int lanes;    // 1: one lane per source row (a LANES instantiation may serve)
 };
 
 // Host-side launcher; returns false if no compiled variant matches `map`.

@@ -90,6 +90,38 @@ static bool matches(const GatherMap &m) {
     if (b >= 0) return b;                      \
   }
 
+// one lane per source row (group 1, Euclidean form): no shared memory
+template <typename T, int VEC, int NCH, int U>
+static bool try_launch_lanes(const GatherMap &m, const GatherArgs &args, int grid,
+                             cudaStream_t st) {
+  if (m.vec != VEC || m.group != 1 || m.nch != NCH || m.unroll != U || m.sim || !m.lanes)
+    return false;
+  gather_kernel<T, VEC, 1, NCH, U, false, false, true><<<grid, m.block, 0, st>>>(args);
+  return true;
+}
+
+template <typename T, int VEC, int NCH, int U>
+static int occ_blocks_lanes(const GatherMap &m) {
+  if (m.vec != VEC || m.group != 1 || m.nch != NCH || m.unroll != U || m.sim || !m.lanes)
+    return -1;
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &blocks, gather_kernel<T, VEC, 1, NCH, U, false, false, true>, m.block, 0) !=
+      cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+#define SNG_LANE_SHAPES(T, V, X) \
+  X(T, V, 1, 2) X(T, V, 1, 4) X(T, V, 2, 2) X(T, V, 2, 4) X(T, V, 4, 2) X(T, V, 4, 4)
+#define SNG_TRY_L(T, V, N, U) \
+  if (try_launch_lanes<T, V, N, U>(map, args, grid, stream)) return true;
+#define SNG_OCC_L(T, V, N, U)                        \
+  {                                                  \
+    int b = occ_blocks_lanes<T, V, N, U>(map);       \
+    if (b >= 0) return b;                            \
+  }
+
 // full rows (d == group * nch * vec), Euclidean form
 #define SNG_TRY_F(T, V, G, N, U) \
   if (try_launch<T, V, G, N, U, false, true>(map, args, grid, stream)) return true;

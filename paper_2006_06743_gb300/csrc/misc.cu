@@ -9,6 +9,7 @@ namespace sng {
 SNG_UNIT(f32_a) SNG_UNIT(f32_b) SNG_UNIT(f32_c) SNG_UNIT(bf16_a) SNG_UNIT(bf16_b) SNG_UNIT(bf16_c)
 SNG_UNIT(sim_f32_a) SNG_UNIT(sim_f32_b) SNG_UNIT(sim_bf16_a) SNG_UNIT(sim_bf16_b)
 SNG_UNIT(full_f32) SNG_UNIT(full_bf16) SNG_UNIT(full_sim_f32) SNG_UNIT(full_sim_bf16)
+SNG_UNIT(lanes_f32) SNG_UNIT(lanes_bf16)
 #undef SNG_UNIT
 bool has_sim_f32_a(const GatherMap &);
 bool has_sim_f32_b(const GatherMap &);
@@ -52,6 +53,9 @@ bool launch_gather(int dtype, const GatherMap &map, const GatherArgs &args, int 
       return launch_sim_f32_a(map, args, grid, stream) || launch_sim_f32_b(map, args, grid, stream);
     return launch_sim_bf16_a(map, args, grid, stream) || launch_sim_bf16_b(map, args, grid, stream);
   }
+  if (map.lanes && (dtype == SNG_F32 ? launch_lanes_f32(map, args, grid, stream)
+                                      : launch_lanes_bf16(map, args, grid, stream)))
+    return true;
   if (map.full && (dtype == SNG_F32 ? launch_full_f32(map, args, grid, stream)
                                      : launch_full_bf16(map, args, grid, stream)))
     return true;
@@ -75,6 +79,8 @@ int gather_max_blocks_per_sm(int dtype, const GatherMap &map) {
     }
     return 0;
   }
+  if (map.lanes && (b = dtype == SNG_F32 ? occ_lanes_f32(map) : occ_lanes_bf16(map)) >= 0)
+    return b;
   if (map.full && (b = dtype == SNG_F32 ? occ_full_f32(map) : occ_full_bf16(map)) >= 0) return b;
   if (dtype == SNG_F32) {
     if ((b = occ_f32_a(map)) >= 0 || (b = occ_f32_b(map)) >= 0 || (b = occ_f32_c(map)) >= 0)

@@ -326,6 +326,39 @@ def test_prefetch_on_off_same_graph(orc, n, d, dtype):
         np.testing.assert_array_equal(outs[0][1], col)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 8, 16])
+def test_lane_per_row_graph_matches_oracle(orc, dtype, d):
+    """Rows of at most 4 vectors and enough of them (n = 100,000) run one lane
+    per source row; m = 40 leaves a partial keep-bit word per row.  The
+    graph equals the oracle's and the warp-per-row kernel's
+    (SNG_FLAG_WARP_ROWS), and the labels agree."""
+    torch, sng = need_gpu()
+    n, m = 100_000, 40
+    x = datagen.random_points(n, d, seed=d + 50)
+    eps = float(np.float32(0.02 * math.sqrt(d) if d > 1 else 0.0005))
+    if dtype == "bf16":
+        bits = datagen.bf16_round(x)
+        xo = datagen.bf16_to_f32(bits)
+        xg = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+        master, band = torch.from_numpy(xo).cuda(), BAND_BF16
+    else:
+        xo, xg, master, band = x, torch.from_numpy(x).cuda(), None, BAND_F32
+    rp, col, bpairs, _ = orc.build_rows(xo, eps, 3, m, band_rel=band)
+    assert col.size > 0
+    for flags in (0, sng.SNG_FLAG_WARP_ROWS):
+        p = sng.Params(eps=eps, min_pts=2, m=m, seed=3, flags=flags)
+        g = sng.build_graph(xg, p, x_master=master)
+        np.testing.assert_array_equal(g["row_ptr"].cpu().numpy(), rp)
+        np.testing.assert_array_equal(g["col"].cpu().numpy(), col)
+        np.testing.assert_array_equal(g["deg"].cpu().numpy(), orc.degrees(n, rp, col))
+        assert g["stats"]["band_pairs"] == bpairs
+        assert g["stats"]["map_group"] == 1
+    r = orc.cluster(xo, eps, 3, m, 2, band_rel=band)
+    labels, _ = sng.cluster(xg, sng.Params(eps=eps, min_pts=2, m=m, seed=3), x_master=master)
+    np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
+
+
 def test_no_sync_form_matches_and_replays_as_a_cuda_graph(orc):
     """SNG_FLAG_NO_SYNC: the same labels and counters as the synchronous call,
     and the call captured once in a CUDA graph replays correctly, also after

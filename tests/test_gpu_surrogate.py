@@ -110,12 +110,15 @@ def test_training_steps_match_oracle_adam():
         assert torch.equal(net.params[nt:], p0[nt:])
 
 
-def test_gated_cluster_matches_oracle_gated_form(orc):
+@pytest.mark.parametrize("n", [6000, 100_000])
+def test_gated_cluster_matches_oracle_gated_form(orc, n):
     """Given the gate's decisions (from the network's probabilities), the
-    surrogate path is exactly the oracle's gated form of Algorithm 1."""
+    surrogate path is exactly the oracle's gated form of Algorithm 1 (at
+    n = 100,000 the gather runs one lane per row, with per-row draw counts
+    and weights)."""
     torch, sng = need_gpu()
     from paper_2006_06743_gb300 import surrogate as sg
-    n, d, m = 6000, 8, 120
+    d, m = 8, 120
     x = datagen.gaussian_mixture(n, d, 8, 0.05, seed=2, centre_std=1.0, sigma_lo=0.05,
                                  sigma_hi=0.1)
     eps = datagen.eps_quantile(x, 0.05, 200_000, seed=2)
