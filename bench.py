@@ -123,7 +123,7 @@ BATCHED_INST_PER_QUERY = {"batched_kernel<4, 1, 1, 4, 1>": 14_119_942_974 / 3_51
 # launch, from one ncu capture of this workload and kernel.  Reported only
 # while the timed launch uses that same kernel and mapping.
 CAPTURED_TRAFFIC = {
-    ("mixture-n1M-d64", "gather_kernel<float, 4, 4, 4, 2, 0, 1>"): 168_524_939_776 + 456_195_584,
+    ("mixture-n1M-d64", "gather_kernel<float, 4, 4, 4, 2, 0, 1, 0>"): 168_524_939_776 + 456_195_584,
 }
 
 
@@ -262,7 +262,7 @@ def bench_sng(args, w):
     achieved = alg / (g_ms * 1e-3) / 1e9
     full = stats["map_group"] * stats["map_nch"] * stats["map_vec"] == d
     kname = (f"gather_kernel<float, {stats['map_vec']}, {stats['map_group']}, "
-             f"{stats['map_nch']}, {stats['map_unroll']}, 0{', 1' if full else ''}>")
+             f"{stats['map_nch']}, {stats['map_unroll']}, 0, {int(full)}, 0>")
     traffic = None
     if params.map_passes <= 1 and not (params.flags & sng.SNG_FLAG_PREFETCH):
         traffic = CAPTURED_TRAFFIC.get((args.workload, kname))
