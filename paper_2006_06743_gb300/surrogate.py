@@ -55,6 +55,77 @@ def unpack(v, d: int) -> tuple[dict, np.ndarray, np.ndarray]:
     return out, v[o:o + d], v[o + d:o + 2 * d]
 
 
+# ------------------------------------------------------------ checkpoints
+#
+# File layout (little-endian): the 8-byte magic b"SNGMLP01", then int32
+# version (1), d, hidden, parameter count P, trained count T, flags (bit 0:
+# Adam moments follow), int64 Adam step, then P FP32 parameters in the
+# library's layout (w1, b1, w2, b2, w3, b3, mean, std) and, with bit 0, the T
+# FP32 first moments and T FP32 second moments.
+
+MAGIC = b"SNGMLP01"
+_HEADER = np.dtype([("version", "<i4"), ("d", "<i4"), ("hidden", "<i4"), ("n_params", "<i4"),
+                    ("n_trained", "<i4"), ("flags", "<i4"), ("step", "<i8")])
+
+
+def _counts(d: int, hidden: int = HIDDEN) -> tuple[int, int]:
+    trained = hidden * d + hidden + hidden * hidden + hidden + hidden + 1
+    return trained + 2 * d, trained
+
+
+def save_params(path: str, params, d: int, step: int = 0, m=None, v=None) -> None:
+    """Write a parameter vector (and optionally Adam moments) to ``path``."""
+    n_params, n_trained = _counts(d)
+    params = np.ascontiguousarray(params, dtype="<f4").ravel()
+    if params.size != n_params:
+        raise ValueError(f"expected {n_params} parameters for d = {d}, got {params.size}")
+    moments = m is not None and v is not None
+    hdr = np.zeros(1, dtype=_HEADER)
+    hdr[0] = (1, d, HIDDEN, n_params, n_trained, 1 if moments else 0, step)
+    with open(path, "wb") as f:
+        f.write(MAGIC)
+        f.write(hdr.tobytes())
+        f.write(params.tobytes())
+        if moments:
+            for a in (m, v):
+                a = np.ascontiguousarray(a, dtype="<f4").ravel()
+                if a.size != n_trained:
+                    raise ValueError(f"expected {n_trained} moments, got {a.size}")
+                f.write(a.tobytes())
+
+
+def load_params(path: str) -> dict:
+    """Read a file written by ``save_params``: d, step, params, and m / v
+    (None when the file holds no moments).  Raises ValueError on a wrong
+    magic, version, size or truncated file."""
+    with open(path, "rb") as f:
+        blob = f.read()
+    if blob[:8] != MAGIC:
+        raise ValueError("not a surrogate checkpoint (bad magic)")
+    if len(blob) < 8 + _HEADER.itemsize:
+        raise ValueError("truncated checkpoint header")
+    hdr = np.frombuffer(blob, dtype=_HEADER, count=1, offset=8)[0]
+    if int(hdr["version"]) != 1 or int(hdr["hidden"]) != HIDDEN:
+        raise ValueError("unsupported checkpoint version or hidden width")
+    d = int(hdr["d"])
+    n_params, n_trained = _counts(d)
+    if int(hdr["n_params"]) != n_params or int(hdr["n_trained"]) != n_trained:
+        raise ValueError("checkpoint sizes do not match its d")
+    moments = bool(int(hdr["flags"]) & 1)
+    need = 8 + _HEADER.itemsize + 4 * (n_params + (2 * n_trained if moments else 0))
+    if len(blob) != need:
+        raise ValueError(f"checkpoint is {len(blob)} bytes, expected {need}")
+    o = 8 + _HEADER.itemsize
+    params = np.frombuffer(blob, dtype="<f4", count=n_params, offset=o).astype(np.float32)
+    m = v = None
+    if moments:
+        o += 4 * n_params
+        m = np.frombuffer(blob, dtype="<f4", count=n_trained, offset=o).astype(np.float32)
+        v = np.frombuffer(blob, dtype="<f4", count=n_trained,
+                          offset=o + 4 * n_trained).astype(np.float32)
+    return {"d": d, "step": int(hdr["step"]), "params": params, "m": m, "v": v}
+
+
 @dataclass
 class TrainConfig:
     batch: int = 4096
@@ -88,6 +159,29 @@ class Surrogate:
         self.m = torch.zeros(nt, dtype=torch.float32, device=device)
         self.v = torch.zeros(nt, dtype=torch.float32, device=device)
         self.step = 0
+
+    def save(self, path: str, optimizer: bool = True) -> None:
+        """Checkpoint the parameters (and the Adam state) to ``path``."""
+        m, v = (self.m.cpu().numpy(), self.v.cpu().numpy()) if optimizer else (None, None)
+        save_params(path, self.params.cpu().numpy(), self.d, self.step, m, v)
+
+    @classmethod
+    def load(cls, path: str, device="cuda", cfg: TrainConfig | None = None) -> "Surrogate":
+        """A network restored from ``save``; training resumes from its Adam
+        state and step when the file holds them."""
+        import torch
+        ck = load_params(path)
+        net = cls.__new__(cls)
+        net.d = ck["d"]
+        net.cfg = cfg or TrainConfig()
+        net.params = torch.from_numpy(ck["params"]).to(device)
+        nt = _counts(net.d)[1]
+        net.m = (torch.from_numpy(ck["m"]).to(device) if ck["m"] is not None
+                 else torch.zeros(nt, dtype=torch.float32, device=device))
+        net.v = (torch.from_numpy(ck["v"]).to(device) if ck["v"] is not None
+                 else torch.zeros(nt, dtype=torch.float32, device=device))
+        net.step = ck["step"]
+        return net
 
     def standardize(self, x):
         _rows(x, SNG_F32)

@@ -184,3 +184,29 @@ def test_surrogate_gain_on_sibling_dataset():
     assert st["queries"] < 0.75 * pst["queries"], (st["queries"], pst["queries"])
     assert ari >= 0.99, ari
     assert agree >= 0.99, agree
+
+
+def test_checkpoint_resume_is_exact(tmp_path):
+    """A network saved mid-training and loaded back predicts identically, and
+    training resumed from the checkpoint (Adam state and step included)
+    matches training continued in place."""
+    torch, sng = need_gpu()
+    from paper_2006_06743_gb300 import surrogate as sg
+    d, n = 8, 20_000
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    y = (x[:, 0] + 0.5 * x[:, 1] > 0).astype(np.uint8)
+    xg, yg = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    cfg = sg.TrainConfig(batch=512, lr=3e-3)
+    net = sg.Surrogate(datagen.mlp_init(d, 128, 1), cfg=cfg)
+    net.standardize(xg)
+    net.train(xg, yg, 50)
+    path = str(tmp_path / "net.bin")
+    net.save(path)
+    back = sg.Surrogate.load(path, cfg=cfg)
+    assert back.step == net.step
+    assert torch.equal(back.predict(xg), net.predict(xg))
+    la = net.train(xg, yg, 20)
+    lb = back.train(xg, yg, 20)
+    np.testing.assert_array_equal(la, lb)
+    assert torch.equal(back.params, net.params)
