@@ -369,6 +369,7 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     cudaMemsetAsync(gb->out_cnt, 0, (size_t)n * 4, st);
   }
   tm->mark(st, 0);
+  NvtxRange nvtx_graph("step 2: sampled graph");
   if (r.map.passes <= 1) {
     if (!launch_gather(p->dtype, r.map, ga, grid, st))
       return fail(SNG_EINVAL, "no compiled gather for vec=%d group=%d nch=%d unroll=%d",
@@ -539,6 +540,7 @@ sng_status sng_gather_mapping(const void *x, const sng_params *params, int32_t *
 sng_status sng_cluster_edges(int64_t n, const int32_t *src, const int32_t *col, int64_t num_edges,
                              const int32_t *deg, const sng_params *params, int32_t *labels,
                              uint8_t *core, sng_stats *stats, void *stream) {
+  NvtxRange nvtx_range("sng_cluster_edges");
   if (!params || !labels) return fail(SNG_EINVAL, "NULL argument");
   const bool simple = params->degree_mode == SNG_DEG_SIMPLE;
   if (!deg && !simple) return fail(SNG_EINVAL, "deg is NULL");
@@ -591,6 +593,7 @@ sng_status sng_cluster_edges(int64_t n, const int32_t *src, const int32_t *col, 
 
 sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels, uint8_t *core,
                        sng_stats *stats, void *stream) {
+  NvtxRange nvtx_range("sng_cluster");
   Resolved r;
   sng_status rc = validate(x, params, &r);
   if (rc) return rc;
@@ -644,6 +647,7 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
 
 sng_status sng_build_graph(const void *x, const sng_params *params, sng_graph *out,
                            sng_stats *stats, void *stream) {
+  NvtxRange nvtx_range("sng_build_graph");
   Resolved r;
   sng_status rc = validate(x, params, &r);
   if (rc) return rc;

@@ -3,6 +3,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gather.cuh"
 
 namespace sng {
@@ -21,6 +23,15 @@ struct Resolved {
   int32_t metric = 0;
   float sim_c1 = 0.f, sim_c2 = 0.f, band_f = 0.f;
   GatherMap map{};
+};
+
+// NVTX range for the host-side span of an entry point or phase (shown by
+// Nsight tools on the CPU timeline, next to the kernels it launched).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // Stream-ordered device scratch, released on scope exit.

@@ -326,6 +326,7 @@ extern "C" {
 
 sng_status sng_batch_plan_create(const int64_t *offsets, int32_t n_clouds, const sng_params *base,
                                  const int64_t *m_per_cloud, sng_batch_plan **plan) {
+  NvtxRange nvtx_range("sng_batch_plan_create");
   if (!plan) return fail(SNG_EINVAL, "plan is NULL");
   *plan = nullptr;
   if (!offsets || !base) return fail(SNG_EINVAL, "offsets / base is NULL");
@@ -459,6 +460,7 @@ sng_status sng_batch_plan_create(const int64_t *offsets, int32_t n_clouds, const
 
 sng_status sng_batch_run(sng_batch_plan *p, const void *x, int32_t *labels, sng_stats *stats,
                          void *stream) {
+  NvtxRange nvtx_range("sng_batch_run");
   if (!p || !x || !labels) return fail(SNG_EINVAL, "NULL argument");
   if ((uintptr_t)x % (p->map.vec * 4)) return fail(SNG_EINVAL, "x_concat misaligned for its rows");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -238,6 +238,7 @@ using namespace sng;
 extern "C" {
 
 sng_status sng_ari(const int32_t *a, const int32_t *b, int64_t n, double *ari, void *stream) {
+  NvtxRange nvtx_range("sng_ari");
   if (!a || !b || !ari) return fail(SNG_EINVAL, "NULL argument");
   if (n < 0 || n > 0x7fffffffLL) return fail(SNG_EINVAL, "n out of range");
   if (n < 2) {
@@ -269,6 +270,7 @@ sng_status sng_ari(const int32_t *a, const int32_t *b, int64_t n, double *ari, v
 
 sng_status sng_ami(const int32_t *a, const int32_t *b, int64_t n, int32_t average,
                    sng_mi_terms *out, void *stream) {
+  NvtxRange nvtx_range("sng_ami");
   if (!a || !b || !out) return fail(SNG_EINVAL, "NULL argument");
   if (n < 0 || n > 0x7fffffffLL) return fail(SNG_EINVAL, "n out of range");
   if (average < SNG_AMI_MIN || average > SNG_AMI_MAX) return fail(SNG_EINVAL, "unknown average");

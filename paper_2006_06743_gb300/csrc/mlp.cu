@@ -756,6 +756,7 @@ sng_status sng_mlp_loss_grad(const float *x, const uint8_t *y, int64_t n,
 sng_status sng_mlp_train(const float *x, const uint8_t *y, int64_t n, const sng_mlp_config *cfg,
                          float *params, float *adam_m, float *adam_v, int64_t step0,
                          int64_t steps, float *loss_trace, void *stream) {
+  NvtxRange nvtx_range("sng_mlp_train");
   sng_status rc = check_cfg(cfg);
   if (rc) return rc;
   if (!x || !y || !params || !adam_m || !adam_v) return fail(SNG_EINVAL, "NULL argument");
@@ -795,6 +796,7 @@ sng_status sng_mlp_train(const float *x, const uint8_t *y, int64_t n, const sng_
 
 sng_status sng_mlp_predict(const float *x, int64_t n, const sng_mlp_config *cfg,
                            const float *params, float *prob, void *stream) {
+  NvtxRange nvtx_range("sng_mlp_predict");
   sng_status rc = check_cfg(cfg);
   if (rc) return rc;
   if (!x || !params || !prob) return fail(SNG_EINVAL, "NULL argument");
@@ -826,6 +828,7 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
                                  const sng_mlp_config *cfg, const float *mlp_params,
                                  const sng_gate *gate, int32_t *labels, uint8_t *core,
                                  sng_stats *stats, void *stream) {
+  NvtxRange nvtx_range("sng_cluster_surrogate");
   Resolved r;
   sng_status rc = validate(x, params, &r);
   if (rc) return rc;

@@ -77,6 +77,7 @@ extern "C" {
 
 sng_status sng_cluster_noalloc(const float *x, const sng_params *params, int32_t *labels,
                                sng_stats *stats, void *stream) {
+  NvtxRange nvtx_range("sng_cluster_noalloc");
   Resolved r;
   sng_status rc = validate(x, params, &r);
   if (rc) return rc;
