@@ -119,7 +119,8 @@ typedef struct {
                              band_rel*eps^2 (similarity: |sim-eps| <=
                              band_rel*|eps|); 0 selects 1e-5 (F32) / 1e-3 (BF16) */
     double s;             /* sampling rate in (0, 1]; m = ceil(s*n)          */
-    int64_t m_override;   /* > 0: use this m instead of ceil(s*n)            */
+    int64_t m_override;   /* > 0: use this m instead of ceil(s*n); every m
+                             must be in [1, 2^31 - 1025]                     */
     uint64_t seed;        /* partner-hash seed                               */
     const float *x_f32_master; /* device, n x ld FP32; BF16 form: the FP32 values
                              the FP64 recheck reads (required for SNG_BF16)    */

@@ -146,7 +146,7 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
     if (!(p->s > 0.0) || !(p->s <= 1.0)) return fail(SNG_EINVAL, "s must be in (0, 1]");
     m = ceil_s_n(p->s, p->n);
   }
-  if (m < 1 || m > 0x7fffffffLL) return fail(SNG_EINVAL, "m must be in [1, 2^31-1]");
+  if (m < 1 || m > kMaxDraws) return fail(SNG_EINVAL, "m must be in [1, 2^31-1025]");
   r->n = p->n;
   r->d = p->d;
   r->m = m;

@@ -390,7 +390,7 @@ sng_status sng_batch_plan_create(const int64_t *offsets, int32_t n_clouds, const
     else if (m_per_cloud) mb = m_per_cloud[b];
     else if (base->m_override > 0) mb = base->m_override;
     else mb = (int64_t)std::ceil(base->s * (double)nb);
-    if (mb < 1 || mb > 0x7fffffffLL) {
+    if (mb < 1 || mb > kMaxDraws) {
       plan_free(p);
       return fail(SNG_EINVAL, "cloud %d: draws per point must be >= 1", b);
     }

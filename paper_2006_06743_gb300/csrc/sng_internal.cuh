@@ -21,6 +21,9 @@ namespace sng {
 
 constexpr uint32_t kFullMask = 0xffffffffu;
 constexpr int32_t kNoLabel = 0x7fffffff;
+// Largest draw count per point: the gather loops step a 32-bit draw index by
+// up to 256 draws, which must not overflow.
+constexpr int64_t kMaxDraws = 0x7fffffffLL - 1024;
 
 // Device status word bits (written by kernels, read back by the host).
 constexpr uint32_t kErrUnionLimit = 1u << 0;   // union-find retry bound hit

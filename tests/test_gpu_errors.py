@@ -28,6 +28,18 @@ def test_invalid_params_rejected(field, value):
     assert sng.launch_count() == before
 
 
+def test_draw_count_limit():
+    """m within 1024 of 2^31 would overflow the gather's 32-bit draw index:
+    rejected before any launch, like SAMPLE_ALL beyond it."""
+    torch, sng = need_gpu()
+    x = torch.from_numpy(datagen.random_points(100, 3, seed=0)).cuda()
+    before = sng.launch_count()
+    with pytest.raises(sng.SngError) as e:
+        sng.cluster(x, sng.Params(eps=0.1, min_pts=3, m=2**31 - 1000))
+    assert e.value.status == sng.SNG_EINVAL
+    assert sng.launch_count() == before
+
+
 def test_invalid_shapes_rejected():
     torch, sng = need_gpu()
     x = torch.zeros((1, 3), device="cuda")
