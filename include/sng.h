@@ -215,6 +215,19 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
                        uint8_t *core, sng_stats *stats, void *stream);
 
 /*
+ * sng_cluster on HOST buffers: x_host (n x ld elements of params->dtype;
+ * with SNG_BF16, params->x_f32_master is a HOST n x ld FP32 array as well)
+ * is copied to the device (in up to four concurrent pieces, so several copy
+ * engines can serve it; pinned memory runs at full speed, pageable memory
+ * works), Algorithm 1 runs as in sng_cluster, and labels_host (int32[n]) and
+ * core_host (uint8[n] or NULL) receive the result.  Device memory for the
+ * copies is allocated and freed inside the call.  Synchronises `stream`
+ * before returning (the host outputs are then valid).
+ */
+sng_status sng_cluster_host(const void *x_host, const sng_params *params, int32_t *labels_host,
+                            uint8_t *core_host, sng_stats *stats, void *stream);
+
+/*
  * Many independent point clouds in one persistent launch.  x_concat: device,
  * clouds stored back to back (rows of ld elements, F32 only).  offsets: HOST
  * int64[n_clouds+1], cloud b = rows offsets[b]..offsets[b+1]-1, each cloud

@@ -112,6 +112,8 @@ SIGNATURES = {
     "sng_graph_free": (None, [ctypes.POINTER(sng_graph)]),
     "sng_cluster": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P, _P,
                                      ctypes.POINTER(sng_stats), _P]),
+    "sng_cluster_host": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P, _P,
+                                          ctypes.POINTER(sng_stats), _P]),
     "sng_cluster_edges": (ctypes.c_int32, [ctypes.c_int64, _P, _P, ctypes.c_int64, _P,
                                            ctypes.POINTER(sng_params), _P, _P,
                                            ctypes.POINTER(sng_stats), _P]),
@@ -277,6 +279,36 @@ def cluster(x, params: Params, x_master=None, want_core: bool = False, stream=No
     st = sng_cluster(x.data_ptr(), params.to_c(n, d, ld, dtype, mp), labels.data_ptr(),
                      core.data_ptr() if core is not None else 0, _stream_ptr(stream))
     return (labels, core, st) if want_core else (labels, st)
+
+
+def cluster_host(x, params: Params, x_master=None, want_core: bool = False, stream=None):
+    """Algorithm 1 on HOST points (a C-contiguous float32 numpy array or CPU
+    tensor, ideally pinned; bfloat16 CPU tensor with a float32 ``x_master``):
+    the library copies them to the device, clusters, and copies the labels
+    back.  Returns ``(labels, stats)`` or ``(labels, core, stats)`` as numpy
+    arrays."""
+    import numpy as np
+    import torch
+    t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
+    if t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("cluster_host takes a 2-D host array with unit column stride")
+    dtype = SNG_BF16 if t.dtype == torch.bfloat16 else SNG_F32
+    if dtype == SNG_F32 and t.dtype != torch.float32:
+        raise ValueError("points must be float32 or bfloat16")
+    n, d, ld = t.shape[0], t.shape[1], t.stride(0)
+    mp = 0
+    if dtype == SNG_BF16:
+        if x_master is None or x_master.dtype != torch.float32 or x_master.stride(0) != ld:
+            raise ValueError("bf16 input needs a float32 host x_master with the same row stride")
+        mp = x_master.data_ptr()
+    labels = np.empty(n, dtype=np.int32)
+    core = np.empty(n, dtype=np.uint8) if want_core else None
+    st = sng_stats()
+    _check(lib().sng_cluster_host(t.data_ptr(), ctypes.byref(params.to_c(n, d, ld, dtype, mp)),
+                                  labels.ctypes.data,
+                                  core.ctypes.data if core is not None else None,
+                                  ctypes.byref(st), _stream_ptr(stream)))
+    return (labels, core, st.as_dict()) if want_core else (labels, st.as_dict())
 
 
 def cluster_async(x, params: Params, labels, counters=None, core=None, stream=None):

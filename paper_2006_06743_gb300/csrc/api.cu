@@ -645,6 +645,95 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
   return rc;
 }
 
+sng_status sng_cluster_host(const void *x_host, const sng_params *params, int32_t *labels_host,
+                            uint8_t *core_host, sng_stats *stats, void *stream) {
+  NvtxRange nvtx_range("sng_cluster_host");
+  if (!params || !x_host || !labels_host) return fail(SNG_EINVAL, "NULL argument");
+  if (params->n < 2 || params->n > 0x7fffffffLL || params->ld < params->d || params->d < 1)
+    return fail(SNG_EINVAL, "bad n / d / ld");
+  if (params->dtype != SNG_F32 && params->dtype != SNG_BF16)
+    return fail(SNG_EINVAL, "unknown dtype");
+  if (params->dtype == SNG_BF16 && !params->x_f32_master)
+    return fail(SNG_EINVAL, "BF16 form needs x_f32_master");
+  if (params->flags & SNG_FLAG_NO_SYNC)
+    return fail(SNG_EINVAL, "the host-buffer call synchronises (no SNG_FLAG_NO_SYNC)");
+  device_sms();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = params->n;
+  const size_t esize = params->dtype == SNG_F32 ? 4 : 2;
+  const size_t xbytes = (size_t)n * (size_t)params->ld * esize;
+  const size_t mbytes = params->dtype == SNG_BF16 ? (size_t)n * (size_t)params->ld * 4 : 0;
+  Scratch s(st);
+  void *xd = nullptr;
+  float *md = nullptr;
+  int32_t *ld = nullptr;
+  uint8_t *cd = nullptr;
+  sng_status rc;
+  if ((rc = s.alloc(&xd, xbytes, "device points")) ||
+      (mbytes && (rc = s.alloc((void **)&md, mbytes, "device FP32 master"))) ||
+      (rc = s.alloc((void **)&ld, (size_t)n * 4, "device labels")) ||
+      (core_host && (rc = s.alloc((void **)&cd, (size_t)n, "device core mask"))))
+    return rc;
+  // host -> device in up to four pieces on streams forked from `st`, so
+  // several copy engines can take part; the pieces join `st` before use
+  struct Piece {
+    char *dst;
+    const char *src;
+    size_t bytes;
+  };
+  std::vector<Piece> pieces;
+  auto split = [&](void *dst, const void *src, size_t bytes) {
+    const size_t k = bytes >= ((size_t)64 << 20) ? 4 : 1;
+    const size_t step = ((bytes + k - 1) / k + 255) / 256 * 256;
+    for (size_t o = 0; o < bytes; o += step)
+      pieces.push_back({static_cast<char *>(dst) + o, static_cast<const char *>(src) + o,
+                        bytes - o < step ? bytes - o : step});
+  };
+  split(xd, x_host, xbytes);
+  if (mbytes) split(md, params->x_f32_master, mbytes);
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> done;
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, st);
+  for (size_t k = 0; e == cudaSuccess && k < pieces.size(); ++k) {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    side.push_back(cs);
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) break;
+    done.push_back(ev);
+    if ((e = cudaStreamWaitEvent(cs, fork, 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(pieces[k].dst, pieces[k].src, pieces[k].bytes,
+                             cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(ev, cs)) != cudaSuccess) break;
+    e = cudaStreamWaitEvent(st, ev, 0);
+  }
+  for (cudaEvent_t ev : done) cudaEventDestroy(ev);   // released once complete
+  for (cudaStream_t cs : side) cudaStreamDestroy(cs);
+  if (fork) cudaEventDestroy(fork);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(st);
+    return cuda_fail(e, "host to device copy");
+  }
+  sng_params pd = *params;
+  pd.x_f32_master = md;
+  rc = sng_cluster(xd, &pd, ld, cd, stats, stream);
+  if (rc) {
+    cudaStreamSynchronize(st);
+    return rc;
+  }
+  e = cudaMemcpyAsync(labels_host, ld, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && core_host)
+    e = cudaMemcpyAsync(core_host, cd, (size_t)n, cudaMemcpyDeviceToHost, st);
+  s.release();
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = e2;
+  return e == cudaSuccess ? SNG_OK : cuda_fail(e, "device to host copy");
+}
+
 sng_status sng_build_graph(const void *x, const sng_params *params, sng_graph *out,
                            sng_stats *stats, void *stream) {
   NvtxRange nvtx_range("sng_build_graph");

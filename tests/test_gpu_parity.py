@@ -417,3 +417,31 @@ def test_no_sync_form_rejections():
     with pytest.raises(sng.SngError) as e:
         sng.cluster(x, p)
     assert e.value.status == sng.SNG_EINVAL
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_buffer_call_matches_device_call(orc, pinned):
+    """sng_cluster_host: host points in (pinned or pageable, FP32 and BF16 with
+    a host FP32 master), host labels and core mask out, equal to the device
+    call; 80 MB of points so the copy is split over several streams."""
+    torch, sng = need_gpu()
+    n, d = 1_250_000, 16
+    x = datagen.random_points(n, d, seed=21)
+    p = sng.Params(eps=float(np.float32(0.05)), min_pts=4, m=30, seed=2)
+    ref, ref_core, _ = sng.cluster(torch.from_numpy(x).cuda(), p, want_core=True)
+    xt = torch.from_numpy(x)
+    if pinned:
+        xt = xt.pin_memory()
+    labels, core, st = sng.cluster_host(xt, p, want_core=True)
+    np.testing.assert_array_equal(labels, ref.cpu().numpy())
+    np.testing.assert_array_equal(core, ref_core.cpu().numpy())
+    assert st["queries"] == n * 30
+    # BF16 storage with the FP32 master on the host
+    bits = datagen.bf16_round(x)
+    xb = torch.from_numpy(bits.view(np.int16)).view(torch.bfloat16)
+    xq = torch.from_numpy(datagen.bf16_to_f32(bits))
+    if pinned:
+        xb, xq = xb.pin_memory(), xq.pin_memory()
+    lb, _ = sng.cluster_host(xb, p, x_master=xq)
+    ref_b, _ = sng.cluster(xb.cuda(), p, x_master=xq.cuda())
+    np.testing.assert_array_equal(lb, ref_b.cpu().numpy())
