@@ -89,7 +89,8 @@ typedef int32_t sng_status;
 #define SNG_FLAG_WARP_ROWS 8u /* one warp per source row even where the default
                                 is one lane per source row: the Euclidean form
                                 with one lane per pair (rows of at most 4
-                                vectors and at least 32 x 16 rows per SM; in
+                                vectors and at least 32 x 64 rows per SM, or
+                                32 x 16 with SNG_SAMPLE_ALL; in
                                 the batched form, rows of one float4), where
                                 each lane hashes, tests and
                                 records its own row's draws with 2 or 4

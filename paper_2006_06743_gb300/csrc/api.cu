@@ -198,12 +198,16 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   r->map.unroll = p->map_unroll > 0 ? p->map_unroll : (vec == vmax && nch * vec >= 16 ? 2 : 4);
   // one lane per pair and short rows: one lane per source row (compiled for
   // 2 and 4 partner rows in flight), unless one warp per row is asked for or
-  // the rows would give fewer than 16 warps per SM (32 rows per warp: small
-  // sets run faster with a warp per row)
+  // there are too few rows (32 rows per warp).  Hashed draws want 64 warps
+  // per SM (with fewer a warp per row hides latency better: measured slower
+  // at 10^5 rows, faster at 10^6); with every pair queried the 32 lanes walk
+  // the same partners and 16 warps per SM suffice (faster at 10^5 rows).
   const int64_t rows = (p->row_begin == 0 && p->row_end == 0) ? p->n : p->row_end - p->row_begin;
+  const int64_t min_warps_per_sm = p->sample_mode == SNG_SAMPLE_ALL ? 16 : 64;
   r->map.lanes = group == 1 && p->metric == SNG_METRIC_L2 &&
                  (r->map.unroll == 2 || r->map.unroll == 4) &&
-                 !(p->flags & SNG_FLAG_WARP_ROWS) && rows >= 32LL * 16 * device_sms();
+                 !(p->flags & SNG_FLAG_WARP_ROWS) &&
+                 rows >= 32LL * min_warps_per_sm * device_sms();
   if (p->map_passes < 0 || p->map_passes > 64) return fail(SNG_EINVAL, "map_passes must be in [0, 64]");
   r->map.passes = p->map_passes > 0 ? p->map_passes : 1;
   if (r->map.passes > p->n) r->map.passes = (int)p->n;

@@ -329,12 +329,12 @@ def test_prefetch_on_off_same_graph(orc, n, d, dtype):
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("d", [1, 2, 3, 4, 8, 16])
 def test_lane_per_row_graph_matches_oracle(orc, dtype, d):
-    """Rows of at most 4 vectors and enough of them (n = 100,000) run one lane
+    """Rows of at most 4 vectors and enough of them (n = 400,000) run one lane
     per source row; m = 40 leaves a partial keep-bit word per row.  The
     graph equals the oracle's and the warp-per-row kernel's
     (SNG_FLAG_WARP_ROWS), and the labels agree."""
     torch, sng = need_gpu()
-    n, m = 100_000, 40
+    n, m = 400_000, 40
     x = datagen.random_points(n, d, seed=d + 50)
     eps = float(np.float32(0.02 * math.sqrt(d) if d > 1 else 0.0005))
     if dtype == "bf16":

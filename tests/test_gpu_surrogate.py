@@ -110,11 +110,11 @@ def test_training_steps_match_oracle_adam():
         assert torch.equal(net.params[nt:], p0[nt:])
 
 
-@pytest.mark.parametrize("n", [6000, 100_000])
+@pytest.mark.parametrize("n", [6000, 400_000])
 def test_gated_cluster_matches_oracle_gated_form(orc, n):
     """Given the gate's decisions (from the network's probabilities), the
     surrogate path is exactly the oracle's gated form of Algorithm 1 (at
-    n = 100,000 the gather runs one lane per row, with per-row draw counts
+    n = 400,000 the gather runs one lane per row, with per-row draw counts
     and weights)."""
     torch, sng = need_gpu()
     from paper_2006_06743_gb300 import surrogate as sg
