@@ -445,3 +445,26 @@ def test_host_buffer_call_matches_device_call(orc, pinned):
     lb, _ = sng.cluster_host(xb, p, x_master=xq)
     ref_b, _ = sng.cluster(xb.cuda(), p, x_master=xq.cuda())
     np.testing.assert_array_equal(lb, ref_b.cpu().numpy())
+
+
+def test_lane_per_row_every_pair(orc):
+    """Every pair queried (s = 1) at n = 80,000 in d = 3 runs one lane per
+    row: the graph equals the warp-per-row kernel's, and 150 sampled rows
+    equal the oracle's (its full n^2 pass would take too long)."""
+    torch, sng = need_gpu()
+    n = 80_000
+    x = datagen.random_points(n, 3, seed=77)
+    eps = float(np.float32(0.01))
+    xg = torch.from_numpy(x).cuda()
+    graphs = [sng.build_graph(xg, sng.Params(eps=eps, min_pts=3, sample_mode=1, flags=f))
+              for f in (0, sng.SNG_FLAG_WARP_ROWS)]
+    for k in ("row_ptr", "col", "deg"):
+        assert torch.equal(graphs[0][k], graphs[1][k]), k
+    rp = graphs[0]["row_ptr"].cpu().numpy()
+    col = graphs[0]["col"].cpu().numpy()
+    assert col.size > n
+    rows = np.sort(np.random.default_rng(3).choice(n, 150, replace=False))
+    orp, ocol, _, _ = orc.build_rows(x, eps, 0, n - 1, sample_all=True, rows=rows,
+                                     band_rel=BAND_F32)
+    for t, i in enumerate(rows):
+        np.testing.assert_array_equal(col[rp[i]:rp[i + 1]], ocol[orp[t]:orp[t + 1]])
