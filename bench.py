@@ -303,7 +303,12 @@ def bench_sng(args, w):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": kname, "peak_kind": peak_kind,
-                     "algorithmic_bytes": alg, "kernel_ms": g_ms},
+                     "algorithmic_bytes": alg, "kernel_ms": g_ms,
+                     # DRAM-level view: the captured traffic over this run's
+                     # kernel time (frac above 1 comes from partner rows that
+                     # hit in L2, the share given by 1 - traffic / algorithmic)
+                     "traffic_frac": (traffic / (g_ms * 1e-3) / 1e9 / peak) if traffic else None,
+                     "l2_served_share": (1.0 - traffic / alg) if traffic else None},
         "phases_ms": {k: v for k, v in stats["ms"].items()},
         "stats": {k: stats[k] for k in ("kept_edges", "band_pairs", "band_points", "cores",
                                         "clusters", "noise", "recheck_pairs")},
