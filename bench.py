@@ -188,10 +188,13 @@ def bench_sng(args, w):
     params = sng.Params(eps=w["eps"], min_pts=w["min_pts"], s=w["s"], seed=w["seed"],
                         flags=sng.SNG_FLAG_TIMING, map_group=args.map_group,
                         map_unroll=args.map_unroll, map_block=args.map_block,
-                        map_passes=args.map_passes, degree_mode=args.degree_mode)
+                        map_passes=args.map_passes, degree_mode=args.degree_mode,
+                        map_tile=args.map_tile)
+    if args.tiled:
+        params.flags |= sng.SNG_FLAG_TILED
     tuned = None
     if args.autotune and not (args.map_group or args.map_unroll or args.map_block
-                              or args.map_passes):
+                              or args.map_passes or args.tiled):
         from paper_2006_06743_gb300 import autotune
         tuned = autotune.tune(x, params, reps=2, budget_s=args.tune_budget,
                               verbose=args.verbose, force=args.retune)
@@ -269,7 +272,8 @@ def bench_sng(args, w):
     kname = (f"gather_kernel<float, {stats['map_vec']}, {stats['map_group']}, "
              f"{stats['map_nch']}, {stats['map_unroll']}, 0, {int(full)}, 0>")
     traffic = None
-    if params.map_passes <= 1 and not (params.flags & sng.SNG_FLAG_PREFETCH):
+    if params.map_passes <= 1 and not (params.flags & (sng.SNG_FLAG_PREFETCH |
+                                                       sng.SNG_FLAG_TILED)):
         traffic = CAPTURED_TRAFFIC.get((args.workload, kname))
     truth = w["truth"].astype(np.int32)
     ari_truth = sng.ari(labels, torch.from_numpy(truth).to(dev))
@@ -290,7 +294,9 @@ def bench_sng(args, w):
                               "distinct neighbours"][args.degree_mode],
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"dp{world}",
                    "gather_mapping": {**{k: getattr(params, k) for k in
-                                         ("map_group", "map_unroll", "map_block", "map_passes")},
+                                         ("map_group", "map_unroll", "map_block", "map_passes",
+                                          "map_tile")},
+                                      "tiled": bool(params.flags & sng.SNG_FLAG_TILED),
                                       "prefetch": bool(params.flags & sng.SNG_FLAG_PREFETCH)},
                    "autotuned": tuned is not None},
         "e2e": {"value": Q * world / (t_e2e * 1e-3), "unit": "queries/s",
@@ -813,6 +819,8 @@ def main():
     ap.add_argument("--map-unroll", type=int, default=0)
     ap.add_argument("--map-block", type=int, default=0)
     ap.add_argument("--map-passes", type=int, default=0)
+    ap.add_argument("--map-tile", type=int, default=0)
+    ap.add_argument("--tiled", type=int, default=0, help="1: the L2-tiled gather")
     ap.add_argument("--autotune", type=int, default=1, help="1: tune the gather mapping first")
     ap.add_argument("--degree-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0 undirected multigraph, 1 out-degree, 2 distinct neighbours")

@@ -96,6 +96,12 @@ typedef int32_t sng_status;
                                 records its own row's draws with 2 or 4
                                 batches in flight (map_unroll 1 or 8 selects
                                 one warp per row as well)                    */
+#define SNG_FLAG_TILED 16u  /* step 2 tile by tile: every draw is first bucketed by
+                                (source slice, partner slice) -- map_tile slices
+                                per axis, 0 = enough for two slices to fit in L2 --
+                                then each tile is tested while its two slices
+                                stay in L2.  Euclidean form, 16-byte vectors;
+                                same results; ~8 bytes of scratch per draw      */
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The
                                 edge arrays are sized for all n*m draws (8 bytes

@@ -33,6 +33,7 @@ SNG_FLAG_TIMING = 1
 SNG_FLAG_PREFETCH = 2
 SNG_FLAG_NO_SYNC = 4
 SNG_FLAG_WARP_ROWS = 8
+SNG_FLAG_TILED = 16
 
 PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total", "gate")
 

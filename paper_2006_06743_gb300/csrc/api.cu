@@ -3,6 +3,7 @@
 // Host-side work only: argument validation, the gather mapping policy, the
 // FP32 guard band, device scratch (stream-ordered pool allocations) and the
 // order of kernel launches for Algorithm 1 (Jiang, Jang & Lacki 2020, Sec. 3).
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cmath>
@@ -16,6 +17,7 @@
 #include "api_common.cuh"
 #include "gather.cuh"
 #include "graph.cuh"
+#include "tiled.cuh"
 
 namespace sng {
 
@@ -341,6 +343,85 @@ sng_status simple_degrees(int64_t n, const int32_t *src, const int32_t *col, int
   return e == cudaSuccess ? SNG_OK : cuda_fail(e, "simple-degree launch");
 }
 
+// The L2-tiled gather (SNG_FLAG_TILED): partition every draw into k x k tile
+// buckets, then test tile by tile.  *done = false when the form does not
+// apply or a bucket overflowed (the caller runs the direct gather).
+static sng_status run_tiled(const sng_params *p, const Resolved &r, Scratch &s,
+                            const GatherArgs &ga, GraphBufs *gb, bool *done) {
+  *done = false;
+  cudaStream_t st = s.stream;
+  const int64_t n = r.n;
+  const int blocks = tile_test_blocks_per_sm(p->dtype, r.map);
+  if (blocks < 0 || r.map.sim || r.map.lanes || r.map.passes > 1) return SNG_OK;
+  const size_t esize = p->dtype == SNG_F32 ? 4 : 2;
+  int k = p->map_tile > 0 ? p->map_tile
+                          : (int)((2 * (int64_t)n * p->ld * esize + (88ll << 20) - 1) / (88ll << 20));
+  if (k < 2) k = 2;
+  if (k > kMaxTiles) k = kMaxTiles;
+  const int64_t slice = (n + k - 1) / k;
+  const int tiles = k * k;
+  std::vector<int64_t> cap(tiles), eoff(tiles), roff(tiles);
+  int64_t etot = 0, rtot = 0;
+  for (int b = 0; b < tiles; ++b) {
+    const int rs = b / k, ps = b % k;
+    const int64_t rows = std::max<int64_t>(0, std::min<int64_t>(slice, n - (int64_t)rs * slice));
+    const int64_t plen = std::max<int64_t>(0, std::min<int64_t>(slice, n - (int64_t)ps * slice));
+    double expect;
+    if (p->sample_mode == SNG_SAMPLE_ALL)
+      expect = (double)rows * (double)plen;   // every other point once: at most plen per row
+    else
+      expect = (double)rows * (double)r.m * (double)plen / (double)(n - 1);
+    cap[b] = (int64_t)(expect + 8.0 * std::sqrt(expect) + 1024.0);
+    eoff[b] = etot;
+    roff[b] = rtot;
+    etot += cap[b];
+    rtot += rows;
+  }
+  int64_t *d_cap = nullptr, *d_eoff = nullptr, *d_roff = nullptr;
+  unsigned long long *d_entries = nullptr, *d_cursor = nullptr;
+  int4 *d_runs = nullptr;
+  unsigned int *d_rcur = nullptr;
+  sng_status rc;
+  if ((rc = s.alloc((void **)&d_entries, (size_t)etot * 8, "tile buckets")) ||
+      (rc = s.alloc((void **)&d_runs, (size_t)(rtot > 0 ? rtot : 1) * 16, "tile runs")) ||
+      (rc = s.alloc((void **)&d_cap, (size_t)tiles * 8, "tile capacities")) ||
+      (rc = s.alloc((void **)&d_eoff, (size_t)tiles * 8, "tile offsets")) ||
+      (rc = s.alloc((void **)&d_roff, (size_t)tiles * 8, "tile run offsets")) ||
+      (rc = s.alloc((void **)&d_cursor, (size_t)tiles * 8, "tile cursors")) ||
+      (rc = s.alloc((void **)&d_rcur, (size_t)tiles * 4, "tile run cursors")))
+    return rc;
+  cudaMemcpyAsync(d_cap, cap.data(), (size_t)tiles * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_eoff, eoff.data(), (size_t)tiles * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_roff, roff.data(), (size_t)tiles * 8, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(d_cursor, 0, (size_t)tiles * 8, st);
+  cudaMemsetAsync(d_rcur, 0, (size_t)tiles * 4, st);
+  TileArgs t{k, slice, d_entries, d_eoff, d_cap, d_cursor, d_runs, d_roff, d_rcur};
+  launch_tile_partition(ga, t, device_sms() * 16, st);
+  note_launch();
+  // a bucket overflow (far outside the binomial spread) falls back
+  unsigned long long status = 0;
+  cudaError_t e = cudaMemcpyAsync(&status, gb->counters + kCntStatus, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "tile partition");
+  if (status & kErrTileOverflow) {
+    cudaMemsetAsync(gb->counters + kCntStatus, 0, 8, st);
+    return SNG_OK;
+  }
+  // the test kernels set keep bits and add counts: both start at zero
+  cudaMemsetAsync(gb->bitmask, 0, (size_t)n * r.W * 4, st);
+  cudaMemsetAsync(gb->out_cnt, 0, (size_t)n * 4, st);
+  const int grid = device_sms() * (blocks > 0 ? blocks : 1);
+  for (int b = 0; b < tiles; ++b) {
+    if (!launch_tile_test(p->dtype, r.map, ga, t, b, grid, st))
+      return fail(SNG_EINTERNAL, "tile test mapping vanished");
+    note_launch();
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tile test launches");
+  *done = true;
+  return SNG_OK;
+}
+
 sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scratch &s,
                      GraphBufs *gb, const int32_t *m_row, Timer *tm, const int32_t *w_row) {
   cudaStream_t st = s.stream;
@@ -374,7 +455,11 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   }
   tm->mark(st, 0);
   NvtxRange nvtx_graph("step 2: sampled graph");
-  if (r.map.passes <= 1) {
+  bool tiled = false;
+  if ((p->flags & SNG_FLAG_TILED) && (rc = run_tiled(p, r, s, ga, gb, &tiled))) return rc;
+  if (tiled) {
+    // done by the tiled form
+  } else if (r.map.passes <= 1) {
     if (!launch_gather(p->dtype, r.map, ga, grid, st))
       return fail(SNG_EINVAL, "no compiled gather for vec=%d group=%d nch=%d unroll=%d",
                   r.map.vec, r.map.group, r.map.nch, r.map.unroll);

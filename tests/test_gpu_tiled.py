@@ -1,0 +1,110 @@
+"""The L2-tiled form of step 2 (SNG_FLAG_TILED) against the oracle and the
+direct gather: CSR, degrees, band counts and labels equal, for several slice
+counts, full-row and general mappings, FP32 and BF16, the three degree
+definitions, every pair queried, and source-row ranges."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import BAND_BF16, BAND_F32, need_gpu
+from paper_2006_06743_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+def _graph(sng, xg, p, master=None):
+    g = sng.build_graph(xg, p, x_master=master)
+    return {k: g[k].cpu().numpy() for k in ("row_ptr", "col", "deg", "core")}, g["stats"]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("n,d,tiles", [(5000, 64, 0), (7000, 64, 3), (4000, 128, 2),
+                                       (6000, 32, 8), (3000, 60, 4), (5000, 16, 5)])
+def test_tiled_graph_matches_oracle_and_direct(orc, dtype, n, d, tiles):
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=n + d + tiles)
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    m = 90
+    if dtype == "bf16":
+        bits = datagen.bf16_round(x)
+        xo = datagen.bf16_to_f32(bits)
+        xg = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+        master, band = torch.from_numpy(xo).cuda(), BAND_BF16
+    else:
+        xo, xg, master, band = x, torch.from_numpy(x).cuda(), None, BAND_F32
+    base = dict(eps=eps, min_pts=4, m=m, seed=d)
+    tiled, st = _graph(sng, xg, sng.Params(**base, flags=sng.SNG_FLAG_TILED, map_tile=tiles),
+                       master)
+    direct, _ = _graph(sng, xg, sng.Params(**base), master)
+    for k in tiled:
+        np.testing.assert_array_equal(tiled[k], direct[k], err_msg=k)
+    rp, col, bpairs, _ = orc.build_rows(xo, eps, d, m, band_rel=band)
+    np.testing.assert_array_equal(tiled["row_ptr"], rp)
+    np.testing.assert_array_equal(tiled["col"], col)
+    assert st["band_pairs"] == bpairs
+    labels, _ = sng.cluster(xg, sng.Params(**base, flags=sng.SNG_FLAG_TILED, map_tile=tiles),
+                            x_master=master)
+    r = orc.cluster(xo, eps, d, m, 4, band_rel=band)
+    np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
+
+
+@pytest.mark.parametrize("deg_mode", [0, 1, 2])
+def test_tiled_degree_modes_and_every_pair(orc, deg_mode):
+    torch, sng = need_gpu()
+    n, d = 2500, 32
+    x = datagen.random_points(n, d, seed=deg_mode)
+    eps = float(np.float32(0.1 * math.sqrt(d)))
+    xg = torch.from_numpy(x).cuda()
+    for extra in (dict(m=150, seed=3), dict(sample_mode=1)):
+        p = sng.Params(eps=eps, min_pts=4, degree_mode=deg_mode, flags=sng.SNG_FLAG_TILED,
+                       map_tile=3, **extra)
+        labels, core, st = sng.cluster(xg, p, want_core=True)
+        m = n - 1 if extra.get("sample_mode") else 150
+        r = orc.cluster(x, eps, extra.get("seed", 0), m, 4, deg_mode=deg_mode,
+                        sample_all=bool(extra.get("sample_mode")), band_rel=BAND_F32)
+        np.testing.assert_array_equal(core.cpu().numpy(), r["core"])
+        np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
+        assert st["kept_edges"] == r["kept_edges"]
+
+
+def test_tiled_row_ranges_recompose(orc):
+    """Source-row shards built in the tiled form give the rows of the whole
+    graph and sum to its degrees (the multi-GPU exchange's inputs)."""
+    torch, sng = need_gpu()
+    n, d, m = 6000, 64, 80
+    x = datagen.random_points(n, d, seed=9)
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    xg = torch.from_numpy(x).cuda()
+    whole, _ = _graph(sng, xg, sng.Params(eps=eps, min_pts=4, m=m, seed=2))
+    deg = np.zeros(n, dtype=np.int64)
+    for lo, hi in ((0, 2500), (2500, 6000)):
+        part, _ = _graph(sng, xg, sng.Params(eps=eps, min_pts=4, m=m, seed=2, row_begin=lo,
+                                             row_end=hi, flags=sng.SNG_FLAG_TILED, map_tile=4))
+        rp = part["row_ptr"]
+        for i in (lo, (lo + hi) // 2, hi - 1):
+            np.testing.assert_array_equal(part["col"][rp[i]:rp[i + 1]],
+                                          whole["col"][whole["row_ptr"][i]:whole["row_ptr"][i + 1]])
+        deg += part["deg"]
+    np.testing.assert_array_equal(deg, whole["deg"])
+
+
+@pytest.mark.parametrize("m", [1023, 1024, 1025, 2600])
+def test_tiled_rows_past_the_partition_cache(orc, m):
+    """Rows of up to 1024 draws keep their partners in shared memory between
+    the partition's passes; longer rows hash again.  Both sides of the limit
+    give the direct gather's graph and the oracle's rows."""
+    torch, sng = need_gpu()
+    n, d = 3000, 64
+    x = datagen.random_points(n, d, seed=m)
+    eps = float(np.float32(0.1 * math.sqrt(d)))
+    xg = torch.from_numpy(x).cuda()
+    base = dict(eps=eps, min_pts=4, m=m, seed=7)
+    tiled, st = _graph(sng, xg, sng.Params(**base, flags=sng.SNG_FLAG_TILED, map_tile=5))
+    direct, _ = _graph(sng, xg, sng.Params(**base))
+    for k in tiled:
+        np.testing.assert_array_equal(tiled[k], direct[k], err_msg=k)
+    rp, col, bpairs, _ = orc.build_rows(x, eps, 7, m, band_rel=BAND_F32)
+    np.testing.assert_array_equal(tiled["row_ptr"], rp)
+    np.testing.assert_array_equal(tiled["col"], col)
+    assert st["band_pairs"] == bpairs and st["kept_edges"] > 0
