@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
                           : Raw<T, VEC>::zero();
           }
         }
+        float part[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           float acc = 0.f;
@@ -230,10 +231,44 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
             }
           }
           if constexpr (FULL && VEC % 2 == 0) acc = f32x2_sum(acc2);
+          part[u] = acc;
+        }
+        // Transposed group reduction: at each butterfly level (lane distance
+        // o = G/2, ..., 1) a lane with more than one partial keeps half of
+        // them (the upper half if bit o of its group lane is set) and receives
+        // the partner lane's copy of the same half, so one shuffle moves two
+        // partials' worth of work.  Every sum adds the same two operands as
+        // the plain butterfly, so the results are identical.  Afterwards the
+        // lane holds the totals of steps first .. first + held - 1; lanes
+        // whose low bits (below G / U) are zero decide them.
+        int first = 0;
+        constexpr int held = U >= G ? U / G : 1;
 #pragma unroll
-          for (int o = G / 2; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
-          const int32_t p = pv[u];
-          if (gl == 0 && p >= 0) {
+        for (int o = G / 2, nv = U; o >= 1; o >>= 1) {
+          if (nv > 1) {
+            const int half = nv / 2;
+            const bool hi = (gl & o) != 0;
+#pragma unroll
+            for (int q = 0; q < half; ++q) {
+              const float keep = hi ? part[q + half] : part[q];
+              const float send = hi ? part[q] : part[q + half];
+              part[q] = keep + __shfl_xor_sync(kFullMask, send, o);
+            }
+            if (hi) first += half;
+            nv = half;
+          } else {
+            part[0] += __shfl_xor_sync(kFullMask, part[0], o);
+          }
+        }
+        constexpr int low = U >= G ? 1 : G / U;
+#pragma unroll
+        for (int q = 0; q < held; ++q) {
+          int32_t p = -1;
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (u == first + q) p = pv[u];
+          const float acc = part[q];
+          if ((gl & (low - 1)) == 0 && p >= 0) {
             bool keep = false;
             if (acc < a.lo_thr) {
               keep = true;
@@ -241,7 +276,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
               keep = recheck_pair<T>(a, i, p);
             }
             if (keep) {
-              const int32_t j = sj[(t0 + u) * R + grp];
+              const int32_t j = sj[(t0 + first + q) * R + grp];
               atomicOr(a.bitmask + (int64_t)i * a.W + (j >> 5), 1u << (j & 31));
               if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
               ++cnt;
@@ -289,6 +324,9 @@ static int occ_tile(const GatherMap &m) {
   X(T, V, 4, 4, 4, true) X(T, V, 8, 4, 4, true) X(T, V, 8, 2, 2, true)                   \
   X(T, V, 4, 2, 2, true) X(T, V, 16, 2, 2, true) X(T, V, 4, 4, 2, false)                 \
   X(T, V, 8, 4, 2, false) X(T, V, 16, 4, 2, false) X(T, V, 8, 2, 2, false)
+// FP32 only: two lanes per pair, one shuffle per 16 pairs (BF16 rows this
+// wide would hold 64 FP32 source values per lane)
+#define SNG_TILE_SHAPES_F32(X) X(float, 4, 2, 8, 2, true) X(float, 4, 2, 8, 1, true)
 #define SNG_TILE_TRY(T, V, G, N, U, F) \
   if (try_tile<T, V, G, N, U, F>(m, a, t, b, grid, st)) return true;
 #define SNG_TILE_OCC(T, V, G, N, U, F)      \
@@ -301,6 +339,7 @@ bool launch_tile_test(int dtype, const GatherMap &m, const GatherArgs &a, const 
                       int b, int grid, cudaStream_t st) {
   if (dtype == SNG_F32) {
     SNG_TILE_SHAPES(SNG_TILE_TRY, float, 4)
+    SNG_TILE_SHAPES_F32(SNG_TILE_TRY)
   } else {
     SNG_TILE_SHAPES(SNG_TILE_TRY, uint16_t, 8)
   }
@@ -310,6 +349,7 @@ bool launch_tile_test(int dtype, const GatherMap &m, const GatherArgs &a, const 
 int tile_test_blocks_per_sm(int dtype, const GatherMap &m) {
   if (dtype == SNG_F32) {
     SNG_TILE_SHAPES(SNG_TILE_OCC, float, 4)
+    SNG_TILE_SHAPES_F32(SNG_TILE_OCC)
   } else {
     SNG_TILE_SHAPES(SNG_TILE_OCC, uint16_t, 8)
   }

@@ -108,3 +108,26 @@ def test_tiled_rows_past_the_partition_cache(orc, m):
     np.testing.assert_array_equal(tiled["row_ptr"], rp)
     np.testing.assert_array_equal(tiled["col"], col)
     assert st["band_pairs"] == bpairs and st["kept_edges"] > 0
+
+
+@pytest.mark.parametrize("group,unroll", [(2, 1), (2, 2), (4, 4), (8, 2), (4, 2)])
+def test_tiled_lane_groups_and_steps(orc, group, unroll):
+    """FP32 rows of 64 values tested by 2, 4 or 8 lanes per pair with 1, 2 or
+    4 partner steps in flight: the group reduction hands each lane whole
+    sums of different steps (fewer or more steps than lanes), and every
+    arrangement gives the default mapping's graph and the oracle's rows."""
+    torch, sng = need_gpu()
+    n, d, m = 6000, 64, 140
+    x = datagen.random_points(n, d, seed=20 + unroll + group)
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    xg = torch.from_numpy(x).cuda()
+    base = dict(eps=eps, min_pts=4, m=m, seed=11)
+    tiled, st = _graph(sng, xg, sng.Params(**base, flags=sng.SNG_FLAG_TILED, map_tile=3,
+                                           map_group=group, map_unroll=unroll))
+    assert st["map_group"] == group
+    direct, _ = _graph(sng, xg, sng.Params(**base))
+    for k in tiled:
+        np.testing.assert_array_equal(tiled[k], direct[k], err_msg=k)
+    rp, col, bpairs, _ = orc.build_rows(x, eps, 11, m, band_rel=BAND_F32)
+    np.testing.assert_array_equal(tiled["col"], col)
+    assert st["band_pairs"] == bpairs
