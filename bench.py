@@ -269,11 +269,18 @@ def bench_sng(args, w):
     alg = gather_algorithmic_bytes(n, d, m, 4, stats["kept_edges"])
     achieved = alg / (g_ms * 1e-3) / 1e9
     full = stats["map_group"] * stats["map_nch"] * stats["map_vec"] == d
-    kname = (f"gather_kernel<float, {stats['map_vec']}, {stats['map_group']}, "
-             f"{stats['map_nch']}, {stats['map_unroll']}, 0, {int(full)}, 0>")
+    tiles = stats["map_tiles"]
+    if tiles:
+        # the tiled form: one partition launch, then one test launch per tile;
+        # the gather phase (all of them) is the unit the roofline times
+        kname = (f"tile_partition_kernel + {tiles * tiles} x tile_test_kernel<float, "
+                 f"{stats['map_vec']}, {stats['map_group']}, {stats['map_nch']}, "
+                 f"{stats['map_unroll']}, {int(full)}>")
+    else:
+        kname = (f"gather_kernel<float, {stats['map_vec']}, {stats['map_group']}, "
+                 f"{stats['map_nch']}, {stats['map_unroll']}, 0, {int(full)}, 0>")
     traffic = None
-    if params.map_passes <= 1 and not (params.flags & (sng.SNG_FLAG_PREFETCH |
-                                                       sng.SNG_FLAG_TILED)):
+    if params.map_passes <= 1 and not (params.flags & sng.SNG_FLAG_PREFETCH):
         traffic = CAPTURED_TRAFFIC.get((args.workload, kname))
     truth = w["truth"].astype(np.int32)
     ari_truth = sng.ari(labels, torch.from_numpy(truth).to(dev))
@@ -297,6 +304,7 @@ def bench_sng(args, w):
                                          ("map_group", "map_unroll", "map_block", "map_passes",
                                           "map_tile")},
                                       "tiled": bool(params.flags & sng.SNG_FLAG_TILED),
+                                      "tiles_per_axis": tiles,
                                       "prefetch": bool(params.flags & sng.SNG_FLAG_PREFETCH)},
                    "autotuned": tuned is not None},
         "e2e": {"value": Q * world / (t_e2e * 1e-3), "unit": "queries/s",

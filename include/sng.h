@@ -101,7 +101,12 @@ typedef int32_t sng_status;
                                 per axis, 0 = enough for two slices to fit in L2 --
                                 then each tile is tested while its two slices
                                 stay in L2.  Euclidean form, 16-byte vectors;
-                                same results; ~8 bytes of scratch per draw      */
+                                same results; ~8 bytes of scratch per draw.
+                                Falls back to the direct gather (stats
+                                map_tiles = 0) where it does not apply: other
+                                metrics, one lane per row, map_passes > 1,
+                                SNG_FLAG_NO_SYNC, or a bucket past its
+                                capacity (mean + 8 standard deviations)        */
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The
                                 edge arrays are sized for all n*m draws (8 bytes
@@ -171,6 +176,9 @@ typedef struct {
                              [3] core+union [4] labels [5] finalize [6] total
                              (gather to finalize) [7] surrogate gate        */
     int32_t map_vec, map_group, map_nch, map_unroll; /* gather mapping used     */
+    int32_t map_tiles;    /* slices per axis of the tiled gather (SNG_FLAG_TILED)
+                             when it ran; 0 = the direct gather             */
+    int32_t reserved0;    /* 0                                               */
 } sng_stats;
 
 typedef struct {

@@ -3,7 +3,9 @@
 The gather's cost depends on how a warp is split over pairs (lanes per pair),
 how many partner rows each warp keeps in flight, the block size and, for
 point sets larger than L2, how many L2-resident slices of the partner range
-the launch is split into.  The library picks a rule-of-thumb mapping; this
+the launch is split into, or whether the L2-tiled form (draws bucketed by
+source and partner slice, then tested tile by tile) beats the direct gather.
+The library picks a rule-of-thumb mapping; this
 module times a small set of candidates on the caller's own data, through the
 library's per-phase CUDA-event timers, and caches the fastest per
 (dtype, d, row stride, n bucket, m bucket) in a JSON file.
@@ -16,7 +18,7 @@ import os
 import statistics
 import time
 
-from . import SNG_FLAG_PREFETCH, SNG_FLAG_TIMING, Params, SngError, cluster
+from . import SNG_FLAG_PREFETCH, SNG_FLAG_TILED, SNG_FLAG_TIMING, Params, SngError, cluster
 
 CACHE_ENV = "SNG_AUTOTUNE_CACHE"
 
@@ -63,6 +65,18 @@ def candidates(x, p: Params) -> list[dict]:
         base = max(2, int(math.ceil(x_bytes / (48 << 20))))
         passes += sorted({2, base, base + 2, 2 * base} - {1})
     out = []
+    # the L2-tiled form (Euclidean, hashed draws): its slice count from the
+    # library's rule (two slices in about 88 MiB of L2) and one finer; it
+    # needs ~8.4 bytes of scratch per draw, so it is tried only where that
+    # leaves half the free memory
+    if x_bytes > (48 << 20) and not p.metric and p.sample_mode == 0:
+        free = torch.cuda.mem_get_info(x.device)[0] if x.is_cuda else 0
+        if 8.4 * n * p.draws(n) < 0.5 * free:
+            k0 = min(8, max(2, -(-2 * x_bytes // (88 << 20))))
+            for k in sorted({0, min(8, k0 + 2)}):
+                for u in (2, 4):
+                    out.append(dict(map_group=0, map_unroll=u, map_block=256, map_passes=0,
+                                    prefetch=False, tiled=True, map_tile=k))
     for ps in passes:
         for g in groups:
             for u in (1, 2, 4, 8):
@@ -76,9 +90,14 @@ def candidates(x, p: Params) -> list[dict]:
 def _params_for(base: dict, cand: dict) -> Params:
     c = dict(cand)
     pf = c.pop("prefetch", False)
-    flags = base.get("flags", 0) & ~SNG_FLAG_PREFETCH
+    tiled = c.pop("tiled", False)
+    flags = base.get("flags", 0) & ~(SNG_FLAG_PREFETCH | SNG_FLAG_TILED)
     if pf:
         flags |= SNG_FLAG_PREFETCH
+    if tiled:
+        flags |= SNG_FLAG_TILED
+    else:
+        c.setdefault("map_tile", 0)
     return Params(**{**base, **c, "flags": flags})
 
 

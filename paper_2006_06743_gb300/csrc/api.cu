@@ -352,7 +352,11 @@ static sng_status run_tiled(const sng_params *p, const Resolved &r, Scratch &s,
   cudaStream_t st = s.stream;
   const int64_t n = r.n;
   const int blocks = tile_test_blocks_per_sm(p->dtype, r.map);
-  if (blocks < 0 || r.map.sim || r.map.lanes || r.map.passes > 1) return SNG_OK;
+  // not for the similarity form, one lane per row or slice passes; and not
+  // in the no-sync form (the overflow check reads the status on the host)
+  if (blocks < 0 || r.map.sim || r.map.lanes || r.map.passes > 1 ||
+      (p->flags & SNG_FLAG_NO_SYNC))
+    return SNG_OK;
   const size_t esize = p->dtype == SNG_F32 ? 4 : 2;
   int k = p->map_tile > 0 ? p->map_tile
                           : (int)((2 * (int64_t)n * p->ld * esize + (88ll << 20) - 1) / (88ll << 20));
@@ -418,6 +422,7 @@ static sng_status run_tiled(const sng_params *p, const Resolved &r, Scratch &s,
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tile test launches");
+  gb->tiles = k;
   *done = true;
   return SNG_OK;
 }
@@ -730,6 +735,7 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
     return SNG_OK;
   }
   rc = read_stats(gb.counters, r, stats, st, &tm);
+  if (stats) stats->map_tiles = gb.tiles;
   s.release();
   return rc;
 }
@@ -877,6 +883,7 @@ sng_status sng_build_graph(const void *x, const sng_params *params, sng_graph *o
   CoreArgs ca{r.n, params->min_pts, gb.deg, nullptr, core, parent, labels};
   launch_core_init(ca, device_sms(), st);
   rc = read_stats(gb.counters, r, stats, st, &tm);
+  if (stats) stats->map_tiles = gb.tiles;
   if (rc) {
     free_all();
     return rc;

@@ -73,6 +73,7 @@ struct GraphBufs {
   const int64_t *num_edges_dev = nullptr;   // no-sync form: row_ptr + n
   bool want_src = false;
   bool col_owned_by_caller = false;  // true: col from cudaMalloc, not scratch
+  int tiles = 0;             // slices per axis of the tiled gather; 0 = direct
 };
 
 sng_status fail(sng_status st, const char *fmt, ...);

@@ -131,3 +131,39 @@ def test_tiled_lane_groups_and_steps(orc, group, unroll):
     rp, col, bpairs, _ = orc.build_rows(x, eps, 11, m, band_rel=BAND_F32)
     np.testing.assert_array_equal(tiled["col"], col)
     assert st["band_pairs"] == bpairs
+
+
+def test_tiled_reports_its_slices_and_falls_back(orc):
+    """stats map_tiles is the slice count when the tiled form ran and 0 where
+    it does not apply (cosine similarity; the no-sync form, which must stay
+    capturable in a CUDA graph) -- those calls run the direct gather and give
+    the same labels."""
+    torch, sng = need_gpu()
+    n, d, m = 4000, 64, 100
+    x = datagen.random_points(n, d, seed=31)
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    xg = torch.from_numpy(x).cuda()
+    p = sng.Params(eps=eps, min_pts=4, m=m, seed=5, flags=sng.SNG_FLAG_TILED, map_tile=3)
+    labels, st = sng.cluster(xg, p)
+    assert st["map_tiles"] == 3
+    _, st_direct = sng.cluster(xg, sng.Params(eps=eps, min_pts=4, m=m, seed=5))
+    assert st_direct["map_tiles"] == 0
+    _, st_cos = sng.cluster(xg, sng.Params(eps=0.2, min_pts=4, m=m, seed=5, metric=2,
+                                           flags=sng.SNG_FLAG_TILED, map_tile=3))
+    assert st_cos["map_tiles"] == 0
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        sng.cluster_async(xg, p, out)                   # warm-up off the capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        sng.cluster_async(xg, p, out)
+    out.fill_(-7)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, labels)
+    r = orc.cluster(x, eps, 5, m, 4, band_rel=BAND_F32)
+    np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
