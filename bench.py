@@ -129,6 +129,10 @@ BATCHED_INST_PER_QUERY = {"batched_kernel<4, 1, 1, 4, 1>": 14_119_942_974 / 3_51
 # while the timed launch uses that same kernel and mapping.
 CAPTURED_TRAFFIC = {
     ("mixture-n1M-d64", "gather_kernel<float, 4, 4, 4, 2, 0, 1, 0>"): 168_524_939_776 + 456_195_584,
+    # the tiled form: the partition launch plus all 36 tile tests of one step
+    ("mixture-n1M-d64",
+     "tile_partition_kernel + 36 x tile_test_kernel<float, 4, 4, 4, 2, 1, 1>"):
+        21_152_768 + 8_046_635_264 + 11_682_028_800 + 173_744_384,
 }
 
 
@@ -275,7 +279,7 @@ def bench_sng(args, w):
         # the gather phase (all of them) is the unit the roofline times
         kname = (f"tile_partition_kernel + {tiles * tiles} x tile_test_kernel<float, "
                  f"{stats['map_vec']}, {stats['map_group']}, {stats['map_nch']}, "
-                 f"{stats['map_unroll']}, {int(full)}>")
+                 f"{stats['map_unroll']}, {int(full)}, {stats['map_tex']}>")
     else:
         kname = (f"gather_kernel<float, {stats['map_vec']}, {stats['map_group']}, "
                  f"{stats['map_nch']}, {stats['map_unroll']}, 0, {int(full)}, 0>")
@@ -322,7 +326,11 @@ def bench_sng(args, w):
                      # kernel time (frac above 1 comes from partner rows that
                      # hit in L2, the share given by 1 - traffic / algorithmic)
                      "traffic_frac": (traffic / (g_ms * 1e-3) / 1e9 / peak) if traffic else None,
-                     "l2_served_share": (1.0 - traffic / alg) if traffic else None},
+                     "l2_served_share": (1.0 - traffic / alg) if traffic else None,
+                     # what the profile shows saturated: the direct gather
+                     # streams DRAM; the tiled form's tile tests are bound by
+                     # L1's load/store data pipe (partner rows from L2)
+                     "limiter": "L1 load/store data pipe" if tiles else "DRAM"},
         "phases_ms": {k: v for k, v in stats["ms"].items()},
         "stats": {k: stats[k] for k in ("kept_edges", "band_pairs", "band_points", "cores",
                                         "clusters", "noise", "recheck_pairs")},

@@ -178,7 +178,8 @@ typedef struct {
     int32_t map_vec, map_group, map_nch, map_unroll; /* gather mapping used     */
     int32_t map_tiles;    /* slices per axis of the tiled gather (SNG_FLAG_TILED)
                              when it ran; 0 = the direct gather             */
-    int32_t reserved0;    /* 0                                               */
+    int32_t map_tex;      /* tiled gather: 16-byte chunks of each partner row
+                             read through the texture unit (0 or 1)        */
 } sng_stats;
 
 typedef struct {

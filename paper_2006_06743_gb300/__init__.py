@@ -76,7 +76,7 @@ class sng_stats(ctypes.Structure):
                 ("ms", ctypes.c_float * 8), ("map_vec", ctypes.c_int32),
                 ("map_group", ctypes.c_int32), ("map_nch", ctypes.c_int32),
                 ("map_unroll", ctypes.c_int32), ("map_tiles", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32)]
+                ("map_tex", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "ms"}

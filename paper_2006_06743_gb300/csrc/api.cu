@@ -67,6 +67,11 @@ int device_sms() {
 Scratch::~Scratch() { release(); }
 
 void Scratch::release() {
+  if (!textures.empty()) {
+    cudaStreamSynchronize(stream);
+    for (unsigned long long t : textures) cudaDestroyTextureObject((cudaTextureObject_t)t);
+    textures.clear();
+  }
   for (void *p : ptrs) cudaFreeAsync(p, stream);
   ptrs.clear();
 }
@@ -399,7 +404,37 @@ static sng_status run_tiled(const sng_params *p, const Resolved &r, Scratch &s,
   cudaMemcpyAsync(d_roff, roff.data(), (size_t)tiles * 8, cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(d_cursor, 0, (size_t)tiles * 8, st);
   cudaMemsetAsync(d_rcur, 0, (size_t)tiles * 4, st);
-  TileArgs t{k, slice, d_entries, d_eoff, d_cap, d_cursor, d_runs, d_roff, d_rcur};
+  TileArgs t{k, slice, d_entries, d_eoff, d_cap, d_cursor, d_runs, d_roff, d_rcur, 0, 0};
+  // FP32 rows: one of each partner row's four 16-byte chunks comes through
+  // the texture unit, whose data path runs beside the load/store unit's (the
+  // tile test is bound by the latter; one chunk in four measured fastest)
+  // (compiled for full rows with four lanes per pair and two steps in flight)
+  if (p->dtype == SNG_F32 && r.map.vec == 4 && r.map.group == 4 && r.map.nch == 4 &&
+      r.map.unroll == 2 && r.map.full) {
+    int dev = 0, align = 0, width = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&align, cudaDevAttrTextureAlignment, dev);
+    cudaDeviceGetAttribute(&width, cudaDevAttrMaxTexture1DLinearWidth, dev);
+    // the rows' extent, (n - 1) * ld + d floats (d = 64 here; ld % 4 == 0)
+    const int64_t texels = ((n - 1) * p->ld + p->d) / 4;
+    if (align > 0 && (uintptr_t)ga.x % (uintptr_t)align == 0 && texels <= (int64_t)width) {
+      cudaResourceDesc rd{};
+      rd.resType = cudaResourceTypeLinear;
+      rd.res.linear.devPtr = const_cast<void *>(ga.x);
+      rd.res.linear.desc = cudaCreateChannelDesc<float4>();
+      rd.res.linear.sizeInBytes = (size_t)texels * 16;
+      cudaTextureDesc td{};
+      td.readMode = cudaReadModeElementType;
+      cudaTextureObject_t tex = 0;
+      if (cudaCreateTextureObject(&tex, &rd, &td, nullptr) == cudaSuccess) {
+        s.textures.push_back((unsigned long long)tex);
+        t.tex = (unsigned long long)tex;
+        t.tex_chunks = 1;
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
   launch_tile_partition(ga, t, device_sms() * 16, st);
   note_launch();
   // a bucket overflow (far outside the binomial spread) falls back
@@ -423,6 +458,7 @@ static sng_status run_tiled(const sng_params *p, const Resolved &r, Scratch &s,
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tile test launches");
   gb->tiles = k;
+  gb->tex_chunks = t.tex_chunks;
   *done = true;
   return SNG_OK;
 }
@@ -735,7 +771,10 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
     return SNG_OK;
   }
   rc = read_stats(gb.counters, r, stats, st, &tm);
-  if (stats) stats->map_tiles = gb.tiles;
+  if (stats) {
+    stats->map_tiles = gb.tiles;
+    stats->map_tex = gb.tex_chunks;
+  }
   s.release();
   return rc;
 }
@@ -883,7 +922,10 @@ sng_status sng_build_graph(const void *x, const sng_params *params, sng_graph *o
   CoreArgs ca{r.n, params->min_pts, gb.deg, nullptr, core, parent, labels};
   launch_core_init(ca, device_sms(), st);
   rc = read_stats(gb.counters, r, stats, st, &tm);
-  if (stats) stats->map_tiles = gb.tiles;
+  if (stats) {
+    stats->map_tiles = gb.tiles;
+    stats->map_tex = gb.tex_chunks;
+  }
   if (rc) {
     free_all();
     return rc;

@@ -42,6 +42,9 @@ struct Scratch {
   void release();
   cudaStream_t stream;
   std::vector<void *> ptrs;
+  // texture objects of this call: destroyed by release() once the stream
+  // has drained (there is no stream-ordered destroy)
+  std::vector<unsigned long long> textures;
 };
 
 // Per-phase CUDA-event marks for sng_stats.ms (SNG_FLAG_TIMING).
@@ -74,6 +77,7 @@ struct GraphBufs {
   bool want_src = false;
   bool col_owned_by_caller = false;  // true: col from cudaMalloc, not scratch
   int tiles = 0;             // slices per axis of the tiled gather; 0 = direct
+  int tex_chunks = 0;        // tiled gather: partner-row chunks read as texture
 };
 
 sng_status fail(sng_status st, const char *fmt, ...);

@@ -10,6 +10,8 @@
 // stream from DRAM.  Keep bits are set with atomicOr (a row's kept draws are
 // spread over k runs), row counts and degrees with atomicAdd.  Decisions,
 // keep bits, counts and degrees are those of the direct gather.
+#include <type_traits>
+
 #include "api_common.cuh"
 #include "tiled.cuh"
 
@@ -133,7 +135,29 @@ __global__ void __launch_bounds__(32 * kPartWarps) tile_partition_kernel(GatherA
 // Test one tile: warps take runs (one source row's draws into this tile's
 // partner slice), stage the (partner, draw) list U*32 entries at a time and
 // test them with G lanes per pair exactly as gather_row does.
-template <typename T, int VEC, int G, int NCH, int U, bool FULL>
+// One 16-byte chunk of a partner row through the texture path: the bits as
+// stored (element read mode, no filtering), returned by the texture unit's
+// own data path instead of the load/store unit's.
+template <typename T, int VEC>
+struct TexRaw {
+  static __device__ __forceinline__ typename Raw<T, VEC>::type fetch(unsigned long long, int64_t) {
+    return Raw<T, VEC>::zero();   // not compiled for other vector shapes
+  }
+};
+template <>
+struct TexRaw<float, 4> {
+  static __device__ __forceinline__ float4 fetch(unsigned long long t, int64_t i) {
+    return tex1Dfetch<float4>((cudaTextureObject_t)t, (int)i);
+  }
+};
+template <>
+struct TexRaw<uint16_t, 8> {
+  static __device__ __forceinline__ uint4 fetch(unsigned long long t, int64_t i) {
+    return tex1Dfetch<uint4>((cudaTextureObject_t)t, (int)i);
+  }
+};
+
+template <typename T, int VEC, int G, int NCH, int U, bool FULL, int TEXC>
 __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
     tile_test_kernel(GatherArgs a, TileArgs t, int b) {
   extern __shared__ int32_t smem_tile[];
@@ -199,9 +223,14 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
 #pragma unroll
           for (int c = 0; c < NCH; ++c) {
             const int off = (c * G + gl) * VEC;
-            v[u][c] = (p >= 0 && (FULL || off < d))
-                          ? Raw<T, VEC>::load(X + (int64_t)p * a.ld + off)
-                          : Raw<T, VEC>::zero();
+            if (p >= 0 && (FULL || off < d)) {
+              if (TEXC > 0 && c >= NCH - TEXC)
+                v[u][c] = TexRaw<T, VEC>::fetch(t.tex, ((int64_t)p * a.ld + off) / VEC);
+              else
+                v[u][c] = Raw<T, VEC>::load(X + (int64_t)p * a.ld + off);
+            } else {
+              v[u][c] = Raw<T, VEC>::zero();
+            }
           }
         }
         float part[U];
@@ -295,13 +324,34 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
   }
 }
 
+template <typename T, int VEC, int G, int NCH, int U, bool FULL, int TEXC>
+static void launch_tt(const GatherMap &m, const GatherArgs &a, const TileArgs &t, int b, int grid,
+                      cudaStream_t st) {
+  const size_t smem = (size_t)(m.block / 32) * 2 * 32 * U * sizeof(int32_t);
+  tile_test_kernel<T, VEC, G, NCH, U, FULL, TEXC><<<grid, m.block, smem, st>>>(a, t, b);
+}
+
+// shapes compiled with a texture chunk: full FP32 rows of 16 float4 chunks,
+// four lanes per pair, two steps in flight (the tuned tiled mapping at d = 64)
+template <typename T, int VEC, int G, int NCH, int U, bool FULL>
+constexpr bool tex_shape() {
+  return FULL && G == 4 && U == 2 && NCH == 4 && std::is_same<T, float>::value && VEC == 4;
+}
+
 template <typename T, int VEC, int G, int NCH, int U, bool FULL>
 static bool try_tile(const GatherMap &m, const GatherArgs &a, const TileArgs &t, int b, int grid,
                      cudaStream_t st) {
   if (m.vec != VEC || m.group != G || m.nch != NCH || m.unroll != U || FULL != (m.full != 0))
     return false;
-  const size_t smem = (size_t)(m.block / 32) * 2 * 32 * U * sizeof(int32_t);
-  tile_test_kernel<T, VEC, G, NCH, U, FULL><<<grid, m.block, smem, st>>>(a, t, b);
+  if constexpr (tex_shape<T, VEC, G, NCH, U, FULL>()) {
+    if (t.tex) {
+      if (t.tex_chunks == 1) {
+        launch_tt<T, VEC, G, NCH, U, FULL, 1>(m, a, t, b, grid, st);
+        return true;
+      }
+    }
+  }
+  launch_tt<T, VEC, G, NCH, U, FULL, 0>(m, a, t, b, grid, st);
   return true;
 }
 
@@ -312,7 +362,7 @@ static int occ_tile(const GatherMap &m) {
   int blocks = 0;
   const size_t smem = (size_t)(m.block / 32) * 2 * 32 * U * sizeof(int32_t);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &blocks, tile_test_kernel<T, VEC, G, NCH, U, FULL>, m.block, smem) != cudaSuccess)
+          &blocks, tile_test_kernel<T, VEC, G, NCH, U, FULL, 0>, m.block, smem) != cudaSuccess)
     return 0;
   return blocks;
 }

@@ -18,6 +18,8 @@ struct TileArgs {
   int4 *runs;                    // per tile: (row, base_hi, base_lo, count) of each run
   const int64_t *run_off;        // per tile: first run
   unsigned int *run_cursor;      // per tile: runs written (zeroed)
+  unsigned long long tex;        // linear texture over the points (16-byte texels) or 0
+  int tex_chunks;                // chunks of each partner row fetched through it (0 or 1)
 };
 
 void launch_tile_partition(const GatherArgs &a, const TileArgs &t, int grid, cudaStream_t st);

@@ -167,3 +167,25 @@ def test_tiled_reports_its_slices_and_falls_back(orc):
     assert torch.equal(out, labels)
     r = orc.cluster(x, eps, 5, m, 4, band_rel=BAND_F32)
     np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
+
+
+@pytest.mark.parametrize("ld", [64, 68, 96])
+def test_tiled_texture_chunk_on_padded_rows(orc, ld):
+    """FP32 rows of 64 values take one 16-byte chunk per partner through the
+    texture unit.  Rows with a padded stride, in a buffer that ends right
+    after the last row's 64 values (padding holding NaN), give the oracle's
+    graph."""
+    torch, sng = need_gpu()
+    n, d, m = 5000, 64, 120
+    x = datagen.random_points(n, d, seed=ld)
+    flat = torch.full(((n - 1) * ld + d,), float("nan"), dtype=torch.float32, device="cuda")
+    xg = flat.as_strided((n, d), (ld, 1))
+    xg.copy_(torch.from_numpy(x))
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    p = sng.Params(eps=eps, min_pts=4, m=m, seed=3, flags=sng.SNG_FLAG_TILED, map_tile=4)
+    g, st = _graph(sng, xg, p)
+    assert st["map_tiles"] == 4 and st["map_group"] == 4 and st["map_unroll"] == 2
+    rp, col, bpairs, _ = orc.build_rows(x, eps, 3, m, band_rel=BAND_F32)
+    np.testing.assert_array_equal(g["row_ptr"], rp)
+    np.testing.assert_array_equal(g["col"], col)
+    assert st["band_pairs"] == bpairs
