@@ -35,6 +35,9 @@ WORKLOADS = {
     "mixture-n100k-d64": (100_000, 64, 100, 0.02, 0.01, 10),
     # profiling case of the same gather: same points (256 MB > L2), 100 draws
     "mixture-n1M-d64-s1e-4": (1_000_000, 64, 100, 0.02, 0.0001, 10),
+    # profiling case of the tiled form: the headline's 1000 draws per point on
+    # 4e5 points (102 MB, 3 x 3 tiles, 3.2 GB of tile buckets)
+    "mixture-n400k-d64-m1000": (400_000, 64, 100, 0.02, 0.0025, 10),
 }
 
 
