@@ -26,6 +26,17 @@ void note_launch(int count) { g_launches.fetch_add(count, std::memory_order_rela
 
 static thread_local std::string g_last_error;
 
+// Copies of the point coordinates still in flight on other streams (the
+// host-buffer entry point's input pieces): the first kernel that reads the
+// coordinates waits for them, so work that does not (the tiled form's
+// partition) overlaps the copy.
+static thread_local std::vector<cudaEvent_t> g_inputs_pending;
+
+void wait_inputs(cudaStream_t st) {
+  for (cudaEvent_t ev : g_inputs_pending) cudaStreamWaitEvent(st, ev, 0);
+  g_inputs_pending.clear();
+}
+
 sng_status fail(sng_status st, const char *fmt, ...) {
   char buf[512];
   va_list ap;
@@ -450,6 +461,7 @@ static sng_status run_tiled(const sng_params *p, const Resolved &r, Scratch &s,
   cudaMemsetAsync(gb->bitmask, 0, (size_t)n * r.W * 4, st);
   cudaMemsetAsync(gb->out_cnt, 0, (size_t)n * 4, st);
   const int grid = device_sms() * (blocks > 0 ? blocks : 1);
+  wait_inputs(st);   // the partition read no coordinates; the tests do
   for (int b = 0; b < tiles; ++b) {
     if (!launch_tile_test(p->dtype, r.map, ga, t, b, grid, st))
       return fail(SNG_EINTERNAL, "tile test mapping vanished");
@@ -501,12 +513,14 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   if (tiled) {
     // done by the tiled form
   } else if (r.map.passes <= 1) {
+    wait_inputs(st);
     if (!launch_gather(p->dtype, r.map, ga, grid, st))
       return fail(SNG_EINVAL, "no compiled gather for vec=%d group=%d nch=%d unroll=%d",
                   r.map.vec, r.map.group, r.map.nch, r.map.unroll);
     note_launch();
   } else {
     // slices of the partner range, each small enough to stay in L2
+    wait_inputs(st);
     const int64_t slice = (n + r.map.passes - 1) / r.map.passes;
     for (int64_t lo = 0; lo < n; lo += slice) {
       const int64_t hi = lo + slice < n ? lo + slice : n;
@@ -842,19 +856,32 @@ sng_status sng_cluster_host(const void *x_host, const sng_params *params, int32_
     if ((e = cudaMemcpyAsync(pieces[k].dst, pieces[k].src, pieces[k].bytes,
                              cudaMemcpyHostToDevice, cs)) != cudaSuccess)
       break;
-    if ((e = cudaEventRecord(ev, cs)) != cudaSuccess) break;
-    e = cudaStreamWaitEvent(st, ev, 0);
+    e = cudaEventRecord(ev, cs);
   }
-  for (cudaEvent_t ev : done) cudaEventDestroy(ev);   // released once complete
-  for (cudaStream_t cs : side) cudaStreamDestroy(cs);
+  for (cudaStream_t cs : side) cudaStreamDestroy(cs);   // released once drained
   if (fork) cudaEventDestroy(fork);
+  // the stream joins the copies where the clustering first reads the
+  // points (after the tiled form's partition); whatever the call did not
+  // consume (an error, an early return) is joined here, so no copy from the
+  // caller's buffer outlives the call
+  auto join_copies = [&]() {
+    g_inputs_pending.clear();
+    for (cudaEvent_t ev : done) {
+      cudaStreamWaitEvent(st, ev, 0);
+      cudaEventDestroy(ev);
+    }
+    done.clear();
+  };
   if (e != cudaSuccess) {
+    join_copies();
     cudaStreamSynchronize(st);
     return cuda_fail(e, "host to device copy");
   }
   sng_params pd = *params;
   pd.x_f32_master = md;
+  g_inputs_pending = done;
   rc = sng_cluster(xd, &pd, ld, cd, stats, stream);
+  join_copies();
   if (rc) {
     cudaStreamSynchronize(st);
     return rc;

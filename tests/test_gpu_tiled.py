@@ -189,3 +189,26 @@ def test_tiled_texture_chunk_on_padded_rows(orc, ld):
     np.testing.assert_array_equal(g["row_ptr"], rp)
     np.testing.assert_array_equal(g["col"], col)
     assert st["band_pairs"] == bpairs
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_tiled_host_buffer_call_overlaps_copy(pinned):
+    """sng_cluster_host in the tiled form: the partition reads no
+    coordinates, so it runs while the points are still being copied in (four
+    pieces on side streams); the tile tests wait for the copies.  Labels,
+    core flags and counts equal the device call's."""
+    torch, sng = need_gpu()
+    n, d, m = 400_000, 64, 60
+    x = datagen.gaussian_mixture(n, d, 40, 0.02, seed=8)
+    p = sng.Params(eps=8.0, min_pts=6, m=m, seed=6, flags=sng.SNG_FLAG_TILED)
+    ref, ref_core, st_ref = sng.cluster(torch.from_numpy(x).cuda(), p, want_core=True)
+    assert st_ref["map_tiles"] >= 2
+    xt = torch.from_numpy(x)
+    if pinned:
+        xt = xt.pin_memory()
+    for _ in range(2):
+        labels, core, st = sng.cluster_host(xt, p, want_core=True)
+        np.testing.assert_array_equal(labels, ref.cpu().numpy())
+        np.testing.assert_array_equal(core, ref_core.cpu().numpy())
+        assert st["map_tiles"] == st_ref["map_tiles"]
+        assert st["kept_edges"] == st_ref["kept_edges"] and st["kept_edges"] > 0
