@@ -141,7 +141,9 @@ typedef struct {
                              power of two), 0 = library default             */
     int32_t map_unroll;   /* partner batches in flight per warp, 0 = default */
     int32_t map_block;    /* threads per block of the gather, 0 = default    */
-    int32_t map_tile;     /* batched form: source rows per work item, 0 = default */
+    int32_t map_tile;     /* batched form: source rows per work item, 0 = default;
+                             tiled gather (SNG_FLAG_TILED): slices per axis,
+                             clamped to [2, 32], 0 = two slices in ~88 MiB  */
     int32_t map_passes;   /* gather: 0/1 = one pass over all partners; k > 1 = k
                              launches, each testing only the draws whose partner
                              lies in one of k equal slices of X (L2-resident) */

@@ -72,8 +72,8 @@ def candidates(x, p: Params) -> list[dict]:
     if x_bytes > (48 << 20) and not p.metric and p.sample_mode == 0:
         free = torch.cuda.mem_get_info(x.device)[0] if x.is_cuda else 0
         if 8.4 * n * p.draws(n) < 0.5 * free:
-            k0 = min(8, max(2, -(-2 * x_bytes // (88 << 20))))
-            for k in sorted({0, min(8, k0 + 2)}):
+            k0 = min(32, max(2, -(-2 * x_bytes // (88 << 20))))
+            for k in sorted({0, max(2, k0 // 2), min(32, k0 + 2)}):
                 for u in (2, 4):
                     out.append(dict(map_group=0, map_unroll=u, map_block=256, map_passes=0,
                                     prefetch=False, tiled=True, map_tile=k))

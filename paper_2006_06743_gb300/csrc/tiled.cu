@@ -26,8 +26,8 @@ namespace sng {
 // rows hash again in pass 2 and repeat the grouping.  Between the passes one
 // lane per slice reserves the row's run in that tile's bucket.
 constexpr int kPartWarps = 4;
-constexpr int kPartCache = 1024;   // places fit in the tag's low 12 bits
-constexpr int kTagShift = 12;
+constexpr int kPartCache = 1024;   // places (< 1024) fit in the tag's low 10 bits,
+constexpr int kTagShift = 10;      // slices (< 32) in the 6 above them
 
 // floor(p / slice) for 0 <= p < 2^31 from inv = floor((2^32 - 1) / slice):
 // the product's high word is the quotient or one below it, and one compare
@@ -212,8 +212,11 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
         sj[u * 32 + lane] = j;
       }
       __syncwarp();
+      // only the steps that hold entries (the run's last stage is partial;
+      // STEPS is a multiple of U, so t0 + u stays inside the stage)
+      const int steps = min(STEPS, (len - jb + R - 1) / R);
 #pragma unroll 1
-      for (int t0 = 0; t0 < STEPS; t0 += U) {
+      for (int t0 = 0; t0 < steps; t0 += U) {
         typename Raw<T, VEC>::type v[U][NCH];
         int32_t pv[U];
 #pragma unroll

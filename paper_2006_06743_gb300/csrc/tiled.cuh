@@ -5,7 +5,7 @@
 
 namespace sng {
 
-constexpr int kMaxTiles = 8;                     // slices per axis
+constexpr int kMaxTiles = 32;                    // slices per axis (one lane each)
 constexpr uint32_t kErrTileOverflow = 1u << 4;   // a tile bucket overflowed (host falls back)
 
 struct TileArgs {

@@ -20,7 +20,8 @@ def _graph(sng, xg, p, master=None):
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("n,d,tiles", [(5000, 64, 0), (7000, 64, 3), (4000, 128, 2),
-                                       (6000, 32, 8), (3000, 60, 4), (5000, 16, 5)])
+                                       (6000, 32, 8), (3000, 60, 4), (5000, 16, 5),
+                                       (6000, 64, 17), (9000, 64, 32), (4000, 128, 40)])
 def test_tiled_graph_matches_oracle_and_direct(orc, dtype, n, d, tiles):
     torch, sng = need_gpu()
     x = datagen.random_points(n, d, seed=n + d + tiles)
