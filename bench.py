@@ -135,7 +135,7 @@ CAPTURED_TRAFFIC = {
     # the tiled form: the partition launch plus all 36 tile tests of one step
     ("mixture-n1M-d64",
      "tile_partition_kernel + 36 x tile_test_kernel<float, 4, 4, 4, 2, 1, 1>"):
-        21_152_768 + 8_046_635_264 + 11_682_028_800 + 173_744_384,
+        21_680_128 + 8_046_274_048 + 11_679_285_760 + 172_615_680,
 }
 
 
