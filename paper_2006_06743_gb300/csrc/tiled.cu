@@ -9,7 +9,9 @@
 // resident in L2 while its pairs are tested, and only the bucket lists
 // stream from DRAM.  Keep bits are set with atomicOr (a row's kept draws are
 // spread over k runs), row counts and degrees with atomicAdd.  Decisions,
-// keep bits, counts and degrees are those of the direct gather.
+// keep bits, counts and degrees are those of the direct gather.  The test is
+// bound by the load/store unit's data path, so for FP32 rows one 16-byte
+// chunk of each partner row is fetched through the texture unit instead.
 #include <type_traits>
 
 #include "api_common.cuh"
@@ -148,12 +150,6 @@ template <>
 struct TexRaw<float, 4> {
   static __device__ __forceinline__ float4 fetch(unsigned long long t, int64_t i) {
     return tex1Dfetch<float4>((cudaTextureObject_t)t, (int)i);
-  }
-};
-template <>
-struct TexRaw<uint16_t, 8> {
-  static __device__ __forceinline__ uint4 fetch(unsigned long long t, int64_t i) {
-    return tex1Dfetch<uint4>((cudaTextureObject_t)t, (int)i);
   }
 };
 
