@@ -100,3 +100,57 @@ def test_autotuner_candidates_are_compiled():
                 if rc == 0 and m[6] == 1:
                     n_ok += 1
         assert n_ok >= 4
+
+
+class _FakeCudaRows:
+    """Stands in for a CUDA tensor of n x d rows (shape, stride, dtype, device)
+    so the autotuner's candidate list can be checked without a GPU."""
+
+    def __init__(self, n, d, dtype):
+        import torch
+        self.shape = (n, d)
+        self.dtype = dtype
+        self.is_cuda = True
+        self.device = torch.device("cuda", 0)
+        self._ld = d
+
+    def stride(self, dim=None):
+        return (self._ld, 1) if dim is None else (self._ld, 1)[dim]
+
+
+def test_autotuner_offers_the_tiled_form_where_it_fits(monkeypatch):
+    """Tiled candidates come first for Euclidean hashed draws on point sets
+    over 48 MiB whose buckets (~8.4 B per draw) fit in half the free memory;
+    their slice counts are the library's rule (two slices in 88 MiB, clamped
+    to [2, 32]), half of it and two more; none for small sets, similarity
+    metrics, every-pair sampling or too little memory."""
+    import torch
+    from paper_2006_06743_gb300 import Params, autotune
+    free = [200 << 30]
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda dev=None: (free[0], 280 << 30))
+
+    def tiled(n, d, dtype=torch.float32, **kw):
+        cands = autotune.candidates(_FakeCudaRows(n, d, dtype), Params(eps=1.0, min_pts=5, **kw))
+        t = [c for c in cands if c.get("tiled")]
+        if t:
+            first = next(i for i, c in enumerate(cands) if not c.get("tiled"))
+            assert first == len(t)                   # tiled candidates lead the list
+        return sorted({c["map_tile"] for c in t}), {c["map_unroll"] for c in t}
+
+    # 10^6 x 64 FP32 = 256 MB: rule k = ceil(512 MB / 88 MiB) = 6 -> {6 (as 0), 3, 8}
+    ks, us = tiled(1_000_000, 64, s=0.001)
+    assert ks == [0, 3, 8] and us == {2, 4}
+    # 5e6 x 128 FP32 = 2.56 GB: rule 56 -> clamped to 32 -> {32 (as 0), 16, 32}
+    assert tiled(5_000_000, 128, m=1000)[0] == [0, 16, 32]
+    # 4e5 x 64 FP32 = 102 MB: rule ceil(204.8 MB / 92.3 MB) = 3 -> {3, 2, 5}
+    assert tiled(400_000, 64, m=1000)[0] == [0, 2, 5]
+    # small sets, similarity metrics and every-pair sampling: none
+    assert tiled(100_000, 64, m=100)[0] == []
+    assert tiled(1_000_000, 64, m=1000, metric=2)[0] == []
+    assert tiled(200_000, 64, sample_mode=1)[0] == []
+    # buckets must fit in half the free memory: 8.4 B x 10^9 draws = 8.4 GB
+    # (15 GiB free: half is 8.05 GB; 17 GiB: 9.1 GB)
+    free[0] = 15 << 30
+    assert tiled(1_000_000, 64, m=1000)[0] == []
+    free[0] = 17 << 30
+    assert tiled(1_000_000, 64, m=1000)[0] == [0, 3, 8]
