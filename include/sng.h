@@ -105,8 +105,9 @@ typedef int32_t sng_status;
                                 Falls back to the direct gather (stats
                                 map_tiles = 0) where it does not apply: other
                                 metrics, one lane per row, map_passes > 1,
-                                SNG_FLAG_NO_SYNC, or a bucket past its
-                                capacity (mean + 8 standard deviations)        */
+                                SNG_FLAG_NO_SYNC, no device memory for the
+                                buckets, or a bucket past its capacity (mean +
+                                8 standard deviations)                         */
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The
                                 edge arrays are sized for all n*m draws (8 bytes

@@ -409,7 +409,9 @@ static sng_status run_tiled(const sng_params *p, const Resolved &r, Scratch &s,
       (rc = s.alloc((void **)&d_roff, (size_t)tiles * 8, "tile run offsets")) ||
       (rc = s.alloc((void **)&d_cursor, (size_t)tiles * 8, "tile cursors")) ||
       (rc = s.alloc((void **)&d_rcur, (size_t)tiles * 4, "tile run cursors")))
-    return rc;
+    // no room for the buckets (about 8.4 bytes per draw): the direct gather
+    // runs instead, as for any case the tiled form does not cover
+    return rc == SNG_ENOMEM ? SNG_OK : rc;
   cudaMemcpyAsync(d_cap, cap.data(), (size_t)tiles * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_eoff, eoff.data(), (size_t)tiles * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_roff, roff.data(), (size_t)tiles * 8, cudaMemcpyHostToDevice, st);

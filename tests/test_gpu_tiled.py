@@ -213,3 +213,31 @@ def test_tiled_host_buffer_call_overlaps_copy(pinned):
         np.testing.assert_array_equal(core, ref_core.cpu().numpy())
         assert st["map_tiles"] == st_ref["map_tiles"]
         assert st["kept_edges"] == st_ref["kept_edges"] and st["kept_edges"] > 0
+
+
+def test_tiled_falls_back_when_its_buckets_cannot_be_allocated(orc):
+    """A failed allocation of the tiled form's buckets, runs or counters
+    (host-side injection: the k-th scratch allocation of the call fails; the
+    seven before them are the graph's own) makes the call run the direct
+    gather: same labels, map_tiles 0, no error."""
+    import os
+    torch, sng = need_gpu()
+    n, d, m = 4000, 64, 80
+    x = datagen.random_points(n, d, seed=44)
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    xg = torch.from_numpy(x).cuda()
+    p = sng.Params(eps=eps, min_pts=4, m=m, seed=9, flags=sng.SNG_FLAG_TILED, map_tile=3)
+    ref, st_ref = sng.cluster(xg, p)
+    assert st_ref["map_tiles"] == 3
+    for k in (8, 9, 14):
+        os.environ["SNG_FAULT_ALLOC"] = str(k)
+        try:
+            got, st = sng.cluster(xg, p)
+        finally:
+            del os.environ["SNG_FAULT_ALLOC"]
+        assert st["map_tiles"] == 0, k
+        assert torch.equal(got, ref), k
+    r = orc.cluster(x, eps, 9, m, 4, band_rel=BAND_F32)
+    np.testing.assert_array_equal(ref.cpu().numpy(), r["labels"])
+    _, st_again = sng.cluster(xg, p)
+    assert st_again["map_tiles"] == 3
