@@ -17,7 +17,8 @@ Contents
   * ``ami``: the adjusted mutual information of Vinh, Epps & Bailey (2010),
     the paper's second score, with its expected mutual information summed
     over every term of the hypergeometric model.
-  * ``mlp``: FP64 forward/backward/Adam for the core-point surrogate network.
+  * ``mlp``: FP64 forward/backward/Adam for the core-point surrogate network;
+    ``gate_decisions``: the rule by which that network gates the points.
 
 Parity status per function is listed in each docstring; every function here is
 pinned by a ``-m "not gpu"`` test against something other than itself.
@@ -25,6 +26,7 @@ pinned by a ``-m "not gpu"`` test against something other than itself.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -305,6 +307,47 @@ def cluster_gated(x, eps: float, seed: int, m: int, min_pts: int, forced, m_row,
                       w_row=w_row)
     r["queries"] = int(np.minimum(np.asarray(m_row, dtype=np.int64), m).sum())
     return r
+
+
+GATE_DEG_UNIT = 16   # degree units per kept draw when the gate reweights
+
+
+def gate_decisions(prob, m: int, p_noise: float, p_core: float, core_draw_frac: float,
+                   noise_draw_frac: float = 0.0, reweight: bool = False,
+                   deg_unit: int = GATE_DEG_UNIT):
+    """The surrogate gate's rule (an extension; the paper has no learned part):
+    a point whose core probability is below ``p_noise`` is declared not core
+    and draws the first ceil(noise_draw_frac * m) partners of its stream; one
+    above ``p_core`` is declared core and draws ceil(core_draw_frac * m);
+    every other point draws all m and is tested by its degree (both
+    comparisons strict).  Thresholds and fractions are read as the float32
+    values the caller passes.  With ``reweight`` each kept draw of a point
+    that drew m_i partners counts round(deg_unit * m / m_i) degree units (an
+    unbiased estimate of its full count; deg_unit when m_i = 0).
+
+    Returns forced (uint8: 0 by degree, 1 core, 2 not core), draws per point
+    (int32) and the per-point weights (int32, or None without reweighting).
+    Pinned by the hand-worked cases of tests/golden/gate_rule.txt."""
+    prob = np.asarray(prob, dtype=np.float64).ravel()
+    lo = float(np.float32(p_noise))
+    hi = float(np.float32(p_core))
+    forced = np.zeros(prob.size, dtype=np.uint8)
+    forced[prob > hi] = 1
+    forced[prob < lo] = 2
+    m_core = int(math.ceil(float(np.float32(core_draw_frac)) * m))
+    m_noise = int(math.ceil(float(np.float32(noise_draw_frac)) * m))
+    draws = {0: m, 1: m_core, 2: m_noise}
+    m_row = np.array([draws[int(f)] for f in range(3)], dtype=np.int32)[forced]
+    if not reweight:
+        return forced, m_row, None
+
+    def weight(mi: int) -> int:
+        if mi <= 0:
+            return deg_unit
+        return int(math.floor(deg_unit * m / mi + 0.5))
+
+    w = np.array([weight(draws[f]) for f in range(3)], dtype=np.int32)
+    return forced, m_row, w[forced]
 
 
 def dbscan_bruteforce(x, eps: float, min_pts_db: int) -> tuple[np.ndarray, np.ndarray]:

@@ -18,7 +18,9 @@ the optimiser is Adam (Kingma & Ba 2015) with bias correction.
 Pins (tests/test_oracle_mlp.py): central finite differences of ``loss`` for
 every parameter tensor, GELU against Phi values from the error function,
 BCE against its closed form at z = 0 (log 2), the first Adam step equal to
-lr * sign(g) up to eps, and training that drives the loss of a separable
+lr * sign(g) up to eps, three hand-worked Adam steps with changing gradients
+(moments, both bias corrections and the updates, tests/golden/
+adam_three_steps.txt), and training that drives the loss of a separable
 problem down.
 """
 from __future__ import annotations

@@ -12,7 +12,6 @@ module packs parameters and drives the calls.
 from __future__ import annotations
 
 import ctypes
-import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -238,32 +237,3 @@ class Surrogate:
             core.data_ptr() if core is not None else None, ctypes.byref(st), _stream_ptr()))
         out = st.as_dict()
         return (labels, core, out) if want_core else (labels, out)
-
-
-DEG_UNIT = 16
-
-
-def gate_decisions(prob, m: int, p_noise: float, p_core: float, core_draw_frac: float,
-                   noise_draw_frac: float = 0.0, reweight: bool = False):
-    """The gate's rule on given probabilities (host mirror, for checking):
-    forced (0 uncertain, 1 core, 2 noise), draws per point and, when
-    reweighting, the degree weight of each point's kept draws."""
-    prob = np.asarray(prob, np.float32)
-    forced = np.zeros(prob.size, np.uint8)
-    forced[prob > np.float32(p_core)] = 1
-    forced[prob < np.float32(p_noise)] = 2
-    m_core = int(math.ceil(np.float64(np.float32(core_draw_frac)) * m))
-    m_noise = int(math.ceil(np.float64(np.float32(noise_draw_frac)) * m))
-    m_row = np.full(prob.size, m, np.int32)
-    m_row[forced == 1] = m_core
-    m_row[forced == 2] = m_noise
-    if not reweight:
-        return forced, m_row, None
-
-    def w(mi):
-        return DEG_UNIT if mi <= 0 else int(math.floor(DEG_UNIT * m / mi + 0.5))
-
-    w_row = np.full(prob.size, w(m), np.int32)
-    w_row[forced == 1] = w(m_core)
-    w_row[forced == 2] = w(m_noise)
-    return forced, m_row, w_row

@@ -110,12 +110,36 @@ def test_training_steps_match_oracle_adam():
         assert torch.equal(net.params[nt:], p0[nt:])
 
 
-@pytest.mark.parametrize("n", [6000, 400_000])
-def test_gated_cluster_matches_oracle_gated_form(orc, n):
-    """Given the gate's decisions (from the network's probabilities), the
-    surrogate path is exactly the oracle's gated form of Algorithm 1 (at
-    n = 400,000 the gather runs one lane per row, with per-row draw counts
-    and weights)."""
+def _gap_threshold(prob, target: float, tol: float, span: float = 0.15) -> float:
+    """A float32 threshold near ``target`` with no oracle probability within
+    ``tol`` of it (the kernels' probabilities are within ``tol`` of the
+    oracle's), so that the gate's decision on every point is the oracle's."""
+    if target <= 0.0 or target >= 1.0:
+        return target          # nothing is below 0 or above 1
+    lo, hi = target - span, target + span
+    inside = np.sort(prob[(prob > lo - tol) & (prob < hi + tol)])
+    edges = np.concatenate([[lo - tol], inside, [hi + tol]])
+    best, best_t = 0.0, None
+    for a, b in zip(edges[:-1], edges[1:]):
+        t = float(np.float32(0.5 * (a + b)))
+        room = min(t - a, b - t)
+        if room > 2 * tol and (best_t is None or abs(t - target) < abs(best_t - target)):
+            best, best_t = room, t
+    assert best_t is not None, f"no gap of {2 * tol} near {target}"
+    return best_t
+
+
+@pytest.mark.parametrize("n,fp32_act", [(6000, False), (6000, True), (400_000, True)])
+def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act):
+    """The surrogate path against the oracle's gated form of Algorithm 1, with
+    every expected value from the oracle: the gate's probabilities from the
+    FP64 network oracle on the trained network's FP16-rounded weights, its
+    decisions from the oracle's gate rule, the clustering from the oracle's
+    gated form.  Thresholds are moved to the nearest place where no oracle
+    probability lies within the kernels' stated error of them (2e-5 with
+    FP32 activations, 2e-3 on tensor cores), so that no decision can fall
+    either way.  At n = 400,000 the gather runs one lane per row, with
+    per-row draw counts and weights."""
     torch, sng = need_gpu()
     from paper_2006_06743_gb300 import surrogate as sg
     d, m = 8, 120
@@ -128,12 +152,17 @@ def test_gated_cluster_matches_oracle_gated_form(orc, n):
     net = sg.Surrogate(datagen.mlp_init(d, 128, 2), cfg=sg.TrainConfig(batch=1024, lr=3e-3))
     net.standardize(xg)
     net.train(xg, plain_core, 300)
-    prob = net.predict(xg).cpu().numpy()
+    net.cfg.fp32_activations = fp32_act
+    tol = 2e-5 if fp32_act else 2e-3
+    w, mean, std = sg.unpack(net.params.cpu().numpy(), d)
+    f = omlp.forward(_fp16(w), x, mean.astype(np.float64), std.astype(np.float64))
+    prob = 1.0 / (1.0 + np.exp(-f["z"]))
     for pn, pc, frac, nfrac, rw in ((0.1, 0.9, 0.25, 0.0, False), (0.3, 0.6, 0.5, 0.0, False),
                                     (0.0, 1.0, 0.25, 0.0, False), (0.1, 0.9, 0.25, 0.1, True),
                                     (0.05, 0.95, 0.3, 0.5, True), (0.2, 0.8, 0.5, 0.0, True)):
+        pn, pc = _gap_threshold(prob, pn, tol), _gap_threshold(prob, pc, tol)
         labels, core, st = net.cluster(xg, p, pn, pc, frac, nfrac, rw, want_core=True)
-        forced, m_row, w_row = sg.gate_decisions(prob, m, pn, pc, frac, nfrac, rw)
+        forced, m_row, w_row = orc.gate_decisions(prob, m, pn, pc, frac, nfrac, rw)
         r = orc.cluster_gated(x, eps, p.seed, m, p.min_pts, forced, m_row, w_row=w_row)
         np.testing.assert_array_equal(core.cpu().numpy(), r["core"])
         np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])

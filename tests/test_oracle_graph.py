@@ -318,6 +318,32 @@ def test_gated_weighted_degrees(orc):
     np.testing.assert_array_equal(r["deg"], [32, 64, 0, 32])
 
 
+def test_gate_rule_hand_cases(orc):
+    """The gate's rule (thresholds, draw budgets, degree weights) against the
+    hand-worked rows of tests/golden/gate_rule.txt, one point at a time and
+    all points of one setting together."""
+    from golden_io import read_rows
+    rows = read_rows("gate_rule.txt")
+    groups = {}
+    for r in rows:
+        key = tuple(r[:6])
+        groups.setdefault(key, []).append(r[6:])
+        m, pn, pc, cf, nf, rw = int(r[0]), float(r[1]), float(r[2]), float(r[3]), float(r[4]), \
+            bool(int(r[5]))
+        forced, m_row, w_row = orc.gate_decisions([float(r[6])], m, pn, pc, cf, nf, rw)
+        assert int(forced[0]) == int(r[7]), r
+        assert int(m_row[0]) == int(r[8]), r
+        if r[9] == "-":
+            assert w_row is None
+        else:
+            assert int(w_row[0]) == int(r[9]), r
+    for key, pts in groups.items():
+        m, pn, pc, cf, nf, rw = int(key[0]), *(float(v) for v in key[1:5]), bool(int(key[5]))
+        forced, m_row, _ = orc.gate_decisions([float(p[0]) for p in pts], m, pn, pc, cf, nf, rw)
+        np.testing.assert_array_equal(forced, [int(p[1]) for p in pts])
+        np.testing.assert_array_equal(m_row, [int(p[2]) for p in pts])
+
+
 def test_uniform_balls_recovery_improves_with_n(orc):
     """Theorem 1 / Figure 1: with s ~ 20 ln n / n the sampled graph recovers
     well-separated clusters once n is large enough; on three uniform balls the

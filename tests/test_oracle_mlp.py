@@ -1,5 +1,6 @@
 """Pins for the FP64 surrogate-network oracle (oracle/mlp.py): finite
-differences, closed forms of GELU / BCE / the first Adam step, and the ARI."""
+differences, closed forms of GELU / BCE / the first Adam step, three hand-worked Adam
+steps, and the ARI."""
 import math
 
 import numpy as np
@@ -75,6 +76,29 @@ def test_adam_first_step_is_lr_sign():
         np.testing.assert_allclose(step, 1e-3 * np.sign(g[k]) * (0.3 / (0.3 + 1e-8)),
                                    rtol=1e-9)
     assert st["t"] == 1
+
+
+def test_adam_three_hand_worked_steps():
+    """Three Adam steps with a different gradient each time, against the
+    hand-worked moments, bias corrections and updates of
+    tests/golden/adam_three_steps.txt (exact fractions)."""
+    from fractions import Fraction as Fr
+    kv = read_kv("adam_three_steps.txt")
+    lr, b1, b2 = (float(Fr(kv[k][0])) for k in ("lr", "beta1", "beta2"))
+    theta = np.array([float(Fr(v)) for v in kv["theta0"]])
+    st = {}
+    for t in (1, 2, 3):
+        row = [Fr(v) for v in kv[f"step{t}"]]
+        g, m, v, mhat, vhat = (np.array([float(a), float(b)]) for a, b in
+                               zip(row[0::2], row[1::2]))
+        q = mlp.adam_step({"w": theta}, {"w": g}, st, lr=lr, beta1=b1, beta2=b2, eps=0.0)
+        assert st["t"] == t
+        np.testing.assert_allclose(st["m_w"], m, rtol=1e-15, atol=0)
+        np.testing.assert_allclose(st["v_w"], v, rtol=1e-15, atol=0)
+        np.testing.assert_allclose(st["m_w"] / (1 - b1 ** t), mhat, rtol=1e-14)
+        np.testing.assert_allclose(st["v_w"] / (1 - b2 ** t), vhat, rtol=1e-14)
+        np.testing.assert_allclose(theta - q["w"], lr * mhat / np.sqrt(vhat), rtol=1e-13)
+        theta = q["w"]
 
 
 def test_training_reduces_loss():
