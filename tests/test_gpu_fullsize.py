@@ -59,6 +59,55 @@ def test_headline_config_n1M_d64(orc):
     assert st["clusters"] == r["clusters"] and st["noise"] == r["noise"]
 
 
+def _tiled_fullsize(orc, torch, sng, x, p, rows, tiles, min_pts):
+    """Build the graph and cluster in the L2-tiled form exactly as the bench
+    times it; sampled rows exact against the oracle, steps 3-5 exact on the
+    GPU's whole edge list, and the tiled stats as the bench reports them."""
+    n = x.shape[0]
+    m = p.draws(n)
+    xg = torch.from_numpy(x).cuda()
+    g = sng.build_graph(xg, p)
+    assert g["stats"]["map_tiles"] == tiles
+    assert _check_rows(orc, x, g, p, m, rows, BAND_F32) == 0
+    labels, core, st = sng.cluster(xg, p, want_core=True)
+    assert st["map_tiles"] == tiles
+    assert st["kept_edges"] == g["col"].numel()
+    r = _check_cc(orc, g, labels, core, min_pts)
+    assert st["clusters"] == r["clusters"] and st["noise"] == r["noise"]
+    return st
+
+
+def test_headline_config_tiled_as_benched(orc):
+    """The headline workload (n = 1,000,000 in d = 64, m = 1000, eps = 1%
+    distance quantile, MinPts = 10) in the launch configuration the bench
+    times: the L2-tiled gather with 6 x 6 tiles, two partner steps in
+    flight, 256-thread blocks, and one 16-byte chunk of each partner row
+    through the texture unit."""
+    torch, sng = need_gpu()
+    n, d = 1_000_000, 64
+    x = datagen.gaussian_mixture(n, d, 100, 0.02, seed=0)
+    eps = datagen.eps_quantile(x, 0.01, 1_000_000, seed=0)
+    p = sng.Params(eps=eps, min_pts=10, s=0.001, seed=0, flags=sng.SNG_FLAG_TILED,
+                   map_tile=6, map_unroll=2, map_block=256)
+    rows = np.sort(np.random.default_rng(3).choice(n, 3000, replace=False))
+    st = _tiled_fullsize(orc, torch, sng, x, p, rows, 6, 10)
+    assert st["map_tex"] == 1
+
+
+def test_fp32_embeddings_tiled_16x16(orc):
+    """n = 5,000,000 unit vectors in d = 128 (sigma = 0.0375, so that the graph
+    has edges), m = 1000, eps = 0.6, MinPts = 8, FP32 in the tiled form with
+    16 x 16 tiles (the autotuner's pick at this size)."""
+    torch, sng = need_gpu()
+    n, d = 5_000_000, 128
+    x = datagen.sphere_embeddings(n, d, 1000, 0.0375, seed=0)
+    p = sng.Params(eps=0.6, min_pts=8, s=0.0002, seed=0, flags=sng.SNG_FLAG_TILED,
+                   map_tile=16, map_unroll=2, map_block=256)
+    rows = np.sort(np.random.default_rng(4).choice(n, 600, replace=False))
+    st = _tiled_fullsize(orc, torch, sng, x, p, rows, 16, 8)
+    assert st["kept_edges"] > 1_000_000
+
+
 @pytest.mark.parametrize("sigma", [0.15, 0.0375])
 def test_bf16_config_n5M_d128(orc, sigma):
     """n = 5,000,000 unit vectors in d = 128 stored as BF16, s = 0.0002 (m =
