@@ -393,22 +393,27 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
                                  sng_stats *stats, void *stream);
 
 /*
- * Clustering that allocates no memory (the paper has no counterpart: this is
- * an interface for callers that cannot allocate device memory at call time,
- * e.g. a plugin whose host application reserved all device memory up front,
- * or a real-time loop that cannot afford cudaMalloc's device synchronisation
- * or its failure under memory pressure).  Same result as sng_cluster on the
- * same arguments (Algorithm 1), computed by the persistent kernel of the
- * batched form with all scratch in a fixed 16 MiB device array built into
- * the library (resident on every GPU that loads it, until exit).
- * x: device FP32, n x ld (row shapes of the batched form: d <= 64 with ld a
- * multiple of 4, or d <= 4).  labels: device int32[n].  Requires
- * n * (4 * ceil(m/32) + 10) bytes plus a few KiB of scratch to fit in 16 MiB,
- * otherwise SNG_EINVAL.  No cudaMalloc / cudaFree or other allocation.  The
- * first call on a device looks up the array's device address (call it once
- * before any stream capture).  All calls share the array: calls that overlap
- * on the GPU race and must be serialised by the caller.  Synchronises
- * `stream` (to read the status word and fill stats, which may be NULL).
+ * Clustering that allocates no memory.  The paper has no counterpart: this
+ * is an interface for callers that cannot allocate device memory when they
+ * cluster -- a plugin whose host application reserved all device memory up
+ * front, or a real-time loop that cannot afford cudaMalloc's implicit device
+ * synchronisation or its failure under memory pressure.  It gives the same
+ * labels and counts as sng_cluster on the same arguments, computed by the
+ * batched form's persistent kernel with all scratch in one fixed 16 MiB
+ * device array compiled into the library.
+ * x: device FP32, n x ld; d <= 64 with ld a multiple of 4 and 16-byte aligned
+ * rows, or d <= 4 with any ld.  labels: device int32[n] (caller-owned).
+ * Requires n * (4 * ceil(m/32) + 10) bytes plus a few KiB of scratch to fit
+ * in 16 MiB, otherwise SNG_EINVAL before any work.  Calls no cudaMalloc,
+ * cudaFree or allocating library routine.  The array belongs to this entry
+ * point's device code, which CUDA loads on a device the first time it is
+ * used there: the first call on each device therefore makes the driver
+ * reserve the 16 MiB (kept until the process exits) and looks up the
+ * array's device address; make that first call before reserving the rest of
+ * device memory and before any stream capture.  Every call shares the array
+ * and clears what must start at zero; calls that overlap on the GPU race and
+ * must be serialised by the caller.  Synchronises `stream` (to read the
+ * status word and fill stats, which may be NULL).
  */
 sng_status sng_cluster_noalloc(const float *x, const sng_params *params, int32_t *labels,
                                sng_stats *stats, void *stream);

@@ -11,9 +11,14 @@
 // with every byte of scratch taken from a fixed array compiled into this
 // library.  The caller still provides the points and the label array.
 //
-// The scratch array lives in device memory for as long as the library is
-// loaded (on every GPU the process uses), so it is kept modest: 16 MiB.  A
-// point set needs n * (4 * ceil(m / 32) + 10) bytes plus a few kilobytes;
+// The scratch array is part of this file's device code.  CUDA loads that code
+// on a device when it is first used there (the default lazy module loading),
+// which is during the first call of this entry point on that device: the
+// driver then reserves the 16 MiB array (and the kernel images) on the
+// device, once, and keeps them until the process exits.  That first call can
+// therefore fail for lack of device memory; callers that reserve all device
+// memory up front make one small call first.  Later calls allocate nothing.
+// A point set needs n * (4 * ceil(m / 32) + 10) bytes plus a few kilobytes;
 // larger requests are rejected with SNG_EINVAL.
 //
 // All calls share the one array.  Calls whose work overlaps on the GPU (on
@@ -120,8 +125,24 @@ sng_status sng_cluster_noalloc(const float *x, const sng_params *params, int32_t
                 "n = %lld with m = %lld needs %zu bytes of scratch; the no-allocation path "
                 "holds %zu (use sng_cluster)",
                 (long long)n, (long long)r.m, off, kNoAllocBytes);
+  // the persistent kernel's compiled row shapes: 16-byte rows of up to 16
+  // float4 chunks take one chunk per lane (4, 8 or 16 lanes per pair) unless
+  // the caller chose the lanes per pair; rows of at most four values (any
+  // vector width) take one lane per pair as validate() chose
   BatchMap map{r.map.vec, r.map.group, r.map.nch,
-               params->map_unroll > 0 ? params->map_unroll : 4};
+               params->map_unroll > 0 ? params->map_unroll : 4, 0};
+  const int chunks = (params->d + r.map.vec - 1) / r.map.vec;
+  if (params->map_group == 0 && r.map.vec == 4 && chunks > 1 && chunks <= 16) {
+    int g = 4;
+    while (g < chunks) g <<= 1;
+    map.group = g;
+    map.nch = 1;
+  }
+  // one float4 per row: one lane per source row (as the batched form does),
+  // unless one warp per row is asked for
+  if (map.vec == 4 && map.group == 1 && map.nch == 1 && (map.unroll == 2 || map.unroll == 4) &&
+      !(params->flags & SNG_FLAG_WARP_ROWS))
+    map.lanes = 1;
   int occ = 0;
   BatchArgs probe{};
   if (!launch_batched_kernel(map, probe, 0, block, nullptr, &occ))
