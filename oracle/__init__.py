@@ -37,23 +37,28 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sng_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_OMP_LIB_PATH = os.path.join(_OUT_DIR, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp_lib = None
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, openmp: bool = False) -> str:
     """Compile ``sng_oracle.c`` into ``oracle/_build/liboracle.so`` (gcc, FP64,
-    no contraction, no fast-math).  Rebuilds when the source is newer."""
+    no contraction, no fast-math), or with ``openmp`` the same source with
+    -fopenmp into ``liboracle_omp.so`` (the multi-core CPU baseline).
+    Rebuilds when the source is newer."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    path = _OMP_LIB_PATH if openmp else _LIB_PATH
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
+           "-shared"] + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class _Graph(ctypes.Structure):
@@ -62,12 +67,14 @@ class _Graph(ctypes.Structure):
                 ("col", ctypes.POINTER(ctypes.c_int32)), ("band_pairs", ctypes.c_int64)]
 
 
-def _load():
-    global _lib
+def _load(openmp: bool = False):
+    global _lib, _omp_lib
     with _lock:
-        if _lib is not None:
+        if openmp and _omp_lib is not None:
+            return _omp_lib
+        if not openmp and _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(build(openmp=openmp))
         P = ctypes.c_void_p
         i64, i32, u64, f32, f64 = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                    ctypes.c_float, ctypes.c_double)
@@ -116,7 +123,15 @@ def _load():
         lib.orc_cluster_metric.restype = i32
         lib.orc_dbscan_bruteforce.argtypes = [i64, i32, i64, P, f32, i32, P, P]
         lib.orc_dbscan_bruteforce.restype = i32
-        _lib = lib
+        lib.orc_build_rows_blocks.argtypes = [i64, i32, i64, P, f32, u64, i64, i32, f64, i64,
+                                              i64, ctypes.POINTER(_Graph)]
+        lib.orc_build_rows_blocks.restype = i32
+        lib.orc_threads.argtypes = []
+        lib.orc_threads.restype = i32
+        if openmp:
+            _omp_lib = lib
+        else:
+            _lib = lib
         return lib
 
 
@@ -212,6 +227,35 @@ def build_rows(x, eps: float, seed: int, m: int, sample_all: bool = False,
     finally:
         lib.orc_graph_free(ctypes.byref(g))
     return row_ptr, col, band_pairs, bp
+
+
+def build_rows_blocks(x, eps: float, seed: int, m: int, block: int = 4096,
+                      openmp: bool = False, n_rows: int | None = None
+                      ) -> tuple[np.ndarray, np.ndarray, int]:
+    """Step 2 over the source rows 0..n_rows-1 (default all) in blocks of
+    consecutive rows joined in order (the same graph as ``build_rows``); with
+    ``openmp`` the blocks run on all host cores (the liboracle_omp.so build of
+    the same source).  Returns ``(row_ptr, col, band_pairs)``."""
+    x, n, d, ld = _f32_rows(x)
+    nr = n if n_rows is None else int(n_rows)
+    lib = _load(openmp)
+    g = _Graph()
+    if lib.orc_build_rows_blocks(n, d, ld, _ptr(x), ctypes.c_float(eps), seed & (2**64 - 1), m,
+                                 0, 1e-5, block, nr, ctypes.byref(g)) != 0:
+        raise ValueError("orc_build_rows_blocks failed (bad arguments or out of memory)")
+    try:
+        row_ptr = np.ctypeslib.as_array(g.row_ptr, shape=(nr + 1,)).copy()
+        ne = int(g.num_edges)
+        col = (np.ctypeslib.as_array(g.col, shape=(ne,)).copy() if ne
+               else np.zeros(0, dtype=np.int32))
+        return row_ptr, col, int(g.band_pairs)
+    finally:
+        lib.orc_graph_free(ctypes.byref(g))
+
+
+def threads(openmp: bool = True) -> int:
+    """Host threads the OpenMP build uses (1 for the plain build)."""
+    return int(_load(openmp).orc_threads())
 
 
 def degrees(n: int, row_ptr, col, mode: int = 0) -> np.ndarray:

@@ -239,6 +239,74 @@ int32_t orc_build_rows_metric(int64_t n, int32_t d, int64_t ld, const float *x, 
     return 0;
 }
 
+/*
+ * Step 2 over the source rows 0..n_rows-1 (n_rows = n: all of them), cut into
+ * blocks of `block` consecutive rows that orc_build_rows_metric builds one by
+ * one and that are then joined in row order, so the graph equals the
+ * one-call result row for row.  Built with
+ * OpenMP (-fopenmp) the blocks are shared among the host cores: this is the
+ * multi-core timing of the CPU baseline.  Without OpenMP the pragma is
+ * ignored and the blocks run in order.  No band points (NULL) are recorded.
+ */
+int32_t orc_build_rows_blocks(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
+                              uint64_t seed, int64_t m, int32_t sample_all, double band_rel,
+                              int64_t block, int64_t n_rows, orc_graph *out)
+{
+    if (n < 2 || block < 1 || n_rows < 1 || n_rows > n || !out) return -1;
+    int64_t nb = (n_rows + block - 1) / block;
+    orc_graph *part = (orc_graph *)calloc((size_t)nb, sizeof(orc_graph));
+    if (!part) return -1;
+    int failed = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : failed)
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t lo = b * block, hi = lo + block < n_rows ? lo + block : n_rows;
+        int64_t *rows = (int64_t *)malloc((size_t)(hi - lo) * sizeof(int64_t));
+        if (!rows) { failed |= 1; continue; }
+        for (int64_t r = lo; r < hi; ++r) rows[r - lo] = r;
+        failed |= orc_build_rows_metric(n, d, ld, x, eps, seed, m, sample_all, band_rel, rows,
+                                        hi - lo, &part[b], NULL, NULL, 0) != 0;
+        free(rows);
+    }
+    int64_t e = 0, bp = 0;
+    for (int64_t b = 0; b < nb && !failed; ++b) { e += part[b].num_edges; bp += part[b].band_pairs; }
+    int64_t *row_ptr = failed ? NULL : (int64_t *)malloc((size_t)(n_rows + 1) * sizeof(int64_t));
+    int32_t *col = failed ? NULL : (int32_t *)malloc((size_t)(e > 0 ? e : 1) * sizeof(int32_t));
+    if (!row_ptr || !col) failed = 1;
+    if (!failed) {
+        int64_t at = 0;
+        row_ptr[0] = 0;
+        for (int64_t b = 0; b < nb; ++b) {
+            int64_t lo = b * block;
+            for (int64_t r = 0; r < part[b].n_rows; ++r) row_ptr[lo + r + 1] = at + part[b].row_ptr[r + 1];
+            if (part[b].num_edges)
+                memcpy(col + at, part[b].col, (size_t)part[b].num_edges * sizeof(int32_t));
+            at += part[b].num_edges;
+        }
+    }
+    for (int64_t b = 0; b < nb; ++b) orc_graph_free(&part[b]);
+    free(part);
+    if (failed) { free(row_ptr); free(col); return -1; }
+    out->n_rows = n_rows;
+    out->num_edges = e;
+    out->row_ptr = row_ptr;
+    out->col = col;
+    out->band_pairs = bp;
+    return 0;
+}
+
+/* Host threads the blocks above may use (1 without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int32_t orc_threads(void)
+{
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------ graph processing */
 
 /* Degree of every vertex of G (Algorithm 1, step 3).  mode 0: undirected

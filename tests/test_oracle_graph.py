@@ -318,6 +318,26 @@ def test_gated_weighted_degrees(orc):
     np.testing.assert_array_equal(r["deg"], [32, 64, 0, 32])
 
 
+@pytest.mark.parametrize("openmp", [False, True])
+@pytest.mark.parametrize("block", [1, 97, 5000, 100_000])
+def test_row_blocks_equal_one_call(orc, openmp, block):
+    """The CPU baseline's row-block driver (plain and OpenMP builds of the same
+    source) gives exactly the one-call step-2 graph."""
+    n, d, m = 5000, 8, 40
+    x = datagen.random_points(n, d, seed=block)
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    rp, col, bp, _ = orc.build_rows(x, eps, 11, m)
+    rp2, col2, bp2 = orc.build_rows_blocks(x, eps, 11, m, block=block, openmp=openmp)
+    np.testing.assert_array_equal(rp2, rp)
+    np.testing.assert_array_equal(col2, col)
+    assert bp2 == bp
+    assert orc.threads(openmp) >= 1
+    # a leading range of rows: the first rows of the same graph
+    rp3, col3, _ = orc.build_rows_blocks(x, eps, 11, m, block=block, openmp=openmp, n_rows=1234)
+    np.testing.assert_array_equal(rp3, rp[:1235])
+    np.testing.assert_array_equal(col3, col[:rp[1234]])
+
+
 def test_gate_rule_hand_cases(orc):
     """The gate's rule (thresholds, draw budgets, degree weights) against the
     hand-worked rows of tests/golden/gate_rule.txt, one point at a time and
