@@ -108,6 +108,19 @@ typedef int32_t sng_status;
                                 SNG_FLAG_NO_SYNC, no device memory for the
                                 buckets, or a bucket past its capacity (mean +
                                 8 standard deviations)                         */
+#define SNG_FLAG_SCREEN16 32u /* FP32 points, Euclidean form: the gather tests pairs
+                                on a BF16 copy of the points made inside the call
+                                (2 bytes per value of scratch, plus 4 per point),
+                                and decides a pair from it only where a bound
+                                on the copy's rounding (2^-8 of the two rows'
+                                norms) cannot change the decision; every other
+                                pair is summed again from the FP32 points and
+                                decided as without the flag.  Results are
+                                identical; stats report map_screen and
+                                screen_pairs.  Applies to the direct and the
+                                tiled gather; ignored for BF16 points, other
+                                metrics, one lane per row, map_passes > 1 and
+                                SNG_FLAG_NO_SYNC                                */
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The
                                 edge arrays are sized for all n*m draws (8 bytes
@@ -183,6 +196,11 @@ typedef struct {
                              when it ran; 0 = the direct gather             */
     int32_t map_tex;      /* tiled gather: 16-byte chunks of each partner row
                              read through the texture unit (0 or 1)        */
+    int32_t map_screen;   /* 1: pairs were tested on the BF16 copy
+                             (SNG_FLAG_SCREEN16); map_vec .. map_unroll then
+                             describe the mapping over that copy            */
+    int64_t screen_pairs; /* SNG_FLAG_SCREEN16: pairs the BF16 screen left
+                             open, summed again from the FP32 points       */
 } sng_stats;
 
 typedef struct {
@@ -426,6 +444,17 @@ sng_status sng_cluster_noalloc(const float *x, const sng_params *params, int32_t
  * call would fail with SNG_EINVAL).
  */
 sng_status sng_gather_mapping(const void *x, const sng_params *params, int32_t *mapping);
+
+/*
+ * Measurement aid (no counterpart in the paper): the rate at which the SMs of
+ * the current device read from L2.  A device buffer of `bytes` (1 MiB .. 1
+ * GiB; pick one well below the L2 size) is allocated, filled, read twice to
+ * warm L2, then read `passes` times with 16-byte loads that bypass L1, by
+ * every SM; *gbs receives the bytes read per second / 1e9 between two CUDA
+ * events.  The roofline of the L2-resident gather forms.  Allocates and
+ * frees its buffer; synchronises `stream`.
+ */
+sng_status sng_measure_l2_read(int64_t bytes, int32_t passes, double *gbs, void *stream);
 
 /* Number of kernels this library has launched in this process. */
 int64_t sng_launch_count(void);

@@ -34,6 +34,7 @@ SNG_FLAG_PREFETCH = 2
 SNG_FLAG_NO_SYNC = 4
 SNG_FLAG_WARP_ROWS = 8
 SNG_FLAG_TILED = 16
+SNG_FLAG_SCREEN16 = 32
 
 PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total", "gate")
 
@@ -76,7 +77,8 @@ class sng_stats(ctypes.Structure):
                 ("ms", ctypes.c_float * 8), ("map_vec", ctypes.c_int32),
                 ("map_group", ctypes.c_int32), ("map_nch", ctypes.c_int32),
                 ("map_unroll", ctypes.c_int32), ("map_tiles", ctypes.c_int32),
-                ("map_tex", ctypes.c_int32)]
+                ("map_tex", ctypes.c_int32), ("map_screen", ctypes.c_int32),
+                ("screen_pairs", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "ms"}
@@ -145,6 +147,8 @@ SIGNATURES = {
     "sng_cluster_noalloc": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P,
                                              ctypes.POINTER(sng_stats), _P]),
     "sng_gather_mapping": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P]),
+    "sng_measure_l2_read": (ctypes.c_int32, [ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_double), _P]),
     "sng_launch_count": (ctypes.c_int64, []),
     "sng_last_error": (ctypes.c_char_p, []),
     "sng_strerror": (ctypes.c_char_p, [ctypes.c_int32]),
@@ -419,6 +423,15 @@ def ami(a, b, average: str = "arithmetic", stream=None) -> dict:
     _check(lib().sng_ami(a.data_ptr(), b.data_ptr(), a.numel(), AMI_AVERAGES[average],
                          ctypes.byref(t), _stream_ptr(stream)))
     return {k: getattr(t, k) for k, _ in t._fields_}
+
+
+def measure_l2_read(bytes_: int = 48 << 20, passes: int = 200, stream=None) -> float:
+    """GB/s the SMs read from an L2-resident buffer (the library's own probe
+    kernel; see sng_measure_l2_read)."""
+    v = ctypes.c_double()
+    _check(lib().sng_measure_l2_read(int(bytes_), int(passes), ctypes.byref(v),
+                                     _stream_ptr(stream)))
+    return float(v.value)
 
 
 def ari(a, b, stream=None) -> float:

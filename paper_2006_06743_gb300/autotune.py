@@ -3,8 +3,9 @@
 The gather's cost depends on how a warp is split over pairs (lanes per pair),
 how many partner rows each warp keeps in flight, the block size and, for
 point sets larger than L2, how many L2-resident slices of the partner range
-the launch is split into, or whether the L2-tiled form (draws bucketed by
-source and partner slice, then tested tile by tile) beats the direct gather.
+the launch is split into, whether the L2-tiled form (draws bucketed by
+source and partner slice, then tested tile by tile) beats the direct gather,
+and, for FP32 points, whether testing pairs on a certified BF16 copy pays.
 The library picks a rule-of-thumb mapping; this
 module times a small set of candidates on the caller's own data, through the
 library's per-phase CUDA-event timers, and caches the fastest per
@@ -18,7 +19,8 @@ import os
 import statistics
 import time
 
-from . import SNG_FLAG_PREFETCH, SNG_FLAG_TILED, SNG_FLAG_TIMING, Params, SngError, cluster
+from . import (SNG_FLAG_PREFETCH, SNG_FLAG_SCREEN16, SNG_FLAG_TILED, SNG_FLAG_TIMING, Params,
+               SngError, cluster)
 
 CACHE_ENV = "SNG_AUTOTUNE_CACHE"
 
@@ -65,12 +67,34 @@ def candidates(x, p: Params) -> list[dict]:
         base = max(2, int(math.ceil(x_bytes / (48 << 20))))
         passes += sorted({2, base, base + 2, 2 * base} - {1})
     out = []
+    free = None
+    # the certified BF16 screen of FP32 points (Euclidean, hashed draws): the
+    # gather reads a BF16 copy (2 bytes per value of scratch), directly or
+    # tiled with the slice count of the copy's size
+    if esize == 4 and not p.metric and p.sample_mode == 0:
+        free = torch.cuda.mem_get_info(x.device)[0] if x.is_cuda else 0
+        gb = _default_group(d, 8)
+        ldb = -(-d // 8) * 8
+        xb_bytes = n * ldb * 2
+        if xb_bytes < 0.25 * free:
+            for g in sorted({max(1, gb // 2), gb}):
+                for u in (2, 4):
+                    out.append(dict(map_group=g, map_unroll=u, map_block=256, map_passes=0,
+                                    prefetch=False, screen=True))
+        if xb_bytes > (48 << 20) and 8.4 * n * p.draws(n) + xb_bytes < 0.5 * free:
+            kb = min(32, max(2, -(-2 * xb_bytes // (88 << 20))))
+            for k in sorted({kb, min(32, kb + 1)}):
+                for g in sorted({0, gb}):
+                    for u in (2, 4):
+                        out.append(dict(map_group=g, map_unroll=u, map_block=256, map_passes=0,
+                                        prefetch=False, tiled=True, map_tile=k, screen=True))
     # the L2-tiled form (Euclidean, hashed draws): its slice count from the
     # library's rule (two slices in about 88 MiB of L2) and one finer; it
     # needs ~8.4 bytes of scratch per draw, so it is tried only where that
     # leaves half the free memory
     if x_bytes > (48 << 20) and not p.metric and p.sample_mode == 0:
-        free = torch.cuda.mem_get_info(x.device)[0] if x.is_cuda else 0
+        if free is None:
+            free = torch.cuda.mem_get_info(x.device)[0] if x.is_cuda else 0
         if 8.4 * n * p.draws(n) < 0.5 * free:
             k0 = min(32, max(2, -(-2 * x_bytes // (88 << 20))))
             for k in sorted({0, max(2, k0 // 2), min(32, k0 + 2)}):
@@ -91,9 +115,12 @@ def _params_for(base: dict, cand: dict) -> Params:
     c = dict(cand)
     pf = c.pop("prefetch", False)
     tiled = c.pop("tiled", False)
-    flags = base.get("flags", 0) & ~(SNG_FLAG_PREFETCH | SNG_FLAG_TILED)
+    screen = c.pop("screen", False)
+    flags = base.get("flags", 0) & ~(SNG_FLAG_PREFETCH | SNG_FLAG_TILED | SNG_FLAG_SCREEN16)
     if pf:
         flags |= SNG_FLAG_PREFETCH
+    if screen:
+        flags |= SNG_FLAG_SCREEN16
     if tiled:
         flags |= SNG_FLAG_TILED
     else:

@@ -17,6 +17,7 @@
 #include "api_common.cuh"
 #include "gather.cuh"
 #include "graph.cuh"
+#include "screen.cuh"
 #include "tiled.cuh"
 
 namespace sng {
@@ -118,6 +119,31 @@ sng_status Scratch::alloc(void **out, size_t bytes, const char *what) {
 // ------------------------------------------------------------ validation
 
 static int64_t ceil_s_n(double s, int64_t n) { return (int64_t)std::ceil(s * (double)n); }
+
+// Smallest float not below v.
+static float round_up_f(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+// FP32 guard band around eps^2 for a squared distance summed with `fmas`
+// fused multiply-adds per lane and `levels` shuffle levels: twice a bound on
+// the relative error (one rounding for each difference, one per fused
+// multiply-add, one per level, plus slack) and the reported band; the FP32
+// thresholds are rounded outwards.
+static void fp32_guard(double eps2, float band_rel, int fmas, int levels, float *lo_thr,
+                       float *hi_thr) {
+  const double u = std::ldexp(1.0, -24);
+  const double delta = 2.0 * (double)(fmas + levels + 3) * u + std::ldexp(1.0, -22);
+  const double screen = (double)band_rel + delta;
+  const double lo = eps2 * (1.0 - screen), hi = eps2 * (1.0 + screen);
+  float lof = (float)lo, hif = (float)hi;
+  if ((double)lof > lo) lof = std::nextafter(lof, 0.f);
+  if ((double)hif < hi) hif = std::nextafter(hif, INFINITY);
+  *lo_thr = lof;
+  *hi_thr = hif;
+}
 
 sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   if (!p) return fail(SNG_EINVAL, "params is NULL");
@@ -252,14 +278,7 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
   int lg = 0;
   while ((1 << lg) < group) ++lg;
   const double u = std::ldexp(1.0, -24);
-  const double delta = 2.0 * (double)(nch * vec + lg + 3) * u + std::ldexp(1.0, -22);
-  const double screen = (double)r->band_rel + delta;
-  const double lo = r->eps2 * (1.0 - screen), hi = r->eps2 * (1.0 + screen);
-  float lof = (float)lo, hif = (float)hi;
-  if ((double)lof > lo) lof = std::nextafter(lof, 0.f);
-  if ((double)hif < hi) hif = std::nextafter(hif, INFINITY);
-  r->lo_thr = lof;
-  r->hi_thr = hif;
+  fp32_guard(r->eps2, r->band_rel, nch * vec, lg, &r->lo_thr, &r->hi_thr);
 
   // similarity form: |dot32 - dot| <= (K + 1) u sum|a_k b_k| <= (K + 1) u
   // |a| |b| with K roundings per term (nch*vec fused multiply-adds, log2
@@ -318,6 +337,12 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
   g->sim_c1 = r.sim_c1;
   g->sim_c2 = r.sim_c2;
   g->band_f = r.band_f;
+  g->screen = 0;
+  g->screen_vec4 = 0;
+  g->screen_lo_eps = g->screen_hi_eps = 0.f;
+  g->screen_u = g->screen_abs = g->screen_g = 0.f;
+  g->nrm = nullptr;
+  g->nrm_max = nullptr;
   // L2 prefetch of partner rows when rows start on 16 bytes (16-byte vectors)
   const int esize = p->dtype == SNG_F32 ? 4 : 2;
   g->pf_bytes = 0;
@@ -363,7 +388,8 @@ sng_status simple_degrees(int64_t n, const int32_t *src, const int32_t *col, int
 // buckets, then test tile by tile.  *done = false when the form does not
 // apply or a bucket overflowed (the caller runs the direct gather).
 static sng_status run_tiled(const sng_params *p, const Resolved &r, Scratch &s,
-                            const GatherArgs &ga, GraphBufs *gb, bool *done) {
+                            const GatherArgs &ga, GraphBufs *gb, bool *done,
+                            const Shadow *sh) {
   *done = false;
   cudaStream_t st = s.stream;
   const int64_t n = r.n;
@@ -448,6 +474,8 @@ static sng_status run_tiled(const sng_params *p, const Resolved &r, Scratch &s,
       }
     }
   }
+  // the BF16 screen bounds each tile's partners by its slice's largest norm
+  if (sh && (rc = shadow_slice_max(*sh, n, slice, k, st))) return rc;
   launch_tile_partition(ga, t, device_sms() * 16, st);
   note_launch();
   // a bucket overflow (far outside the binomial spread) falls back
@@ -502,7 +530,6 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   ga.deg = gb->deg;
   ga.band_flag = gb->band_flag;
   ga.counters = gb->counters;
-  const int grid = gather_grid(p->dtype, r.map, r.row_end - r.row_begin);
   if (r.map.passes > 1 || r.row_begin > 0 || r.row_end < n) {
     // rows outside the processed range (or filled slice by slice) start empty
     cudaMemsetAsync(gb->bitmask, 0, (size_t)n * r.W * 4, st);
@@ -510,15 +537,80 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   }
   tm->mark(st, 0);
   NvtxRange nvtx_graph("step 2: sampled graph");
+  // The BF16 screen (SNG_FLAG_SCREEN16): the gather runs over a BF16 copy
+  // of the FP32 points with the BF16 mapping; the FP32 points stay the
+  // source of every decision the screen leaves open.
+  const sng_params *pg = p;   // parameters the gather's mapping follows
+  const Resolved *rg = &r;
+  sng_params pb;
+  Resolved rb;
+  Shadow sh;
+  const bool screen = (p->flags & SNG_FLAG_SCREEN16) && p->dtype == SNG_F32 &&
+                      p->metric == SNG_METRIC_L2 && r.map.passes <= 1 && !r.map.lanes &&
+                      !(p->flags & SNG_FLAG_NO_SYNC);
+  if (screen) {
+    wait_inputs(st);
+    if ((rc = make_shadow(static_cast<const float *>(x), p->ld, p->d, n, s, &sh))) return rc;
+    pb = *p;
+    pb.dtype = SNG_BF16;
+    pb.ld = (int32_t)sh.ldb;
+    pb.x_f32_master = static_cast<const float *>(x);
+    pb.band_rel = r.band_rel;
+    if ((rc = validate(sh.xb, &pb, &rb))) return rc;
+    rb.map.lanes = 0;
+    fill_gather_args(sh.xb, &pb, rb, &ga);
+    ga.m_row = m_row;
+    ga.w_row = w_row;
+    ga.bitmask = gb->bitmask;
+    ga.out_cnt = gb->out_cnt;
+    ga.deg = gb->deg;
+    ga.band_flag = gb->band_flag;
+    ga.counters = gb->counters;
+    ga.xm = static_cast<const float *>(x);
+    ga.ldm = p->ld;
+    ga.eps2 = r.eps2;
+    ga.band = r.band;
+    ga.screen = 1;
+    ga.screen_vec4 = (p->d % 4 == 0) && (p->ld % 4 == 0) && ((uintptr_t)x % 16 == 0);
+    {
+      float lo_e = (float)((double)p->eps * std::sqrt(1.0 - (double)r.band_rel));
+      if ((double)lo_e > (double)p->eps * std::sqrt(1.0 - (double)r.band_rel))
+        lo_e = std::nextafter(lo_e, 0.f);
+      ga.screen_lo_eps = lo_e;
+      ga.screen_hi_eps = round_up_f((double)p->eps * std::sqrt(1.0 + (double)r.band_rel));
+    }
+    ga.nrm = sh.nrm;
+    ga.nrm_max = sh.nmax;
+    // the FP32 sum over the BF16 values: one rounding per difference, one
+    // per fused multiply-add in a lane, one per shuffle level (as the
+    // plain guard band); g adds 2^-20 for the rounding of the thresholds
+    // themselves and of the FP64 reference decision
+    int lg = 0;
+    while ((1 << lg) < rb.map.group) ++lg;
+    const double u = std::ldexp(1.0, -24);
+    const double delta = 2.0 * (double)(rb.map.nch * rb.map.vec + lg + 3) * u + std::ldexp(1.0, -22);
+    ga.screen_g = round_up_f(delta + std::ldexp(1.0, -20));
+    ga.screen_u = round_up_f(std::ldexp(1.0, -8) * (1.0 + std::ldexp(1.0, -20)));
+    ga.screen_abs = std::ldexp(1.0f, -60);
+    // open pairs are summed in order with one fused multiply-add per element
+    fp32_guard(r.eps2, r.band_rel, p->d, 0, &ga.lo_thr, &ga.hi_thr);
+    pg = &pb;
+    rg = &rb;
+  }
+  const int grid = gather_grid(pg->dtype, rg->map, r.row_end - r.row_begin);
   bool tiled = false;
-  if ((p->flags & SNG_FLAG_TILED) && (rc = run_tiled(p, r, s, ga, gb, &tiled))) return rc;
+  if ((p->flags & SNG_FLAG_TILED) &&
+      (rc = run_tiled(pg, *rg, s, ga, gb, &tiled, screen ? &sh : nullptr)))
+    return rc;
+  gb->screened = screen;
+  gb->map = rg->map;
   if (tiled) {
     // done by the tiled form
-  } else if (r.map.passes <= 1) {
+  } else if (rg->map.passes <= 1) {
     wait_inputs(st);
-    if (!launch_gather(p->dtype, r.map, ga, grid, st))
+    if (!launch_gather(pg->dtype, rg->map, ga, grid, st))
       return fail(SNG_EINVAL, "no compiled gather for vec=%d group=%d nch=%d unroll=%d",
-                  r.map.vec, r.map.group, r.map.nch, r.map.unroll);
+                  rg->map.vec, rg->map.group, rg->map.nch, rg->map.unroll);
     note_launch();
   } else {
     // slices of the partner range, each small enough to stay in L2
@@ -602,6 +694,7 @@ sng_status read_stats(const unsigned long long *counters, const Resolved &r, sng
     stats->clusters = (int64_t)c[kCntClusters];
     stats->noise = (int64_t)c[kCntNoise];
     stats->recheck_pairs = (int64_t)c[kCntRecheck];
+    stats->screen_pairs = (int64_t)c[kCntScreen];
     if (tm) tm->fill(stats->ms);
     stats->map_vec = r.map.vec;
     stats->map_group = r.map.group;
@@ -612,6 +705,19 @@ sng_status read_stats(const unsigned long long *counters, const Resolved &r, sng
     return fail(SNG_ETIMEOUT, "a bounded device loop gave up (status 0x%x)", status);
   if (status & kErrIndex) return fail(SNG_EINTERNAL, "device index check failed (0x%x)", status);
   return SNG_OK;
+}
+
+void note_mapping(const GraphBufs &gb, sng_stats *stats) {
+  if (!stats) return;
+  stats->map_tiles = gb.tiles;
+  stats->map_tex = gb.tex_chunks;
+  stats->map_screen = gb.screened ? 1 : 0;
+  if (gb.screened) {
+    stats->map_vec = gb.map.vec;
+    stats->map_group = gb.map.group;
+    stats->map_nch = gb.map.nch;
+    stats->map_unroll = gb.map.unroll;
+  }
 }
 
 // ----------------------------------------------------------------- timer
@@ -787,10 +893,7 @@ sng_status sng_cluster(const void *x, const sng_params *params, int32_t *labels,
     return SNG_OK;
   }
   rc = read_stats(gb.counters, r, stats, st, &tm);
-  if (stats) {
-    stats->map_tiles = gb.tiles;
-    stats->map_tex = gb.tex_chunks;
-  }
+  note_mapping(gb, stats);
   s.release();
   return rc;
 }
@@ -951,10 +1054,7 @@ sng_status sng_build_graph(const void *x, const sng_params *params, sng_graph *o
   CoreArgs ca{r.n, params->min_pts, gb.deg, nullptr, core, parent, labels};
   launch_core_init(ca, device_sms(), st);
   rc = read_stats(gb.counters, r, stats, st, &tm);
-  if (stats) {
-    stats->map_tiles = gb.tiles;
-    stats->map_tex = gb.tex_chunks;
-  }
+  note_mapping(gb, stats);
   if (rc) {
     free_all();
     return rc;

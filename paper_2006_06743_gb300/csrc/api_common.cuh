@@ -78,7 +78,12 @@ struct GraphBufs {
   bool col_owned_by_caller = false;  // true: col from cudaMalloc, not scratch
   int tiles = 0;             // slices per axis of the tiled gather; 0 = direct
   int tex_chunks = 0;        // tiled gather: partner-row chunks read as texture
+  bool screened = false;     // pairs tested on the BF16 copy (SNG_FLAG_SCREEN16)
+  GatherMap map{};           // the mapping the gather ran with
 };
+
+// The gather's form (tiles, texture chunk, screen and its mapping) into stats.
+void note_mapping(const GraphBufs &gb, sng_stats *stats);
 
 sng_status fail(sng_status st, const char *fmt, ...);
 sng_status cuda_fail(cudaError_t e, const char *what);

@@ -152,6 +152,9 @@ __global__ void __launch_bounds__(256, LANES ? 4 : 1) batched_kernel(BatchArgs a
     g.m_row = nullptr;
     g.w_row = nullptr;
     g.pf_bytes = 0;
+    g.screen = 0;
+    g.nrm = nullptr;
+    g.nrm_max = nullptr;
     g.bitmask = a.bitmask + c.bm_off;
     g.out_cnt = nullptr;
     g.deg = a.deg + c.off;

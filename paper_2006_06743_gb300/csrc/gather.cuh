@@ -31,6 +31,8 @@
 // huge or non-finite rows) certify nothing.
 #pragma once
 
+#include <type_traits>
+
 #include "sng_internal.cuh"
 
 namespace sng {
@@ -61,6 +63,21 @@ struct GatherArgs {
                           // (both ends); NULL = weight 1
   int32_t pf_bytes;       // > 0: bulk-prefetch this many bytes of each partner
                           // row into L2 one stage ahead (16-byte rows only)
+  // BF16 screen of FP32 points (screen = 1): x holds a BF16 copy of the
+  // FP32 points xm.  A pair whose FP32 sum over the BF16 values lies below
+  // keep_thr or above drop_thr (per-row thresholds from the rows' norm
+  // bounds, screen_thresholds) is decided by it; any other pair is summed
+  // again from xm in order, one lane, and decided by lo_thr / hi_thr (set for
+  // that sequential sum) and the FP64 recheck, exactly as without the screen.
+  int32_t screen;
+  int32_t screen_vec4;    // xm rows load as float4 (d and ldm multiples of 4)
+  float screen_lo_eps;    // eps sqrt(1 - band_rel), rounded down
+  float screen_hi_eps;    // eps sqrt(1 + band_rel), rounded up
+  float screen_u;         // BF16 rounding bound per unit of norm (rounded up)
+  float screen_abs;       // absolute slack: values below BF16's normal range
+  float screen_g;         // relative bound of the FP32 sum, plus margins
+  const float *nrm;       // per-row upper bounds of |x_i| (FP32 points)
+  const float *nrm_max;   // [0] over all rows; [1 + s] over partner slice s
   uint32_t *bitmask;      // n x W
   int32_t *out_cnt;       // n, nullable
   int32_t *deg;           // n (zeroed before launch in multigraph mode)
@@ -103,6 +120,59 @@ __device__ __forceinline__ bool recheck_pair(const GatherArgs &a, int32_t i, int
   return s <= a.eps2;
 }
 
+// Keep / drop thresholds of the BF16 screen for source row norm bound nrm_i
+// against partner rows of norm bound at most nrm_p.  With a' = bf16(a) (round
+// to nearest: |a'_k - a_k| <= 2^-8 |a_k| in the normal range, and at most
+// 2^-134 below it) the triangle inequality gives
+// | |a - b| - |a' - b'| | <= |a - a'| + |b - b'| <= eta = 2^-8 (|a| + |b|) +
+// slack.  The kernel's FP32 sum s of (a'_k - b'_k)^2 is within a relative
+// delta of |a' - b'|^2, so s <= (eps - eta)^2 (1 - g) proves |a - b| <= eps
+// (the pair is kept) and s > (eps + eta)^2 (1 + g) proves |a - b| > eps
+// (dropped), with g = delta plus margins for the rounding of these
+// thresholds and of the FP64 reference decision.  eps is taken as
+// eps sqrt(1 -/+ band_rel) on the two sides, so that no pair of the reported
+// band is decided here (those are all rechecked and counted as without the
+// screen).  NaN and infinite bounds certify nothing.
+__device__ __forceinline__ void screen_thresholds(const GatherArgs &a, float nrm_i, float nrm_p,
+                                                  float &keep_thr, float &drop_thr) {
+  const float eta = fmaf(a.screen_u, nrm_i + nrm_p, a.screen_abs);
+  const float lo = a.screen_lo_eps - eta;
+  const float hi = a.screen_hi_eps + eta;
+  keep_thr = lo > 0x1p-10f * a.screen_lo_eps ? (lo * lo) * (1.f - a.screen_g) : -1.f;
+  drop_thr = (hi * hi) * (1.f + a.screen_g);
+}
+
+// A pair the BF16 screen left open: the FP32 squared distance of the FP32
+// rows, summed in order with one fused multiply-add per element (the bound
+// behind lo_thr / hi_thr), then the FP64 recheck inside the guard band --
+// the decision of the plain FP32 path, so of the FP64 oracle.
+static __device__ __noinline__ bool screen_pair(const GatherArgs &a, int32_t i, int32_t p) {
+  const float *xa = a.xm + (int64_t)i * a.ldm, *xb = a.xm + (int64_t)p * a.ldm;
+  float acc = 0.f;
+  if (a.screen_vec4) {
+    for (int k = 0; k < a.d; k += 4) {
+      const float4 u = __ldg(reinterpret_cast<const float4 *>(xa + k));
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(xb + k));
+      float t = u.x - v.x;
+      acc = fmaf(t, t, acc);
+      t = u.y - v.y;
+      acc = fmaf(t, t, acc);
+      t = u.z - v.z;
+      acc = fmaf(t, t, acc);
+      t = u.w - v.w;
+      acc = fmaf(t, t, acc);
+    }
+  } else {
+    for (int k = 0; k < a.d; ++k) {
+      const float t = __ldg(xa + k) - __ldg(xb + k);
+      acc = fmaf(t, t, acc);
+    }
+  }
+  if (acc < a.lo_thr) return true;
+  if (acc > a.hi_thr) return false;
+  return recheck_pair<float>(a, i, p);
+}
+
 // Bulk prefetch of the start of partner row p into L2 (the copy engine
 // fetches it while the warp works on the current stage).  Only for rows that
 // start on 16 bytes (16-byte vector mappings); the size is a multiple of 16.
@@ -136,7 +206,7 @@ __device__ __forceinline__ void stage_partners(const GatherArgs &a, int32_t i, u
 // being tested and the next one, hashed (and prefetched) one stage ahead.
 template <typename T, int VEC, int G, int NCH, int U, bool SIM = false, bool FULL = false>
 __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_t mi,
-                                          int32_t *sp, int lane) {
+                                          int32_t *sp, int lane, unsigned int *screen_cnt = nullptr) {
   constexpr int R = 32 / G;      // pairs per warp step
   constexpr int S = 32 * U;      // draws per stage
   constexpr int STEPS = S / R;   // warp steps per stage
@@ -146,6 +216,11 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
   const int d = a.d;
   const uint64_t key = row_key(a.seed, i);
   const int32_t wi = a.w_row ? a.w_row[i] : 1;
+  constexpr bool kScreenable = std::is_same<T, uint16_t>::value && !SIM;
+  float keep_thr = 0.f, drop_thr = 0.f;
+  if constexpr (kScreenable) {
+    if (a.screen) screen_thresholds(a, a.nrm[i], a.nrm_max[0], keep_thr, drop_thr);
+  }
 
   // this lane's slice of row i; elements at or past d read as zero
   float xi[NCH][VEC];
@@ -291,10 +366,24 @@ __device__ __forceinline__ int gather_row(const GatherArgs &a, int32_t i, int32_
               keep = recheck_sim(a, i, p);
             }
           } else {
-            if (acc < a.lo_thr) {
-              keep = true;
-            } else if (!(acc > a.hi_thr)) {
-              keep = recheck_pair<T>(a, i, p);
+            bool screened = false;
+            if constexpr (kScreenable) {
+              if (a.screen) {
+                screened = true;
+                if (acc < keep_thr) {
+                  keep = true;
+                } else if (!(acc > drop_thr)) {
+                  keep = screen_pair(a, i, p);
+                  if (screen_cnt) atomicAdd(screen_cnt, 1u);   // shared-memory tally
+                }
+              }
+            }
+            if (!screened) {
+              if (acc < a.lo_thr) {
+                keep = true;
+              } else if (!(acc > a.hi_thr)) {
+                keep = recheck_pair<T>(a, i, p);
+              }
             }
           }
           if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
@@ -463,13 +552,18 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U, SIM>::value)
     return;
   }
   int32_t *sp = smem_partner + warp * 64 * U;   // two stages of 32*U partners
+  __shared__ unsigned int s_screen;               // pairs the BF16 screen left open
+  if (threadIdx.x == 0) s_screen = 0;
+  __syncthreads();
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = a.row_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
        row < a.row_end; row += warps_total) {
     const int32_t i = (int32_t)row;
     const int32_t mi = a.m_row ? a.m_row[i] : a.m;
-    gather_row<T, VEC, G, NCH, U, SIM, FULL>(a, i, mi, sp, lane);
+    gather_row<T, VEC, G, NCH, U, SIM, FULL>(a, i, mi, sp, lane, &s_screen);
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_screen) atomicAdd(a.counters + kCntScreen, (unsigned long long)s_screen);
 }
 
 // L2-blocked form: one launch per slice [lo, hi) of partner indices.  Each

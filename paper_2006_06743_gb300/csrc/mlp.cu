@@ -923,10 +923,7 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "surrogate cluster launches");
   rc = read_stats(gb.counters, r, stats, st, &tm);
-  if (stats) {
-    stats->map_tiles = gb.tiles;
-    stats->map_tex = gb.tex_chunks;
-  }
+  note_mapping(gb, stats);
   if (stats && rc == SNG_OK) {
     unsigned long long g[4];
     e = cudaMemcpyAsync(g, gcnt, sizeof(g), cudaMemcpyDeviceToHost, st);

@@ -1,0 +1,109 @@
+// screen.cu -- the BF16 copy behind the certified screen of FP32 points
+// (SNG_FLAG_SCREEN16; Algorithm 1, step 2).
+//
+// The gather of FP32 points reads d * 4 bytes of every partner row; with the
+// screen it reads a BF16 copy (half the bytes, and a point set that fits in
+// L2 twice as easily) and decides each pair from it wherever the rounding of
+// the copy cannot change the decision (screen_thresholds in gather.cuh).
+// This file makes the copy, rounding each value to the nearest BF16, and an
+// upper bound of every row's Euclidean norm, with the maximum over all rows
+// (and, for the tiled form, over each slice of rows).
+#include <cuda_bf16.h>
+
+#include "api_common.cuh"
+#include "screen.cuh"
+
+namespace sng {
+
+// Largest bits of non-negative floats (or NaN, whose bits order above +inf,
+// so that a NaN norm certifies nothing) over a block, one atomic per block.
+__device__ __forceinline__ void block_max_bits(unsigned int v, unsigned int *out) {
+  __shared__ unsigned int s_max;
+  if (threadIdx.x == 0) s_max = 0u;
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v = max(v, __shfl_xor_sync(kFullMask, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_max, v);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_max) atomicMax(out, s_max);
+}
+
+// One warp per row: the BF16 copy (round to nearest even; the padding of
+// each copied row up to ldb is zero) and the row's norm bound.  The FP32 sum
+// of squares (per-lane fused multiply-adds, then a 5-level butterfly) is
+// within (d/32 + 6) 2^-24 relative of the exact one; the correctly rounded
+// square root times (1 + 2^-11) is then an upper bound of |x_i| for every
+// supported d.  Sums that overflow give +inf (no certificate); values too
+// small to square in FP32 are covered by the screen's absolute slack.
+__global__ void __launch_bounds__(256) shadow_kernel(const float *x, int64_t ld, int32_t d,
+                                                     int64_t n, uint16_t *xb, int64_t ldb,
+                                                     float *nrm, unsigned int *nmax_all) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned int mx = 0u;
+  for (int64_t i = warp; i < n; i += warps) {
+    const float *row = x + i * ld;
+    uint16_t *out = xb + i * ldb;
+    float ss = 0.f;
+    for (int64_t k = lane; k < ldb; k += 32) {
+      const float v = k < d ? __ldg(row + k) : 0.f;
+      out[k] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+      ss = fmaf(v, v, ss);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFullMask, ss, o);
+    const float bound = sqrtf(ss) * (1.f + 0x1p-11f);
+    if (lane == 0) nrm[i] = bound;
+    mx = max(mx, __float_as_uint(bound));
+  }
+  block_max_bits(mx, nmax_all);
+}
+
+// Maximum norm bound over each slice of `slice` consecutive rows, into
+// nmax[1 + s] (the tiled form's partner slices).
+__global__ void __launch_bounds__(256) slice_max_kernel(const float *nrm, int64_t n,
+                                                        int64_t slice, int32_t k,
+                                                        unsigned int *nmax) {
+  for (int s = 0; s < k; ++s) {
+    const int64_t lo = (int64_t)s * slice;
+    const int64_t hi = lo + slice < n ? lo + slice : n;
+    unsigned int mx = 0u;
+    for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
+         i += (int64_t)gridDim.x * blockDim.x)
+      mx = max(mx, __float_as_uint(__ldg(nrm + i)));
+    block_max_bits(mx, nmax + 1 + s);
+  }
+}
+
+sng_status make_shadow(const float *x, int64_t ld, int32_t d, int64_t n, Scratch &s,
+                       Shadow *out) {
+  cudaStream_t st = s.stream;
+  out->ldb = ((int64_t)d + 7) / 8 * 8;
+  sng_status rc;
+  if ((rc = s.alloc((void **)&out->xb, (size_t)n * out->ldb * 2, "BF16 screen copy")) ||
+      (rc = s.alloc((void **)&out->nrm, (size_t)n * 4, "row norm bounds")) ||
+      (rc = s.alloc((void **)&out->nmax, (size_t)(1 + kShadowSlices) * 4, "norm maxima")))
+    return rc;
+  cudaMemsetAsync(out->nmax, 0, (size_t)(1 + kShadowSlices) * 4, st);
+  const int64_t blocks_needed = (n + 7) / 8;
+  const int64_t cap = (int64_t)device_sms() * 8;
+  const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
+  shadow_kernel<<<grid, 256, 0, st>>>(x, ld, d, n, out->xb, out->ldb, out->nrm,
+                                      reinterpret_cast<unsigned int *>(out->nmax));
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SNG_OK : cuda_fail(e, "BF16 screen copy");
+}
+
+sng_status shadow_slice_max(const Shadow &sh, int64_t n, int64_t slice, int k, cudaStream_t st) {
+  if (k < 1 || k > kShadowSlices) return fail(SNG_EINTERNAL, "slice count %d out of range", k);
+  const int grid = device_sms();
+  slice_max_kernel<<<grid, 256, 0, st>>>(sh.nrm, n, slice, k,
+                                         reinterpret_cast<unsigned int *>(sh.nmax));
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SNG_OK : cuda_fail(e, "norm maxima per slice");
+}
+
+}  // namespace sng

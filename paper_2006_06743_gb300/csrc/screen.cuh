@@ -1,0 +1,24 @@
+// screen.cuh -- the BF16 copy of FP32 points for the certified screen
+// (screen.cu; SNG_FLAG_SCREEN16).
+#pragma once
+
+#include "api_common.cuh"
+
+namespace sng {
+
+constexpr int kShadowSlices = 32;   // the tiled form's largest slice count
+
+struct Shadow {
+  uint16_t *xb = nullptr;   // n x ldb BF16 bit patterns (ldb = d rounded up to 8)
+  int64_t ldb = 0;
+  float *nrm = nullptr;     // n: upper bounds of the rows' Euclidean norms
+  float *nmax = nullptr;    // [0] max over all rows, [1 + s] over slice s
+};
+
+// BF16 copy, norm bounds and their maximum (stream-ordered; scratch from s).
+sng_status make_shadow(const float *x, int64_t ld, int32_t d, int64_t n, Scratch &s,
+                       Shadow *out);
+// Maxima of the norm bounds over k slices of `slice` rows into nmax[1..k].
+sng_status shadow_slice_max(const Shadow &sh, int64_t n, int64_t slice, int k, cudaStream_t st);
+
+}  // namespace sng

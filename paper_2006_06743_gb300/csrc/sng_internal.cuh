@@ -42,6 +42,7 @@ enum CounterSlot : int {
   kCntNoise = 6,
   kCntEdges = 7,      // scan total
   kCntStatus = 8,     // error bits (uint32 stored in a 64-bit slot)
+  kCntScreen = 9,     // pairs the BF16 screen of FP32 points left open
   kCntSlots = 16
 };
 

@@ -172,12 +172,21 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
   const int4 *runs = t.runs + t.run_off[b];
   const unsigned long long *list = t.entries + t.entry_off[b];
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  constexpr bool kScreenable = std::is_same<T, uint16_t>::value;
+  __shared__ unsigned int s_screen;   // pairs the BF16 screen left open
+  if (threadIdx.x == 0) s_screen = 0;
+  __syncthreads();
+  const float nrm_p = kScreenable && a.screen ? a.nrm_max[1 + b % t.k] : 0.f;
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; r < nruns; r += warps_total) {
     const int4 run = runs[r];
     const int32_t i = run.x;
     const int64_t base = ((int64_t)(uint32_t)run.y << 32) | (uint32_t)run.z;
     const int len = run.w;
     const int32_t wi = a.w_row ? a.w_row[i] : 1;
+    float keep_thr = 0.f, drop_thr = 0.f;
+    if constexpr (kScreenable) {
+      if (a.screen) screen_thresholds(a, a.nrm[i], nrm_p, keep_thr, drop_thr);
+    }
     float xi[NCH][VEC];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
@@ -298,10 +307,24 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
           const float acc = part[q];
           if ((gl & (low - 1)) == 0 && p >= 0) {
             bool keep = false;
-            if (acc < a.lo_thr) {
-              keep = true;
-            } else if (!(acc > a.hi_thr)) {
-              keep = recheck_pair<T>(a, i, p);
+            bool screened = false;
+            if constexpr (kScreenable) {
+              if (a.screen) {
+                screened = true;
+                if (acc < keep_thr) {
+                  keep = true;
+                } else if (!(acc > drop_thr)) {
+                  keep = screen_pair(a, i, p);
+                  atomicAdd(&s_screen, 1u);
+                }
+              }
+            }
+            if (!screened) {
+              if (acc < a.lo_thr) {
+                keep = true;
+              } else if (!(acc > a.hi_thr)) {
+                keep = recheck_pair<T>(a, i, p);
+              }
             }
             if (keep) {
               const int32_t j = sj[(t0 + first + q) * R + grp];
@@ -321,6 +344,8 @@ __global__ void __launch_bounds__(256, MinBlocks<T, VEC, NCH, U>::value)
       atomicAdd(a.deg + i, cnt * wi);   // both degree modes: the rows' runs add up
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_screen) atomicAdd(a.counters + kCntScreen, (unsigned long long)s_screen);
 }
 
 template <typename T, int VEC, int G, int NCH, int U, bool FULL, int TEXC>
@@ -372,7 +397,8 @@ static int occ_tile(const GatherMap &m) {
   X(T, V, 4, 4, 2, true) X(T, V, 8, 4, 2, true) X(T, V, 16, 4, 2, true)                  \
   X(T, V, 4, 4, 4, true) X(T, V, 8, 4, 4, true) X(T, V, 8, 2, 2, true)                   \
   X(T, V, 4, 2, 2, true) X(T, V, 16, 2, 2, true) X(T, V, 4, 4, 2, false)                 \
-  X(T, V, 8, 4, 2, false) X(T, V, 16, 4, 2, false) X(T, V, 8, 2, 2, false)
+  X(T, V, 8, 4, 2, false) X(T, V, 16, 4, 2, false) X(T, V, 8, 2, 2, false)                \
+  X(T, V, 8, 1, 2, true) X(T, V, 8, 1, 4, true) X(T, V, 16, 1, 2, true)
 // FP32 only: two lanes per pair, one shuffle per 16 pairs (BF16 rows this
 // wide would hold 64 FP32 source values per lane)
 #define SNG_TILE_SHAPES_F32(X) X(float, 4, 2, 8, 2, true) X(float, 4, 2, 8, 1, true)

@@ -131,6 +131,7 @@ def test_autotuner_offers_the_tiled_form_where_it_fits(monkeypatch):
 
     def tiled(n, d, dtype=torch.float32, **kw):
         cands = autotune.candidates(_FakeCudaRows(n, d, dtype), Params(eps=1.0, min_pts=5, **kw))
+        cands = [c for c in cands if not c.get("screen")]
         t = [c for c in cands if c.get("tiled")]
         if t:
             first = next(i for i, c in enumerate(cands) if not c.get("tiled"))
@@ -154,3 +155,36 @@ def test_autotuner_offers_the_tiled_form_where_it_fits(monkeypatch):
     assert tiled(1_000_000, 64, m=1000)[0] == []
     free[0] = 17 << 30
     assert tiled(1_000_000, 64, m=1000)[0] == [0, 3, 8]
+
+
+def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
+    """Screened candidates (SNG_FLAG_SCREEN16) lead the list for FP32 points,
+    Euclidean form, hashed draws: the direct gather over the BF16 copy with
+    the default lanes per pair for 8-value chunks and half of it, and, for
+    copies over 48 MiB whose buckets fit, the tiled form with the copy's
+    slice count and one more.  None for BF16 points, similarity metrics or
+    every-pair sampling; the flag reaches the parameters."""
+    import torch
+    from paper_2006_06743_gb300 import SNG_FLAG_SCREEN16, Params, autotune
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda dev=None: (200 << 30, 280 << 30))
+
+    def screened(n, d, dtype=torch.float32, **kw):
+        cands = autotune.candidates(_FakeCudaRows(n, d, dtype), Params(eps=1.0, min_pts=5, **kw))
+        sc = [c for c in cands if c.get("screen")]
+        assert cands[:len(sc)] == sc                 # screened candidates lead the list
+        return sc
+
+    sc = screened(1_000_000, 64, s=0.001)
+    direct = [c for c in sc if not c.get("tiled")]
+    tiled = [c for c in sc if c.get("tiled")]
+    assert {c["map_group"] for c in direct} == {4, 8} and {c["map_unroll"] for c in direct} == {2, 4}
+    # BF16 copy of 10^6 x 64 = 128 MB: ceil(256 MB / 88 MiB) = 3 -> {3, 4}
+    assert sorted({c["map_tile"] for c in tiled}) == [3, 4]
+    assert {c["map_group"] for c in tiled} == {0, 8}
+    p = autotune.apply(Params(eps=1.0, min_pts=5), {"mapping": sc[0]})
+    assert p.flags & SNG_FLAG_SCREEN16
+    # small point sets: the direct screened gather only
+    assert all(not c.get("tiled") for c in screened(100_000, 64, m=100))
+    assert screened(1_000_000, 64, dtype=torch.bfloat16, m=1000) == []
+    assert screened(1_000_000, 64, m=1000, metric=2) == []
+    assert screened(200_000, 64, sample_mode=1) == []
