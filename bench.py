@@ -167,6 +167,46 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def gather_kernel_name_and_bytes(stats: dict, n: int, d: int, m: int) -> tuple[str, int]:
+    """Kernels of the gather phase as they ran, and the bytes the SMs must
+    move in it: partner and own rows of the form's layout (a 16 * k-tile-wide
+    BF16 copy for the tensor-core screen, d rounded up to 8 for the CUDA-core
+    screen, FP32 otherwise), the squared norm per partner (tensor-core
+    screen), the tiled form's 8-byte bucket entry per draw (written once,
+    read once) and source row per run, keep words, degree updates, the FP32
+    rows of every pair the screen left open, and the making of the copy."""
+    kept = stats["kept_edges"]
+    words = (m + 31) // 32
+    screen, tiles = stats["map_screen"], stats["map_tiles"]
+    full = stats["map_group"] * stats["map_nch"] * stats["map_vec"] == d
+    common = n * words * 4 + n * 4 + kept * 8 + n * 8
+    if screen == 2:
+        kt = stats["map_nch"]
+        row = 16 * kt * 2
+        byts = n * m * (row + 4) + n * (row + 8) + common
+        name = f"shadow_kernel + gather_mma_kernel<{kt}>"
+    else:
+        esize, vec = (2, 8) if screen else (4, 4)
+        row = (-(-d // 8) * 8 if screen else d) * esize
+        typ = "unsigned short" if screen else "float"
+        if tiles:
+            byts = n * m * (row + 16) + n * tiles * (row + 16) + common
+            name = (f"tile_partition_kernel + {tiles * tiles} x tile_test_kernel<{typ}, "
+                    f"{stats['map_vec']}, {stats['map_group']}, {stats['map_nch']}, "
+                    f"{stats['map_unroll']}, {int(full)}, {stats['map_tex']}>")
+        else:
+            byts = n * m * row + n * row + common
+            name = (f"gather_kernel<{typ}, {stats['map_vec']}, {stats['map_group']}, "
+                    f"{stats['map_nch']}, {stats['map_unroll']}, 0, {int(full)}, 0>")
+        if screen:
+            name = "shadow_kernel + " + ("slice_max_kernel + " if tiles else "") + name
+    if screen:
+        row = (16 * stats["map_nch"] if screen == 2 else -(-d // 8) * 8) * 2
+        byts += n * (d * 4 + row + 12)                   # the copy: read FP32, write BF16
+        byts += stats.get("screen_pairs", 0) * 2 * d * 4  # open pairs from the FP32 rows
+    return name, int(byts)
+
+
 def run_cpu_baseline(w: dict, budget_s: float = 8.0, omp_budget_s: float = 30.0) -> dict:
     """The FP64 oracle as written, timed on the host's cores.
 
@@ -238,11 +278,11 @@ def bench_sng(args, w):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    # default (weak scaling): every rank clusters its own independent dataset
-    # (no collective on the data path); rank r uses seed base + r.
-    # --sharded (strong scaling): one dataset, step 2 split by source rows,
-    # degrees all-reduced and edges all-gathered over NCCL.
-    if rank > 0 and not args.sharded:
+    # N > 1 (default, strong scaling): one dataset, step 2 split by source
+    # rows, degrees all-reduced and edges all-gathered over NCCL.
+    # --replicas (weak scaling): every rank clusters its own independent
+    # dataset (no collective on the data path); rank r uses seed base + r.
+    if rank > 0 and args.replicas:
         w = make_workload(args.workload, seed=args.seed + rank)
     x_host = torch.from_numpy(w["x"]).pin_memory()
     x = x_host.to(dev)
@@ -264,8 +304,10 @@ def bench_sng(args, w):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    if args.sharded and world > 1:
-        return bench_sharded(args, w, x, params, rank, world, dev)
+    if world > 1 and not args.replicas:
+        out = bench_sharded(args, w, x, x_host, params, rank, world, dev, flush)
+        dist.destroy_process_group()
+        return out
     for _ in range(args.warmup):
         labels, st = sng.cluster(x, params)
     torch.cuda.synchronize(dev)
@@ -328,22 +370,17 @@ def bench_sng(args, w):
     Q = n * m
     peak, peak_kind = peaks()
     g_ms = statistics.mean(gather_ms)
+    # the section 8(d) model: every partner row from HBM (FP32 rows)
     alg = gather_algorithmic_bytes(n, d, m, 4, stats["kept_edges"])
-    achieved = alg / (g_ms * 1e-3) / 1e9
-    full = stats["map_group"] * stats["map_nch"] * stats["map_vec"] == d
-    tiles = stats["map_tiles"]
-    if tiles:
-        # the tiled form: one partition launch, then one test launch per tile;
-        # the gather phase (all of them) is the unit the roofline times
-        kname = (f"tile_partition_kernel + {tiles * tiles} x tile_test_kernel<float, "
-                 f"{stats['map_vec']}, {stats['map_group']}, {stats['map_nch']}, "
-                 f"{stats['map_unroll']}, {int(full)}, {stats['map_tex']}>")
-    else:
-        kname = (f"gather_kernel<float, {stats['map_vec']}, {stats['map_group']}, "
-                 f"{stats['map_nch']}, {stats['map_unroll']}, 0, {int(full)}, 0>")
+    kname, alg_l2 = gather_kernel_name_and_bytes(stats, n, d, m)
     traffic = None
     if params.map_passes <= 1 and not (params.flags & sng.SNG_FLAG_PREFETCH):
         traffic = CAPTURED_TRAFFIC.get((args.workload, kname))
+    # the roofline that bounds the gather: its working set (the BF16 copy of
+    # the points, or one tile's two slices) stays in L2, so the peak is the
+    # rate the SMs read from L2, measured here by the library's own probe
+    l2_peak = sng.measure_l2_read(48 << 20, 200)
+    achieved_l2 = alg_l2 / (g_ms * 1e-3) / 1e9
     truth = w["truth"].astype(np.int32)
     ari_truth = sng.ari(labels, torch.from_numpy(truth).to(dev))
     out = {
@@ -376,22 +413,22 @@ def bench_sng(args, w):
                 "api": "sng_cluster_host (host buffers in and out)",
                 "h2d_one_stream_ms": h2d_one_stream_ms, "step_ms": e2e_ms},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": kname, "peak_kind": peak_kind,
-                     "algorithmic_bytes": alg, "kernel_ms": g_ms,
-                     # DRAM-level view: the captured traffic over this run's
-                     # kernel time (frac above 1 comes from partner rows that
-                     # hit in L2, the share given by 1 - traffic / algorithmic)
+        "roofline": {"bound": "l2", "achieved": achieved_l2, "peak": l2_peak, "unit": "GB/s",
+                     "frac": achieved_l2 / l2_peak, "traffic": traffic,
+                     "kernel": kname, "peak_kind": "measured (sng_measure_l2_read, this run)",
+                     "algorithmic_bytes": alg_l2, "kernel_ms": g_ms,
                      "traffic_frac": (traffic / (g_ms * 1e-3) / 1e9 / peak) if traffic else None,
-                     "l2_served_share": (1.0 - traffic / alg) if traffic else None,
-                     # what the profile shows saturated: the direct gather
-                     # streams DRAM; the tiled form's tile tests are bound by
-                     # L1's load/store data pipe (partner rows from L2)
-                     "limiter": "L1 load/store data pipe" if tiles else "DRAM"},
+                     "hbm_model": {"bound": "hbm", "algorithmic_bytes": alg,
+                                   "achieved": alg / (g_ms * 1e-3) / 1e9, "peak": peak,
+                                   "peak_kind": peak_kind, "unit": "GB/s",
+                                   "frac": alg / (g_ms * 1e-3) / 1e9 / peak,
+                                   "note": "256 B of FP32 partner row per query, all from HBM "
+                                           "(the survey's model); the gather reads a BF16 "
+                                           "copy or L2-resident tiles instead"}},
         "phases_ms": {k: v for k, v in stats["ms"].items()},
         "stats": {k: stats[k] for k in ("kept_edges", "band_pairs", "band_points", "cores",
-                                        "clusters", "noise", "recheck_pairs")},
+                                        "clusters", "noise", "recheck_pairs", "screen_pairs",
+                                        "map_screen", "map_tiles")},
         "ari_vs_generating_mixture": ari_truth,
         "ami_vs_generating_mixture": sng.ami(labels, torch.from_numpy(truth).to(dev))["ami"],
         "clocks": clk,
@@ -405,36 +442,91 @@ def bench_sng(args, w):
     return out if rank == 0 else None
 
 
-def bench_sharded(args, w, x, params, rank, world, dev):
-    """One dataset across all ranks (strong scaling): each step is the whole
-    pass, step 2 split by source rows, one all-reduce of the degrees and one
-    all-gather of the kept edges."""
+def bench_sharded(args, w, x, x_host, params, rank, world, dev, flush):
+    """One dataset across all ranks (strong scaling, the multi-GPU form of the
+    plain path): each step is the whole pass, step 2 split by source rows,
+    one NCCL all-reduce of the degrees and one all-gather of the kept edges,
+    then steps 3-5 on every rank.  Timed with CUDA events on the launching
+    stream (the collectives join it), max over ranks."""
     import torch
     import torch.distributed as dist
 
-    from paper_2006_06743_gb300.distributed import GpuCompute, cluster_sharded
+    import paper_2006_06743_gb300 as sng
+    from paper_2006_06743_gb300.distributed import GpuCompute, cluster_sharded, row_range
     comp = GpuCompute(x, params)
-    n = w["n"]
+    n, d, m = w["n"], w["d"], w["m"]
+    stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         cluster_sharded(comp, n)
     torch.cuda.synchronize(dev)
     dist.barrier()
-    t0 = time.perf_counter()
+    launches0 = sng.launch_count()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    step_ms, gather_ms = [], []
     for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         labels, core, _ = cluster_sharded(comp, n)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        gather_ms.append(comp.last_stats["ms"]["gather"])
     torch.cuda.synchronize(dev)
-    dt = torch.tensor([(time.perf_counter() - t0) / args.steps], device=dev)
-    dist.all_reduce(dt, op=dist.ReduceOp.MAX)
-    t_step = float(dt.item()) * 1e3
-    Q = n * w["m"]
+    clk = clocks.stop()
+    dist.barrier()
+    launches = sng.launch_count() - launches0
+    t = torch.tensor([statistics.mean(step_ms), statistics.mean(gather_ms)], device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_step, g_ms = float(t[0].item()), float(t[1].item())
+    # end to end through the same call: every rank copies the points from
+    # pinned host memory (they are replicated) and reads the labels back
+    e2e_ms = []
+    for it in range(1 + max(2, min(args.steps, 5))):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        dist.barrier()
+        t0 = time.perf_counter()
+        comp.x = x_host.to(dev, non_blocking=True)
+        lab, _, _ = cluster_sharded(comp, n)
+        lab_host = lab.cpu()
+        torch.cuda.synchronize(dev)
+        if it >= 1:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    comp.x = x
+    te = torch.tensor([statistics.mean(e2e_ms)], device=dev)
+    dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    t_e2e = float(te.item())
+    lo, hi = row_range(n, rank, world)
+    st = comp.last_stats
+    Q = n * m
+    peak, peak_kind = peaks()
+    # this rank's shard of the gather: its rows' queries and own rows
+    alg = gather_algorithmic_bytes(hi - lo, d, m, 4, st["kept_edges"])
     out = {"metric": HEADLINE_METRIC,
            "value": Q / (t_step * 1e-3), "unit": "queries/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded Gaussian mixture, no dataset)",
-           "config": {"workload": args.workload, "n": n, "d": w["d"], "m": w["m"],
-                      "parallelism": f"rows-sharded x{world}, NCCL all-reduce + all-gather"}}
-    dist.destroy_process_group()
+           "config": {"workload": args.workload, "n": n, "d": d, "m": m, "s": w["s"],
+                      "eps": w["eps"], "min_pts": w["min_pts"], "queries_per_step": Q,
+                      "l2": "flushed between steps (512 MB write)",
+                      "parallelism": f"rows-sharded x{world}: NCCL all-reduce of degrees + "
+                                     f"all-gather of kept edges"},
+           "e2e": {"value": Q / (t_e2e * 1e-3), "unit": "queries/s", "seconds": t_e2e * 1e-3,
+                   "h2d_bytes_per_step": int(x_host.numel() * 4),
+                   "d2h_bytes_per_step": int(n * 4),
+                   "api": "distributed.cluster_sharded (points copied from pinned host memory "
+                          "on every rank, labels read back)"},
+           "gpu_launches": int(launches),
+           "roofline": {"bound": "hbm", "achieved": alg / (g_ms * 1e-3) / 1e9, "peak": peak,
+                        "unit": "GB/s", "frac": alg / (g_ms * 1e-3) / 1e9 / peak,
+                        "traffic": None, "peak_kind": peak_kind,
+                        "kernel": "gather of one rank's row shard (slowest rank)",
+                        "algorithmic_bytes": alg, "kernel_ms": g_ms},
+           "clocks": clk}
     return out if rank == 0 else None
 
 
@@ -853,6 +945,48 @@ def bench_sweep(args):
             "dtype": "f32"}
 
 
+def run_extensions(args) -> dict:
+    """The extension forms' key results, folded into the default line (each
+    at its stated size, fewer repetitions than their own lines): the BF16
+    form against FP32 on the same points (the sigma = 0.0375 companion, where
+    the graph has edges and the decision error means something), the batched
+    form against per-cloud calls, and the learned surrogate against the plain
+    method at the gate the configuration states and at the tuned gate."""
+    import copy
+
+    import torch
+    out = {}
+    a = copy.copy(args)
+    a.steps, a.warmup, a.tune_budget = 3, 1, args.ext_tune_budget
+    t0 = time.perf_counter()
+    a.bf16_sigma = 0.0375
+    r = bench_bf16(a)
+    out["bf16"] = {"workload": r["config"]["workload"], "ms_bf16": r["ms_bf16"],
+                   "ms_fp32": r["ms_fp32"], "speedup_vs_fp32": r["speedup_vs_fp32"],
+                   "ari_vs_fp32": r["ari_bf16_vs_fp32"],
+                   "edge_decision_error_vs_fp64": r["edge_decision_error_vs_fp64"],
+                   "seconds": time.perf_counter() - t0}
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    a.seq_clouds = 256
+    r = bench_batched(a)
+    out["batched"] = {"workload": r["config"]["workload"], "ms_batched": r["ms_batched"],
+                      "ms_sequential_est": r["ms_sequential_est"],
+                      "speedup_vs_sequential": r["speedup_vs_sequential"],
+                      "labels_equal_sequential": r["labels_equal_sequential"],
+                      "queries_per_s": r["value"], "seconds": time.perf_counter() - t0}
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    r = bench_surrogate(a)
+    out["surrogate"] = {k: r[k] for k in ("ms_surrogate", "ms_plain", "speedup_vs_plain",
+                                          "ari_vs_plain", "core_mask_agreement",
+                                          "queries_issued_frac") if k in r}
+    out["surrogate"].update({"workload": r["config"]["workload"],
+                             "gates": r.get("gates"), "seconds": time.perf_counter() - t0})
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_reference(args, w):
     """The reference arm: the FP64 CPU oracle, timed as it stands on the host.
     Each step runs step 2 of Algorithm 1 (the OpenMP build of the oracle on
@@ -935,8 +1069,9 @@ def main():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tune-budget", type=float, default=40.0)
     ap.add_argument("--verbose", action="store_true")
-    ap.add_argument("--sharded", action="store_true",
-                    help="N > 1: split one dataset's rows across ranks (strong scaling)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: independent datasets per rank (weak scaling) instead of one "
+                         "dataset's rows split across ranks")
     ap.add_argument("--form", default="plain",
                     choices=["plain", "bf16", "batched", "surrogate", "balls", "sweep", "cosine",
                              "graph"])
@@ -961,6 +1096,9 @@ def main():
     ap.add_argument("--noise-frac", type=float, default=0.0)
     ap.add_argument("--reweight", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extensions", type=int, default=1,
+                    help="1: add the BF16, batched and surrogate forms' key results")
+    ap.add_argument("--ext-tune-budget", type=float, default=12.0)
     ap.add_argument("--cpu-budget", type=float, default=8.0)
     ap.add_argument("--omp-budget", type=float, default=30.0)
     ap.add_argument("--ref-budget", type=float, default=5.0)
@@ -985,6 +1123,9 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         out = bench_sng(args, w)
+    if out is not None and rank == 0 and args.impl != "reference" and world == 1 \
+            and args.extensions:
+        out["extensions"] = run_extensions(args)
     if out is not None and rank == 0:
         print(json.dumps(out), flush=True)
 

@@ -121,6 +121,14 @@ typedef int32_t sng_status;
                                 tiled gather; ignored for BF16 points, other
                                 metrics, one lane per row, map_passes > 1 and
                                 SNG_FLAG_NO_SYNC                                */
+#define SNG_FLAG_SCREEN_MMA 64u /* with SNG_FLAG_SCREEN16 and d <= 128: the direct
+                                gather forms each pair's squared distance on the
+                                BF16 copy as |a|^2 + |b|^2 - 2 a.b with the dot
+                                products of 16 partners at a time from BF16
+                                tensor-core MMAs (FP32 accumulation); the
+                                screen's thresholds are widened by the bound of
+                                that computation.  Same results.  The tiled
+                                form and map_group / map_unroll do not apply   */
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The
                                 edge arrays are sized for all n*m draws (8 bytes
@@ -198,7 +206,9 @@ typedef struct {
                              read through the texture unit (0 or 1)        */
     int32_t map_screen;   /* 1: pairs were tested on the BF16 copy
                              (SNG_FLAG_SCREEN16); map_vec .. map_unroll then
-                             describe the mapping over that copy            */
+                             describe the mapping over that copy; 2: with
+                             tensor-core dot products (SNG_FLAG_SCREEN_MMA;
+                             map_group 16 partners per MMA, map_nch k-tiles) */
     int64_t screen_pairs; /* SNG_FLAG_SCREEN16: pairs the BF16 screen left
                              open, summed again from the FP32 points       */
 } sng_stats;

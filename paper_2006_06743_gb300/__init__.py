@@ -35,6 +35,7 @@ SNG_FLAG_NO_SYNC = 4
 SNG_FLAG_WARP_ROWS = 8
 SNG_FLAG_TILED = 16
 SNG_FLAG_SCREEN16 = 32
+SNG_FLAG_SCREEN_MMA = 64
 
 PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total", "gate")
 

@@ -5,7 +5,8 @@ how many partner rows each warp keeps in flight, the block size and, for
 point sets larger than L2, how many L2-resident slices of the partner range
 the launch is split into, whether the L2-tiled form (draws bucketed by
 source and partner slice, then tested tile by tile) beats the direct gather,
-and, for FP32 points, whether testing pairs on a certified BF16 copy pays.
+and, for FP32 points, whether testing pairs on a certified BF16 copy (with
+CUDA-core sums or tensor-core dot products) pays.
 The library picks a rule-of-thumb mapping; this
 module times a small set of candidates on the caller's own data, through the
 library's per-phase CUDA-event timers, and caches the fastest per
@@ -19,8 +20,8 @@ import os
 import statistics
 import time
 
-from . import (SNG_FLAG_PREFETCH, SNG_FLAG_SCREEN16, SNG_FLAG_TILED, SNG_FLAG_TIMING, Params,
-               SngError, cluster)
+from . import (SNG_FLAG_PREFETCH, SNG_FLAG_SCREEN16, SNG_FLAG_SCREEN_MMA, SNG_FLAG_TILED,
+               SNG_FLAG_TIMING, Params, SngError, cluster)
 
 CACHE_ENV = "SNG_AUTOTUNE_CACHE"
 
@@ -77,6 +78,9 @@ def candidates(x, p: Params) -> list[dict]:
         ldb = -(-d // 8) * 8
         xb_bytes = n * ldb * 2
         if xb_bytes < 0.25 * free:
+            if d <= 128:    # tensor-core dot products (16, 32 or 64 values per k-tile set)
+                out.append(dict(map_group=0, map_unroll=0, map_block=256, map_passes=0,
+                                prefetch=False, screen=True, mma=True))
             for g in sorted({max(1, gb // 2), gb}):
                 for u in (2, 4):
                     out.append(dict(map_group=g, map_unroll=u, map_block=256, map_passes=0,
@@ -116,7 +120,11 @@ def _params_for(base: dict, cand: dict) -> Params:
     pf = c.pop("prefetch", False)
     tiled = c.pop("tiled", False)
     screen = c.pop("screen", False)
-    flags = base.get("flags", 0) & ~(SNG_FLAG_PREFETCH | SNG_FLAG_TILED | SNG_FLAG_SCREEN16)
+    mma = c.pop("mma", False)
+    flags = base.get("flags", 0) & ~(SNG_FLAG_PREFETCH | SNG_FLAG_TILED | SNG_FLAG_SCREEN16 |
+                                     SNG_FLAG_SCREEN_MMA)
+    if mma:
+        flags |= SNG_FLAG_SCREEN_MMA
     if pf:
         flags |= SNG_FLAG_PREFETCH
     if screen:

@@ -17,6 +17,7 @@
 #include "api_common.cuh"
 #include "gather.cuh"
 #include "graph.cuh"
+#include "gather_mma.cuh"
 #include "screen.cuh"
 #include "tiled.cuh"
 
@@ -548,9 +549,11 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   const bool screen = (p->flags & SNG_FLAG_SCREEN16) && p->dtype == SNG_F32 &&
                       p->metric == SNG_METRIC_L2 && r.map.passes <= 1 && !r.map.lanes &&
                       !(p->flags & SNG_FLAG_NO_SYNC);
+  const int mma_kt = screen && (p->flags & SNG_FLAG_SCREEN_MMA) ? mma_tiles_for(p->d) : 0;
   if (screen) {
     wait_inputs(st);
-    if ((rc = make_shadow(static_cast<const float *>(x), p->ld, p->d, n, s, &sh))) return rc;
+    if ((rc = make_shadow(static_cast<const float *>(x), p->ld, p->d, n, 16 * mma_kt, s, &sh)))
+      return rc;
     pb = *p;
     pb.dtype = SNG_BF16;
     pb.ld = (int32_t)sh.ldb;
@@ -581,6 +584,8 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     }
     ga.nrm = sh.nrm;
     ga.nrm_max = sh.nmax;
+    ga.nb2 = sh.nb2;
+    ga.screen_cabs = std::ldexp(1.0f, -15);
     // the FP32 sum over the BF16 values: one rounding per difference, one
     // per fused multiply-add in a lane, one per shuffle level (as the
     // plain guard band); g adds 2^-20 for the rounding of the thresholds
@@ -599,12 +604,22 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   }
   const int grid = gather_grid(pg->dtype, rg->map, r.row_end - r.row_begin);
   bool tiled = false;
-  if ((p->flags & SNG_FLAG_TILED) &&
+  if (!mma_kt && (p->flags & SNG_FLAG_TILED) &&
       (rc = run_tiled(pg, *rg, s, ga, gb, &tiled, screen ? &sh : nullptr)))
     return rc;
   gb->screened = screen;
   gb->map = rg->map;
-  if (tiled) {
+  if (mma_kt) {
+    // the tensor-core form of the screen (direct gather only): 16 partners
+    // per MMA, mma_kt k-tiles of 16 values per row
+    gb->mma = true;
+    gb->map.group = 16;
+    gb->map.nch = mma_kt;
+    gb->map.unroll = 0;
+    if (!launch_gather_mma(mma_kt, ga, r.row_end - r.row_begin, st))
+      return fail(SNG_EINTERNAL, "tensor-core gather not compiled for d = %d", p->d);
+    note_launch();
+  } else if (tiled) {
     // done by the tiled form
   } else if (rg->map.passes <= 1) {
     wait_inputs(st);
@@ -711,7 +726,7 @@ void note_mapping(const GraphBufs &gb, sng_stats *stats) {
   if (!stats) return;
   stats->map_tiles = gb.tiles;
   stats->map_tex = gb.tex_chunks;
-  stats->map_screen = gb.screened ? 1 : 0;
+  stats->map_screen = gb.screened ? (gb.mma ? 2 : 1) : 0;
   if (gb.screened) {
     stats->map_vec = gb.map.vec;
     stats->map_group = gb.map.group;

@@ -79,6 +79,7 @@ struct GraphBufs {
   int tiles = 0;             // slices per axis of the tiled gather; 0 = direct
   int tex_chunks = 0;        // tiled gather: partner-row chunks read as texture
   bool screened = false;     // pairs tested on the BF16 copy (SNG_FLAG_SCREEN16)
+  bool mma = false;          // ... with tensor-core dot products (SNG_FLAG_SCREEN_MMA)
   GatherMap map{};           // the mapping the gather ran with
 };
 

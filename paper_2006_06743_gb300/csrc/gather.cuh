@@ -78,6 +78,10 @@ struct GatherArgs {
   float screen_g;         // relative bound of the FP32 sum, plus margins
   const float *nrm;       // per-row upper bounds of |x_i| (FP32 points)
   const float *nrm_max;   // [0] over all rows; [1 + s] over partner slice s
+  // tensor-core form of the screen (gather_mma.cu): squared norms of the
+  // BF16 rows (FP32 sums) and the coefficient of its absolute error bound
+  const float *nb2;
+  float screen_cabs;
   uint32_t *bitmask;      // n x W
   int32_t *out_cnt;       // n, nullable
   int32_t *deg;           // n (zeroed before launch in multigraph mode)
@@ -150,7 +154,29 @@ static __device__ __noinline__ bool screen_pair(const GatherArgs &a, int32_t i, 
   const float *xa = a.xm + (int64_t)i * a.ldm, *xb = a.xm + (int64_t)p * a.ldm;
   float acc = 0.f;
   if (a.screen_vec4) {
-    for (int k = 0; k < a.d; k += 4) {
+    // eight 16-byte chunks of each row in flight, then their terms in order
+    constexpr int B = 8;
+    int k = 0;
+    for (; k + 4 * B <= a.d; k += 4 * B) {
+      float4 u[B], v[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        u[c] = __ldg(reinterpret_cast<const float4 *>(xa + k) + c);
+        v[c] = __ldg(reinterpret_cast<const float4 *>(xb + k) + c);
+      }
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        float t = u[c].x - v[c].x;
+        acc = fmaf(t, t, acc);
+        t = u[c].y - v[c].y;
+        acc = fmaf(t, t, acc);
+        t = u[c].z - v[c].z;
+        acc = fmaf(t, t, acc);
+        t = u[c].w - v[c].w;
+        acc = fmaf(t, t, acc);
+      }
+    }
+    for (; k < a.d; k += 4) {
       const float4 u = __ldg(reinterpret_cast<const float4 *>(xa + k));
       const float4 v = __ldg(reinterpret_cast<const float4 *>(xb + k));
       float t = u.x - v.x;

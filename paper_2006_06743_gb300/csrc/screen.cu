@@ -5,9 +5,10 @@
 // screen it reads a BF16 copy (half the bytes, and a point set that fits in
 // L2 twice as easily) and decides each pair from it wherever the rounding of
 // the copy cannot change the decision (screen_thresholds in gather.cuh).
-// This file makes the copy, rounding each value to the nearest BF16, and an
+// This file makes the copy, rounding each value to the nearest BF16, an
 // upper bound of every row's Euclidean norm, with the maximum over all rows
-// (and, for the tiled form, over each slice of rows).
+// (and, for the tiled form, over each slice of rows), and the squared norm
+// of every copied row (for the tensor-core form).
 #include <cuda_bf16.h>
 
 #include "api_common.cuh"
@@ -37,7 +38,8 @@ __device__ __forceinline__ void block_max_bits(unsigned int v, unsigned int *out
 // small to square in FP32 are covered by the screen's absolute slack.
 __global__ void __launch_bounds__(256) shadow_kernel(const float *x, int64_t ld, int32_t d,
                                                      int64_t n, uint16_t *xb, int64_t ldb,
-                                                     float *nrm, unsigned int *nmax_all) {
+                                                     float *nrm, float *nb2,
+                                                     unsigned int *nmax_all) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -45,16 +47,25 @@ __global__ void __launch_bounds__(256) shadow_kernel(const float *x, int64_t ld,
   for (int64_t i = warp; i < n; i += warps) {
     const float *row = x + i * ld;
     uint16_t *out = xb + i * ldb;
-    float ss = 0.f;
+    float ss = 0.f, sb = 0.f;
     for (int64_t k = lane; k < ldb; k += 32) {
       const float v = k < d ? __ldg(row + k) : 0.f;
-      out[k] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      out[k] = __bfloat16_as_ushort(h);
       ss = fmaf(v, v, ss);
+      const float vb = __bfloat162float(h);
+      sb = fmaf(vb, vb, sb);   // the square of a BF16 value is exact in FP32
     }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFullMask, ss, o);
+    for (int o = 16; o >= 1; o >>= 1) {
+      ss += __shfl_xor_sync(kFullMask, ss, o);
+      sb += __shfl_xor_sync(kFullMask, sb, o);
+    }
     const float bound = sqrtf(ss) * (1.f + 0x1p-11f);
-    if (lane == 0) nrm[i] = bound;
+    if (lane == 0) {
+      nrm[i] = bound;
+      nb2[i] = sb;
+    }
     mx = max(mx, __float_as_uint(bound));
   }
   block_max_bits(mx, nmax_all);
@@ -76,20 +87,21 @@ __global__ void __launch_bounds__(256) slice_max_kernel(const float *nrm, int64_
   }
 }
 
-sng_status make_shadow(const float *x, int64_t ld, int32_t d, int64_t n, Scratch &s,
+sng_status make_shadow(const float *x, int64_t ld, int32_t d, int64_t n, int64_t ldb, Scratch &s,
                        Shadow *out) {
   cudaStream_t st = s.stream;
-  out->ldb = ((int64_t)d + 7) / 8 * 8;
+  out->ldb = ldb > 0 ? ldb : ((int64_t)d + 7) / 8 * 8;
   sng_status rc;
   if ((rc = s.alloc((void **)&out->xb, (size_t)n * out->ldb * 2, "BF16 screen copy")) ||
       (rc = s.alloc((void **)&out->nrm, (size_t)n * 4, "row norm bounds")) ||
+      (rc = s.alloc((void **)&out->nb2, (size_t)n * 4, "squared norms of the copy")) ||
       (rc = s.alloc((void **)&out->nmax, (size_t)(1 + kShadowSlices) * 4, "norm maxima")))
     return rc;
   cudaMemsetAsync(out->nmax, 0, (size_t)(1 + kShadowSlices) * 4, st);
   const int64_t blocks_needed = (n + 7) / 8;
   const int64_t cap = (int64_t)device_sms() * 8;
   const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
-  shadow_kernel<<<grid, 256, 0, st>>>(x, ld, d, n, out->xb, out->ldb, out->nrm,
+  shadow_kernel<<<grid, 256, 0, st>>>(x, ld, d, n, out->xb, out->ldb, out->nrm, out->nb2,
                                       reinterpret_cast<unsigned int *>(out->nmax));
   note_launch();
   cudaError_t e = cudaGetLastError();

@@ -13,10 +13,12 @@ struct Shadow {
   int64_t ldb = 0;
   float *nrm = nullptr;     // n: upper bounds of the rows' Euclidean norms
   float *nmax = nullptr;    // [0] max over all rows, [1 + s] over slice s
+  float *nb2 = nullptr;     // n: squared norms of the copied rows (FP32 sums)
 };
 
-// BF16 copy, norm bounds and their maximum (stream-ordered; scratch from s).
-sng_status make_shadow(const float *x, int64_t ld, int32_t d, int64_t n, Scratch &s,
+// BF16 copy (row stride ldb, 0 = d rounded up to 8), norm bounds, their
+// maximum and the copy's squared norms (stream-ordered; scratch from s).
+sng_status make_shadow(const float *x, int64_t ld, int32_t d, int64_t n, int64_t ldb, Scratch &s,
                        Shadow *out);
 // Maxima of the norm bounds over k slices of `slice` rows into nmax[1..k].
 sng_status shadow_slice_max(const Shadow &sh, int64_t n, int64_t slice, int k, cudaStream_t st);

@@ -41,6 +41,7 @@ class GpuCompute:
     def __init__(self, x, params, x_master=None):
         self.x, self.params, self.x_master = x, params, x_master
         self.simple_degree = params.degree_mode == 2
+        self.last_stats = None      # stats of the last local graph (phase times)
 
     def local_graph(self, lo: int, hi: int) -> LocalGraph:
         import torch
@@ -53,6 +54,7 @@ class GpuCompute:
             return LocalGraph(z, z.clone(), torch.zeros(n, dtype=torch.int32,
                                                         device=self.x.device))
         g = build_graph(self.x, p, x_master=self.x_master)
+        self.last_stats = g["stats"]
         rp = g["row_ptr"]
         counts = rp[lo + 1:hi + 1] - rp[lo:hi]
         rows = torch.arange(lo, hi, device=rp.device, dtype=torch.int32)

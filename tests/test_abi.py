@@ -165,7 +165,7 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
     slice count and one more.  None for BF16 points, similarity metrics or
     every-pair sampling; the flag reaches the parameters."""
     import torch
-    from paper_2006_06743_gb300 import SNG_FLAG_SCREEN16, Params, autotune
+    from paper_2006_06743_gb300 import SNG_FLAG_SCREEN16, SNG_FLAG_SCREEN_MMA, Params, autotune
     monkeypatch.setattr(torch.cuda, "mem_get_info", lambda dev=None: (200 << 30, 280 << 30))
 
     def screened(n, d, dtype=torch.float32, **kw):
@@ -175,7 +175,10 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
         return sc
 
     sc = screened(1_000_000, 64, s=0.001)
-    direct = [c for c in sc if not c.get("tiled")]
+    assert sc[0].get("mma")                      # tensor-core dot products first
+    assert [c for c in sc if c.get("mma")] == [sc[0]]
+    assert not any(c.get("mma") for c in screened(1_000_000, 200, m=100))   # d > 128
+    direct = [c for c in sc if not c.get("tiled") and not c.get("mma")]
     tiled = [c for c in sc if c.get("tiled")]
     assert {c["map_group"] for c in direct} == {4, 8} and {c["map_unroll"] for c in direct} == {2, 4}
     # BF16 copy of 10^6 x 64 = 128 MB: ceil(256 MB / 88 MiB) = 3 -> {3, 4}
@@ -183,6 +186,8 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
     assert {c["map_group"] for c in tiled} == {0, 8}
     p = autotune.apply(Params(eps=1.0, min_pts=5), {"mapping": sc[0]})
     assert p.flags & SNG_FLAG_SCREEN16
+    p = autotune.apply(Params(eps=1.0, min_pts=5), {"mapping": sc[0]})
+    assert p.flags & SNG_FLAG_SCREEN_MMA and p.flags & SNG_FLAG_SCREEN16
     # small point sets: the direct screened gather only
     assert all(not c.get("tiled") for c in screened(100_000, 64, m=100))
     assert screened(1_000_000, 64, dtype=torch.bfloat16, m=1000) == []

@@ -22,12 +22,14 @@ def _graph(sng, xg, p):
     return {k: g[k].cpu().numpy() for k in ("row_ptr", "col", "deg", "core")}, g["stats"]
 
 
-def _check_exact(orc, sng, torch, x, p, m, min_pts, tiled_k=0):
+def _check_exact(orc, sng, torch, x, p, m, min_pts, tiled_k=0, mma=False):
     xg = torch.from_numpy(x).cuda()
     flags = sng.SNG_FLAG_SCREEN16 | (sng.SNG_FLAG_TILED if tiled_k else 0)
+    if mma:
+        flags |= sng.SNG_FLAG_SCREEN_MMA
     q = sng.Params(**{**p.__dict__, "flags": flags, "map_tile": tiled_k})
     g, st = _graph(sng, xg, q)
-    assert st["map_screen"] == 1
+    assert st["map_screen"] == (2 if mma and x.shape[1] <= 128 else 1)
     rp, col, bpairs, _ = orc.build_rows(x, p.eps, p.seed, m, band_rel=BAND_F32)
     np.testing.assert_array_equal(g["row_ptr"], rp)
     np.testing.assert_array_equal(g["col"], col)
@@ -60,7 +62,22 @@ def test_screen_matches_oracle(orc, n, d, group, unroll, tiled_k):
         assert st["map_tiles"] == tiled_k
 
 
-def test_screen_open_pairs_far_from_origin(orc):
+@pytest.mark.parametrize("n,d", [(6000, 64), (4000, 128), (4000, 32), (3000, 60), (5000, 16),
+                                 (3000, 3), (2500, 100), (2000, 200)])
+def test_screen_tensor_cores_match_oracle(orc, n, d):
+    """The tensor-core form (SNG_FLAG_SCREEN_MMA): 2, 4 or 8 k-tiles of 16
+    values per row (d <= 32, 64, 128; beyond that the CUDA-core screen)."""
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=3 * n + d)
+    eps = float(np.float32(0.12 * math.sqrt(d)))
+    m = 90
+    p = sng.Params(eps=eps, min_pts=4, m=m, seed=d + 1)
+    st = _check_exact(orc, sng, torch, x, p, m, 4, mma=True)
+    assert st["kept_edges"] > 0
+
+
+@pytest.mark.parametrize("mma", [False, True])
+def test_screen_open_pairs_far_from_origin(orc, mma):
     """Points offset far from the origin make every norm bound large, so the
     screen certifies little and most pairs are summed again in FP32: the
     result is still the oracle's."""
@@ -69,11 +86,12 @@ def test_screen_open_pairs_far_from_origin(orc):
     x = (datagen.random_points(n, d, seed=3) + 3000.0).astype(np.float32)
     eps = float(np.float32(0.12 * math.sqrt(d)))
     p = sng.Params(eps=eps, min_pts=4, m=m, seed=5)
-    st = _check_exact(orc, sng, torch, x, p, m, 4)
+    st = _check_exact(orc, sng, torch, x, p, m, 4, mma=mma)
     assert st["screen_pairs"] > 0.5 * n * m
 
 
-def test_screen_integer_ties_and_mixed_scales(orc):
+@pytest.mark.parametrize("mma", [False, True])
+def test_screen_integer_ties_and_mixed_scales(orc, mma):
     """Integer coordinates (exact in every format) with eps^2 an integer put
     many pairs exactly on the ball's boundary (kept: closed ball), all of
     them in the reported band; the same points scaled by 2^-40 and 2^40 test
@@ -83,15 +101,16 @@ def test_screen_integer_ties_and_mixed_scales(orc):
     x = datagen.random_points(n, d, seed=7, kind="grid")
     eps = 2.0                                    # eps^2 = 4 = a sum of integer squares
     p = sng.Params(eps=eps, min_pts=3, m=m, seed=9)
-    st = _check_exact(orc, sng, torch, x, p, m, 3)
+    st = _check_exact(orc, sng, torch, x, p, m, 3, mma=mma)
     assert st["band_pairs"] > 0
     for scale in (2.0 ** -40, 2.0 ** 40):
         xs = (x * np.float32(scale)).astype(np.float32)
         ps = sng.Params(eps=float(np.float32(eps * scale)), min_pts=3, m=m, seed=9)
-        _check_exact(orc, sng, torch, xs, ps, m, 3)
+        _check_exact(orc, sng, torch, xs, ps, m, 3, mma=mma)
 
 
-def test_screen_non_finite_rows(orc):
+@pytest.mark.parametrize("mma", [False, True])
+def test_screen_non_finite_rows(orc, mma):
     """Rows holding inf or NaN give unbounded norms, which certify nothing:
     their pairs (and, through the maximum norm, every pair) are decided from
     the FP32 points, as the oracle decides them (a NaN or infinite distance
@@ -104,11 +123,11 @@ def test_screen_non_finite_rows(orc):
     x[400, 15] = -np.inf
     eps = float(np.float32(0.12 * math.sqrt(d)))
     p = sng.Params(eps=eps, min_pts=4, m=m, seed=2)
-    _check_exact(orc, sng, torch, x, p, m, 4)
+    _check_exact(orc, sng, torch, x, p, m, 4, mma=mma)
 
 
-@pytest.mark.parametrize("tiled_k", [0, 3])
-def test_screen_equals_plain_fp32_path(orc, tiled_k):
+@pytest.mark.parametrize("tiled_k,mma", [(0, False), (3, False), (0, True)])
+def test_screen_equals_plain_fp32_path(orc, tiled_k, mma):
     """On a Gaussian mixture shaped like the headline workload (smaller n)
     the screened and the plain FP32 gathers give the same CSR, degrees and
     labels."""
@@ -120,10 +139,11 @@ def test_screen_equals_plain_fp32_path(orc, tiled_k):
     base = dict(eps=eps, min_pts=10, m=500, seed=3)
     plain, _ = _graph(sng, xg, sng.Params(**base))
     flags = sng.SNG_FLAG_SCREEN16 | (sng.SNG_FLAG_TILED if tiled_k else 0)
+    flags |= sng.SNG_FLAG_SCREEN_MMA if mma else 0
     scr, st = _graph(sng, xg, sng.Params(**base, flags=flags, map_tile=tiled_k))
     for k in plain:
         np.testing.assert_array_equal(scr[k], plain[k], err_msg=k)
-    assert st["map_screen"] == 1 and 0 < st["screen_pairs"] < 0.02 * n * 500
+    assert st["map_screen"] == (2 if mma else 1) and 0 < st["screen_pairs"] < 0.02 * n * 500
     rows = np.sort(np.random.default_rng(0).choice(n, 300, replace=False))
     rp, col, _, _ = orc.build_rows(x, eps, 3, 500, band_rel=BAND_F32, rows=rows)
     for k, i in enumerate(rows):
