@@ -403,7 +403,9 @@ def bench_sng(args, w):
                                          ("map_group", "map_unroll", "map_block", "map_passes",
                                           "map_tile")},
                                       "tiled": bool(params.flags & sng.SNG_FLAG_TILED),
-                                      "tiles_per_axis": tiles,
+                                      "tiles_per_axis": stats["map_tiles"],
+                                      "screen": ["none", "bf16 copy", "bf16 copy, tensor cores"]
+                                                [stats["map_screen"]],
                                       "prefetch": bool(params.flags & sng.SNG_FLAG_PREFETCH)},
                    "autotuned": tuned is not None},
         "e2e": {"value": Q * world / (t_e2e * 1e-3), "unit": "queries/s",
