@@ -294,9 +294,11 @@ def bench_sng(args, w):
                         map_tile=args.map_tile)
     if args.tiled:
         params.flags |= sng.SNG_FLAG_TILED
+    if args.screen:
+        params.flags |= sng.SNG_FLAG_SCREEN16 | (sng.SNG_FLAG_SCREEN_MMA if args.screen == 2 else 0)
     tuned = None
     if args.autotune and not (args.map_group or args.map_unroll or args.map_block
-                              or args.map_passes or args.tiled):
+                              or args.map_passes or args.tiled or args.screen):
         from paper_2006_06743_gb300 import autotune
         tuned = autotune.tune(x, params, reps=2, budget_s=args.tune_budget,
                               verbose=args.verbose, force=args.retune)
@@ -855,26 +857,44 @@ def bench_surrogate(args):
     net.standardize(xtr)
     t_train, trace = _timed(lambda: net.train(xtr, ytr, args.train_steps), 1)
     p = sng.Params(eps=eps, min_pts=8, s=0.0005, seed=99, flags=sng.SNG_FLAG_TIMING)
-    g = dict(p_noise=args.p_noise, p_core=args.p_core, core_draw_frac=args.core_frac,
-             noise_draw_frac=args.noise_frac, reweight=bool(args.reweight))
+    gates = {
+        # the configuration as written: confidence in [0.1, 0.9] falls back to
+        # full queries (confident core draws core_frac of them, confident
+        # noise none)
+        "as_written": dict(p_noise=0.1, p_core=0.9, core_draw_frac=0.5,
+                           noise_draw_frac=0.0, reweight=False),
+        # the tuned gate: the same upper threshold, no noise gating (a point
+        # gated as noise loses the draws that attach it to a cluster as a
+        # border point)
+        "tuned": dict(p_noise=args.p_noise, p_core=args.p_core, core_draw_frac=args.core_frac,
+                      noise_draw_frac=args.noise_frac, reweight=bool(args.reweight)),
+    }
     for _ in range(args.warmup):
         sng.cluster(xt, p)
-        net.cluster(xt, p, **g)
+        net.cluster(xt, p, **gates["tuned"])
     p_ms, (plain, pcore, pst) = _timed(lambda: sng.cluster(xt, p, want_core=True), args.steps)
-    s_ms, (lab, core, sst) = _timed(lambda: net.cluster(xt, p, want_core=True, **g), args.steps)
+    res = {}
+    for name, g in gates.items():
+        s_ms, (lab, core, sst) = _timed(lambda: net.cluster(xt, p, want_core=True, **g), args.steps)
+        res[name] = {"gate": g, "ms": s_ms, "speedup_vs_plain": p_ms / s_ms,
+                     "ari_vs_plain": sng.ari(lab, plain),
+                     "core_mask_agreement": float((core == pcore).float().mean().item()),
+                     "queries_issued_frac": sst["queries"] / pst["queries"],
+                     "gated_core": sst["surrogate_core"], "gated_noise": sst["surrogate_noise"],
+                     "phases_ms": sst["ms"]}
+    t = res["tuned"]
     return {"form": "surrogate", "metric": "e2e cluster time, surrogate vs plain",
-            "value": n * m / (s_ms * 1e-3), "unit": "queries/s (nominal n*m)",
-            "ms_surrogate": s_ms, "ms_plain": p_ms, "speedup_vs_plain": p_ms / s_ms,
-            "ari_vs_plain": sng.ari(lab, plain),
-            "core_mask_agreement": float((core == pcore).float().mean().item()),
-            "queries_issued_frac": sst["queries"] / pst["queries"],
-            "gated_core": sst["surrogate_core"], "gated_noise": sst["surrogate_noise"],
-            "phases_ms_surrogate": sst["ms"], "phases_ms_plain": pst["ms"],
-            "train": {"steps": args.train_steps, "seconds": t_train * 1e-3,
+            "value": n * m / (t["ms"] * 1e-3), "unit": "queries/s (nominal n*m)",
+            "ms_surrogate": t["ms"], "ms_plain": p_ms, "speedup_vs_plain": t["speedup_vs_plain"],
+            "ari_vs_plain": t["ari_vs_plain"], "core_mask_agreement": t["core_mask_agreement"],
+            "queries_issued_frac": t["queries_issued_frac"], "gates": res,
+            "phases_ms_plain": pst["ms"],
+            "train": {"steps": args.train_steps, "siblings": args.siblings,
+                      "seconds": t_train * 1e-3,
                       "loss_first": float(trace[:50].mean()), "loss_last": float(trace[-200:].mean()),
                       "label_seconds": t_label},
-            "config": {"workload": f"mixture-n{n}-d{d}-k200", "m": m, "eps": eps, "min_pts": 8,
-                       **g}, "dtype": "f32", "steps": args.steps}
+            "config": {"workload": f"mixture-n{n}-d{d}-k200", "m": m, "eps": eps, "min_pts": 8},
+            "dtype": "f32", "steps": args.steps}
 
 
 def bench_balls(args):
@@ -1065,6 +1085,8 @@ def main():
     ap.add_argument("--map-passes", type=int, default=0)
     ap.add_argument("--map-tile", type=int, default=0)
     ap.add_argument("--tiled", type=int, default=0, help="1: the L2-tiled gather")
+    ap.add_argument("--screen", type=int, default=0, choices=[0, 1, 2],
+                    help="1: certified BF16 screen of the FP32 points; 2: its tensor-core form")
     ap.add_argument("--autotune", type=int, default=1, help="1: tune the gather mapping first")
     ap.add_argument("--degree-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0 undirected multigraph, 1 out-degree, 2 distinct neighbours")
@@ -1093,8 +1115,8 @@ def main():
     ap.add_argument("--siblings", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--p-noise", type=float, default=0.0)
-    ap.add_argument("--p-core", type=float, default=0.95)
-    ap.add_argument("--core-frac", type=float, default=0.5)
+    ap.add_argument("--p-core", type=float, default=0.9)
+    ap.add_argument("--core-frac", type=float, default=0.75)
     ap.add_argument("--noise-frac", type=float, default=0.0)
     ap.add_argument("--reweight", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

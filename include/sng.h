@@ -407,6 +407,10 @@ typedef struct {
     float core_draw_frac;   /* (0, 1] */
     float noise_draw_frac;  /* [0, 1] */
     int32_t reweight;       /* 0 or 1 */
+    int32_t by_degree;      /* 0: gated points are declared core / not core;
+                               1: the gate sets only their draw budgets and
+                               every point keeps the degree test (with
+                               reweight, an unbiased estimate of its degree) */
 } sng_gate;
 
 /*

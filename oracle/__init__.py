@@ -358,7 +358,7 @@ GATE_DEG_UNIT = 16   # degree units per kept draw when the gate reweights
 
 def gate_decisions(prob, m: int, p_noise: float, p_core: float, core_draw_frac: float,
                    noise_draw_frac: float = 0.0, reweight: bool = False,
-                   deg_unit: int = GATE_DEG_UNIT):
+                   deg_unit: int = GATE_DEG_UNIT, by_degree: bool = False):
     """The surrogate gate's rule (an extension; the paper has no learned part):
     a point whose core probability is below ``p_noise`` is declared not core
     and draws the first ceil(noise_draw_frac * m) partners of its stream; one
@@ -368,6 +368,9 @@ def gate_decisions(prob, m: int, p_noise: float, p_core: float, core_draw_frac: 
     values the caller passes.  With ``reweight`` each kept draw of a point
     that drew m_i partners counts round(deg_unit * m / m_i) degree units (an
     unbiased estimate of its full count; deg_unit when m_i = 0).
+
+    With ``by_degree`` the gate sets only the draw budgets (and weights):
+    every point keeps the degree test, so nothing is forced.
 
     Returns forced (uint8: 0 by degree, 1 core, 2 not core), draws per point
     (int32) and the per-point weights (int32, or None without reweighting).
@@ -382,6 +385,9 @@ def gate_decisions(prob, m: int, p_noise: float, p_core: float, core_draw_frac: 
     m_noise = int(math.ceil(float(np.float32(noise_draw_frac)) * m))
     draws = {0: m, 1: m_core, 2: m_noise}
     m_row = np.array([draws[int(f)] for f in range(3)], dtype=np.int32)[forced]
+    cls = forced
+    if by_degree:
+        forced = np.zeros_like(forced)
     if not reweight:
         return forced, m_row, None
 
@@ -391,7 +397,7 @@ def gate_decisions(prob, m: int, p_noise: float, p_core: float, core_draw_frac: 
         return int(math.floor(deg_unit * m / mi + 0.5))
 
     w = np.array([weight(draws[f]) for f in range(3)], dtype=np.int32)
-    return forced, m_row, w[forced]
+    return forced, m_row, w[cls]
 
 
 def dbscan_bruteforce(x, eps: float, min_pts_db: int) -> tuple[np.ndarray, np.ndarray]:

@@ -97,7 +97,7 @@ class sng_mlp_config(ctypes.Structure):
 class sng_gate(ctypes.Structure):
     _fields_ = [("p_noise", ctypes.c_float), ("p_core", ctypes.c_float),
                 ("core_draw_frac", ctypes.c_float), ("noise_draw_frac", ctypes.c_float),
-                ("reweight", ctypes.c_int32)]
+                ("reweight", ctypes.c_int32), ("by_degree", ctypes.c_int32)]
 
 
 class sng_graph(ctypes.Structure):

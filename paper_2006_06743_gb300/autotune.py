@@ -78,9 +78,10 @@ def candidates(x, p: Params) -> list[dict]:
         ldb = -(-d // 8) * 8
         xb_bytes = n * ldb * 2
         if xb_bytes < 0.25 * free:
-            if d <= 128:    # tensor-core dot products (16, 32 or 64 values per k-tile set)
-                out.append(dict(map_group=0, map_unroll=0, map_block=256, map_passes=0,
-                                prefetch=False, screen=True, mma=True))
+            if d <= 128:    # tensor-core dot products; map_unroll = blocks per SM budgeted
+                for u in ((0, 4, 2) if d <= 64 else (0, 3)):
+                    out.append(dict(map_group=0, map_unroll=u, map_block=256, map_passes=0,
+                                    prefetch=False, screen=True, mma=True))
             for g in sorted({max(1, gb // 2), gb}):
                 for u in (2, 4):
                     out.append(dict(map_group=g, map_unroll=u, map_block=256, map_passes=0,

@@ -615,9 +615,11 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     gb->mma = true;
     gb->map.group = 16;
     gb->map.nch = mma_kt;
-    gb->map.unroll = 0;
-    if (!launch_gather_mma(mma_kt, ga, r.row_end - r.row_begin, st))
-      return fail(SNG_EINTERNAL, "tensor-core gather not compiled for d = %d", p->d);
+    // map_unroll selects the register budget (resident blocks per SM)
+    gb->map.unroll = p->map_unroll;
+    if (!launch_gather_mma(mma_kt, p->map_unroll, ga, r.row_end - r.row_begin, st))
+      return fail(SNG_EINVAL, "no tensor-core gather for d = %d with map_unroll = %d", p->d,
+                  p->map_unroll);
     note_launch();
   } else if (tiled) {
     // done by the tiled form

@@ -81,8 +81,8 @@ __device__ __forceinline__ void mma_thresholds(const GatherArgs &a, float nrm_i,
 // the stage: it hashes it, loads its partner's squared norm, receives its dot
 // product from the lanes that hold that MMA row and decides it, so the keep
 // bits come out of one ballot in draw order.
-template <int KT>
-__global__ void __launch_bounds__(256, KT <= 4 ? 3 : 2) gather_mma_kernel(GatherArgs a) {
+template <int KT, int MINB>
+__global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int g = lane >> 2, q = lane & 3;
@@ -110,11 +110,13 @@ __global__ void __launch_bounds__(256, KT <= 4 ? 3 : 2) gather_mma_kernel(Gather
     mma_thresholds(a, __ldg(a.nrm + i), nrm_pmax, keep_thr, drop_thr);
     int cnt = 0;
     int jb = 0;
+    // draws past the row's count read row 0 and decide nothing
+    auto draw = [&](int j) -> int32_t {
+      return j < mi ? (a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm)) : 0;
+    };
+    int32_t p = draw(lane);
     for (; jb < mi; jb += 32) {
-      const int j = jb + lane;
-      const bool live = j < mi;
-      const int32_t p = live ? (a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm))
-                             : 0;   // past the row's draws: row 0 is read, nothing is decided
+      const bool live = jb + lane < mi;
       const float nbp = __ldg(a.nb2 + p);
       // the stage's 32 partner rows, four per lane group, all in flight:
       // group t holds draws 8 t .. 8 t + 7 (row g of it: draw 8 t + g)
@@ -124,6 +126,8 @@ __global__ void __launch_bounds__(256, KT <= 4 ? 3 : 2) gather_mma_kernel(Gather
         const int32_t pt = __shfl_sync(kFullMask, p, 8 * t + g);
         load_slice<KT>(X + (int64_t)pt * a.ld, q, r[t]);
       }
+      // the next stage's partners, hashed while these rows are on their way
+      const int32_t p_next = draw(jb + 32 + lane);
       float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int ks = 0; ks < KT; ++ks) {
@@ -151,6 +155,7 @@ __global__ void __launch_bounds__(256, KT <= 4 ? 3 : 2) gather_mma_kernel(Gather
       const uint32_t word = __ballot_sync(kFullMask, keep);
       if (lane == 0) __stcs(a.bitmask + (int64_t)i * a.W + (jb >> 5), word);
       cnt += __popc(word);
+      p = p_next;
     }
     // words past this row's draws (per-row draw counts) are zero
     for (int w = (jb >> 5) + lane; w < a.W; w += 32) __stcs(a.bitmask + (int64_t)i * a.W + w, 0u);
@@ -174,34 +179,34 @@ int mma_tiles_for(int d) {
   return 0;
 }
 
-template <int KT>
-static int occ_mma() {
-  int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, gather_mma_kernel<KT>, 256, 0) !=
-      cudaSuccess)
-    return 1;
-  return blocks > 0 ? blocks : 1;
-}
-
-bool launch_gather_mma(int kt, const GatherArgs &a, int64_t rows, cudaStream_t st) {
-  const int sms = device_sms();
-  int per_sm;
-  switch (kt) {
-    case 2: per_sm = occ_mma<2>(); break;
-    case 4: per_sm = occ_mma<4>(); break;
-    case 8: per_sm = occ_mma<8>(); break;
-    default: return false;
-  }
+template <int KT, int MINB>
+static void launch_kt(const GatherArgs &a, int64_t rows, cudaStream_t st) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_mma_kernel<KT, MINB>, 256,
+                                                    0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
   const int64_t need = (rows + 7) / 8;
-  int64_t grid = (int64_t)sms * per_sm;
+  int64_t grid = (int64_t)device_sms() * per_sm;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  switch (kt) {
-    case 2: gather_mma_kernel<2><<<(int)grid, 256, 0, st>>>(a); break;
-    case 4: gather_mma_kernel<4><<<(int)grid, 256, 0, st>>>(a); break;
-    case 8: gather_mma_kernel<8><<<(int)grid, 256, 0, st>>>(a); break;
+  gather_mma_kernel<KT, MINB><<<(int)grid, 256, 0, st>>>(a);
+}
+
+bool launch_gather_mma(int kt, int minb, const GatherArgs &a, int64_t rows, cudaStream_t st) {
+  // minb: resident blocks per SM the register budget is set for (0: 3 for
+  // up to 64 values per row, 2 above)
+  if (minb == 0) minb = kt <= 4 ? 3 : 2;
+  switch (kt * 10 + minb) {
+    case 22: launch_kt<2, 2>(a, rows, st); return true;
+    case 23: launch_kt<2, 3>(a, rows, st); return true;
+    case 24: launch_kt<2, 4>(a, rows, st); return true;
+    case 42: launch_kt<4, 2>(a, rows, st); return true;
+    case 43: launch_kt<4, 3>(a, rows, st); return true;
+    case 44: launch_kt<4, 4>(a, rows, st); return true;
+    case 82: launch_kt<8, 2>(a, rows, st); return true;
+    case 83: launch_kt<8, 3>(a, rows, st); return true;
+    default: return false;
   }
-  return true;
 }
 
 }  // namespace sng

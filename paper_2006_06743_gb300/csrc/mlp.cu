@@ -146,6 +146,7 @@ struct GateArgs {
   int32_t m, m_core, m_noise;  // draws for uncertain / confident-core / -noise points
   int32_t w_full, w_core, w_noise;  // degree weight per kept draw of each class
   uint8_t *forced;      // nullable: 2 noise, 1 core, 0 uncertain
+  int32_t by_degree;    // 1: gated points keep the degree test (forced stays 0)
   int32_t *m_row;       // nullable
   int32_t *w_row;       // nullable
   unsigned long long *counters;  // nullable: [0] queries [1] core [2] noise
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(128, 1) mlp_gate_kernel(GateArgs a) {
         wi = a.w_core;
         ++nc;
       }
-      a.forced[i] = f;
+      a.forced[i] = a.by_degree ? 0 : f;
       a.m_row[i] = mi;
       if (a.w_row) a.w_row[i] = wi;
       q += (unsigned long long)mi;
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(128) mlp_gate_mma_kernel(GateArgs a) {
             wi = a.w_core;
             ++nc;
           }
-          a.forced[i] = f;
+          a.forced[i] = a.by_degree ? 0 : f;
           a.m_row[i] = mi;
           if (a.w_row) a.w_row[i] = wi;
           nq += (unsigned long long)mi;
@@ -817,6 +818,7 @@ sng_status sng_mlp_predict(const float *x, int64_t n, const sng_mlp_config *cfg,
              1,
              1,
              nullptr,
+             0,
              nullptr,
              nullptr,
              nullptr};
@@ -848,6 +850,7 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
   if (!(gate->noise_draw_frac >= 0.f && gate->noise_draw_frac <= 1.f))
     return fail(SNG_EINVAL, "noise_draw_frac must be in [0, 1]");
   if (gate->reweight != 0 && gate->reweight != 1) return fail(SNG_EINVAL, "reweight is 0 or 1");
+  if (gate->by_degree != 0 && gate->by_degree != 1) return fail(SNG_EINVAL, "by_degree is 0 or 1");
   if (params->flags & SNG_FLAG_NO_SYNC)
     return fail(SNG_EINVAL, "SNG_FLAG_NO_SYNC is for sng_cluster only");
   if (params->metric != SNG_METRIC_L2)
@@ -894,6 +897,7 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
               weight(m_core),
               weight(m_noise),
               forced,
+              gate->by_degree,
               m_row,
               w_row,
               gcnt};

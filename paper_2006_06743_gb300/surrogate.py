@@ -220,8 +220,10 @@ class Surrogate:
 
     def cluster(self, x, p: Params, p_noise: float = 0.0, p_core: float = 0.95,
                 core_draw_frac: float = 0.5, noise_draw_frac: float = 0.0,
-                reweight: bool = False, want_core: bool = False):
-        """Algorithm 1 gated by this network; returns (labels[, core], stats)."""
+                reweight: bool = False, want_core: bool = False, by_degree: bool = False):
+        """Algorithm 1 gated by this network; returns (labels[, core], stats).
+        ``by_degree``: the gate only sets draw budgets; every point keeps the
+        degree test (use with ``reweight``)."""
         import torch
         n, d, ld = _rows(x, SNG_F32)
         labels = torch.empty(n, dtype=torch.int32, device=x.device)
@@ -231,6 +233,7 @@ class Surrogate:
         g = sng_gate()
         g.p_noise, g.p_core = p_noise, p_core
         g.core_draw_frac, g.noise_draw_frac, g.reweight = core_draw_frac, noise_draw_frac, int(reweight)
+        g.by_degree = int(by_degree)
         _check(lib().sng_cluster_surrogate(
             x.data_ptr(), ctypes.byref(p.to_c(n, d, ld, SNG_F32)), ctypes.byref(c),
             self.params.data_ptr(), ctypes.byref(g), labels.data_ptr(),

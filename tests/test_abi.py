@@ -175,8 +175,8 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
         return sc
 
     sc = screened(1_000_000, 64, s=0.001)
-    assert sc[0].get("mma")                      # tensor-core dot products first
-    assert [c for c in sc if c.get("mma")] == [sc[0]]
+    mma = [c for c in sc if c.get("mma")]        # tensor-core dot products first
+    assert sc[:len(mma)] == mma and {c["map_unroll"] for c in mma} == {0, 4, 2}
     assert not any(c.get("mma") for c in screened(1_000_000, 200, m=100))   # d > 128
     direct = [c for c in sc if not c.get("tiled") and not c.get("mma")]
     tiled = [c for c in sc if c.get("tiled")]

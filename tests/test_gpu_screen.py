@@ -62,16 +62,19 @@ def test_screen_matches_oracle(orc, n, d, group, unroll, tiled_k):
         assert st["map_tiles"] == tiled_k
 
 
-@pytest.mark.parametrize("n,d", [(6000, 64), (4000, 128), (4000, 32), (3000, 60), (5000, 16),
-                                 (3000, 3), (2500, 100), (2000, 200)])
-def test_screen_tensor_cores_match_oracle(orc, n, d):
+@pytest.mark.parametrize("n,d,budget", [(6000, 64, 0), (6000, 64, 2), (6000, 64, 4),
+                                        (4000, 128, 0), (4000, 128, 3), (4000, 32, 0),
+                                        (4000, 32, 4), (3000, 60, 0), (5000, 16, 0),
+                                        (3000, 3, 0), (2500, 100, 0), (2000, 200, 0)])
+def test_screen_tensor_cores_match_oracle(orc, n, d, budget):
     """The tensor-core form (SNG_FLAG_SCREEN_MMA): 2, 4 or 8 k-tiles of 16
-    values per row (d <= 32, 64, 128; beyond that the CUDA-core screen)."""
+    values per row (d <= 32, 64, 128; beyond that the CUDA-core screen), with
+    registers budgeted for 2, 3 or 4 resident blocks per SM (map_unroll)."""
     torch, sng = need_gpu()
     x = datagen.random_points(n, d, seed=3 * n + d)
     eps = float(np.float32(0.12 * math.sqrt(d)))
     m = 90
-    p = sng.Params(eps=eps, min_pts=4, m=m, seed=d + 1)
+    p = sng.Params(eps=eps, min_pts=4, m=m, seed=d + 1, map_unroll=budget)
     st = _check_exact(orc, sng, torch, x, p, m, 4, mma=True)
     assert st["kept_edges"] > 0
 

