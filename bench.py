@@ -551,7 +551,10 @@ def _timed(fn, reps: int):
 def bench_bf16(args):
     """BF16 form: n = 5,000,000 unit-norm vectors in d = 128 (1000 centres on
     the sphere, per-coordinate noise sigma, renormalised); s = 0.0002 (m =
-    1000); eps = 0.6; MinPts = 8.  Plain FP32 on the same points beside it."""
+    1000); eps = 0.6; MinPts = 8.  Beside it, on the same points: the plain
+    FP32 form (FP32 rows read by the gather) and the FP32 form with the
+    certified BF16 screen (which reads a BF16 copy and keeps every FP64
+    decision)."""
     import torch
 
     import paper_2006_06743_gb300 as sng
@@ -562,20 +565,25 @@ def bench_bf16(args):
     del x
     xb = xf.to(torch.bfloat16)
     p = sng.Params(eps=0.6, min_pts=8, s=0.0002, seed=args.seed, flags=sng.SNG_FLAG_TIMING)
-    pf, pb = p, p
+    pf = pb = ps = p
     tuned = {}
     if args.autotune:
         from paper_2006_06743_gb300 import autotune
         tf = autotune.tune(xf, p, reps=1, budget_s=args.tune_budget, force=args.retune,
+                           verbose=args.verbose, screen=False)
+        ts = autotune.tune(xf, p, reps=1, budget_s=args.tune_budget, force=args.retune,
                            verbose=args.verbose)
         tb = autotune.tune(xb, p, x_master=xf, reps=1, budget_s=args.tune_budget,
                            force=args.retune, verbose=args.verbose)
-        pf, pb = autotune.apply(p, tf), autotune.apply(p, tb)
-        tuned = {"fp32": tf.get("mapping"), "bf16": tb.get("mapping")}
+        pf, ps, pb = autotune.apply(p, tf), autotune.apply(p, ts), autotune.apply(p, tb)
+        tuned = {"fp32": tf.get("mapping"), "fp32_screened": ts.get("mapping"),
+                 "bf16": tb.get("mapping")}
     for _ in range(args.warmup):
         sng.cluster(xf, pf)
+        sng.cluster(xf, ps)
         sng.cluster(xb, pb, x_master=xf)
     f_ms, (lf, sf) = _timed(lambda: sng.cluster(xf, pf), args.steps)
+    s_ms, (ls, ss) = _timed(lambda: sng.cluster(xf, ps), args.steps)
     b_ms, (lb, sb) = _timed(lambda: sng.cluster(xb, pb, x_master=xf), args.steps)
     # edge-decision error of the BF16 form against FP64: the FP32 form's
     # decisions equal the FP64 ones on every pair (guard band + FP64
@@ -603,7 +611,10 @@ def bench_bf16(args):
     return {"form": "bf16", "metric": "sampled eps-queries/s, BF16 vs FP32 form",
             "value": Q / (b_ms * 1e-3), "unit": "queries/s", "fp32_value": Q / (f_ms * 1e-3),
             "speedup_vs_fp32": f_ms / b_ms, "ms_bf16": b_ms, "ms_fp32": f_ms,
-            "ari_bf16_vs_fp32": sng.ari(lb, lf), "edge_decision_error_vs_fp64": edge_error,
+            "ms_fp32_screened": s_ms, "speedup_vs_fp32_screened": s_ms / b_ms,
+            "ari_bf16_vs_fp32": sng.ari(lb, lf),
+            "fp32_screened_labels_equal_fp32": bool(torch.equal(ls, lf)),
+            "edge_decision_error_vs_fp64": edge_error,
             "roofline_bf16": {"achieved": alg_b / (sb["ms"]["gather"] * 1e-3) / 1e9, "peak": peak,
                               "frac": alg_b / (sb["ms"]["gather"] * 1e-3) / 1e9 / peak,
                               "kernel_ms": sb["ms"]["gather"], "peak_kind": kind},
@@ -985,6 +996,8 @@ def run_extensions(args) -> dict:
     r = bench_bf16(a)
     out["bf16"] = {"workload": r["config"]["workload"], "ms_bf16": r["ms_bf16"],
                    "ms_fp32": r["ms_fp32"], "speedup_vs_fp32": r["speedup_vs_fp32"],
+                   "ms_fp32_screened": r["ms_fp32_screened"],
+                   "speedup_vs_fp32_screened": r["speedup_vs_fp32_screened"],
                    "ari_vs_fp32": r["ari_bf16_vs_fp32"],
                    "edge_decision_error_vs_fp64": r["edge_decision_error_vs_fp64"],
                    "seconds": time.perf_counter() - t0}

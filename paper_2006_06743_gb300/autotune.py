@@ -53,7 +53,7 @@ def _default_group(d: int, vec: int) -> int:
     return g
 
 
-def candidates(x, p: Params) -> list[dict]:
+def candidates(x, p: Params, screen: bool = True) -> list[dict]:
     import torch
     n, d = x.shape
     esize = 2 if x.dtype == torch.bfloat16 else 4
@@ -72,7 +72,7 @@ def candidates(x, p: Params) -> list[dict]:
     # the certified BF16 screen of FP32 points (Euclidean, hashed draws): the
     # gather reads a BF16 copy (2 bytes per value of scratch), directly or
     # tiled with the slice count of the copy's size
-    if esize == 4 and not p.metric and p.sample_mode == 0:
+    if screen and esize == 4 and not p.metric and p.sample_mode == 0:
         free = torch.cuda.mem_get_info(x.device)[0] if x.is_cuda else 0
         gb = _default_group(d, 8)
         ldb = -(-d // 8) * 8
@@ -148,11 +148,13 @@ def _time(x, p: Params, reps: int, x_master=None) -> float:
 
 
 def tune(x, p: Params, x_master=None, reps: int = 3, budget_s: float = 60.0,
-         cache: str | None = None, force: bool = False, verbose: bool = False) -> dict:
+         cache: str | None = None, force: bool = False, verbose: bool = False,
+         screen: bool = True) -> dict:
     """Fastest gather mapping for (x, p); returns the Params overrides and
-    the timing table.  Results are cached per shape bucket."""
+    the timing table.  Results are cached per shape bucket.  ``screen``
+    False leaves out the BF16 screen of FP32 points (the plain FP32 form)."""
     path = _cache_path(cache)
-    key = key_for(x, p)
+    key = key_for(x, p) + ("" if screen else "-noscreen")
     table = {}
     if os.path.exists(path):
         try:
@@ -166,7 +168,7 @@ def tune(x, p: Params, x_master=None, reps: int = 3, budget_s: float = 60.0,
     base["flags"] = base.get("flags", 0) | SNG_FLAG_TIMING
     results = []
     t_start = time.perf_counter()
-    for cand in candidates(x, p):
+    for cand in candidates(x, p, screen=screen):
         if time.perf_counter() - t_start > budget_s:
             break
         q = _params_for(base, cand)
