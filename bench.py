@@ -136,6 +136,9 @@ CAPTURED_TRAFFIC = {
     ("mixture-n1M-d64",
      "tile_partition_kernel + 36 x tile_test_kernel<float, 4, 4, 4, 2, 1, 1>"):
         21_680_128 + 8_046_274_048 + 11_679_285_760 + 172_615_680,
+    # the tensor-core screen: one gather_mma_kernel launch
+    # (profiles/gather_mma_mixture-n1M-d64.md)
+    ("mixture-n1M-d64", "gather_mma_kernel<4, 3>"): 51_708_475_392 + 444_700_928,
 }
 
 
@@ -184,7 +187,7 @@ def gather_kernel_name_and_bytes(stats: dict, n: int, d: int, m: int) -> tuple[s
         kt = stats["map_nch"]
         row = 16 * kt * 2
         byts = n * m * (row + 4) + n * (row + 8) + common
-        name = f"shadow_kernel + gather_mma_kernel<{kt}>"
+        name = f"gather_mma_kernel<{kt}, {stats['map_unroll'] or (3 if kt <= 4 else 2)}>"
     else:
         esize, vec = (2, 8) if screen else (4, 4)
         row = (-(-d // 8) * 8 if screen else d) * esize
@@ -200,6 +203,8 @@ def gather_kernel_name_and_bytes(stats: dict, n: int, d: int, m: int) -> tuple[s
                     f"{stats['map_nch']}, {stats['map_unroll']}, 0, {int(full)}, 0>")
         if screen:
             name = "shadow_kernel + " + ("slice_max_kernel + " if tiles else "") + name
+    # (kernel_ms is the whole gather phase: with the screen it includes
+    # shadow_kernel, 0.15 ms at the headline)
     if screen:
         row = (16 * stats["map_nch"] if screen == 2 else -(-d // 8) * 8) * 2
         byts += n * (d * 4 + row + 12)                   # the copy: read FP32, write BF16
