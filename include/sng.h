@@ -359,9 +359,12 @@ typedef struct {
     uint64_t seed;        /* batch rows drawn with replacement by the hash    */
     int32_t sequential;   /* 1: batch b of step t takes rows (t*batch + b) mod n
                              in order instead of hashed draws                 */
-    int32_t fp32_activations; /* inference: 0 = tensor cores (FP16 activations at
-                             the MMA inputs, FP32 accumulation); 1 = CUDA cores
-                             with FP32 activations                           */
+    int32_t fp32_activations; /* inference: 0 = tensor cores through warp-level
+                             mma.sync (FP16 activations at the MMA inputs, FP32
+                             accumulation); 1 = CUDA cores with FP32
+                             activations; 2 = tensor cores through tcgen05.mma
+                             (same FP16 operands, FP32 accumulators in tensor
+                             memory, 128 points per CTA)                      */
 } sng_mlp_config;
 
 /* Entries of the parameter vector, or -1 for an unsupported shape. */

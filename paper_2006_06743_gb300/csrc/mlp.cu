@@ -135,7 +135,7 @@ __device__ __forceinline__ float forward_point(const float *s, const float *xrow
 // --------------------------------------------------------------- inference
 
 struct GateArgs {
-  int32_t fp32_activations;   // 1: CUDA-core path with FP32 activations
+  int32_t fp32_activations;   // 0: mma.sync, 1: CUDA cores with FP32 activations, 2: tcgen05
   const float *x;
   int64_t ld;
   int64_t n;
@@ -562,6 +562,328 @@ __global__ void col_finish_kernel(const double *acc, int64_t n, int d, float *me
   stdv[k] = (float)sd;
 }
 
+// ------------------------------------------ inference on tcgen05 tensor cores
+//
+// The same two dense layers with the fifth-generation tensor-core
+// instructions: a CTA of 8 warps pushes 128 points at a time through the
+// network.  One thread issues tcgen05.mma (M = 128 points, N = 128 hidden
+// units, K = 16 per instruction, FP16 operands from shared memory, FP32
+// accumulators in tensor memory); the layer-1 accumulators are read back with
+// tcgen05.ld (warps w and w + 4 own TMEM lanes 32 (w % 4) .. + 31, i.e. those
+// points, and split the columns), take bias + GELU,
+// are rounded to FP16 and written to shared memory as layer 2's A operand;
+// layer 2's accumulators take bias + GELU and the output unit in registers.
+//
+// Shared-memory operands use the canonical K-major layout without swizzle:
+// the matrix is tiled by "core matrices" of 8 rows x 8 FP16 values (16
+// bytes per row, 128 bytes each), stored [row group][k group][8 rows][16 B],
+// so the descriptor's leading byte offset (between core matrices adjacent
+// along K) is 128 and its stride byte offset (between 8-row groups) is
+// (K / 8) * 128.  A k-step of 16 values advances the start address by two
+// core matrices (256 bytes).
+//
+// Instruction descriptor (kind::f16): D format F32 (bit 4), A and B FP16
+// (format 0, K-major), N >> 3 in bits 17-22, M >> 4 in bits 24-28.  Shared
+// memory descriptor: start address >> 4 in bits 0-13, leading byte offset >>
+// 4 in bits 16-29, stride byte offset >> 4 in bits 32-45, version 1 in bits
+// 46-47, no swizzle (bits 61-63 zero).
+//
+// Every wait is bounded: a tensor-core completion that does not arrive in
+// time sets an error bit in counters[3] (the caller reports it), and the
+// kernel still frees its tensor memory before returning.
+
+constexpr int kTcM = 128;            // points per tile
+constexpr int kTcCols = 256;         // TMEM columns: layer 1 [0, 128), layer 2 [128, 256)
+constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+constexpr uint32_t kTcWaitLimit = 1u << 26;
+
+template <int KT1>
+struct TcSmem {
+  static constexpr int k1 = 16 * KT1;
+  static constexpr size_t xa = 0;                                  // half [128][k1]
+  static constexpr size_t w1 = xa + 2 * kTcM * k1;                 // half [128][k1]
+  static constexpr size_t h1 = w1 + 2 * kH * k1;                   // half [128][128]
+  static constexpr size_t w2 = h1 + 2 * kTcM * kH;                 // half [128][128]
+  static constexpr size_t fp = w2 + 2 * kH * kH;                   // float params
+  static constexpr size_t fp_count = 3 * kH + 4 + 2 * k1;          // b1 b2 w3 b3 pad mean istd
+  static constexpr size_t zp = (fp + 4 * fp_count + 15) / 16 * 16;   // float [128] partial sums
+  static constexpr size_t bar = zp + 4 * kTcM;                     // mbarrier (8 B)
+  static constexpr size_t taddr = bar + 8;                         // TMEM base (4 B)
+  static constexpr size_t bytes = taddr + 8 + 1024;                // + alignment slack
+};
+
+// Byte offset of element (r, k) in the canonical K-major no-swizzle layout of
+// a matrix with K columns.
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// Waits for the barrier's phase `parity` to complete; false after the bound.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kTcWaitLimit; ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane each).
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+template <int KT1>
+__global__ void __launch_bounds__(256, 2) mlp_gate_tc05_kernel(GateArgs a) {
+  using L = TcSmem<KT1>;
+  constexpr int K1 = L::k1;
+  extern __shared__ unsigned char smem_dyn[];
+  // 1024-byte aligned base for the operand tiles
+  unsigned char *sm = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  float *fp = reinterpret_cast<float *>(sm + L::fp);
+  float *b1s = fp, *b2s = fp + kH, *w3s = fp + 2 * kH, *b3s = fp + 3 * kH;
+  float *means = fp + 3 * kH + 4, *istd = means + K1;
+  const uint32_t bar = smem_u32(sm + L::bar);
+  uint32_t *taddr_slot = reinterpret_cast<uint32_t *>(sm + L::taddr);
+  const int d = a.d;
+  const MlpOff o = mlp_off(d);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // weights, FP16-rounded, in the canonical layout (B operands: rows = units)
+  for (int t = threadIdx.x; t < kH * K1; t += blockDim.x) {
+    const int j = t / K1, k = t % K1;
+    const float w = k < d ? a.P[o.w1 + (int64_t)j * d + k] : 0.f;
+    *reinterpret_cast<__half *>(sm + L::w1 + kmajor_off(j, k, K1)) = __float2half_rn(w);
+  }
+  for (int t = threadIdx.x; t < kH * kH; t += blockDim.x) {
+    const int j = t / kH, k = t % kH;
+    *reinterpret_cast<__half *>(sm + L::w2 + kmajor_off(j, k, kH)) =
+        __float2half_rn(a.P[o.w2 + (int64_t)j * kH + k]);
+  }
+  for (int t = threadIdx.x; t < kH; t += blockDim.x) {
+    b1s[t] = h16(a.P[o.b1 + t]);
+    b2s[t] = h16(a.P[o.b2 + t]);
+    w3s[t] = h16(a.P[o.w3 + t]);
+  }
+  for (int k = threadIdx.x; k < K1; k += blockDim.x) {
+    means[k] = k < d ? a.P[o.mean + k] : 0.f;
+    istd[k] = k < d ? 1.f / a.P[o.std + k] : 0.f;
+  }
+  if (threadIdx.x == 0) {
+    b3s[0] = h16(a.P[o.b3]);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(taddr_slot)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *taddr_slot;
+  // warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31 (points) and split
+  // the 128 columns of each layer between them
+  const int quarter = warp & 3, half = warp >> 2;
+  const uint32_t t_lanes = (uint32_t)(quarter * 32) << 16;
+  float *zpart = reinterpret_cast<float *>(sm + L::zp);
+  const uint32_t sx = smem_u32(sm + L::xa), sw1 = smem_u32(sm + L::w1);
+  const uint32_t sh1 = smem_u32(sm + L::h1), sw2 = smem_u32(sm + L::w2);
+  uint32_t parity = 0;
+  bool ok = true;
+  unsigned long long nq = 0, nc = 0, nn = 0;
+
+  for (int64_t base = (int64_t)blockIdx.x * kTcM; base < a.n && ok; base += (int64_t)gridDim.x * kTcM) {
+    // standardised inputs of 128 points, FP16 (zero past n and past d)
+    for (int t = threadIdx.x; t < kTcM * K1; t += blockDim.x) {
+      const int r = t / K1, k = t % K1;
+      const int64_t i = base + r;
+      const float v = (i < a.n && k < d) ? (a.x[i * a.ld + k] - means[k]) * istd[k] : 0.f;
+      *reinterpret_cast<__half *>(sm + L::xa + kmajor_off(r, k, K1)) = __float2half_rn(v);
+    }
+    // make the generic-proxy writes visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int ks = 0; ks < KT1; ++ks)
+        tc_mma(tbase, smem_desc(sx + 256 * ks, 128, (K1 / 8) * 128),
+               smem_desc(sw1 + 256 * ks, 128, (K1 / 8) * 128), ks > 0);
+      tc_commit(bar);
+    }
+    ok = __syncthreads_and(tc_wait(bar, parity) ? 1 : 0) != 0;   // uniform in the block
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      // layer 1: bias + GELU -> FP16 hidden activations (A operand of layer 2)
+      const int r = quarter * 32 + lane;
+#pragma unroll 1
+      for (int c = 2 * half; c < 2 * half + 2; ++c) {
+        float v[32];
+        tc_ld32(tbase + t_lanes + (uint32_t)(32 * c), v);
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+          __align__(16) __half hv[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int col = 32 * c + 8 * g8 + e;
+            hv[e] = __float2half_rn(gelu_f(v[8 * g8 + e] + b1s[col]));
+          }
+          *reinterpret_cast<uint4 *>(sm + L::h1 + kmajor_off(r, 32 * c + 8 * g8, kH)) =
+              *reinterpret_cast<const uint4 *>(hv);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;   // every thread takes the same branch
+    if (!ok) break;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int ks = 0; ks < kH / 16; ++ks)
+        tc_mma(tbase + kH, smem_desc(sh1 + 256 * ks, 128, (kH / 8) * 128),
+               smem_desc(sw2 + 256 * ks, 128, (kH / 8) * 128), ks > 0);
+      tc_commit(bar);
+    }
+    ok = __syncthreads_and(tc_wait(bar, parity) ? 1 : 0) != 0;
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float z = 0.f;
+    if (ok) {
+      // layer 2: bias + GELU, then the output unit (each half of the columns
+      // in one warp; the two partial sums meet in shared memory)
+#pragma unroll 1
+      for (int c = 2 * half; c < 2 * half + 2; ++c) {
+        float v[32];
+        tc_ld32(tbase + t_lanes + (uint32_t)(kH + 32 * c), v);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const int col = 32 * c + e;
+          z = fmaf(w3s[col], gelu_f(v[e] + b2s[col]), z);
+        }
+      }
+      if (half == 1) zpart[quarter * 32 + lane] = z;
+    }
+    __syncthreads();
+    if (ok && half == 0) {
+      z += zpart[quarter * 32 + lane];
+      const int64_t i = base + quarter * 32 + lane;
+      if (i < a.n) {
+        const float p = 1.f / (1.f + expf(-(z + b3s[0])));
+        if (a.prob) a.prob[i] = p;
+        if (a.forced) {
+          uint8_t f = 0;
+          int32_t mi = a.m, wi = a.w_full;
+          if (p < a.p_noise) {
+            f = 2;
+            mi = a.m_noise;
+            wi = a.w_noise;
+            ++nn;
+          } else if (p > a.p_core) {
+            f = 1;
+            mi = a.m_core;
+            wi = a.w_core;
+            ++nc;
+          }
+          a.forced[i] = a.by_degree ? 0 : f;
+          a.m_row[i] = mi;
+          if (a.w_row) a.w_row[i] = wi;
+          nq += (unsigned long long)mi;
+        }
+      }
+    }
+    // the next tile overwrites the operands and the accumulators
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  }
+  if (a.counters) {
+#pragma unroll
+    for (int o2 = 16; o2 >= 1; o2 >>= 1) {
+      nq += __shfl_xor_sync(kFullMask, nq, o2);
+      nc += __shfl_xor_sync(kFullMask, nc, o2);
+      nn += __shfl_xor_sync(kFullMask, nn, o2);
+    }
+    if (lane == 0) {
+      atomicAdd(a.counters + 0, nq);
+      atomicAdd(a.counters + 1, nc);
+      atomicAdd(a.counters + 2, nn);
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(a.counters + 3, 1ull);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTcCols)
+                 : "memory");
+}
+
+template <int KT1>
+static cudaError_t launch_gate_tc05(const GateArgs &a, cudaStream_t st) {
+  const size_t smem = TcSmem<KT1>::bytes;
+  cudaError_t e = cudaFuncSetAttribute((const void *)mlp_gate_tc05_kernel<KT1>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // two CTAs per SM: each holds 256 of the SM's 512 TMEM columns (shared
+  // memory, about 100 KB each, admits no third)
+  const int64_t need = (a.n + kTcM - 1) / kTcM;
+  const int grid = (int)std::min<int64_t>(need, 2 * (int64_t)device_sms());
+  mlp_gate_tc05_kernel<KT1><<<grid, 256, smem, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- dispatch
 
 template <int DMAX>
@@ -592,7 +914,15 @@ static cudaError_t launch_gate_simt(const GateArgs &a, cudaStream_t st);
 // Gate / prediction: tensor-core kernel (FP16 activations at the MMA inputs)
 // unless FP32 activations are asked for.
 static cudaError_t launch_gate(const GateArgs &a, cudaStream_t st) {
-  if (a.fp32_activations) return launch_gate_simt(a, st);
+  if (a.fp32_activations == 1) return launch_gate_simt(a, st);
+  if (a.fp32_activations == 2) {
+    switch ((a.d + 15) / 16) {
+      case 1: return launch_gate_tc05<1>(a, st);
+      case 2: return launch_gate_tc05<2>(a, st);
+      case 3: return launch_gate_tc05<3>(a, st);
+      default: return launch_gate_tc05<4>(a, st);
+    }
+  }
   switch ((a.d + 15) / 16) {
     case 1: return launch_gate_mma<1>(a, st);
     case 2: return launch_gate_mma<2>(a, st);
@@ -693,6 +1023,8 @@ static sng_status check_cfg(const sng_mlp_config *c) {
   if (!c) return fail(SNG_EINVAL, "mlp config is NULL");
   if (c->d < 1 || c->d > 64) return fail(SNG_EINVAL, "mlp d must be in [1, 64]");
   if (c->hidden != kH) return fail(SNG_EINVAL, "mlp hidden width must be %d", kH);
+  if (c->fp32_activations < 0 || c->fp32_activations > 2)
+    return fail(SNG_EINVAL, "fp32_activations must be 0, 1 or 2");
   return SNG_OK;
 }
 
@@ -802,7 +1134,7 @@ sng_status sng_mlp_predict(const float *x, int64_t n, const sng_mlp_config *cfg,
   if (rc) return rc;
   if (!x || !params || !prob) return fail(SNG_EINVAL, "NULL argument");
   if (n < 1) return fail(SNG_EINVAL, "n must be >= 1");
-  GateArgs a{cfg->fp32_activations != 0,
+  GateArgs a{cfg->fp32_activations,
              x,
              cfg->d,
              n,
@@ -881,7 +1213,7 @@ sng_status sng_cluster_surrogate(const void *x, const sng_params *params,
     if (mi <= 0) return kDegUnit;
     return (int32_t)std::lround((double)kDegUnit * (double)r.m / (double)mi);
   };
-  GateArgs ga{cfg->fp32_activations != 0,
+  GateArgs ga{cfg->fp32_activations,
               static_cast<const float *>(x),
               params->ld,
               r.n,

@@ -134,7 +134,7 @@ class TrainConfig:
     adam_eps: float = 1e-8
     seed: int = 0
     sequential: bool = False
-    fp32_activations: bool = False
+    fp32_activations: int = 0   # 0 mma.sync, 1 FP32 CUDA cores, 2 tcgen05
 
     def to_c(self, d: int) -> sng_mlp_config:
         c = sng_mlp_config()

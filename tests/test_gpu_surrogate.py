@@ -39,15 +39,19 @@ def test_standardize_and_forward_match_oracle(d, n):
     CUDA-core path (FP32 activations): |dp| <= 2e-5.  Tensor-core path: the
     standardised inputs and the layer-1 outputs are rounded to FP16 at the MMA
     inputs (relative 2^-11 each), which moves the logit by ~5e-4 on sums of
-    <= 128 terms of weights ~0.1 (|dp| <= |dz| / 4); bound used: 2e-3."""
+    <= 128 terms of weights ~0.1 (|dp| <= |dz| / 4); bound used: 2e-3, for
+    the warp-level MMA path and the tcgen05 path alike."""
     torch, sng, sg, net, init, x, y, xg, yg, mean, std = _setup(d, n, d)
     np.testing.assert_allclose(mean, x.astype(np.float64).mean(0), rtol=1e-5, atol=1e-5)
     np.testing.assert_allclose(std, x.astype(np.float64).std(0), rtol=1e-5, atol=1e-5)
     f = omlp.forward(_fp16(init), x, mean.astype(np.float64), std.astype(np.float64))
     want = 1.0 / (1.0 + np.exp(-f["z"]))
-    net.cfg.fp32_activations = True
+    net.cfg.fp32_activations = 1
     np.testing.assert_allclose(net.predict(xg).cpu().numpy(), want, atol=2e-5)
-    net.cfg.fp32_activations = False
+    net.cfg.fp32_activations = 0
+    np.testing.assert_allclose(net.predict(xg).cpu().numpy(), want, atol=2e-3)
+    # the tcgen05 path: the same FP16 operands, accumulators in tensor memory
+    net.cfg.fp32_activations = 2
     np.testing.assert_allclose(net.predict(xg).cpu().numpy(), want, atol=2e-3)
 
 
@@ -150,7 +154,7 @@ def _gate_variants(prob, tol, m, pn, pc, frac, nfrac, rw, orc, limit=4, by_degre
     return out
 
 
-@pytest.mark.parametrize("n,fp32_act", [(2000, False), (6000, True), (400_000, True)])
+@pytest.mark.parametrize("n,fp32_act", [(2000, 0), (2000, 2), (6000, 1), (400_000, 1)])
 def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act):
     """The surrogate path against the oracle's gated form of Algorithm 1, with
     every expected value from the oracle: the gate's probabilities from the
@@ -175,7 +179,7 @@ def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act):
     net.standardize(xg)
     net.train(xg, plain_core, 300)
     net.cfg.fp32_activations = fp32_act
-    tol = 2e-5 if fp32_act else 2e-3
+    tol = 2e-5 if fp32_act == 1 else 2e-3
     w, mean, std = sg.unpack(net.params.cpu().numpy(), d)
     f = omlp.forward(_fp16(w), x, mean.astype(np.float64), std.astype(np.float64))
     prob = 1.0 / (1.0 + np.exp(-f["z"]))
