@@ -183,7 +183,11 @@ def gather_kernel_name_and_bytes(stats: dict, n: int, d: int, m: int) -> tuple[s
     screen, tiles = stats["map_screen"], stats["map_tiles"]
     full = stats["map_group"] * stats["map_nch"] * stats["map_vec"] == d
     common = n * words * 4 + n * 4 + kept * 8 + n * 8
-    if screen == 2:
+    if screen == 3:
+        row = 128
+        byts = n * m * (row + 4) + n * (row + 8) + common
+        name = "gather_tc05_kernel"
+    elif screen == 2:
         kt = stats["map_nch"]
         row = 16 * kt * 2
         byts = n * m * (row + 4) + n * (row + 8) + common
@@ -300,7 +304,8 @@ def bench_sng(args, w):
     if args.tiled:
         params.flags |= sng.SNG_FLAG_TILED
     if args.screen:
-        params.flags |= sng.SNG_FLAG_SCREEN16 | (sng.SNG_FLAG_SCREEN_MMA if args.screen == 2 else 0)
+        params.flags |= sng.SNG_FLAG_SCREEN16 | (sng.SNG_FLAG_SCREEN_MMA if args.screen >= 2 else 0)
+        params.flags |= sng.SNG_FLAG_TCGEN05 if args.screen == 3 else 0
     tuned = None
     if args.autotune and not (args.map_group or args.map_unroll or args.map_block
                               or args.map_passes or args.tiled or args.screen):
@@ -411,7 +416,8 @@ def bench_sng(args, w):
                                           "map_tile")},
                                       "tiled": bool(params.flags & sng.SNG_FLAG_TILED),
                                       "tiles_per_axis": stats["map_tiles"],
-                                      "screen": ["none", "bf16 copy", "bf16 copy, tensor cores"]
+                                      "screen": ["none", "bf16 copy", "bf16 copy, tensor cores",
+                                                 "bf16 copy, TMA gathers + tcgen05"]
                                                 [stats["map_screen"]],
                                       "prefetch": bool(params.flags & sng.SNG_FLAG_PREFETCH)},
                    "autotuned": tuned is not None},
@@ -1103,8 +1109,9 @@ def main():
     ap.add_argument("--map-passes", type=int, default=0)
     ap.add_argument("--map-tile", type=int, default=0)
     ap.add_argument("--tiled", type=int, default=0, help="1: the L2-tiled gather")
-    ap.add_argument("--screen", type=int, default=0, choices=[0, 1, 2],
-                    help="1: certified BF16 screen of the FP32 points; 2: its tensor-core form")
+    ap.add_argument("--screen", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="1: certified BF16 screen of the FP32 points; 2: its tensor-core "
+                         "form; 3: with TMA row gathers and tcgen05 dot products")
     ap.add_argument("--autotune", type=int, default=1, help="1: tune the gather mapping first")
     ap.add_argument("--degree-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0 undirected multigraph, 1 out-degree, 2 distinct neighbours")

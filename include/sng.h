@@ -129,6 +129,16 @@ typedef int32_t sng_status;
                                 screen's thresholds are widened by the bound of
                                 that computation.  Same results.  The tiled
                                 form and map_group / map_unroll do not apply   */
+#define SNG_FLAG_TCGEN05 128u /* with SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN_MMA and
+                                d <= 64: the partner rows of the BF16 copy are
+                                fetched by the tensor memory accelerator
+                                (tile::gather4, four rows per copy) into shared
+                                memory and the dot products come from tcgen05
+                                MMAs (128 partners x 4 source rows per MMA,
+                                FP32 accumulators in tensor memory).  Same
+                                thresholds, same results; stats map_screen = 3.
+                                SNG_ECUDA where the driver offers no tensor-map
+                                encoder                                        */
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The
                                 edge arrays are sized for all n*m draws (8 bytes
@@ -208,7 +218,10 @@ typedef struct {
                              (SNG_FLAG_SCREEN16); map_vec .. map_unroll then
                              describe the mapping over that copy; 2: with
                              tensor-core dot products (SNG_FLAG_SCREEN_MMA;
-                             map_group 16 partners per MMA, map_nch k-tiles) */
+                             map_group 16 partners per MMA, map_nch k-tiles);
+                             3: rows gathered by TMA, tcgen05 dot products
+                             (SNG_FLAG_TCGEN05; map_group 128 partners per
+                             MMA)                                           */
     int64_t screen_pairs; /* SNG_FLAG_SCREEN16: pairs the BF16 screen left
                              open, summed again from the FP32 points       */
 } sng_stats;

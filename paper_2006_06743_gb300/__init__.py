@@ -36,6 +36,7 @@ SNG_FLAG_WARP_ROWS = 8
 SNG_FLAG_TILED = 16
 SNG_FLAG_SCREEN16 = 32
 SNG_FLAG_SCREEN_MMA = 64
+SNG_FLAG_TCGEN05 = 128
 
 PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total", "gate")
 

@@ -18,6 +18,7 @@
 #include "gather.cuh"
 #include "graph.cuh"
 #include "gather_mma.cuh"
+#include "gather_tc05.cuh"
 #include "screen.cuh"
 #include "tiled.cuh"
 
@@ -550,9 +551,12 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
                       p->metric == SNG_METRIC_L2 && r.map.passes <= 1 && !r.map.lanes &&
                       !(p->flags & SNG_FLAG_NO_SYNC);
   const int mma_kt = screen && (p->flags & SNG_FLAG_SCREEN_MMA) ? mma_tiles_for(p->d) : 0;
+  // the TMA + tcgen05 form reads rows of 64 BF16 values (zero past d)
+  const bool tc05 = mma_kt && (p->flags & SNG_FLAG_TCGEN05) && p->d <= 64;
   if (screen) {
     wait_inputs(st);
-    if ((rc = make_shadow(static_cast<const float *>(x), p->ld, p->d, n, 16 * mma_kt, s, &sh)))
+    if ((rc = make_shadow(static_cast<const float *>(x), p->ld, p->d, n,
+                          tc05 ? 64 : 16 * mma_kt, s, &sh)))
       return rc;
     pb = *p;
     pb.dtype = SNG_BF16;
@@ -609,7 +613,15 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     return rc;
   gb->screened = screen;
   gb->map = rg->map;
-  if (mma_kt) {
+  if (tc05) {
+    // partner rows by TMA, 128 partners x 4 source rows per tcgen05 MMA
+    gb->mma = true;
+    gb->tc05 = true;
+    gb->map.group = 128;
+    gb->map.nch = 4;
+    // map_unroll selects the ring's stages; stats report the count used
+    if ((rc = launch_gather_tc05(ga, n, sh.ldb, p->map_unroll, &gb->map.unroll, st))) return rc;
+  } else if (mma_kt) {
     // the tensor-core form of the screen (direct gather only): 16 partners
     // per MMA, mma_kt k-tiles of 16 values per row
     gb->mma = true;
@@ -718,7 +730,7 @@ sng_status read_stats(const unsigned long long *counters, const Resolved &r, sng
     stats->map_nch = r.map.nch;
     stats->map_unroll = r.map.unroll;
   }
-  if (status & (kErrUnionLimit | kErrFindLimit | kErrBatchLimit))
+  if (status & (kErrUnionLimit | kErrFindLimit | kErrBatchLimit | kErrDeviceWait))
     return fail(SNG_ETIMEOUT, "a bounded device loop gave up (status 0x%x)", status);
   if (status & kErrIndex) return fail(SNG_EINTERNAL, "device index check failed (0x%x)", status);
   return SNG_OK;
@@ -728,7 +740,7 @@ void note_mapping(const GraphBufs &gb, sng_stats *stats) {
   if (!stats) return;
   stats->map_tiles = gb.tiles;
   stats->map_tex = gb.tex_chunks;
-  stats->map_screen = gb.screened ? (gb.mma ? 2 : 1) : 0;
+  stats->map_screen = gb.screened ? (gb.tc05 ? 3 : gb.mma ? 2 : 1) : 0;
   if (gb.screened) {
     stats->map_vec = gb.map.vec;
     stats->map_group = gb.map.group;

@@ -146,6 +146,23 @@ __device__ __forceinline__ void screen_thresholds(const GatherArgs &a, float nrm
   drop_thr = (hi * hi) * (1.f + a.screen_g);
 }
 
+// Keep / drop thresholds of the tensor-core screen (gather_mma.cu,
+// gather_tc05.cu) for a source row of norm bound nrm_i against partners of
+// norm bound at most nrm_p: the screen's thresholds above, widened by the
+// absolute bound of |a'|^2 + |b'|^2 - 2 a'.b' (screen_cabs (nrm_i + nrm_p)^2
+// + 2^-100).
+__device__ __forceinline__ void mma_screen_thresholds(const GatherArgs &a, float nrm_i,
+                                                      float nrm_p, float &keep_thr,
+                                                      float &drop_thr) {
+  const float eta = fmaf(a.screen_u, nrm_i + nrm_p, a.screen_abs);
+  const float s = nrm_i + nrm_p;
+  const float e_abs = fmaf(a.screen_cabs * s, s, 0x1p-100f);
+  const float lo = a.screen_lo_eps - eta;
+  const float hi = a.screen_hi_eps + eta;
+  keep_thr = lo > 0x1p-10f * a.screen_lo_eps ? fmaf(lo * lo, 1.f - a.screen_g, -e_abs) : -1.f;
+  drop_thr = fmaf(hi * hi, 1.f + a.screen_g, e_abs);
+}
+
 // A pair the BF16 screen left open: the FP32 squared distance of the FP32
 // rows, summed in order with one fused multiply-add per element (the bound
 // behind lo_thr / hi_thr), then the FP64 recheck inside the guard band --

@@ -62,20 +62,6 @@ __device__ __forceinline__ void load_slice(const uint16_t *row, int q, uint32_t 
   }
 }
 
-// Keep / drop thresholds of the tensor-core screen for a source row of norm
-// bound nrm_i against partners of norm bound at most nrm_p (the screen's
-// thresholds of gather.cuh, widened by the computation's absolute bound).
-__device__ __forceinline__ void mma_thresholds(const GatherArgs &a, float nrm_i, float nrm_p,
-                                               float &keep_thr, float &drop_thr) {
-  const float eta = fmaf(a.screen_u, nrm_i + nrm_p, a.screen_abs);
-  const float s = nrm_i + nrm_p;
-  const float e_abs = fmaf(a.screen_cabs * s, s, 0x1p-100f);
-  const float lo = a.screen_lo_eps - eta;
-  const float hi = a.screen_hi_eps + eta;
-  keep_thr = lo > 0x1p-10f * a.screen_lo_eps ? fmaf(lo * lo, 1.f - a.screen_g, -e_abs) : -1.f;
-  drop_thr = fmaf(hi * hi, 1.f + a.screen_g, e_abs);
-}
-
 // One warp per source row, draws in stages of 32 (one hash per lane), each
 // stage as two groups of 16 partners through KT MMAs.  Lane r owns draw r of
 // the stage: it hashes it, loads its partner's squared norm, receives its dot
@@ -107,7 +93,7 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
     load_slice<KT>(X + (int64_t)i * a.ld, q, b);
     const float na2 = __ldg(a.nb2 + i);
     float keep_thr, drop_thr;
-    mma_thresholds(a, __ldg(a.nrm + i), nrm_pmax, keep_thr, drop_thr);
+    mma_screen_thresholds(a, __ldg(a.nrm + i), nrm_pmax, keep_thr, drop_thr);
     int cnt = 0;
     int jb = 0;
     // draws past the row's count read row 0 and decide nothing

@@ -30,6 +30,7 @@ constexpr uint32_t kErrUnionLimit = 1u << 0;   // union-find retry bound hit
 constexpr uint32_t kErrFindLimit = 1u << 1;    // find walked more than n steps
 constexpr uint32_t kErrBatchLimit = 1u << 2;   // batched scheduler bound hit
 constexpr uint32_t kErrIndex = 1u << 3;        // an index fell outside its array
+constexpr uint32_t kErrDeviceWait = 1u << 6;   // a bounded wait on tensor-core / TMA completion gave up
 
 // Counters kept on the device for sng_stats (unsigned long long each).
 enum CounterSlot : int {

@@ -27,9 +27,13 @@ def _check_exact(orc, sng, torch, x, p, m, min_pts, tiled_k=0, mma=False):
     flags = sng.SNG_FLAG_SCREEN16 | (sng.SNG_FLAG_TILED if tiled_k else 0)
     if mma:
         flags |= sng.SNG_FLAG_SCREEN_MMA
+    if mma == "tc05":
+        flags |= sng.SNG_FLAG_TCGEN05
     q = sng.Params(**{**p.__dict__, "flags": flags, "map_tile": tiled_k})
     g, st = _graph(sng, xg, q)
-    assert st["map_screen"] == (2 if mma and x.shape[1] <= 128 else 1)
+    d = x.shape[1]
+    want = (3 if mma == "tc05" and d <= 64 else 2) if mma and d <= 128 else 1
+    assert st["map_screen"] == want
     rp, col, bpairs, _ = orc.build_rows(x, p.eps, p.seed, m, band_rel=BAND_F32)
     np.testing.assert_array_equal(g["row_ptr"], rp)
     np.testing.assert_array_equal(g["col"], col)
@@ -79,7 +83,7 @@ def test_screen_tensor_cores_match_oracle(orc, n, d, budget):
     assert st["kept_edges"] > 0
 
 
-@pytest.mark.parametrize("mma", [False, True])
+@pytest.mark.parametrize("mma", [False, True, "tc05"])
 def test_screen_open_pairs_far_from_origin(orc, mma):
     """Points offset far from the origin make every norm bound large, so the
     screen certifies little and most pairs are summed again in FP32: the
@@ -93,7 +97,7 @@ def test_screen_open_pairs_far_from_origin(orc, mma):
     assert st["screen_pairs"] > 0.5 * n * m
 
 
-@pytest.mark.parametrize("mma", [False, True])
+@pytest.mark.parametrize("mma", [False, True, "tc05"])
 def test_screen_integer_ties_and_mixed_scales(orc, mma):
     """Integer coordinates (exact in every format) with eps^2 an integer put
     many pairs exactly on the ball's boundary (kept: closed ball), all of
@@ -112,7 +116,7 @@ def test_screen_integer_ties_and_mixed_scales(orc, mma):
         _check_exact(orc, sng, torch, xs, ps, m, 3, mma=mma)
 
 
-@pytest.mark.parametrize("mma", [False, True])
+@pytest.mark.parametrize("mma", [False, True, "tc05"])
 def test_screen_non_finite_rows(orc, mma):
     """Rows holding inf or NaN give unbounded norms, which certify nothing:
     their pairs (and, through the maximum norm, every pair) are decided from
@@ -129,7 +133,7 @@ def test_screen_non_finite_rows(orc, mma):
     _check_exact(orc, sng, torch, x, p, m, 4, mma=mma)
 
 
-@pytest.mark.parametrize("tiled_k,mma", [(0, False), (3, False), (0, True)])
+@pytest.mark.parametrize("tiled_k,mma", [(0, False), (3, False), (0, True), (0, "tc05")])
 def test_screen_equals_plain_fp32_path(orc, tiled_k, mma):
     """On a Gaussian mixture shaped like the headline workload (smaller n)
     the screened and the plain FP32 gathers give the same CSR, degrees and
@@ -143,10 +147,12 @@ def test_screen_equals_plain_fp32_path(orc, tiled_k, mma):
     plain, _ = _graph(sng, xg, sng.Params(**base))
     flags = sng.SNG_FLAG_SCREEN16 | (sng.SNG_FLAG_TILED if tiled_k else 0)
     flags |= sng.SNG_FLAG_SCREEN_MMA if mma else 0
+    flags |= sng.SNG_FLAG_TCGEN05 if mma == "tc05" else 0
     scr, st = _graph(sng, xg, sng.Params(**base, flags=flags, map_tile=tiled_k))
     for k in plain:
         np.testing.assert_array_equal(scr[k], plain[k], err_msg=k)
-    assert st["map_screen"] == (2 if mma else 1) and 0 < st["screen_pairs"] < 0.02 * n * 500
+    want = 3 if mma == "tc05" else 2 if mma else 1
+    assert st["map_screen"] == want and 0 < st["screen_pairs"] < 0.02 * n * 500
     rows = np.sort(np.random.default_rng(0).choice(n, 300, replace=False))
     rp, col, _, _ = orc.build_rows(x, eps, 3, 500, band_rel=BAND_F32, rows=rows)
     for k, i in enumerate(rows):
