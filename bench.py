@@ -183,7 +183,12 @@ def gather_kernel_name_and_bytes(stats: dict, n: int, d: int, m: int) -> tuple[s
     screen, tiles = stats["map_screen"], stats["map_tiles"]
     full = stats["map_group"] * stats["map_nch"] * stats["map_vec"] == d
     common = n * words * 4 + n * 4 + kept * 8 + n * 8
-    if screen == 3:
+    if screen == 4:
+        ks = stats["map_nch"]
+        row = 32 * ks
+        byts = n * m * (row + 8) + n * (row + 8) + common
+        name = f"gather_mma8_kernel<{ks}, {stats['map_unroll'] or (2 if ks <= 2 else 3)}>"
+    elif screen == 3:
         row = 128
         byts = n * m * (row + 4) + n * (row + 8) + common
         name = "gather_tc05_kernel"
@@ -208,11 +213,19 @@ def gather_kernel_name_and_bytes(stats: dict, n: int, d: int, m: int) -> tuple[s
         if screen:
             name = "shadow_kernel + " + ("slice_max_kernel + " if tiles else "") + name
     # (kernel_ms is the whole gather phase: with the screen it includes
-    # shadow_kernel, 0.15 ms at the headline)
+    # making the copy, 0.15 ms at the headline, and with the tensor-core
+    # forms the queue of open pairs)
     if screen:
-        row = (16 * stats["map_nch"] if screen == 2 else -(-d // 8) * 8) * 2
-        byts += n * (d * 4 + row + 12)                   # the copy: read FP32, write BF16
-        byts += stats.get("screen_pairs", 0) * 2 * d * 4  # open pairs from the FP32 rows
+        copy_row = {2: 32 * stats["map_nch"], 3: 128, 4: 32 * stats["map_nch"]}.get(
+            screen, -(-d // 8) * 8 * 2)
+        byts += n * (d * 4 + copy_row + 12)              # the copy: read FP32, write the copy
+        if screen == 4:
+            byts += n * d * 4                            # the FP8 copy's scale pass
+        open_pairs = stats.get("screen_pairs", 0)
+        byts += open_pairs * 2 * d * 4                   # open pairs from the FP32 rows
+        if screen in (2, 4):
+            byts += open_pairs * 32                      # queue entry written and read
+            name += " + screen_queue_kernel"
     return name, int(byts)
 
 
@@ -382,7 +395,7 @@ def bench_sng(args, w):
     Q = n * m
     peak, peak_kind = peaks()
     g_ms = statistics.mean(gather_ms)
-    # the section 8(d) model: every partner row from HBM (FP32 rows)
+    # the HBM model: every partner row from HBM (FP32 rows)
     alg = gather_algorithmic_bytes(n, d, m, 4, stats["kept_edges"])
     kname, alg_l2 = gather_kernel_name_and_bytes(stats, n, d, m)
     traffic = None

@@ -129,6 +129,17 @@ typedef int32_t sng_status;
                                 screen's thresholds are widened by the bound of
                                 that computation.  Same results.  The tiled
                                 form and map_group / map_unroll do not apply   */
+#define SNG_FLAG_SCREEN8 256u /* FP32 points, Euclidean form, d <= 128: the screen
+                                of SNG_FLAG_SCREEN16 on an FP8 (E4M3) copy of
+                                x * 2^k (one power of two for the point set;
+                                1 byte per value of scratch), with the dot
+                                products from FP8 tensor-core MMAs.  The
+                                copy's rounding bound is 2^-4 of the norms
+                                (plus its subnormal range), so more pairs are
+                                left open and summed again from the FP32
+                                points; results are identical.  Stats report
+                                map_screen = 4.  Same exclusions as
+                                SNG_FLAG_SCREEN16; takes precedence over it  */
 #define SNG_FLAG_TCGEN05 128u /* with SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN_MMA and
                                 d <= 64: the partner rows of the BF16 copy are
                                 fetched by the tensor memory accelerator
@@ -221,7 +232,8 @@ typedef struct {
                              map_group 16 partners per MMA, map_nch k-tiles);
                              3: rows gathered by TMA, tcgen05 dot products
                              (SNG_FLAG_TCGEN05; map_group 128 partners per
-                             MMA)                                           */
+                             MMA); 4: FP8 copy, tensor-core dot products
+                             (SNG_FLAG_SCREEN8; map_nch k-tiles of 32)     */
     int64_t screen_pairs; /* SNG_FLAG_SCREEN16: pairs the BF16 screen left
                              open, summed again from the FP32 points       */
 } sng_stats;

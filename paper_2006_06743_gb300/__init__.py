@@ -37,6 +37,7 @@ SNG_FLAG_TILED = 16
 SNG_FLAG_SCREEN16 = 32
 SNG_FLAG_SCREEN_MMA = 64
 SNG_FLAG_TCGEN05 = 128
+SNG_FLAG_SCREEN8 = 256
 
 PHASES = ("gather", "scan", "fill", "core_union", "labels", "finalize", "total", "gate")
 

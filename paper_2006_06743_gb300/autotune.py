@@ -20,7 +20,8 @@ import os
 import statistics
 import time
 
-from . import (SNG_FLAG_PREFETCH, SNG_FLAG_SCREEN16, SNG_FLAG_SCREEN_MMA, SNG_FLAG_TILED,
+from . import (SNG_FLAG_PREFETCH, SNG_FLAG_SCREEN8, SNG_FLAG_SCREEN16, SNG_FLAG_SCREEN_MMA,
+               SNG_FLAG_TCGEN05, SNG_FLAG_TILED,
                SNG_FLAG_TIMING, Params, SngError, cluster)
 
 CACHE_ENV = "SNG_AUTOTUNE_CACHE"
@@ -82,6 +83,9 @@ def candidates(x, p: Params, screen: bool = True) -> list[dict]:
                 for u in ((0, 4, 2) if d <= 64 else (0, 3)):
                     out.append(dict(map_group=0, map_unroll=u, map_block=256, map_passes=0,
                                     prefetch=False, screen=True, mma=True))
+                # the FP8 copy (1 byte per value; more pairs left open)
+                out.append(dict(map_group=0, map_unroll=0, map_block=256, map_passes=0,
+                                prefetch=False, screen=True, fp8=True))
             for g in sorted({max(1, gb // 2), gb}):
                 for u in (2, 4):
                     out.append(dict(map_group=g, map_unroll=u, map_block=256, map_passes=0,
@@ -122,10 +126,13 @@ def _params_for(base: dict, cand: dict) -> Params:
     tiled = c.pop("tiled", False)
     screen = c.pop("screen", False)
     mma = c.pop("mma", False)
+    fp8 = c.pop("fp8", False)
     flags = base.get("flags", 0) & ~(SNG_FLAG_PREFETCH | SNG_FLAG_TILED | SNG_FLAG_SCREEN16 |
-                                     SNG_FLAG_SCREEN_MMA)
+                                     SNG_FLAG_SCREEN_MMA | SNG_FLAG_SCREEN8 | SNG_FLAG_TCGEN05)
     if mma:
         flags |= SNG_FLAG_SCREEN_MMA
+    if fp8:
+        flags |= SNG_FLAG_SCREEN8
     if pf:
         flags |= SNG_FLAG_PREFETCH
     if screen:

@@ -18,6 +18,8 @@
 #include "gather.cuh"
 #include "graph.cuh"
 #include "gather_mma.cuh"
+#include "gather_mma8.cuh"
+#include "screen_queue.cuh"
 #include "gather_tc05.cuh"
 #include "screen.cuh"
 #include "tiled.cuh"
@@ -343,6 +345,12 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
   g->screen_vec4 = 0;
   g->screen_lo_eps = g->screen_hi_eps = 0.f;
   g->screen_u = g->screen_abs = g->screen_g = 0.f;
+  g->screen_kexp = nullptr;
+  g->nbe = nullptr;
+  g->openq = nullptr;
+  g->openq_cnt = nullptr;
+  g->openq_cap = 0;
+  g->q_lo_thr = g->q_hi_thr = 0.f;
   g->nrm = nullptr;
   g->nrm_max = nullptr;
   // L2 prefetch of partner rows when rows start on 16 bytes (16-byte vectors)
@@ -547,17 +555,25 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   sng_params pb;
   Resolved rb;
   Shadow sh;
-  const bool screen = (p->flags & SNG_FLAG_SCREEN16) && p->dtype == SNG_F32 &&
+  const bool screen = (p->flags & (SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN8)) && p->dtype == SNG_F32 &&
                       p->metric == SNG_METRIC_L2 && r.map.passes <= 1 && !r.map.lanes &&
                       !(p->flags & SNG_FLAG_NO_SYNC);
-  const int mma_kt = screen && (p->flags & SNG_FLAG_SCREEN_MMA) ? mma_tiles_for(p->d) : 0;
+  // the FP8 form: k-tiles of 32 values (rows of 64 or 128 bytes)
+  const int fp8_ks = screen && (p->flags & SNG_FLAG_SCREEN8) && p->d <= 128
+                         ? (p->d <= 64 ? 2 : 4) : 0;
+  const int mma_kt = screen && !fp8_ks && (p->flags & (SNG_FLAG_SCREEN_MMA | SNG_FLAG_SCREEN8))
+                         ? mma_tiles_for(p->d) : 0;
   // the TMA + tcgen05 form reads rows of 64 BF16 values (zero past d)
   const bool tc05 = mma_kt && (p->flags & SNG_FLAG_TCGEN05) && p->d <= 64;
   if (screen) {
     wait_inputs(st);
-    if ((rc = make_shadow(static_cast<const float *>(x), p->ld, p->d, n,
-                          tc05 ? 64 : 16 * mma_kt, s, &sh)))
+    if (fp8_ks) {
+      if ((rc = make_shadow8(static_cast<const float *>(x), p->ld, p->d, n, 32 * fp8_ks, s, &sh)))
+        return rc;
+    } else if ((rc = make_shadow(static_cast<const float *>(x), p->ld, p->d, n,
+                                 tc05 ? 64 : 16 * mma_kt, s, &sh))) {
       return rc;
+    }
     pb = *p;
     pb.dtype = SNG_BF16;
     pb.ld = (int32_t)sh.ldb;
@@ -601,6 +617,14 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     ga.screen_g = round_up_f(delta + std::ldexp(1.0, -20));
     ga.screen_u = round_up_f(std::ldexp(1.0, -8) * (1.0 + std::ldexp(1.0, -20)));
     ga.screen_abs = std::ldexp(1.0f, -60);
+    if (fp8_ks) {
+      // E4M3: eta from the rows' own rounding-error bounds (nbe), and a
+      // wider allowance for the FP8 tensor core's accumulation
+      ga.screen_u = 0.f;
+      ga.screen_kexp = sh.kexp;
+      ga.nbe = sh.nbe;
+      ga.screen_cabs = std::ldexp(1.0f, -9);
+    }
     // open pairs are summed in order with one fused multiply-add per element
     fp32_guard(r.eps2, r.band_rel, p->d, 0, &ga.lo_thr, &ga.hi_thr);
     pg = &pb;
@@ -608,12 +632,41 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   }
   const int grid = gather_grid(pg->dtype, rg->map, r.row_end - r.row_begin);
   bool tiled = false;
-  if (!mma_kt && (p->flags & SNG_FLAG_TILED) &&
+  if (!mma_kt && !fp8_ks && (p->flags & SNG_FLAG_TILED) &&
       (rc = run_tiled(pg, *rg, s, ga, gb, &tiled, screen ? &sh : nullptr)))
     return rc;
   gb->screened = screen;
   gb->map = rg->map;
-  if (tc05) {
+  if (fp8_ks || (mma_kt && !tc05)) {
+    // the queue of open pairs of the tensor-core forms: room for 1 in 32
+    // draws of the row range (at most 2^26 entries); past it, or without
+    // the memory, the gather decides open pairs itself
+    const int64_t draws = (r.row_end - r.row_begin) * (int64_t)r.m;
+    int64_t cap = draws / 32 > 4096 ? draws / 32 : 4096;
+    if (cap > (int64_t)1 << 26) cap = (int64_t)1 << 26;
+    if ((rc = s.alloc((void **)&ga.openq_cnt, 8, "open-pair count"))) return rc;
+    cudaMemsetAsync(ga.openq_cnt, 0, 8, st);
+    if (s.alloc((void **)&ga.openq, (size_t)cap * sizeof(uint4), "open-pair queue") == SNG_OK) {
+      ga.openq_cap = cap;
+    } else {
+      ga.openq = nullptr;
+      ga.openq_cap = 0;
+    }
+    fp32_guard(r.eps2, r.band_rel, (p->d + 31) / 32, 5, &ga.q_lo_thr, &ga.q_hi_thr);
+  }
+  if (fp8_ks) {
+    // the FP8 copy: 16 partners per MMA, fp8_ks k-tiles of 32 values
+    gb->mma = true;
+    gb->fp8 = true;
+    gb->map.group = 16;
+    gb->map.nch = fp8_ks;
+    gb->map.unroll = p->map_unroll;
+    if (!launch_gather_mma8(fp8_ks, p->map_unroll, ga, r.row_end - r.row_begin, st))
+      return fail(SNG_EINVAL, "no FP8 tensor-core gather for d = %d with map_unroll = %d", p->d,
+                  p->map_unroll);
+    note_launch();
+    if ((rc = launch_screen_queue(ga, st))) return rc;
+  } else if (tc05) {
     // partner rows by TMA, 128 partners x 4 source rows per tcgen05 MMA
     gb->mma = true;
     gb->tc05 = true;
@@ -633,6 +686,7 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
       return fail(SNG_EINVAL, "no tensor-core gather for d = %d with map_unroll = %d", p->d,
                   p->map_unroll);
     note_launch();
+    if ((rc = launch_screen_queue(ga, st))) return rc;
   } else if (tiled) {
     // done by the tiled form
   } else if (rg->map.passes <= 1) {
@@ -740,7 +794,7 @@ void note_mapping(const GraphBufs &gb, sng_stats *stats) {
   if (!stats) return;
   stats->map_tiles = gb.tiles;
   stats->map_tex = gb.tex_chunks;
-  stats->map_screen = gb.screened ? (gb.tc05 ? 3 : gb.mma ? 2 : 1) : 0;
+  stats->map_screen = gb.screened ? (gb.fp8 ? 4 : gb.tc05 ? 3 : gb.mma ? 2 : 1) : 0;
   if (gb.screened) {
     stats->map_vec = gb.map.vec;
     stats->map_group = gb.map.group;

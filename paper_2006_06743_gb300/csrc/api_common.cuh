@@ -81,6 +81,7 @@ struct GraphBufs {
   bool screened = false;     // pairs tested on the BF16 copy (SNG_FLAG_SCREEN16)
   bool mma = false;          // ... with tensor-core dot products (SNG_FLAG_SCREEN_MMA)
   bool tc05 = false;         // ... rows by TMA, dot products by tcgen05 (SNG_FLAG_TCGEN05)
+  bool fp8 = false;          // ... on an FP8 copy (SNG_FLAG_SCREEN8)
   GatherMap map{};           // the mapping the gather ran with
 };
 

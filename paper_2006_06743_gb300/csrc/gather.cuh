@@ -82,6 +82,18 @@ struct GatherArgs {
   // BF16 rows (FP32 sums) and the coefficient of its absolute error bound
   const float *nb2;
   float screen_cabs;
+  // FP8 form (gather_mma8.cu): the copy holds x * 2^k, k = *screen_kexp;
+  // nbe[i] = {|x_i'|^2, bound of |x_i - x_i'|}
+  const int32_t *screen_kexp;
+  const float2 *nbe;
+  // pairs the screen left open, queued for screen_queue_kernel: entries
+  // {i, p, draw j, weight of i}, openq_cnt counts every open pair (past
+  // openq_cap the gather decides them itself); q_lo_thr / q_hi_thr are the
+  // guard band of the queue kernel's warp-wide FP32 sum
+  uint4 *openq;
+  unsigned long long *openq_cnt;
+  int64_t openq_cap;
+  float q_lo_thr, q_hi_thr;
   uint32_t *bitmask;      // n x W
   int32_t *out_cnt;       // n, nullable
   int32_t *deg;           // n (zeroed before launch in multigraph mode)

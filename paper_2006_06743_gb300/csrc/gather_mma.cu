@@ -27,7 +27,8 @@
 // c_abs = 2^-15 covers all of it for d <= 128, the 2^-100 any product
 // flushed below FP32's normal range.  The screen's keep / drop thresholds
 // are widened by that bound; every pair they leave open is decided from
-// the FP32 points exactly as without the screen (screen_pair).
+// the FP32 points exactly as without the screen: queued for
+// screen_queue.cu, or, without room in the queue, here (screen_pair).
 #include "api_common.cuh"
 #include "gather.cuh"
 #include "gather_mma.cuh"
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
   const int warp = threadIdx.x >> 5;
   const int g = lane >> 2, q = lane & 3;
   const uint16_t *X = static_cast<const uint16_t *>(a.x);
-  __shared__ unsigned int s_open;   // pairs the screen left open
+  __shared__ unsigned int s_open;   // open pairs decided here (no room in the queue)
   if (threadIdx.x == 0) s_open = 0;
   __syncthreads();
   const float nrm_pmax = a.nrm_max[0];
@@ -127,17 +128,29 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
       const float d10 = __shfl_sync(kFullMask, c1[0], src_lane);
       const float d12 = __shfl_sync(kFullMask, c1[2], src_lane);
       const float dot = second ? (upper ? d12 : d10) : (upper ? d02 : d00);
-      bool keep = false;
-      if (live) {
-        const float d2 = fmaf(-2.f, dot, na2 + nbp);
-        if (d2 <= keep_thr) {
-          keep = true;
-        } else if (!(d2 > drop_thr)) {
-          keep = screen_pair(a, i, p);
-          atomicAdd(&s_open, 1u);
+      const float d2 = fmaf(-2.f, dot, na2 + nbp);
+      bool keep = live && d2 <= keep_thr;
+      const bool open = live && !keep && !(d2 > drop_thr);
+      const uint32_t om = __ballot_sync(kFullMask, open);
+      if (om) {
+        // open pairs to the queue (one atomic per warp); without a queue, or
+        // past its capacity, decided here
+        unsigned long long base = 0;
+        if (lane == 0 && a.openq_cnt)
+          base = atomicAdd(a.openq_cnt, (unsigned long long)__popc(om));
+        base = __shfl_sync(kFullMask, base, 0);
+        if (open) {
+          const unsigned long long slot = base + __popc(om & ((1u << lane) - 1u));
+          if ((long long)slot < a.openq_cap) {
+            a.openq[slot] = make_uint4((uint32_t)i, (uint32_t)p, (uint32_t)(jb + lane),
+                                       (uint32_t)wi);
+          } else {
+            keep = screen_pair(a, i, p);
+            atomicAdd(&s_open, 1u);
+          }
         }
-        if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
       }
+      if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
       const uint32_t word = __ballot_sync(kFullMask, keep);
       if (lane == 0) __stcs(a.bitmask + (int64_t)i * a.W + (jb >> 5), word);
       cnt += __popc(word);

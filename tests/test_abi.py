@@ -159,13 +159,15 @@ def test_autotuner_offers_the_tiled_form_where_it_fits(monkeypatch):
 
 def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
     """Screened candidates (SNG_FLAG_SCREEN16) lead the list for FP32 points,
-    Euclidean form, hashed draws: the direct gather over the BF16 copy with
+    Euclidean form, hashed draws: the tensor-core forms over the BF16 copy and
+    one over the FP8 copy (d <= 128), the direct gather over the BF16 copy with
     the default lanes per pair for 8-value chunks and half of it, and, for
     copies over 48 MiB whose buckets fit, the tiled form with the copy's
     slice count and one more.  None for BF16 points, similarity metrics or
     every-pair sampling; the flag reaches the parameters."""
     import torch
-    from paper_2006_06743_gb300 import SNG_FLAG_SCREEN16, SNG_FLAG_SCREEN_MMA, Params, autotune
+    from paper_2006_06743_gb300 import (SNG_FLAG_SCREEN8, SNG_FLAG_SCREEN16, SNG_FLAG_SCREEN_MMA,
+                                        Params, autotune)
     monkeypatch.setattr(torch.cuda, "mem_get_info", lambda dev=None: (200 << 30, 280 << 30))
 
     def screened(n, d, dtype=torch.float32, **kw):
@@ -178,7 +180,12 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
     mma = [c for c in sc if c.get("mma")]        # tensor-core dot products first
     assert sc[:len(mma)] == mma and {c["map_unroll"] for c in mma} == {0, 4, 2}
     assert not any(c.get("mma") for c in screened(1_000_000, 200, m=100))   # d > 128
-    direct = [c for c in sc if not c.get("tiled") and not c.get("mma")]
+    fp8 = [c for c in sc if c.get("fp8")]       # one FP8-copy candidate after them
+    assert len(fp8) == 1 and sc[len(mma)] == fp8[0]
+    assert not any(c.get("fp8") for c in screened(1_000_000, 200, m=100))   # d > 128
+    p8 = autotune.apply(Params(eps=1.0, min_pts=5), {"mapping": fp8[0]})
+    assert p8.flags & SNG_FLAG_SCREEN8 and not p8.flags & SNG_FLAG_SCREEN_MMA
+    direct = [c for c in sc if not c.get("tiled") and not c.get("mma") and not c.get("fp8")]
     tiled = [c for c in sc if c.get("tiled")]
     assert {c["map_group"] for c in direct} == {4, 8} and {c["map_unroll"] for c in direct} == {2, 4}
     # BF16 copy of 10^6 x 64 = 128 MB: ceil(256 MB / 88 MiB) = 3 -> {3, 4}
