@@ -136,9 +136,10 @@ CAPTURED_TRAFFIC = {
     ("mixture-n1M-d64",
      "tile_partition_kernel + 36 x tile_test_kernel<float, 4, 4, 4, 2, 1, 1>"):
         21_680_128 + 8_046_274_048 + 11_679_285_760 + 172_615_680,
-    # the tensor-core screen: one gather_mma_kernel launch
-    # (profiles/gather_mma_mixture-n1M-d64.md)
-    ("mixture-n1M-d64", "gather_mma_kernel<4, 3>"): 51_708_475_392 + 444_700_928,
+    # the tensor-core screen: one gather_mma_kernel launch and the queue of
+    # open pairs (profiles/gather_mma_mixture-n1M-d64.md)
+    ("mixture-n1M-d64", "gather_mma_kernel<4, 3> + screen_queue_kernel"):
+        50_133_228_544 + 434_944_000 + 452_224_768 + 28_201_984,
 }
 
 
