@@ -318,8 +318,11 @@ def bench_sng(args, w):
     if args.tiled:
         params.flags |= sng.SNG_FLAG_TILED
     if args.screen:
-        params.flags |= sng.SNG_FLAG_SCREEN16 | (sng.SNG_FLAG_SCREEN_MMA if args.screen >= 2 else 0)
-        params.flags |= sng.SNG_FLAG_TCGEN05 if args.screen == 3 else 0
+        if args.screen == 4:
+            params.flags |= sng.SNG_FLAG_SCREEN8
+        else:
+            params.flags |= sng.SNG_FLAG_SCREEN16 | (sng.SNG_FLAG_SCREEN_MMA if args.screen >= 2 else 0)
+            params.flags |= sng.SNG_FLAG_TCGEN05 if args.screen == 3 else 0
     tuned = None
     if args.autotune and not (args.map_group or args.map_unroll or args.map_block
                               or args.map_passes or args.tiled or args.screen):
@@ -431,7 +434,8 @@ def bench_sng(args, w):
                                       "tiled": bool(params.flags & sng.SNG_FLAG_TILED),
                                       "tiles_per_axis": stats["map_tiles"],
                                       "screen": ["none", "bf16 copy", "bf16 copy, tensor cores",
-                                                 "bf16 copy, TMA gathers + tcgen05"]
+                                                 "bf16 copy, TMA gathers + tcgen05",
+                                                 "fp8 copy, tensor cores"]
                                                 [stats["map_screen"]],
                                       "prefetch": bool(params.flags & sng.SNG_FLAG_PREFETCH)},
                    "autotuned": tuned is not None},
@@ -1123,9 +1127,10 @@ def main():
     ap.add_argument("--map-passes", type=int, default=0)
     ap.add_argument("--map-tile", type=int, default=0)
     ap.add_argument("--tiled", type=int, default=0, help="1: the L2-tiled gather")
-    ap.add_argument("--screen", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--screen", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="1: certified BF16 screen of the FP32 points; 2: its tensor-core "
-                         "form; 3: with TMA row gathers and tcgen05 dot products")
+                         "form; 3: with TMA row gathers and tcgen05 dot products; 4: the "
+                         "screen on an FP8 copy")
     ap.add_argument("--autotune", type=int, default=1, help="1: tune the gather mapping first")
     ap.add_argument("--degree-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0 undirected multigraph, 1 out-degree, 2 distinct neighbours")
