@@ -188,7 +188,7 @@ def gather_kernel_name_and_bytes(stats: dict, n: int, d: int, m: int) -> tuple[s
         ks = stats["map_nch"]
         row = 32 * ks
         byts = n * m * (row + 8) + n * (row + 8) + common
-        name = f"gather_mma8_kernel<{ks}, {stats['map_unroll'] or (2 if ks <= 2 else 3)}>"
+        name = f"gather_mma8_kernel<{ks}, {stats['map_unroll'] or 2}>"
     elif screen == 3:
         row = 128
         byts = n * m * (row + 4) + n * (row + 8) + common
@@ -643,6 +643,10 @@ def bench_bf16(args):
             "ms_fp32_screened": s_ms, "speedup_vs_fp32_screened": s_ms / b_ms,
             "ari_bf16_vs_fp32": sng.ari(lb, lf),
             "fp32_screened_labels_equal_fp32": bool(torch.equal(ls, lf)),
+            "fp32_screened_form": ["none", "bf16 copy", "bf16 copy, tensor cores",
+                                   "bf16 copy, TMA gathers + tcgen05",
+                                   "fp8 copy, tensor cores"][ss["map_screen"]],
+            "fp32_screened_open_pairs": ss["screen_pairs"],
             "edge_decision_error_vs_fp64": edge_error,
             "roofline_bf16": {"achieved": alg_b / (sb["ms"]["gather"] * 1e-3) / 1e9, "peak": peak,
                               "frac": alg_b / (sb["ms"]["gather"] * 1e-3) / 1e9 / peak,
@@ -1026,6 +1030,8 @@ def run_extensions(args) -> dict:
     out["bf16"] = {"workload": r["config"]["workload"], "ms_bf16": r["ms_bf16"],
                    "ms_fp32": r["ms_fp32"], "speedup_vs_fp32": r["speedup_vs_fp32"],
                    "ms_fp32_screened": r["ms_fp32_screened"],
+                   "fp32_screened_form": r["fp32_screened_form"],
+                   "fp32_screened_labels_equal_fp32": r["fp32_screened_labels_equal_fp32"],
                    "speedup_vs_fp32_screened": r["speedup_vs_fp32_screened"],
                    "ari_vs_fp32": r["ari_bf16_vs_fp32"],
                    "edge_decision_error_vs_fp64": r["edge_decision_error_vs_fp64"],

@@ -209,7 +209,7 @@ static void launch_ks(const GatherArgs &a, int64_t rows, cudaStream_t st) {
 }
 
 bool launch_gather_mma8(int ks, int minb, const GatherArgs &a, int64_t rows, cudaStream_t st) {
-  if (minb == 0) minb = ks <= 2 ? 2 : 3;
+  if (minb == 0) minb = 2;
   switch (ks * 10 + minb) {
     case 22: launch_ks<2, 2>(a, rows, st); return true;
     case 23: launch_ks<2, 3>(a, rows, st); return true;
