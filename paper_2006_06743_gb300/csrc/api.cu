@@ -347,6 +347,7 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
   g->screen_u = g->screen_abs = g->screen_g = 0.f;
   g->screen_kexp = nullptr;
   g->nbe = nullptr;
+  g->err_max = nullptr;
   g->openq = nullptr;
   g->openq_cnt = nullptr;
   g->openq_cap = 0;
@@ -605,6 +606,8 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     ga.nrm = sh.nrm;
     ga.nrm_max = sh.nmax;
     ga.nb2 = sh.nb2;
+    ga.nbe = sh.nbe;
+    ga.err_max = sh.nmax + kErrMaxSlot;
     ga.screen_cabs = std::ldexp(1.0f, -15);
     // the FP32 sum over the BF16 values: one rounding per difference, one
     // per fused multiply-add in a lane, one per shuffle level (as the
@@ -622,7 +625,6 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
       // wider allowance for the FP8 tensor core's accumulation
       ga.screen_u = 0.f;
       ga.screen_kexp = sh.kexp;
-      ga.nbe = sh.nbe;
       ga.screen_cabs = std::ldexp(1.0f, -9);
     }
     // open pairs are summed in order with one fused multiply-add per element
@@ -637,7 +639,7 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     return rc;
   gb->screened = screen;
   gb->map = rg->map;
-  if (fp8_ks || (mma_kt && !tc05)) {
+  if (fp8_ks || mma_kt) {
     // the queue of open pairs of the tensor-core forms: room for 1 in 32
     // draws of the row range (at most 2^26 entries); past it, or without
     // the memory, the gather decides open pairs itself
@@ -674,6 +676,7 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     gb->map.nch = 4;
     // map_unroll selects the ring's stages; stats report the count used
     if ((rc = launch_gather_tc05(ga, n, sh.ldb, p->map_unroll, &gb->map.unroll, st))) return rc;
+    if ((rc = launch_screen_queue(ga, st))) return rc;
   } else if (mma_kt) {
     // the tensor-core form of the screen (direct gather only): 16 partners
     // per MMA, mma_kt k-tiles of 16 values per row

@@ -82,10 +82,12 @@ struct GatherArgs {
   // BF16 rows (FP32 sums) and the coefficient of its absolute error bound
   const float *nb2;
   float screen_cabs;
-  // FP8 form (gather_mma8.cu): the copy holds x * 2^k, k = *screen_kexp;
-  // nbe[i] = {|x_i'|^2, bound of |x_i - x_i'|}
-  const int32_t *screen_kexp;
+  // tensor-core forms: nbe[i] = {|x_i'|^2, bound of |x_i - x_i'|}, err_max
+  // -> the largest such bound; FP8 form (gather_mma8.cu): the copy holds
+  // x * 2^k, k = *screen_kexp
   const float2 *nbe;
+  const float *err_max;
+  const int32_t *screen_kexp;
   // pairs the screen left open, queued for screen_queue_kernel: entries
   // {i, p, draw j, weight of i}, openq_cnt counts every open pair (past
   // openq_cap the gather decides them itself); q_lo_thr / q_hi_thr are the
@@ -158,17 +160,13 @@ __device__ __forceinline__ void screen_thresholds(const GatherArgs &a, float nrm
   drop_thr = (hi * hi) * (1.f + a.screen_g);
 }
 
-// Keep / drop thresholds of the tensor-core screen (gather_mma.cu,
-// gather_tc05.cu) for a source row of norm bound nrm_i against partners of
-// norm bound at most nrm_p: the screen's thresholds above, widened by the
-// absolute bound of |a'|^2 + |b'|^2 - 2 a'.b' (screen_cabs (nrm_i + nrm_p)^2
-// + 2^-100).
-__device__ __forceinline__ void mma_screen_thresholds(const GatherArgs &a, float nrm_i,
-                                                      float nrm_p, float &keep_thr,
-                                                      float &drop_thr) {
-  const float eta = fmaf(a.screen_u, nrm_i + nrm_p, a.screen_abs);
-  const float s = nrm_i + nrm_p;
-  const float e_abs = fmaf(a.screen_cabs * s, s, 0x1p-100f);
+// Keep / drop thresholds of a pair (or of a row against every partner) whose
+// distance the copy's rounding moves by at most eta (the sum of the two
+// rows' own error bounds, by the triangle inequality), widened by the
+// evaluation bound e_abs of |a'|^2 + |b'|^2 - 2 a'.b' (gather_mma.cu,
+// gather_mma8.cu).
+__device__ __forceinline__ void pair_thresholds(const GatherArgs &a, float eta, float e_abs,
+                                                float &keep_thr, float &drop_thr) {
   const float lo = a.screen_lo_eps - eta;
   const float hi = a.screen_hi_eps + eta;
   keep_thr = lo > 0x1p-10f * a.screen_lo_eps ? fmaf(lo * lo, 1.f - a.screen_g, -e_abs) : -1.f;

@@ -18,16 +18,19 @@
 // feeds word 2ks + h of that slice to k-tile ks, half h.  Each row is then
 // read as whole 32-byte pieces, a quad of lanes covering one 128-byte line.
 //
-// Error bound.  With a' = bf16(a), the computed value
+// Error bound.  With a' = bf16(a), the copy moves a pair's distance by at
+// most eta = e_a + e_b, the rows' own rounding-error bounds e_i >= |x_i -
+// x_i'| (screen.cu; triangle inequality).  The computed value
 // d2 = fl(fl(|a'|^2 + |b'|^2) - 2 dot) differs from |a' - b'|^2 by at most
 // c_abs (|a| + |b|)^2 + 2^-100: the norm sums (at most d + 5 roundings of
 // 2^-24 each), the final add and fused multiply-add, and the tensor core's
 // FP32 accumulation of exact products (bounded here by 2^-17 of
 // sum |a'_k b'_k| <= |a'| |b'|, well above its documented rounding) --
 // c_abs = 2^-15 covers all of it for d <= 128, the 2^-100 any product
-// flushed below FP32's normal range.  The screen's keep / drop thresholds
-// are widened by that bound; every pair they leave open is decided from
-// the FP32 points exactly as without the screen: queued for
+// flushed below FP32's normal range.  A row's keep / drop thresholds use
+// eta against the largest partner bound and decide almost every pair; a
+// pair between them is tested with its own eta.  Every pair left open is
+// decided from the FP32 points exactly as without the screen: queued for
 // screen_queue.cu, or, without room in the queue, here (screen_pair).
 #include "api_common.cuh"
 #include "gather.cuh"
@@ -78,6 +81,7 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
   if (threadIdx.x == 0) s_open = 0;
   __syncthreads();
   const float nrm_pmax = a.nrm_max[0];
+  const float err_pmax = *a.err_max;   // largest |b - b'| bound of the copy
   // lane r's draw r sits in MMA half r / 16, row r % 16 (c[0] of rows < 8,
   // c[2] of rows >= 8), held by lanes 4 (r % 8) .. 4 (r % 8) + 3
   const int src_lane = 4 * (lane & 7);
@@ -92,9 +96,14 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
     const uint64_t key = row_key(a.seed, i);
     uint32_t b[2 * KT];
     load_slice<KT>(X + (int64_t)i * a.ld, q, b);
-    const float na2 = __ldg(a.nb2 + i);
-    float keep_thr, drop_thr;
-    mma_screen_thresholds(a, __ldg(a.nrm + i), nrm_pmax, keep_thr, drop_thr);
+    const float2 ai = __ldg(a.nbe + i);   // {|a'|^2, |a - a'| bound}
+    // the evaluation bound of d2 for this row against any partner
+    const float nsum = __ldg(a.nrm + i) + nrm_pmax;
+    const float e_abs = fmaf(a.screen_cabs * nsum, nsum, 0x1p-100f);
+    // the row's thresholds against the largest partner error bound, which
+    // decide almost every pair; the rest are tested with their own bound
+    float keep_row, drop_row;
+    pair_thresholds(a, ai.y + err_pmax, e_abs, keep_row, drop_row);
     int cnt = 0;
     int jb = 0;
     // draws past the row's count read row 0 and decide nothing
@@ -104,7 +113,7 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
     int32_t p = draw(lane);
     for (; jb < mi; jb += 32) {
       const bool live = jb + lane < mi;
-      const float nbp = __ldg(a.nb2 + p);
+      const float2 bp = __ldg(a.nbe + p);
       // the stage's 32 partner rows, four per lane group, all in flight:
       // group t holds draws 8 t .. 8 t + 7 (row g of it: draw 8 t + g)
       uint32_t r[4][2 * KT];
@@ -128,9 +137,15 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
       const float d10 = __shfl_sync(kFullMask, c1[0], src_lane);
       const float d12 = __shfl_sync(kFullMask, c1[2], src_lane);
       const float dot = second ? (upper ? d12 : d10) : (upper ? d02 : d00);
-      const float d2 = fmaf(-2.f, dot, na2 + nbp);
-      bool keep = live && d2 <= keep_thr;
-      const bool open = live && !keep && !(d2 > drop_thr);
+      const float d2 = fmaf(-2.f, dot, ai.x + bp.x);
+      bool keep = live && d2 <= keep_row;
+      bool open = live && !keep && !(d2 > drop_row);
+      if (open) {
+        float keep_thr, drop_thr;
+        pair_thresholds(a, ai.y + bp.y, e_abs, keep_thr, drop_thr);
+        keep = d2 <= keep_thr;
+        open = !keep && !(d2 > drop_thr);
+      }
       const uint32_t om = __ballot_sync(kFullMask, open);
       if (om) {
         // open pairs to the queue (one atomic per warp); without a queue, or

@@ -65,17 +65,6 @@ __device__ __forceinline__ void load_slice8(const uint8_t *row, int q, uint32_t 
   }
 }
 
-// Keep / drop thresholds of a pair (or of a row against every partner) whose
-// distance the copy's rounding moves by at most eta: the BF16 form's
-// thresholds, with eta from the rows' own error bounds.
-__device__ __forceinline__ void pair_thresholds(const GatherArgs &a, float eta, float e_abs,
-                                                float &keep_thr, float &drop_thr) {
-  const float lo = a.screen_lo_eps - eta;
-  const float hi = a.screen_hi_eps + eta;
-  keep_thr = lo > 0x1p-10f * a.screen_lo_eps ? fmaf(lo * lo, 1.f - a.screen_g, -e_abs) : -1.f;
-  drop_thr = fmaf(hi * hi, 1.f + a.screen_g, e_abs);
-}
-
 // One warp per source row, draws in stages of 32 (one hash per lane), each
 // stage as two groups of 16 partners through KS MMAs of K = 32.  Lane r owns
 // draw r of the stage (the same hand-off of dot products as gather_mma.cu).
@@ -89,7 +78,7 @@ __global__ void __launch_bounds__(256, MINB) gather_mma8_kernel(GatherArgs a) {
   if (threadIdx.x == 0) s_open = 0;
   __syncthreads();
   const float nrm_pmax = a.nrm_max[0];
-  const float err_pmax = a.nrm_max[1];   // largest |b - b'| bound of the copy
+  const float err_pmax = *a.err_max;   // largest |b - b'| bound of the copy
   // the copy's scale: dot products in units of x are A.B 2^-2k
   const int32_t kx = *a.screen_kexp;
   const float m2inv = -ldexpf(2.f, -2 * kx);

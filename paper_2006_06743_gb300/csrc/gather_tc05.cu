@@ -3,15 +3,15 @@
 // tcgen05 tensor-core instructions.
 //
 // Same decisions as gather_mma.cu (the BF16 copy's squared distance
-// |a'|^2 + |b'|^2 - 2 a'.b', certified thresholds, open pairs decided from
-// the FP32 points), different data path.  A CTA works on four source rows at
+// |a'|^2 + |b'|^2 - 2 a'.b', the same certified thresholds, open pairs
+// queued for screen_queue.cu), different data path.  A CTA works on four source rows at
 // a time (a group), in stages of 32 draws per row, with warp-specialised
 // roles joined by mbarriers:
 //
 //   * producers (warps 4 and 5, two source rows each) wait for a free slot
 //     of an NS-stage shared-memory ring, hash the stage's draws, write the
-//     partner ids, start 4-byte asynchronous copies of the partners' squared
-//     norms, and issue TMA tile::gather4 loads that copy four partner rows
+//     partner ids, start 8-byte asynchronous copies of the partners' squared
+//     norms and error bounds, and issue TMA tile::gather4 loads that copy four partner rows
 //     (128 bytes each) of the BF16 copy per instruction into the slot's A
 //     tile (128 rows, 128-byte swizzle, K-major) -- plus one for the group's
 //     four source rows into the slot's B tile (rows 4..15 stay zero);
@@ -54,8 +54,8 @@ struct T5Layout {
   static constexpr uint32_t a = 0;                        // NS x 128 partner rows x 128 B
   static constexpr uint32_t b = NS * 16384;               // NS x 16 source rows x 128 B
   static constexpr uint32_t idx = b + NS * 2048;          // NS x 128 partner ids
-  static constexpr uint32_t nb = idx + NS * 512;          // NS x 128 partner |b'|^2
-  static constexpr uint32_t bar = nb + NS * 512;          // full, empty, acc_full, acc_empty
+  static constexpr uint32_t nb = idx + NS * 512;          // NS x 128 partner {|b'|^2, e_b}
+  static constexpr uint32_t bar = nb + NS * 1024;         // full, empty, acc_full, acc_empty
   static constexpr uint32_t slot = bar + (2 * NS + 2 * kT5Acc) * 8;   // TMEM base address
   static constexpr uint32_t abort = slot + 4;             // shared abort flag
   static constexpr uint32_t open = abort + 4;             // pairs the screen left open
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kT5Threads) gather_tc05_kernel(
   auto accf = [&](int c) { return bar0 + 8u * (uint32_t)(2 * NS + c); };
   auto acce = [&](int c) { return bar0 + 8u * (uint32_t)(2 * NS + kT5Acc + c); };
   int32_t *idx = reinterpret_cast<int32_t *>(sm + L::idx);
-  float *nbs = reinterpret_cast<float *>(sm + L::nb);
+  float2 *nbs = reinterpret_cast<float2 *>(sm + L::nb);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + L::abort);
   unsigned int *s_open = reinterpret_cast<unsigned int *>(sm + L::open);
   uint32_t *slot = reinterpret_cast<uint32_t *>(sm + L::slot);
@@ -238,9 +238,9 @@ __global__ void __launch_bounds__(kT5Threads) gather_tc05_kernel(
                            : 0;
           const int e = s * 128 + 64 * k + 32 * h + lane;
           idx[e] = p[h];
-          // the partner's |b'|^2, copied asynchronously into the slot
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(t5_smem(nbs + e)),
-                       "l"(a.nb2 + p[h])
+          // the partner's {|b'|^2, error bound}, copied asynchronously
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(t5_smem(nbs + e)),
+                       "l"(a.nbe + p[h])
                        : "memory");
         }
         // this lane's arrival on the slot when its two copies have landed
@@ -325,6 +325,8 @@ __global__ void __launch_bounds__(kT5Threads) gather_tc05_kernel(
     // ---------------------------------------------------------- epilogue
     const uint32_t t_row = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lanes
     const float nrm_pmax = a.nrm_max[0];
+    const float err_pmax = *a.err_max;   // largest |b - b'| bound of the copy
+    const uint32_t lanes_below = (1u << lane) - 1u;
     unsigned int open = 0;
     uint32_t kq = 0;
     bool ok = true;
@@ -335,9 +337,13 @@ __global__ void __launch_bounds__(kT5Threads) gather_tc05_kernel(
       const int32_t i = has_row ? (int32_t)row : 0;
       const int32_t mi = has_row ? (a.m_row ? a.m_row[i] : a.m) : 0;
       const int32_t wi = a.w_row ? a.w_row[i] : 1;
-      const float na2 = __ldg(a.nb2 + i);
-      float keep_thr, drop_thr;
-      mma_screen_thresholds(a, __ldg(a.nrm + i), nrm_pmax, keep_thr, drop_thr);
+      const float2 ai = __ldg(a.nbe + i);   // {|a'|^2, |a - a'| bound}
+      const float nsum = __ldg(a.nrm + i) + nrm_pmax;
+      const float e_abs = fmaf(a.screen_cabs * nsum, nsum, 0x1p-100f);
+      // row thresholds against the largest partner error bound; pairs
+      // between them are tested with their own bound (gather_mma.cu)
+      float keep_row, drop_row;
+      pair_thresholds(a, ai.y + err_pmax, e_abs, keep_row, drop_row);
       int cnt = 0;
       for (int st = 0; st < stages; ++st, ++kq) {
         const int s = (int)(kq % NS), c = (int)(kq % kT5Acc);
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(kT5Threads) gather_tc05_kernel(
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int e = s * 128 + 32 * warp + lane;
         const int32_t p = idx[e];
-        const float nbp = nbs[e];
+        const float2 bp = nbs[e];
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
@@ -361,17 +367,35 @@ __global__ void __launch_bounds__(kT5Threads) gather_tc05_kernel(
           t5_arrive(empty(s));
         }
         const int jb = 32 * st;
-        bool keep = false;
-        if (jb + lane < mi) {
-          const float d2 = fmaf(-2.f, __uint_as_float(v), na2 + nbp);
-          if (d2 <= keep_thr) {
-            keep = true;
-          } else if (!(d2 > drop_thr)) {
-            keep = screen_pair(a, i, p);
-            ++open;
-          }
-          if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
+        const bool live = jb + lane < mi;
+        const float d2 = fmaf(-2.f, __uint_as_float(v), ai.x + bp.x);
+        bool keep = live && d2 <= keep_row;
+        bool in_band = live && !keep && !(d2 > drop_row);
+        if (in_band) {
+          float keep_thr, drop_thr;
+          pair_thresholds(a, ai.y + bp.y, e_abs, keep_thr, drop_thr);
+          keep = d2 <= keep_thr;
+          in_band = !keep && !(d2 > drop_thr);
         }
+        const uint32_t om = __ballot_sync(kFullMask, in_band);
+        if (om) {
+          // open pairs to the queue (one atomic per warp), past its
+          // capacity decided here
+          unsigned long long base = 0;
+          if (lane == 0) base = atomicAdd(a.openq_cnt, (unsigned long long)__popc(om));
+          base = __shfl_sync(kFullMask, base, 0);
+          if (in_band) {
+            const unsigned long long q = base + __popc(om & lanes_below);
+            if ((long long)q < a.openq_cap) {
+              a.openq[q] = make_uint4((uint32_t)i, (uint32_t)p, (uint32_t)(jb + lane),
+                                      (uint32_t)wi);
+            } else {
+              keep = screen_pair(a, i, p);
+              ++open;
+            }
+          }
+        }
+        if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
         const uint32_t word = __ballot_sync(kFullMask, keep);
         if (lane == 0 && jb < mi) __stcs(a.bitmask + (int64_t)i * a.W + (jb >> 5), word);
         cnt += __popc(word);
@@ -416,19 +440,18 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once (thread-safe static initialisation); null if the driver
+  // does not offer it
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-    else
-      cudaGetLastError();
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+    return nullptr;
+  }();
   return fn;
 }
 

@@ -36,19 +36,22 @@ __device__ __forceinline__ void block_max_bits(unsigned int v, unsigned int *out
 // within (d/32 + 6) 2^-24 relative of the exact one; the correctly rounded
 // square root times (1 + 2^-11) is then an upper bound of |x_i| for every
 // supported d.  Sums that overflow give +inf (no certificate); values too
-// small to square in FP32 are covered by the screen's absolute slack.
+// small to square in FP32 are covered by the screen's absolute slack.  The
+// same sum over the differences x - bf16(x) (exact in FP32: they are the
+// low bits of x) bounds the copy's rounding error |x_i - x_i'|, with 2^-60
+// for squares below FP32's range.
 __global__ void __launch_bounds__(256) shadow_kernel(const float *x, int64_t ld, int32_t d,
                                                      int64_t n, uint16_t *xb, int64_t ldb,
-                                                     float *nrm, float *nb2,
+                                                     float *nrm, float *nb2, float2 *nbe,
                                                      unsigned int *nmax_all) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned int mx = 0u;
+  unsigned int mx = 0u, ex = 0u;
   for (int64_t i = warp; i < n; i += warps) {
     const float *row = x + i * ld;
     uint16_t *out = xb + i * ldb;
-    float ss = 0.f, sb = 0.f;
+    float ss = 0.f, sb = 0.f, se = 0.f;
     for (int64_t k = lane; k < ldb; k += 32) {
       const float v = k < d ? __ldg(row + k) : 0.f;
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -56,20 +59,27 @@ __global__ void __launch_bounds__(256) shadow_kernel(const float *x, int64_t ld,
       ss = fmaf(v, v, ss);
       const float vb = __bfloat162float(h);
       sb = fmaf(vb, vb, sb);   // the square of a BF16 value is exact in FP32
+      const float e = v - vb;
+      se = fmaf(e, e, se);
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
       ss += __shfl_xor_sync(kFullMask, ss, o);
       sb += __shfl_xor_sync(kFullMask, sb, o);
+      se += __shfl_xor_sync(kFullMask, se, o);
     }
     const float bound = sqrtf(ss) * (1.f + 0x1p-11f);
+    const float err = fmaf(sqrtf(se), 1.f + 0x1p-11f, 0x1p-60f);
     if (lane == 0) {
       nrm[i] = bound;
       nb2[i] = sb;
+      nbe[i] = make_float2(sb, err);
     }
     mx = max(mx, __float_as_uint(bound));
+    ex = max(ex, __float_as_uint(err));
   }
   block_max_bits(mx, nmax_all);
+  block_max_bits(ex, nmax_all + kErrMaxSlot);
 }
 
 // Maximum norm bound over each slice of `slice` consecutive rows, into
@@ -96,14 +106,15 @@ sng_status make_shadow(const float *x, int64_t ld, int32_t d, int64_t n, int64_t
   if ((rc = s.alloc((void **)&out->xb, (size_t)n * out->ldb * 2, "BF16 screen copy")) ||
       (rc = s.alloc((void **)&out->nrm, (size_t)n * 4, "row norm bounds")) ||
       (rc = s.alloc((void **)&out->nb2, (size_t)n * 4, "squared norms of the copy")) ||
-      (rc = s.alloc((void **)&out->nmax, (size_t)(1 + kShadowSlices) * 4, "norm maxima")))
+      (rc = s.alloc((void **)&out->nbe, (size_t)n * 8, "squared norms and errors of the copy")) ||
+      (rc = s.alloc((void **)&out->nmax, (size_t)(1 + kErrMaxSlot) * 4, "norm maxima")))
     return rc;
-  cudaMemsetAsync(out->nmax, 0, (size_t)(1 + kShadowSlices) * 4, st);
+  cudaMemsetAsync(out->nmax, 0, (size_t)(1 + kErrMaxSlot) * 4, st);
   const int64_t blocks_needed = (n + 7) / 8;
   const int64_t cap = (int64_t)device_sms() * 8;
   const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
   shadow_kernel<<<grid, 256, 0, st>>>(x, ld, d, n, out->xb, out->ldb, out->nrm, out->nb2,
-                                      reinterpret_cast<unsigned int *>(out->nmax));
+                                      out->nbe, reinterpret_cast<unsigned int *>(out->nmax));
   note_launch();
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SNG_OK : cuda_fail(e, "BF16 screen copy");
@@ -190,7 +201,7 @@ __global__ void __launch_bounds__(256) shadow8_kernel(const float *x, int64_t ld
     ex = max(ex, __float_as_uint(err));
   }
   block_max_bits(mx, nmax_all);
-  block_max_bits(ex, nmax_all + 1);
+  block_max_bits(ex, nmax_all + kErrMaxSlot);
 }
 
 sng_status make_shadow8(const float *x, int64_t ld, int32_t d, int64_t n, int64_t ldb,
@@ -204,11 +215,11 @@ sng_status make_shadow8(const float *x, int64_t ld, int32_t d, int64_t n, int64_
   if ((rc = s.alloc((void **)&out->xb, (size_t)n * ldb, "FP8 screen copy")) ||
       (rc = s.alloc((void **)&out->nrm, (size_t)n * 4, "row norm bounds")) ||
       (rc = s.alloc((void **)&out->nbe, (size_t)n * 8, "squared norms and errors of the copy")) ||
-      (rc = s.alloc((void **)&out->nmax, (size_t)(1 + kShadowSlices) * 4, "norm maxima")) ||
+      (rc = s.alloc((void **)&out->nmax, (size_t)(1 + kErrMaxSlot) * 4, "norm maxima")) ||
       (rc = s.alloc((void **)&amax, 8, "largest value")))
     return rc;
   out->kexp = reinterpret_cast<int32_t *>(amax) + 1;
-  cudaMemsetAsync(out->nmax, 0, (size_t)(1 + kShadowSlices) * 4, st);
+  cudaMemsetAsync(out->nmax, 0, (size_t)(1 + kErrMaxSlot) * 4, st);
   cudaMemsetAsync(amax, 0, 4, st);
   const int64_t blocks_needed = (n + 7) / 8;
   const int64_t cap = (int64_t)device_sms() * 8;
