@@ -166,9 +166,49 @@ __global__ void core_init_kernel(CoreArgs a) {
   }
 }
 
+// Thread per edge: hook the larger of the two ends of every core-core edge
+// to the smaller one (atomicMin on its parent entry) -- the ends themselves
+// in the first round, their parent entries (after a compression, their
+// roots) in later rounds.  Each entry only ever moves to a smaller index in
+// the same component, so `parent` stays a valid union-find forest whose
+// roots are each tree's smallest index.  An entry lowered twice keeps only
+// the smaller link, so a round may leave two ends in different trees; the
+// union pass after the rounds joins every edge exactly.  The rounds are
+// streams of independent atomics, where the union pass is a chain of
+// dependent loads and contended compare-and-swaps per edge.
+__global__ void hook_kernel(UnionArgs a, int from_parents) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t num_edges = a.num_edges_dev ? *a.num_edges_dev : a.num_edges;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < num_edges;
+       e += stride) {
+    const int32_t i = a.src[e], p = a.col[e];
+    // out-of-range edges are reported by union_kernel
+    if ((uint32_t)i >= (uint32_t)a.n || (uint32_t)p >= (uint32_t)a.n) continue;
+    if (!a.core[i] || !a.core[p]) continue;
+    const int32_t u = from_parents ? __ldcg(a.parent + i) : i;
+    const int32_t v = from_parents ? __ldcg(a.parent + p) : p;
+    if (u != v) atomicMin(a.parent + (u > v ? u : v), u > v ? v : u);
+  }
+}
+
+// Thread per point: point every core straight at its root.  The walk
+// follows decreasing indices, so it ends (and it is bounded like every
+// union-find loop); concurrent writes only replace an entry by one of its
+// ancestors, so every walk still reaches the same root.
+__global__ void compress_kernel(UnionArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.n; x += stride) {
+    if (!a.core[x]) continue;
+    const int32_t r = uf_root(a.parent, (int32_t)x, status, a.loop_limit);
+    if (r != (int32_t)x) a.parent[x] = r;
+  }
+}
+
 // Thread per edge: join the components of both ends of every core-core
 // edge (edges are independent, so the work is balanced however the kept
-// draws are spread over rows).
+// draws are spread over rows).  After the hooking rounds most edges find
+// both ends with the same parent entry.
 __global__ void union_kernel(UnionArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
@@ -180,7 +220,13 @@ __global__ void union_kernel(UnionArgs a) {
       atomicOr(status, kErrIndex);   // caller-supplied edge out of range: skipped
       continue;
     }
-    if (a.core[i] && a.core[p]) uf_unite(a.parent, i, p, status, a.loop_limit);
+    if (a.core[i] && a.core[p]) {
+      // ends that share a parent entry are in one set already; that test
+      // needs neither root lookup (whose lines every edge of a component
+      // would read); otherwise unite from the two parents
+      const int32_t pi = __ldcg(a.parent + i), pp = __ldcg(a.parent + p);
+      if (pi != pp) uf_unite(a.parent, pi, pp, status, a.loop_limit);
+    }
   }
 }
 
@@ -308,9 +354,19 @@ void launch_core_init(const CoreArgs &a, int sms, cudaStream_t st) {
   note_launch();
 }
 
+// Hooking rounds before the union pass: at 10^6 points and 9.8 * 10^6 kept
+// edges the union phase took 1.36 ms after none, 1.10 after one, 0.37 after
+// two, 0.44 after three (each round streams every edge once more).
+constexpr int kUnionHookRounds = 2;
+
 void launch_union(const UnionArgs &a, int sms, cudaStream_t st) {
+  const int rounds = kUnionHookRounds;
+  for (int r = 0; r < rounds; ++r) {
+    hook_kernel<<<grid_for(a.num_edges, 256, sms * 16), 256, 0, st>>>(a, r > 0);
+    compress_kernel<<<grid_for(a.n, 256, sms * 16), 256, 0, st>>>(a);
+  }
   union_kernel<<<grid_for(a.num_edges, 256, sms * 16), 256, 0, st>>>(a);
-  note_launch();
+  note_launch(2 * rounds + 1);
 }
 
 void launch_label(const UnionArgs &a, int sms, cudaStream_t st) {
