@@ -139,7 +139,7 @@ CAPTURED_TRAFFIC = {
     # the tensor-core screen: one gather_mma_kernel launch and the queue of
     # open pairs (profiles/gather_mma_mixture-n1M-d64.md)
     ("mixture-n1M-d64", "gather_mma_kernel<4, 3> + screen_queue_kernel"):
-        50_133_228_544 + 434_944_000 + 452_224_768 + 28_201_984,
+        54_903_795_968 + 432_543_232 + 174_607_104 + 7_820_288,
 }
 
 
