@@ -193,14 +193,17 @@ __global__ void hook_kernel(UnionArgs a, int from_parents) {
 
 // Thread per point: point every core straight at its root.  The walk
 // follows decreasing indices, so it ends (and it is bounded like every
-// union-find loop); concurrent writes only replace an entry by one of its
+// union-find loop); it halves the path as it goes (uf_find), so a long
+// chain -- a path whose indices increase along it, as in points sorted
+// along a curve -- costs every walker a logarithmic share rather than its
+// whole length; concurrent writes only replace an entry by one of its
 // ancestors, so every walk still reaches the same root.
 __global__ void compress_kernel(UnionArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   uint32_t *status = reinterpret_cast<uint32_t *>(a.counters + kCntStatus);
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.n; x += stride) {
     if (!a.core[x]) continue;
-    const int32_t r = uf_root(a.parent, (int32_t)x, status, a.loop_limit);
+    const int32_t r = uf_find(a.parent, (int32_t)x, status, a.loop_limit);
     if (r != (int32_t)x) a.parent[x] = r;
   }
 }
