@@ -900,7 +900,10 @@ def bench_surrogate(args):
     net = sg.Surrogate(datagen.mlp_init(d, 128, args.seed), cfg=sg.TrainConfig(batch=4096))
     net.standardize(xtr)
     t_train, trace = _timed(lambda: net.train(xtr, ytr, args.train_steps), 1)
-    p = sng.Params(eps=eps, min_pts=8, s=0.0005, seed=99, flags=sng.SNG_FLAG_TIMING)
+    # plain and surrogate both through the tensor-core screen of the FP32
+    # points (exact, the fastest form for this shape)
+    p = sng.Params(eps=eps, min_pts=8, s=0.0005, seed=99,
+                   flags=sng.SNG_FLAG_TIMING | sng.SNG_FLAG_SCREEN16 | sng.SNG_FLAG_SCREEN_MMA)
     gates = {
         # the configuration as written: confidence in [0.1, 0.9] falls back to
         # full queries (confident core draws core_frac of them, confident

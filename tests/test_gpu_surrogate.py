@@ -154,8 +154,11 @@ def _gate_variants(prob, tol, m, pn, pc, frac, nfrac, rw, orc, limit=4, by_degre
     return out
 
 
-@pytest.mark.parametrize("n,fp32_act", [(2000, 0), (2000, 2), (6000, 1), (400_000, 1)])
-def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act):
+@pytest.mark.parametrize("n,fp32_act,form", [(2000, 0, "plain"), (2000, 2, "plain"),
+                                             (6000, 1, "plain"), (400_000, 1, "plain"),
+                                             (6000, 1, "mma"), (6000, 1, "tc05"),
+                                             (6000, 1, "fp8")])
+def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act, form):
     """The surrogate path against the oracle's gated form of Algorithm 1, with
     every expected value from the oracle: the gate's probabilities from the
     FP64 network oracle on the trained network's FP16-rounded weights, its
@@ -165,7 +168,8 @@ def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act):
     with FP32 activations, 2e-3 on tensor cores); the at most four points
     left there may be decided either way, and the result must equal the
     oracle's for one of those combinations.  At n = 400,000 the gather runs one lane per row, with
-    per-row draw counts and weights."""
+    per-row draw counts and weights; the screened forms (tensor-core BF16,
+    TMA + tcgen05, FP8 copy) take the same per-row counts and weights."""
     torch, sng = need_gpu()
     from paper_2006_06743_gb300 import surrogate as sg
     d, m = 8, 120
@@ -173,7 +177,11 @@ def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act):
                                  sigma_hi=0.1)
     eps = datagen.eps_quantile(x, 0.05, 200_000, seed=2)
     xg = torch.from_numpy(x).cuda()
-    p = sng.Params(eps=eps, min_pts=5, m=m, seed=4)
+    flags = {"plain": 0, "mma": sng.SNG_FLAG_SCREEN16 | sng.SNG_FLAG_SCREEN_MMA,
+             "tc05": sng.SNG_FLAG_SCREEN16 | sng.SNG_FLAG_SCREEN_MMA | sng.SNG_FLAG_TCGEN05,
+             "fp8": sng.SNG_FLAG_SCREEN8}[form]
+    want_screen = {"plain": 0, "mma": 2, "tc05": 3, "fp8": 4}[form]
+    p = sng.Params(eps=eps, min_pts=5, m=m, seed=4, flags=flags)
     plain, plain_core, _ = sng.cluster(xg, p, want_core=True)
     net = sg.Surrogate(datagen.mlp_init(d, 128, 2), cfg=sg.TrainConfig(batch=1024, lr=3e-3))
     net.standardize(xg)
@@ -196,6 +204,7 @@ def test_gated_cluster_matches_oracle_gated_form(orc, n, fp32_act):
         assert pn <= pc
         labels, core, st = net.cluster(xg, p, pn, pc, frac, nfrac, rw, want_core=True,
                                        by_degree=bd)
+        assert st["map_screen"] == want_screen
         got_l, got_c = labels.cpu().numpy(), core.cpu().numpy()
         match = False
         for forced, m_row, w_row in _gate_variants(prob, tol, m, pn, pc, frac, nfrac, rw, orc,
