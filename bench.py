@@ -138,7 +138,7 @@ CAPTURED_TRAFFIC = {
         21_680_128 + 8_046_274_048 + 11_679_285_760 + 172_615_680,
     # the tensor-core screen: one gather_mma_kernel launch and the queue of
     # open pairs (profiles/gather_mma_mixture-n1M-d64.md)
-    ("mixture-n1M-d64", "gather_mma_kernel<4, 3> + screen_queue_kernel"):
+    ("mixture-n1M-d64", "gather_mma_kernel<4, 3, false> + screen_queue_kernel"):
         54_903_795_968 + 432_543_232 + 174_607_104 + 7_820_288,
 }
 
@@ -188,7 +188,7 @@ def gather_kernel_name_and_bytes(stats: dict, n: int, d: int, m: int) -> tuple[s
         ks = stats["map_nch"]
         row = 32 * ks
         byts = n * m * (row + 8) + n * (row + 8) + common
-        name = f"gather_mma8_kernel<{ks}, {stats['map_unroll'] or 2}>"
+        name = f"gather_mma8_kernel<{ks}, {stats['map_unroll'] or 2}, false>"
     elif screen == 3:
         row = 128
         byts = n * m * (row + 4) + n * (row + 8) + common
@@ -197,7 +197,7 @@ def gather_kernel_name_and_bytes(stats: dict, n: int, d: int, m: int) -> tuple[s
         kt = stats["map_nch"]
         row = 16 * kt * 2
         byts = n * m * (row + 4) + n * (row + 8) + common
-        name = f"gather_mma_kernel<{kt}, {stats['map_unroll'] or (3 if kt <= 4 else 2)}>"
+        name = f"gather_mma_kernel<{kt}, {stats['map_unroll'] or (3 if kt <= 4 else 2)}, false>"
     else:
         esize, vec = (2, 8) if screen else (4, 4)
         row = (-(-d // 8) * 8 if screen else d) * esize

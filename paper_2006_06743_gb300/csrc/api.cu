@@ -352,6 +352,8 @@ bool fill_gather_args(const void *x, const sng_params *p, const Resolved &r, Gat
   g->openq_cnt = nullptr;
   g->openq_cap = 0;
   g->q_lo_thr = g->q_hi_thr = 0.f;
+  g->sim_screen = 0;
+  g->sim_keep_thr = g->sim_drop_thr = g->sim_cm = 0.f;
   g->nrm = nullptr;
   g->nrm_max = nullptr;
   // L2 prefetch of partner rows when rows start on 16 bytes (16-byte vectors)
@@ -556,16 +558,21 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   sng_params pb;
   Resolved rb;
   Shadow sh;
-  const bool screen = (p->flags & (SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN8)) && p->dtype == SNG_F32 &&
-                      p->metric == SNG_METRIC_L2 && r.map.passes <= 1 && !r.map.lanes &&
-                      !(p->flags & SNG_FLAG_NO_SYNC);
+  const bool sim = p->metric != SNG_METRIC_L2;
+  const bool want_screen = (p->flags & (SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN8)) &&
+                           p->dtype == SNG_F32 && r.map.passes <= 1 && !r.map.lanes &&
+                           !(p->flags & SNG_FLAG_NO_SYNC);
   // the FP8 form: k-tiles of 32 values (rows of 64 or 128 bytes)
-  const int fp8_ks = screen && (p->flags & SNG_FLAG_SCREEN8) && p->d <= 128
+  const int fp8_ks = want_screen && (p->flags & SNG_FLAG_SCREEN8) && p->d <= 128
                          ? (p->d <= 64 ? 2 : 4) : 0;
-  const int mma_kt = screen && !fp8_ks && (p->flags & (SNG_FLAG_SCREEN_MMA | SNG_FLAG_SCREEN8))
+  const int mma_kt = want_screen && !fp8_ks &&
+                             (p->flags & (SNG_FLAG_SCREEN_MMA | SNG_FLAG_SCREEN8))
                          ? mma_tiles_for(p->d) : 0;
-  // the TMA + tcgen05 form reads rows of 64 BF16 values (zero past d)
-  const bool tc05 = mma_kt && (p->flags & SNG_FLAG_TCGEN05) && p->d <= 64;
+  // the similarity metrics are screened by the tensor-core forms only
+  const bool screen = want_screen && (!sim || fp8_ks || mma_kt);
+  // the TMA + tcgen05 form reads rows of 64 BF16 values (zero past d);
+  // Euclidean only
+  const bool tc05 = mma_kt && !sim && (p->flags & SNG_FLAG_TCGEN05) && p->d <= 64;
   if (screen) {
     wait_inputs(st);
     if (fp8_ks) {
@@ -626,6 +633,19 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
       ga.screen_u = 0.f;
       ga.screen_kexp = sh.kexp;
       ga.screen_cabs = std::ldexp(1.0f, -9);
+    }
+    if (sim) {
+      // keep at or above tau + band, drop below tau - band (the band
+      // widened by 2^-20, the thresholds rounded outwards); the MMA's
+      // accumulation allowance as for the Euclidean form's c_abs
+      const double tau = (double)p->eps;
+      const double bw = (double)r.band * (1.0 + std::ldexp(1.0, -20));
+      ga.sim_screen = 1;
+      ga.sim_keep_thr = round_up_f(tau + bw);
+      float dt = (float)(tau - bw);
+      if ((double)dt > tau - bw) dt = std::nextafter(dt, -INFINITY);
+      ga.sim_drop_thr = dt;
+      ga.sim_cm = fp8_ks ? std::ldexp(1.0f, -11) : std::ldexp(1.0f, -17);
     }
     // open pairs are summed in order with one fused multiply-add per element
     fp32_guard(r.eps2, r.band_rel, p->d, 0, &ga.lo_thr, &ga.hi_thr);

@@ -96,6 +96,13 @@ struct GatherArgs {
   unsigned long long *openq_cnt;
   int64_t openq_cap;
   float q_lo_thr, q_hi_thr;
+  // similarity form of the tensor-core screens (sim_screen = 1): keep when
+  // the pair's certified interval of the similarity lies at or above
+  // sim_keep_thr (tau + band, rounded up), drop when below sim_drop_thr
+  // (tau - band, rounded down); sim_cm bounds the MMA's accumulation error
+  // relative to |a'| |b'|
+  int32_t sim_screen;
+  float sim_keep_thr, sim_drop_thr, sim_cm;
   uint32_t *bitmask;      // n x W
   int32_t *out_cnt;       // n, nullable
   int32_t *deg;           // n (zeroed before launch in multigraph mode)
@@ -171,6 +178,46 @@ __device__ __forceinline__ void pair_thresholds(const GatherArgs &a, float eta, 
   const float hi = a.screen_hi_eps + eta;
   keep_thr = lo > 0x1p-10f * a.screen_lo_eps ? fmaf(lo * lo, 1.f - a.screen_g, -e_abs) : -1.f;
   drop_thr = fmaf(hi * hi, 1.f + a.screen_g, e_abs);
+}
+
+// Similarity form of the tensor-core screens: the pair's decision from the
+// copy's inner product `dot` (in the units of x) of rows a', b' with squared
+// norms na2, nb2 (FP32 sums of exact squares) and rounding-error bounds
+// ea >= |a - a'|, eb >= |b - b'|.  <a,b> - <a',b'> = <a - a', b> +
+// <a', b - b'>, so |<a,b> - <a',b'>| <= ea (|b'| + eb) + |a'| eb; the MMA
+// adds at most sim_cm |a'| |b'|, and 2^-24 |a'| |b'| covers the rounding of
+// these terms and of the FP64 reference value.  For cosine the interval of
+// <a,b> is divided by the interval of |a| |b| (|a| within ea of |a'|);
+// norms outside [2^-60, 2^60] certify nothing.  Returns 1 (keep), 0 (drop)
+// or -1 (open: FP64 decides); NaN anywhere leaves the pair open.
+static __device__ __noinline__ int sim_screen_decide(const GatherArgs &a, float dot, float na2,
+                                                     float ea, float nb2, float eb) {
+  const float ra = sqrtf(na2), rb = sqrtf(nb2);   // correctly rounded
+  const float na = ra * (1.f + 0x1p-12f), nb = rb * (1.f + 0x1p-12f);   // >= |a'|, |b'|
+  float eta = fmaf(ea, nb + eb, na * eb);
+  eta = fmaf((a.sim_cm + 0x1p-24f) * na, nb, eta);
+  eta = fmaf(eta, 0x1p-20f, eta) + 0x1p-100f;
+  const float w = 0x1p-22f * fabsf(dot);
+  float lo = dot - eta - w, hi = dot + eta + w;
+  if (a.cosine) {
+    const float al = fmaf(ra, -0x1p-12f, ra) - ea, bl = fmaf(rb, -0x1p-12f, rb) - eb;
+    const float ah = na + ea, bh = nb + eb;
+    if (!(al >= 0x1p-60f && bl >= 0x1p-60f && ah <= 0x1p60f && bh <= 0x1p60f)) return -1;
+    const float pl = (al * bl) * (1.f - 0x1p-22f), ph = (ah * bh) * (1.f + 0x1p-22f);
+    const float cl = lo >= 0.f ? lo / ph : lo / pl;
+    const float ch = hi >= 0.f ? hi / pl : hi / ph;
+    lo = cl - 0x1p-22f * fabsf(cl);
+    hi = ch + 0x1p-22f * fabsf(ch);
+  }
+  if (lo >= a.sim_keep_thr) return 1;
+  if (hi < a.sim_drop_thr) return 0;
+  return -1;
+}
+
+// The FP64 similarity recheck as a call of its own (the tensor-core gathers
+// reach it only for pairs they cannot queue).
+static __device__ __noinline__ bool sim_pair(const GatherArgs &a, int32_t i, int32_t p) {
+  return recheck_sim(a, i, p);
 }
 
 // A pair the BF16 screen left open: the FP32 squared distance of the FP32

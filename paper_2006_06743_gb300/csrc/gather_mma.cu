@@ -71,7 +71,7 @@ __device__ __forceinline__ void load_slice(const uint16_t *row, int q, uint32_t 
 // the stage: it hashes it, loads its partner's squared norm, receives its dot
 // product from the lanes that hold that MMA row and decides it, so the keep
 // bits come out of one ballot in draw order.
-template <int KT, int MINB>
+template <int KT, int MINB, bool SIM>
 __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -137,14 +137,22 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
       const float d10 = __shfl_sync(kFullMask, c1[0], src_lane);
       const float d12 = __shfl_sync(kFullMask, c1[2], src_lane);
       const float dot = second ? (upper ? d12 : d10) : (upper ? d02 : d00);
-      const float d2 = fmaf(-2.f, dot, ai.x + bp.x);
-      bool keep = live && d2 <= keep_row;
-      bool open = live && !keep && !(d2 > drop_row);
-      if (open) {
-        float keep_thr, drop_thr;
-        pair_thresholds(a, ai.y + bp.y, e_abs, keep_thr, drop_thr);
-        keep = d2 <= keep_thr;
-        open = !keep && !(d2 > drop_thr);
+      bool keep, open;
+      if constexpr (SIM) {
+        // inner product / cosine: the pair's certified interval
+        const int dec = live ? sim_screen_decide(a, dot, ai.x, ai.y, bp.x, bp.y) : 0;
+        keep = dec == 1;
+        open = dec < 0;
+      } else {
+        const float d2 = fmaf(-2.f, dot, ai.x + bp.x);
+        keep = live && d2 <= keep_row;
+        open = live && !keep && !(d2 > drop_row);
+        if (open) {
+          float keep_thr, drop_thr;
+          pair_thresholds(a, ai.y + bp.y, e_abs, keep_thr, drop_thr);
+          keep = d2 <= keep_thr;
+          open = !keep && !(d2 > drop_thr);
+        }
       }
       const uint32_t om = __ballot_sync(kFullMask, open);
       if (om) {
@@ -160,7 +168,11 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
             a.openq[slot] = make_uint4((uint32_t)i, (uint32_t)p, (uint32_t)(jb + lane),
                                        (uint32_t)wi);
           } else {
-            keep = screen_pair(a, i, p);
+            if constexpr (SIM) {
+              keep = sim_pair(a, i, p);
+            } else {
+              keep = screen_pair(a, i, p);
+            }
             atomicAdd(&s_open, 1u);
           }
         }
@@ -193,17 +205,25 @@ int mma_tiles_for(int d) {
   return 0;
 }
 
-template <int KT, int MINB>
+template <int KT, int MINB, bool SIM>
 static void launch_kt(const GatherArgs &a, int64_t rows, cudaStream_t st) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_mma_kernel<KT, MINB>, 256,
-                                                    0) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_mma_kernel<KT, MINB, SIM>,
+                                                    256, 0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int64_t need = (rows + 7) / 8;
   int64_t grid = (int64_t)device_sms() * per_sm;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  gather_mma_kernel<KT, MINB><<<(int)grid, 256, 0, st>>>(a);
+  gather_mma_kernel<KT, MINB, SIM><<<(int)grid, 256, 0, st>>>(a);
+}
+
+template <int KT, int MINB>
+static void launch_kt(const GatherArgs &a, int64_t rows, cudaStream_t st) {
+  if (a.sim_screen)
+    launch_kt<KT, MINB, true>(a, rows, st);
+  else
+    launch_kt<KT, MINB, false>(a, rows, st);
 }
 
 bool launch_gather_mma(int kt, int minb, const GatherArgs &a, int64_t rows, cudaStream_t st) {

@@ -68,7 +68,7 @@ __device__ __forceinline__ void load_slice8(const uint8_t *row, int q, uint32_t 
 // One warp per source row, draws in stages of 32 (one hash per lane), each
 // stage as two groups of 16 partners through KS MMAs of K = 32.  Lane r owns
 // draw r of the stage (the same hand-off of dot products as gather_mma.cu).
-template <int KS, int MINB>
+template <int KS, int MINB, bool SIM>
 __global__ void __launch_bounds__(256, MINB) gather_mma8_kernel(GatherArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256, MINB) gather_mma8_kernel(GatherArgs a) {
   // the copy's scale: dot products in units of x are A.B 2^-2k
   const int32_t kx = *a.screen_kexp;
   const float m2inv = -ldexpf(2.f, -2 * kx);
+  const float dscale = ldexpf(1.f, -2 * kx);
   const int src_lane = 4 * (lane & 7);
   const bool upper = (lane & 8) != 0;
   const bool second = lane >= 16;
@@ -136,14 +137,24 @@ __global__ void __launch_bounds__(256, MINB) gather_mma8_kernel(GatherArgs a) {
       const float d10 = __shfl_sync(kFullMask, c1[0], src_lane);
       const float d12 = __shfl_sync(kFullMask, c1[2], src_lane);
       const float dot = second ? (upper ? d12 : d10) : (upper ? d02 : d00);
-      const float d2 = fmaf(m2inv, dot, ai.x + bp.x);
-      bool keep = live && d2 <= keep_row;
-      bool open = live && !keep && !(d2 > drop_row);
-      if (open) {
-        float keep_thr, drop_thr;
-        pair_thresholds(a, ai.y + bp.y, e_abs, keep_thr, drop_thr);
-        keep = d2 <= keep_thr;
-        open = !keep && !(d2 > drop_thr);
+      bool keep, open;
+      if constexpr (SIM) {
+        // inner product / cosine: the pair's certified interval (the dot
+        // product scaled back to the units of x exactly)
+        const int dec =
+            live ? sim_screen_decide(a, dot * dscale, ai.x, ai.y, bp.x, bp.y) : 0;
+        keep = dec == 1;
+        open = dec < 0;
+      } else {
+        const float d2 = fmaf(m2inv, dot, ai.x + bp.x);
+        keep = live && d2 <= keep_row;
+        open = live && !keep && !(d2 > drop_row);
+        if (open) {
+          float keep_thr, drop_thr;
+          pair_thresholds(a, ai.y + bp.y, e_abs, keep_thr, drop_thr);
+          keep = d2 <= keep_thr;
+          open = !keep && !(d2 > drop_thr);
+        }
       }
       const uint32_t om = __ballot_sync(kFullMask, open);
       if (om) {
@@ -158,7 +169,11 @@ __global__ void __launch_bounds__(256, MINB) gather_mma8_kernel(GatherArgs a) {
             a.openq[slot] = make_uint4((uint32_t)i, (uint32_t)p, (uint32_t)(jb + lane),
                                        (uint32_t)wi);
           } else {
-            keep = screen_pair(a, i, p);
+            if constexpr (SIM) {
+              keep = sim_pair(a, i, p);
+            } else {
+              keep = screen_pair(a, i, p);
+            }
             atomicAdd(&s_open, 1u);
           }
         }
@@ -184,17 +199,25 @@ __global__ void __launch_bounds__(256, MINB) gather_mma8_kernel(GatherArgs a) {
   if (threadIdx.x == 0 && s_open) atomicAdd(a.counters + kCntScreen, (unsigned long long)s_open);
 }
 
-template <int KS, int MINB>
+template <int KS, int MINB, bool SIM>
 static void launch_ks(const GatherArgs &a, int64_t rows, cudaStream_t st) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_mma8_kernel<KS, MINB>, 256,
-                                                    0) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_mma8_kernel<KS, MINB, SIM>,
+                                                    256, 0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int64_t need = (rows + 7) / 8;
   int64_t grid = (int64_t)device_sms() * per_sm;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  gather_mma8_kernel<KS, MINB><<<(int)grid, 256, 0, st>>>(a);
+  gather_mma8_kernel<KS, MINB, SIM><<<(int)grid, 256, 0, st>>>(a);
+}
+
+template <int KS, int MINB>
+static void launch_ks(const GatherArgs &a, int64_t rows, cudaStream_t st) {
+  if (a.sim_screen)
+    launch_ks<KS, MINB, true>(a, rows, st);
+  else
+    launch_ks<KS, MINB, false>(a, rows, st);
 }
 
 bool launch_gather_mma8(int ks, int minb, const GatherArgs &a, int64_t rows, cudaStream_t st) {

@@ -2,7 +2,8 @@
 // step 2), decided from the FP32 points after the gather.
 //
 // The FP8 gather (gather_mma8.cu) certifies most pairs from its copy and
-// queues the rest as {i, p, draw j, weight of i}.  Deciding them inside the
+// queues the rest as {i, p, draw j, weight of i}.  (Similarity pairs go
+// straight to the FP64 recheck, one per thread.)  Deciding them inside the
 // gather would stall a whole warp on two FP32 row fetches per open pair;
 // here one warp takes one pair, its lanes read the two rows with coalesced
 // loads, and the pair is decided as the plain FP32 path decides it: the FP32
@@ -16,11 +17,35 @@
 
 namespace sng {
 
+// A kept pair into the gather's results: its keep bit, its row's count, the
+// degrees.
+__device__ __forceinline__ void queue_keep(const GatherArgs &a, int32_t i, int32_t p, uint32_t j,
+                                           int32_t wi) {
+  atomicOr(a.bitmask + (int64_t)i * a.W + (j >> 5), 1u << (j & 31));
+  if (a.out_cnt) atomicAdd(a.out_cnt + i, 1);
+  atomicAdd(a.deg + i, wi);
+  if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
+}
+
 __global__ void __launch_bounds__(256) screen_queue_kernel(GatherArgs a) {
   const int lane = threadIdx.x & 31;
   const unsigned long long queued = *a.openq_cnt;
   const int64_t total =
       (long long)queued < a.openq_cap ? (int64_t)queued : (int64_t)a.openq_cap;
+  if (a.sim_screen) {
+    // inner product / cosine: every open pair straight to the FP64 value in
+    // the oracle's order (the similarity form's recheck, with its band
+    // count), one pair per thread
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t t = t0; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+      const uint4 e = a.openq[t];
+      if (recheck_sim(a, (int32_t)e.x, (int32_t)e.y))
+        queue_keep(a, (int32_t)e.x, (int32_t)e.y, e.z, (int32_t)e.w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && total > 0)
+      atomicAdd(a.counters + kCntScreen, (unsigned long long)total);
+    return;
+  }
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t t = warp; t < total; t += warps) {
@@ -38,12 +63,7 @@ __global__ void __launch_bounds__(256) screen_queue_kernel(GatherArgs a) {
     if (lane == 0) {
       const bool keep =
           acc < a.q_lo_thr ? true : acc > a.q_hi_thr ? false : recheck_pair<float>(a, i, p);
-      if (keep) {
-        atomicOr(a.bitmask + (int64_t)i * a.W + (j >> 5), 1u << (j & 31));
-        if (a.out_cnt) atomicAdd(a.out_cnt + i, 1);
-        atomicAdd(a.deg + i, wi);
-        if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
-      }
+      if (keep) queue_keep(a, i, p, j, wi);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && total > 0)

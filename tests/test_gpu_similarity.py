@@ -183,3 +183,108 @@ def test_similarity_rejected_where_not_supported():
     # a negative threshold is a valid similarity threshold
     labels, _ = sng.cluster(x, sng.Params(eps=-0.25, min_pts=3, m=10, metric=DOT))
     assert labels.numel() == 200
+
+
+# ---------------------------------------------------------------------------
+# The similarity form through the tensor-core screens (a BF16 or FP8 copy of
+# the FP32 points, each pair certified from the copy's inner product and the
+# rows' own rounding-error bounds, the rest decided in FP64): the same graph,
+# band counts and labels as the oracle.
+
+SCREENS = {"mma": 2, "fp8": 4}
+
+
+def _screen_flags(sng, form):
+    return (sng.SNG_FLAG_SCREEN16 | sng.SNG_FLAG_SCREEN_MMA) if form == "mma" \
+        else sng.SNG_FLAG_SCREEN8
+
+
+@pytest.mark.parametrize("form", sorted(SCREENS))
+@pytest.mark.parametrize("metric", [DOT, COS])
+@pytest.mark.parametrize("n,d", [(500, 3), (1000, 7), (900, 16), (2000, 32), (1000, 64),
+                                 (1500, 65), (600, 128)])
+def test_screened_similarity_matches_oracle(orc, form, metric, n, d):
+    torch, sng = need_gpu()
+    x = datagen.random_points(n, d, seed=n + d) - 0.5
+    tau = _threshold(x, metric, 0.97, seed=d)
+    p = sng.Params(eps=tau, min_pts=3, m=min(150, 3 * n), seed=d, metric=metric,
+                   flags=_screen_flags(sng, form))
+    st = _compare(orc, sng, torch, x, torch.from_numpy(np.ascontiguousarray(x)).cuda(), p)
+    assert st["kept_edges"] > 0 and st["map_screen"] == SCREENS[form]
+
+
+@pytest.mark.parametrize("form", sorted(SCREENS))
+def test_screened_similarity_wider_rows_run_unscreened(orc, form):
+    """Past 128 values per row the similarity form reads the FP32 rows."""
+    torch, sng = need_gpu()
+    x = datagen.random_points(400, 200, seed=3) - 0.5
+    tau = _threshold(x, COS, 0.97)
+    p = sng.Params(eps=tau, min_pts=3, m=120, seed=3, metric=COS, flags=_screen_flags(sng, form))
+    st = _compare(orc, sng, torch, x, torch.from_numpy(x).cuda(), p)
+    assert st["map_screen"] == 0
+
+
+@pytest.mark.parametrize("form", sorted(SCREENS))
+def test_screened_dot_exact_ties(orc, form):
+    torch, sng = need_gpu()
+    rng = np.random.default_rng(2)
+    n, d = 2000, 4
+    x = rng.integers(-3, 4, (n, d)).astype(np.float32)
+    p = sng.Params(eps=4.0, min_pts=5, m=200, seed=1, metric=DOT, flags=_screen_flags(sng, form))
+    st = _compare(orc, sng, torch, x, torch.from_numpy(x).cuda(), p)
+    assert st["band_pairs"] > 1000
+
+
+@pytest.mark.parametrize("form", sorted(SCREENS))
+def test_screened_cosine_zero_and_nonfinite_rows(orc, form):
+    torch, sng = need_gpu()
+    n, d = 1500, 16
+    x = datagen.random_points(n, d, seed=9) - 0.5
+    x[::7] = 0.0
+    x[3, 2] = np.nan
+    x[11, 0] = np.inf
+    x[13, 5] = -np.inf
+    p = sng.Params(eps=0.3, min_pts=3, m=200, seed=2, metric=COS, flags=_screen_flags(sng, form))
+    _compare(orc, sng, torch, x, torch.from_numpy(x).cuda(), p)
+
+
+@pytest.mark.parametrize("form", sorted(SCREENS))
+@pytest.mark.parametrize("tau", [-0.2, 0.0, 0.3])
+def test_screened_cosine_extreme_magnitudes(orc, form, tau):
+    torch, sng = need_gpu()
+    n, d = 1200, 8
+    x = datagen.random_points(n, d, seed=12) - 0.5
+    x[::5] *= np.float32(1e20)
+    x[1::5] *= np.float32(1e-25)
+    p = sng.Params(eps=tau, min_pts=3, m=150, seed=4, metric=COS, flags=_screen_flags(sng, form))
+    st = _compare(orc, sng, torch, x, torch.from_numpy(x).cuda(), p)
+    assert st["kept_edges"] > 0
+
+
+@pytest.mark.parametrize("form", sorted(SCREENS))
+@pytest.mark.parametrize("metric", [DOT, COS])
+def test_screened_similarity_degree_modes_and_sample_all(orc, form, metric):
+    torch, sng = need_gpu()
+    n, d = 500, 6
+    x = datagen.random_points(n, d, seed=4) - 0.5
+    tau = _threshold(x, metric, 0.9)
+    for deg_mode in (0, 1, 2):
+        for p in (sng.Params(eps=tau, min_pts=4, m=300, seed=3, metric=metric,
+                             degree_mode=deg_mode, flags=_screen_flags(sng, form)),
+                  sng.Params(eps=tau, min_pts=4, sample_mode=1, metric=metric,
+                             degree_mode=deg_mode, flags=_screen_flags(sng, form))):
+            _compare(orc, sng, torch, x, torch.from_numpy(x).cuda(), p)
+
+
+@pytest.mark.parametrize("form", sorted(SCREENS))
+def test_screened_cosine_embeddings_leave_few_pairs_open(orc, form):
+    """Unit vectors around 100 centres (the embedding workload's recipe at
+    4*10^4 points, d = 128): the same graph and labels as the oracle, and
+    the screen certifies all but a small share of the pairs."""
+    torch, sng = need_gpu()
+    n, d = 40_000, 128
+    x = datagen.sphere_embeddings(n, d, 100, 0.0375, seed=1)
+    p = sng.Params(eps=float(np.float32(1 - 0.6 ** 2 / 2)), min_pts=8, m=200, seed=1,
+                   metric=COS, flags=_screen_flags(sng, form))
+    st = _compare(orc, sng, torch, x, torch.from_numpy(x).cuda(), p)
+    assert st["kept_edges"] > 0 and st["screen_pairs"] < 0.05 * n * 200
