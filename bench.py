@@ -710,6 +710,10 @@ def bench_cosine(args):
                      "frac_of_hbm": alg / (g_ms * 1e-3) / 1e9 / peak,
                      "kept_edges": st["kept_edges"], "recheck_pairs": st["recheck_pairs"],
                      "clusters": st["clusters"], "noise": st["noise"],
+                     "screen": ["none", "bf16 copy", "bf16 copy, tensor cores",
+                                "bf16 copy, TMA gathers + tcgen05",
+                                "fp8 copy, tensor cores"][st["map_screen"]],
+                     "screen_pairs": st["screen_pairs"],
                      "mapping": [st["map_vec"], st["map_group"], st["map_nch"],
                                  st["map_unroll"]]}
     for name in ("cosine_fp32", "dot_fp32", "l2_bf16", "cosine_bf16"):

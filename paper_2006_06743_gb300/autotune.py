@@ -73,7 +73,8 @@ def candidates(x, p: Params, screen: bool = True) -> list[dict]:
     # the certified BF16 screen of FP32 points (Euclidean, hashed draws): the
     # gather reads a BF16 copy (2 bytes per value of scratch), directly or
     # tiled with the slice count of the copy's size
-    if screen and esize == 4 and not p.metric and p.sample_mode == 0:
+    # (the similarity metrics: the tensor-core forms only)
+    if screen and esize == 4 and p.sample_mode == 0 and (not p.metric or d <= 128):
         free = torch.cuda.mem_get_info(x.device)[0] if x.is_cuda else 0
         gb = _default_group(d, 8)
         ldb = -(-d // 8) * 8
@@ -86,11 +87,13 @@ def candidates(x, p: Params, screen: bool = True) -> list[dict]:
                 # the FP8 copy (1 byte per value; more pairs left open)
                 out.append(dict(map_group=0, map_unroll=0, map_block=256, map_passes=0,
                                 prefetch=False, screen=True, fp8=True))
+        if xb_bytes < 0.25 * free and not p.metric:   # the screen on CUDA cores
             for g in sorted({max(1, gb // 2), gb}):
                 for u in (2, 4):
                     out.append(dict(map_group=g, map_unroll=u, map_block=256, map_passes=0,
                                     prefetch=False, screen=True))
-        if xb_bytes > (48 << 20) and 8.4 * n * p.draws(n) + xb_bytes < 0.5 * free:
+        if (not p.metric and xb_bytes > (48 << 20)
+                and 8.4 * n * p.draws(n) + xb_bytes < 0.5 * free):
             kb = min(32, max(2, -(-2 * xb_bytes // (88 << 20))))
             for k in sorted({kb, min(32, kb + 1)}):
                 for g in sorted({0, gb}):

@@ -163,8 +163,9 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
     one over the FP8 copy (d <= 128), the direct gather over the BF16 copy with
     the default lanes per pair for 8-value chunks and half of it, and, for
     copies over 48 MiB whose buckets fit, the tiled form with the copy's
-    slice count and one more.  None for BF16 points, similarity metrics or
-    every-pair sampling; the flag reaches the parameters."""
+    slice count and one more.  For similarity metrics only the tensor-core
+    forms; none for BF16 points or every-pair sampling; the flag reaches the
+    parameters."""
     import torch
     from paper_2006_06743_gb300 import (SNG_FLAG_SCREEN8, SNG_FLAG_SCREEN16, SNG_FLAG_SCREEN_MMA,
                                         Params, autotune)
@@ -198,5 +199,8 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
     # small point sets: the direct screened gather only
     assert all(not c.get("tiled") for c in screened(100_000, 64, m=100))
     assert screened(1_000_000, 64, dtype=torch.bfloat16, m=1000) == []
-    assert screened(1_000_000, 64, m=1000, metric=2) == []
+    # similarity metrics: the tensor-core forms only (d <= 128)
+    sim = screened(1_000_000, 64, m=1000, metric=2)
+    assert sim and all(c.get("mma") or c.get("fp8") for c in sim)
+    assert screened(1_000_000, 200, m=1000, metric=2) == []
     assert screened(200_000, 64, sample_mode=1) == []
