@@ -108,48 +108,51 @@ typedef int32_t sng_status;
                                 SNG_FLAG_NO_SYNC, no device memory for the
                                 buckets, or a bucket past its capacity (mean +
                                 8 standard deviations)                         */
-#define SNG_FLAG_SCREEN16 32u /* FP32 points, Euclidean form: the gather tests pairs
-                                on a BF16 copy of the points made inside the call
-                                (2 bytes per value of scratch, plus 4 per point),
-                                and decides a pair from it only where a bound
-                                on the copy's rounding (2^-8 of the two rows'
-                                norms) cannot change the decision; every other
-                                pair is summed again from the FP32 points and
-                                decided as without the flag.  Results are
-                                identical; stats report map_screen and
-                                screen_pairs.  Applies to the direct and the
-                                tiled gather; ignored for BF16 points, other
-                                metrics, one lane per row, map_passes > 1 and
-                                SNG_FLAG_NO_SYNC                                */
+#define SNG_FLAG_SCREEN16 32u /* FP32 points: the gather tests pairs on a BF16 copy
+                                of the points made inside the call (2 bytes per
+                                value of scratch, plus 20 per point), and
+                                decides a pair from it only where a bound on
+                                the copy's rounding cannot change the decision;
+                                every other pair is summed again from the FP32
+                                points and decided as without the flag.
+                                Results are identical; stats report map_screen
+                                and screen_pairs.  On CUDA cores (Euclidean
+                                form only) the bound is 2^-8 of the two rows'
+                                norms and the direct and tiled gathers apply;
+                                ignored for BF16 points, one lane per row,
+                                map_passes > 1 and SNG_FLAG_NO_SYNC            */
 #define SNG_FLAG_SCREEN_MMA 64u /* with SNG_FLAG_SCREEN16 and d <= 128: the direct
-                                gather forms each pair's squared distance on the
-                                BF16 copy as |a|^2 + |b|^2 - 2 a.b with the dot
-                                products of 16 partners at a time from BF16
-                                tensor-core MMAs (FP32 accumulation); the
-                                screen's thresholds are widened by the bound of
-                                that computation.  Same results.  The tiled
-                                form and map_group / map_unroll do not apply   */
-#define SNG_FLAG_SCREEN8 256u /* FP32 points, Euclidean form, d <= 128: the screen
-                                of SNG_FLAG_SCREEN16 on an FP8 (E4M3) copy of
+                                gather takes each pair's dot product on the
+                                BF16 copy from tensor-core MMAs (16 partners at
+                                a time, FP32 accumulation) -- the squared
+                                distance as |a|^2 + |b|^2 - 2 a.b, or the inner
+                                product or cosine for those metrics -- and
+                                certifies it from the rows' own rounding-error
+                                bounds (|a - a'| + |b - b'|) and the bound of
+                                the MMA.  Pairs it leaves open are queued and
+                                decided after the gather from the FP32 points.
+                                Same results.  map_unroll selects the register
+                                budget (2, 3 or 4 blocks per SM)               */
+#define SNG_FLAG_SCREEN8 256u /* FP32 points, d <= 128: the tensor-core screen of
+                                SNG_FLAG_SCREEN_MMA on an FP8 (E4M3) copy of
                                 x * 2^k (one power of two for the point set;
-                                1 byte per value of scratch), with the dot
-                                products from FP8 tensor-core MMAs.  The
-                                copy's rounding bound is 2^-4 of the norms
-                                (plus its subnormal range), so more pairs are
-                                left open and summed again from the FP32
-                                points; results are identical.  Stats report
-                                map_screen = 4.  Same exclusions as
+                                1 byte per value of scratch), with FP8 MMAs;
+                                every metric.  The copy's rounding is coarser,
+                                so more pairs are left open and decided from
+                                the FP32 points; results are identical.  Stats
+                                report map_screen = 4.  Same exclusions as
                                 SNG_FLAG_SCREEN16; takes precedence over it  */
-#define SNG_FLAG_TCGEN05 128u /* with SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN_MMA and
-                                d <= 64: the partner rows of the BF16 copy are
-                                fetched by the tensor memory accelerator
-                                (tile::gather4, four rows per copy) into shared
-                                memory and the dot products come from tcgen05
-                                MMAs (128 partners x 4 source rows per MMA,
-                                FP32 accumulators in tensor memory).  Same
-                                thresholds, same results; stats map_screen = 3.
-                                SNG_ECUDA where the driver offers no tensor-map
-                                encoder                                        */
+#define SNG_FLAG_TCGEN05 128u /* with SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN_MMA,
+                                Euclidean form, d <= 64: the partner rows of
+                                the BF16 copy are fetched by the tensor memory
+                                accelerator (tile::gather4, four rows per copy)
+                                into shared memory and the dot products come
+                                from tcgen05 MMAs (128 partners x 4 source rows
+                                per MMA, FP32 accumulators in tensor memory).
+                                Same thresholds, same results; stats
+                                map_screen = 3; map_unroll selects the ring's
+                                stages (2..5).  SNG_ECUDA where the driver
+                                offers no tensor-map encoder                  */
 #define SNG_FLAG_NO_SYNC 4u  /* sng_cluster only: no host synchronisation inside the
                                 call, so it can be captured in a CUDA graph.  The
                                 edge arrays are sized for all n*m draws (8 bytes
@@ -234,8 +237,8 @@ typedef struct {
                              (SNG_FLAG_TCGEN05; map_group 128 partners per
                              MMA); 4: FP8 copy, tensor-core dot products
                              (SNG_FLAG_SCREEN8; map_nch k-tiles of 32)     */
-    int64_t screen_pairs; /* SNG_FLAG_SCREEN16: pairs the BF16 screen left
-                             open, summed again from the FP32 points       */
+    int64_t screen_pairs; /* SNG_FLAG_SCREEN16 / SCREEN8: pairs the screen
+                             left open, decided again from the FP32 points */
 } sng_stats;
 
 typedef struct {
