@@ -110,7 +110,7 @@ typedef int32_t sng_status;
                                 8 standard deviations)                         */
 #define SNG_FLAG_SCREEN16 32u /* FP32 points: the gather tests pairs on a BF16 copy
                                 of the points made inside the call (2 bytes per
-                                value of scratch, plus 20 per point), and
+                                value of scratch, plus 16 per point), and
                                 decides a pair from it only where a bound on
                                 the copy's rounding cannot change the decision;
                                 every other pair is summed again from the FP32
@@ -118,9 +118,10 @@ typedef int32_t sng_status;
                                 Results are identical; stats report map_screen
                                 and screen_pairs.  On CUDA cores (Euclidean
                                 form only) the bound is 2^-8 of the two rows'
-                                norms and the direct and tiled gathers apply;
-                                ignored for BF16 points, one lane per row,
-                                map_passes > 1 and SNG_FLAG_NO_SYNC            */
+                                norms and the direct and tiled gathers apply
+                                (the tiled one not with SNG_FLAG_NO_SYNC);
+                                ignored for BF16 points, one lane per row and
+                                map_passes > 1                                 */
 #define SNG_FLAG_SCREEN_MMA 64u /* with SNG_FLAG_SCREEN16 and d <= 128: the direct
                                 gather takes each pair's dot product on the
                                 BF16 copy from tensor-core MMAs (16 partners at

@@ -559,9 +559,10 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   Resolved rb;
   Shadow sh;
   const bool sim = p->metric != SNG_METRIC_L2;
+  // (no host read on this path: the no-sync form and graph capture keep it;
+  // only the tiled form below needs one)
   const bool want_screen = (p->flags & (SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN8)) &&
-                           p->dtype == SNG_F32 && r.map.passes <= 1 && !r.map.lanes &&
-                           !(p->flags & SNG_FLAG_NO_SYNC);
+                           p->dtype == SNG_F32 && r.map.passes <= 1 && !r.map.lanes;
   // the FP8 form: k-tiles of 32 values (rows of 64 or 128 bytes)
   const int fp8_ks = want_screen && (p->flags & SNG_FLAG_SCREEN8) && p->d <= 128
                          ? (p->d <= 64 ? 2 : 4) : 0;

@@ -359,14 +359,19 @@ def test_lane_per_row_graph_matches_oracle(orc, dtype, d):
     np.testing.assert_array_equal(labels.cpu().numpy(), r["labels"])
 
 
-def test_no_sync_form_matches_and_replays_as_a_cuda_graph(orc):
+@pytest.mark.parametrize("form", ["plain", "mma", "fp8"])
+def test_no_sync_form_matches_and_replays_as_a_cuda_graph(orc, form):
     """SNG_FLAG_NO_SYNC: the same labels and counters as the synchronous call,
     and the call captured once in a CUDA graph replays correctly, also after
-    the points are overwritten in place (n = 10,000 mixture, s = 0.01)."""
+    the points are overwritten in place (n = 10,000 mixture, s = 0.01) -- with
+    the plain gather and through the tensor-core screens (their copy, queue
+    and open-pair kernel inside the graph)."""
     torch, sng = need_gpu()
     n = 10_000
     x = datagen.mixture_2d(n, seed=0)
-    p = sng.Params(eps=0.03, min_pts=3, s=0.01, seed=0)
+    flags = {"plain": 0, "mma": sng.SNG_FLAG_SCREEN16 | sng.SNG_FLAG_SCREEN_MMA,
+             "fp8": sng.SNG_FLAG_SCREEN8}[form]
+    p = sng.Params(eps=0.03, min_pts=3, s=0.01, seed=0, flags=flags)
     xg = torch.from_numpy(x).cuda()
     ref, st = sng.cluster(xg, p)
     labels = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -377,6 +382,7 @@ def test_no_sync_form_matches_and_replays_as_a_cuda_graph(orc):
     c = counters.cpu().tolist()
     assert c == [0, st["band_pairs"], st["recheck_pairs"], st["band_points"], st["cores"],
                  st["clusters"], st["noise"], st["kept_edges"], 0]
+    assert (st["map_screen"] > 0) == (form != "plain")
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
