@@ -986,7 +986,9 @@ def bench_sweep(args):
     smaller n), full DBSCAN computed on the GPU with every pair queried
     (s = 1, multigraph degree, MinPts = 2 (min_samples - 1)), and
     SNG-DBSCAN at decreasing s with MinPts scaled by s; ARI and AMI of each
-    against full DBSCAN and against the generating mixture."""
+    against full DBSCAN and against the generating mixture.  Then the
+    radius sweep at one sampling rate (the synthetic analogue of the paper's
+    ARI-against-eps figures): each eps against full DBSCAN at that eps."""
     import numpy as np
     import torch
 
@@ -1014,8 +1016,25 @@ def bench_sweep(args):
                      "speedup_vs_full": full_ms / ms, "ari_vs_full": sng.ari(lab, full),
                      "ari_vs_truth": sng.ari(lab, tg), "ami_vs_full": sng.ami(lab, full)["ami"],
                      "ami_vs_truth": sng.ami(lab, tg)["ami"], "clusters": st["clusters"]})
+    # the eps sweep at a fixed sampling rate: each radius against full
+    # DBSCAN at the same radius (eps from quantiles of the pairwise
+    # distances)
+    eps_rows = []
+    s_eps = args.sweep_eps_s
+    mp = max(2, int(round(2 * (k_db - 1) * s_eps)))
+    for q in args.sweep_eps_q:
+        e = datagen.eps_quantile(x, q, 1_000_000, seed=args.seed)
+        fp = sng.Params(eps=e, min_pts=2 * (k_db - 1), sample_mode=sng.SNG_SAMPLE_ALL)
+        ref, _ = sng.cluster(xg, fp)
+        p = sng.Params(eps=e, min_pts=mp, s=s_eps, seed=args.seed)
+        sng.cluster(xg, p)
+        ms, (lab, st) = _timed(lambda: sng.cluster(xg, p), 3)
+        eps_rows.append({"quantile": q, "eps": e, "ms": ms, "ari_vs_full": sng.ari(lab, ref),
+                         "ari_full_vs_truth": sng.ari(ref, tg), "ari_vs_truth": sng.ari(lab, tg),
+                         "ami_vs_full": sng.ami(lab, ref)["ami"], "clusters": st["clusters"]})
     return {"form": "sweep", "metric": "ARI vs full DBSCAN against sampling rate",
             "value": rows[-1]["ari_vs_full"], "unit": "ARI", "rows": rows,
+            "eps_sweep": {"s": s_eps, "min_pts": mp, "rows": eps_rows},
             "config": {"workload": f"mixture-n{n}-d{d}-k20", "eps": eps, "min_samples": k_db,
                        "min_pts_rule": "round(2 (min_samples - 1) s), at least 2"},
             "dtype": "f32"}
@@ -1160,6 +1179,11 @@ def main():
                     choices=["plain", "bf16", "batched", "surrogate", "balls", "sweep", "cosine",
                              "graph"])
     ap.add_argument("--sweep-n", type=int, default=100_000)
+    ap.add_argument("--sweep-eps-s", type=float, default=0.1,
+                    help="sampling rate of the eps sweep (--form sweep)")
+    ap.add_argument("--sweep-eps-q", type=float, nargs="+",
+                    default=[0.002, 0.005, 0.01, 0.02, 0.05],
+                    help="distance quantiles giving the eps values of the eps sweep")
     ap.add_argument("--sweep-s", type=float, nargs="+",
                     default=[0.3, 0.1, 0.03, 0.01, 0.003, 0.001])
     ap.add_argument("--balls-n", type=int, nargs="+",
