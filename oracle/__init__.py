@@ -99,6 +99,10 @@ def _load(openmp: bool = False):
         lib.orc_dot.restype = f64
         lib.orc_cosine.argtypes = [P, P, i32]
         lib.orc_cosine.restype = f64
+        lib.orc_l1.argtypes = [P, P, i32]
+        lib.orc_l1.restype = f64
+        lib.orc_linf.argtypes = [P, P, i32]
+        lib.orc_linf.restype = f64
         lib.orc_cluster_graph_forced.argtypes = [i64, P, P, i32, i32, P, P, P, P, P]
         lib.orc_cluster_graph_forced.restype = i32
         lib.orc_cluster_graph_gated.argtypes = [i64, P, P, i32, i32, P, P, P, P, P, P]
@@ -174,7 +178,7 @@ def dist2(a, b) -> float:
 
 
 # neighbourhood tests: Euclidean ball, inner product, cosine similarity
-METRIC_L2, METRIC_DOT, METRIC_COSINE = 0, 1, 2
+METRIC_L2, METRIC_DOT, METRIC_COSINE, METRIC_L1, METRIC_LINF = 0, 1, 2, 3, 4
 
 
 def dot(a, b) -> float:
@@ -192,6 +196,22 @@ def cosine(a, b) -> float:
     return float(_load().orc_cosine(_ptr(a), _ptr(b), a.size))
 
 
+def l1(a, b) -> float:
+    """FP64 Manhattan distance: differences, absolute values and sums left to
+    right; NaN when a difference is NaN."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    return float(_load().orc_l1(_ptr(a), _ptr(b), a.size))
+
+
+def linf(a, b) -> float:
+    """FP64 Chebyshev distance (largest |a_k - b_k|); NaN when a difference
+    is NaN."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    return float(_load().orc_linf(_ptr(a), _ptr(b), a.size))
+
+
 # ------------------------------------------------------------ graph build
 
 def build_rows(x, eps: float, seed: int, m: int, sample_all: bool = False,
@@ -199,7 +219,8 @@ def build_rows(x, eps: float, seed: int, m: int, sample_all: bool = False,
     """Algorithm 1, step 2 for the given rows (default all).  ``m_row`` (int32
     per point) limits point i to its first m_row[i] draws (surrogate form).
     ``metric``: METRIC_L2 (edge iff d2 <= eps^2), METRIC_DOT / METRIC_COSINE
-    (edge iff similarity >= eps).
+    (edge iff similarity >= eps), METRIC_L1 / METRIC_LINF (edge iff the
+    Manhattan / Chebyshev distance <= eps).
 
     Returns ``(row_ptr int64[nr+1], col int32[E], band_pairs, band_point uint8[n])``.
     """

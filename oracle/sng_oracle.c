@@ -27,7 +27,11 @@
  *    (Steele, Lea & Flood, OOPSLA 2014).  Duplicate draws are multi-edges.
  *  - Distance: d2 = sum_k ((double)a_k - (double)b_k)^2 summed left to right,
  *    every operation rounded separately (built with -ffp-contract=off);
- *    edge iff d2 <= (double)eps * (double)eps (closed ball, step 2).
+ *    edge iff d2 <= (double)eps * (double)eps (closed ball, step 2).  The
+ *    method needs only similarity queries (Section 1), so other neighbourhood
+ *    tests are offered as well, each in a stated FP64 order: inner product
+ *    and cosine similarity (edge iff sim >= eps), Manhattan and Chebyshev
+ *    distance (edge iff dist <= eps; orc_l1, orc_linf).
  *  - Degree (step 3) default: undirected multigraph degree, each kept draw
  *    (i,p) adds one to both endpoints.  Mode 1: out-degree only (the count
  *    that the proof of Lemma 2 thresholds).  Mode 2: simple-graph degree
@@ -173,10 +177,37 @@ double orc_cosine(const float *a, const float *b, int32_t d)
     return ab / den;
 }
 
+/* Manhattan distance sum_k |a_k - b_k| in FP64: each difference, its
+ * absolute value and each sum left to right; a NaN difference makes the
+ * distance NaN (never within eps). */
+double orc_l1(const float *a, const float *b, int32_t d)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < d; ++k) {
+        double t = (double)a[k] - (double)b[k];
+        s = s + fabs(t);
+    }
+    return s;
+}
+
+/* Chebyshev distance max_k |a_k - b_k| in FP64; a NaN difference makes the
+ * distance NaN (fmax would drop it). */
+double orc_linf(const float *a, const float *b, int32_t d)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < d; ++k) {
+        double t = fabs((double)a[k] - (double)b[k]);
+        if (t != t) return t;
+        if (t > s) s = t;
+    }
+    return s;
+}
+
 /* Algorithm 1, step 2 with the neighbourhood test of `metric`: 0 = Euclidean
  * ball (d2 <= eps^2, band |d2 - eps^2| <= band_rel eps^2); 1 = inner product,
  * 2 = cosine similarity (edge iff sim >= eps, band |sim - eps| <= band_rel
- * |eps|). */
+ * |eps|); 3 = Manhattan, 4 = Chebyshev distance (edge iff dist <= eps, band
+ * |dist - eps| <= band_rel eps). */
 int32_t orc_build_rows_metric(int64_t n, int32_t d, int64_t ld, const float *x, float eps,
                               uint64_t seed, int64_t m, int32_t sample_all, double band_rel,
                               const int64_t *rows, int64_t n_rows, orc_graph *out,
@@ -184,7 +215,7 @@ int32_t orc_build_rows_metric(int64_t n, int32_t d, int64_t ld, const float *x, 
 {
     if (n < 2 || d < 1 || ld < d || m < 0 || !out) return -1;
     if (sample_all && m != n - 1) return -1;
-    if (metric < 0 || metric > 2) return -1;
+    if (metric < 0 || metric > 4) return -1;
     if (!rows) n_rows = n;
     double eps2 = (double)eps * (double)eps;
     double band = band_rel * eps2;
@@ -209,6 +240,10 @@ int32_t orc_build_rows_metric(int64_t n, int32_t d, int64_t ld, const float *x, 
                 v = orc_dist2(xi, x + p * ld, d);
                 gap = v - eps2;
                 keep = v <= eps2;
+            } else if (metric >= 3) {
+                v = metric == 3 ? orc_l1(xi, x + p * ld, d) : orc_linf(xi, x + p * ld, d);
+                gap = v - tau;
+                keep = v <= tau;
             } else {
                 v = metric == 1 ? orc_dot(xi, x + p * ld, d) : orc_cosine(xi, x + p * ld, d);
                 gap = v - tau;
