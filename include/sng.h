@@ -81,6 +81,11 @@ typedef int32_t sng_status;
 #define SNG_METRIC_DOT 1    /* edge iff <a, b> >= eps                          */
 #define SNG_METRIC_COSINE 2 /* edge iff <a, b> / (sqrt(<a,a>) sqrt(<b,b>)) >= eps;
                                a zero vector is similar to nothing            */
+#define SNG_METRIC_L1 3     /* edge iff sum_k |a_k - b_k| <= eps (Manhattan)   */
+#define SNG_METRIC_LINF 4   /* edge iff max_k |a_k - b_k| <= eps (Chebyshev);
+                               L1 / LINF: FP32 points, one lane per pair of the
+                               direct gather (no screens, no tiles); a NaN
+                               difference is within eps of nothing            */
 
 /* flags */
 #define SNG_FLAG_TIMING 1u  /* fill sng_stats.ms with per-phase CUDA-event times */
@@ -171,12 +176,14 @@ typedef struct {
     int32_t degree_mode;  /* SNG_DEG_*                                       */
     int32_t sample_mode;  /* SNG_SAMPLE_*                                    */
     int32_t min_pts;      /* MinPts, >= 1                                    */
-    float eps;            /* SNG_METRIC_L2: radius, 1e-15 <= eps <= 1e18;
+    float eps;            /* SNG_METRIC_L2 / _L1 / _LINF: radius,
+                             1e-15 <= eps <= 1e18;
                              SNG_METRIC_DOT / _COSINE: similarity threshold,
                              any finite value                               */
     float band_rel;       /* half-width of the reported band |d2-eps^2| <=
                              band_rel*eps^2 (similarity: |sim-eps| <=
-                             band_rel*|eps|); 0 selects 1e-5 (F32) / 1e-3 (BF16) */
+                             band_rel*|eps|; L1 / LINF: |dist-eps| <=
+                             band_rel*eps); 0 selects 1e-5 (F32) / 1e-3 (BF16) */
     double s;             /* sampling rate in (0, 1]; m = ceil(s*n)          */
     int64_t m_override;   /* > 0: use this m instead of ceil(s*n); every m
                              must be in [1, 2^31 - 1025]                     */

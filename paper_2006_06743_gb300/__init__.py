@@ -28,6 +28,7 @@ SNG_OK, SNG_EINVAL, SNG_ENOMEM, SNG_ECUDA, SNG_ETIMEOUT, SNG_EINTERNAL = 0, -1, 
 SNG_F32, SNG_BF16 = 0, 1
 SNG_DEG_UNDIRECTED_MULTI, SNG_DEG_OUT, SNG_DEG_SIMPLE = 0, 1, 2
 SNG_METRIC_L2, SNG_METRIC_DOT, SNG_METRIC_COSINE = 0, 1, 2
+SNG_METRIC_L1, SNG_METRIC_LINF = 3, 4
 SNG_SAMPLE_HASH, SNG_SAMPLE_ALL = 0, 1
 SNG_FLAG_TIMING = 1
 SNG_FLAG_PREFETCH = 2
@@ -216,7 +217,8 @@ class Params:
     map_passes: int = 0
     row_begin: int = 0
     row_end: int = 0
-    metric: int = 0             # SNG_METRIC_*: 0 Euclidean ball, 1 inner product, 2 cosine
+    metric: int = 0             # SNG_METRIC_*: 0 Euclidean ball, 1 inner product, 2 cosine,
+                                # 3 Manhattan, 4 Chebyshev distance
 
     def to_c(self, n: int, d: int, ld: int, dtype: int, master_ptr: int = 0) -> sng_params:
         p = sng_params()

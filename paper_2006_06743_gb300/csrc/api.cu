@@ -19,6 +19,7 @@
 #include "graph.cuh"
 #include "gather_mma.cuh"
 #include "gather_mma8.cuh"
+#include "gather_pair.cuh"
 #include "screen_queue.cuh"
 #include "gather_tc05.cuh"
 #include "screen.cuh"
@@ -163,11 +164,15 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
     return fail(SNG_EINVAL, "unknown sample_mode");
   if (p->min_pts < 1) return fail(SNG_EINVAL, "min_pts must be >= 1");
   if (p->metric != SNG_METRIC_L2 && p->metric != SNG_METRIC_DOT &&
-      p->metric != SNG_METRIC_COSINE)
+      p->metric != SNG_METRIC_COSINE && p->metric != SNG_METRIC_L1 &&
+      p->metric != SNG_METRIC_LINF)
     return fail(SNG_EINVAL, "unknown metric");
+  const bool pair_metric = p->metric == SNG_METRIC_L1 || p->metric == SNG_METRIC_LINF;
   if (!std::isfinite(p->eps)) return fail(SNG_EINVAL, "eps must be finite");
-  if (p->metric == SNG_METRIC_L2 && (p->eps < 1e-15f || p->eps > 1e18f))
+  if ((p->metric == SNG_METRIC_L2 || pair_metric) && (p->eps < 1e-15f || p->eps > 1e18f))
     return fail(SNG_EINVAL, "eps must be in [1e-15, 1e18]");
+  if (pair_metric && p->dtype != SNG_F32)
+    return fail(SNG_EINVAL, "the Manhattan and Chebyshev forms take FP32 points");
   if (p->metric != SNG_METRIC_L2 && p->map_passes > 1)
     return fail(SNG_EINVAL, "the similarity form runs in one pass (map_passes <= 1)");
   if (p->flags & SNG_FLAG_NO_SYNC) {
@@ -310,6 +315,24 @@ sng_status validate(const void *x, const sng_params *p, Resolved *r) {
     r->sim_c1 = up(c1);
     r->sim_c2 = up(c2);
     r->band_f = up(r->band);
+  }
+  // Manhattan / Chebyshev distance: one lane sums |a_k - b_k| in order (each
+  // difference and each addition rounded once: within (d + 1) u relative of
+  // the exact sum of the non-negative terms) or takes their maximum (each
+  // term within u); the FP32 value decides outside the guard band eps (1 -+
+  // (band_rel + c)), c twice that bound plus 2^-22 for the FP64 result's own
+  // rounding, the thresholds rounded outwards; inside it the FP64 value does.
+  if (pair_metric) {
+    const double c = (p->metric == SNG_METRIC_L1 ? 2.0 * (double)(p->d + 2) : 4.0) * u +
+                     std::ldexp(1.0, -22);
+    const double eps = (double)p->eps;
+    const double lo = eps * (1.0 - (double)r->band_rel - c);
+    const double hi = eps * (1.0 + (double)r->band_rel + c);
+    float lof = (float)lo, hif = (float)hi;
+    if ((double)lof > lo) lof = std::nextafter(lof, 0.f);
+    if ((double)hif < hi) hif = std::nextafter(hif, INFINITY);
+    r->lo_thr = lof;
+    r->hi_thr = hif;
   }
   return SNG_OK;
 }
@@ -558,11 +581,13 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   sng_params pb;
   Resolved rb;
   Shadow sh;
-  const bool sim = p->metric != SNG_METRIC_L2;
+  const bool pair_metric = p->metric == SNG_METRIC_L1 || p->metric == SNG_METRIC_LINF;
+  const bool sim = p->metric != SNG_METRIC_L2 && !pair_metric;
   // (no host read on this path: the no-sync form and graph capture keep it;
   // only the tiled form below needs one)
   const bool want_screen = (p->flags & (SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN8)) &&
-                           p->dtype == SNG_F32 && r.map.passes <= 1 && !r.map.lanes;
+                           p->dtype == SNG_F32 && r.map.passes <= 1 && !r.map.lanes &&
+                           !pair_metric;
   // the FP8 form: k-tiles of 32 values (rows of 64 or 128 bytes)
   const int fp8_ks = want_screen && (p->flags & SNG_FLAG_SCREEN8) && p->d <= 128
                          ? (p->d <= 64 ? 2 : 4) : 0;
@@ -677,7 +702,11 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     }
     fp32_guard(r.eps2, r.band_rel, (p->d + 31) / 32, 5, &ga.q_lo_thr, &ga.q_hi_thr);
   }
-  if (fp8_ks) {
+  if (pair_metric) {
+    // Manhattan / Chebyshev: one lane per pair over the FP32 points
+    wait_inputs(st);
+    if ((rc = launch_gather_pair(p->metric, ga, st))) return rc;
+  } else if (fp8_ks) {
     // the FP8 copy: 16 partners per MMA, fp8_ks k-tiles of 32 values
     gb->mma = true;
     gb->fp8 = true;
