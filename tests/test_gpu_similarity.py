@@ -174,7 +174,7 @@ def test_bf16_cosine_exact_when_master_is_bf16(orc, n, d):
 def test_similarity_rejected_where_not_supported():
     torch, sng = need_gpu()
     x = torch.from_numpy(datagen.random_points(200, 3, seed=0)).cuda()
-    for p in (sng.Params(eps=0.5, min_pts=3, m=10, metric=3),
+    for p in (sng.Params(eps=0.5, min_pts=3, m=10, metric=5),
               sng.Params(eps=0.5, min_pts=3, m=10, metric=COS, map_passes=2),
               sng.Params(eps=float("nan"), min_pts=3, m=10, metric=DOT)):
         with pytest.raises(sng.SngError) as e:
