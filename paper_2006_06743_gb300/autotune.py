@@ -57,6 +57,9 @@ def _default_group(d: int, vec: int) -> int:
 def candidates(x, p: Params, screen: bool = True) -> list[dict]:
     import torch
     n, d = x.shape
+    if p.metric in (3, 4):
+        # Manhattan / Chebyshev: one pair-kernel gather, nothing to choose
+        return [dict(map_group=0, map_unroll=0, map_block=256, map_passes=0, prefetch=False)]
     esize = 2 if x.dtype == torch.bfloat16 else 4
     vec = 8 if esize == 2 else 4
     if x.stride(0) % vec:
