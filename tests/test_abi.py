@@ -206,6 +206,7 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
     assert screened(200_000, 64, sample_mode=1) == []
     # Manhattan / Chebyshev: the one pair-kernel gather
     for metric in (3, 4):
-        one = autotune.candidates(_FakeCudaRows(1_000_000, 64), Params(eps=1.0, min_pts=5,
-                                                                      metric=metric))
+        one = autotune.candidates(_FakeCudaRows(1_000_000, 64, torch.float32),
+                                  Params(eps=1.0, min_pts=5,
+                                         metric=metric))
         assert len(one) == 1 and not one[0].get("screen")
