@@ -4,14 +4,14 @@
 // neither the Euclidean ball nor an inner product, so no norm identity or
 // tensor-core form applies.
 //
-// One warp per source row, one lane per draw, stages of 32 draws: lane r
-// hashes draw r, walks its partner row (16-byte loads where rows allow;
-// the source row's values are the same address for every lane, a broadcast),
-// and forms the distance in FP32 -- the sum of |a_k - b_k| in order, or their
-// maximum.  Outside the guard band around eps (validate, api.cu) the FP32
-// value decides; inside it the FP64 value in the oracle's order does
+// One warp per source row, stages of 32 draws hashed one per lane; four
+// lanes per pair (below) form the distance in FP32 -- the sum of |a_k - b_k|
+// or their maximum.  Outside the guard band around eps (validate, api.cu)
+// the FP32 value decides; inside it the FP64 value in the oracle's order does
 // (recheck_pair_metric, which also counts the reported band).  Keep bits by
-// ballot, degrees by atomics, as in the other gathers.
+// ballot, degrees by atomics, as in the other gathers.  The group's order of
+// the additions (four partials per lane, their sum, then two shuffle levels)
+// keeps every term's roundings within the (d + 1) u of the guard band.
 #include "api_common.cuh"
 #include "gather.cuh"
 #include "gather_pair.cuh"
@@ -47,21 +47,33 @@ static __device__ __noinline__ bool recheck_pair_metric(const GatherArgs &a, int
   return s <= a.tau64;
 }
 
+// Partial distance: the sum of |u - v| or their maximum.  The terms are
+// non-negative (a NaN's sign cleared by the absolute value too), and for
+// such floats the order of the bit patterns as unsigned integers is the
+// order of the values with NaN above +inf -- so one integer maximum takes
+// the largest term and keeps a NaN (fmaxf would drop it).
 template <int METRIC>
-__device__ __forceinline__ void pair_step(float u, float v, float &acc, bool &nan) {
-  const float t = fabsf(u - v);
-  if (METRIC == SNG_METRIC_L1) {
-    acc += t;
-  } else {
-    nan |= t != t;   // fmaxf would drop a NaN
-    acc = t > acc ? t : acc;
-  }
+__device__ __forceinline__ float pair_combine(float acc, float t) {
+  if (METRIC == SNG_METRIC_L1) return acc + t;
+  return __uint_as_float(max(__float_as_uint(acc), __float_as_uint(t)));
 }
 
+// Group layout (VEC4 rows): four lanes per pair, lane q of a group reading
+// the 16-byte chunks q, q + 4, q + 8, ... of the partner row (so the group's
+// loads cover consecutive bytes) against the same chunks of the source row,
+// kept in registers for rows of up to 64 values; the four partials combine
+// in two shuffle levels.  A warp tests 8 pairs per step, 4 steps per stage
+// of 32 draws; each distance is handed back to the lane that drew it, which
+// decides it, so the stage's keep bits come from one ballot in draw order.
+// Rows whose length is not a multiple of 4 (or whose start is not 16-byte
+// aligned) take one lane per pair with scalar loads.
 template <int METRIC, bool VEC4>
 __global__ void __launch_bounds__(256) gather_pair_kernel(GatherArgs a) {
+  constexpr int kSrcChunks = 4;   // source chunks a lane keeps (rows of <= 64 values)
   const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, q = lane & 3;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int nc = a.d >> 2;        // 16-byte chunks per row (VEC4)
   for (int64_t row = a.row_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
        row < a.row_end; row += warps_total) {
     const int32_t i = (int32_t)row;
@@ -69,6 +81,15 @@ __global__ void __launch_bounds__(256) gather_pair_kernel(GatherArgs a) {
     const int32_t wi = a.w_row ? a.w_row[i] : 1;
     const uint64_t key = row_key(a.seed, i);
     const float *xa = a.xm + (int64_t)i * a.ldm;
+    float4 src[kSrcChunks];
+    if (VEC4) {
+#pragma unroll
+      for (int t = 0; t < kSrcChunks; ++t) {
+        const int c = q + 4 * t;
+        src[t] = c < nc ? __ldg(reinterpret_cast<const float4 *>(xa) + c)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
     int cnt = 0;
     for (int jb = 0; jb < mi; jb += 32) {
       const int j = jb + lane;
@@ -76,28 +97,52 @@ __global__ void __launch_bounds__(256) gather_pair_kernel(GatherArgs a) {
       // draws past the row's count read row 0 and decide nothing
       const int32_t p =
           live ? (a.sample_all ? partner_all(i, j) : partner_from_key(key, i, j, a.fm)) : 0;
-      const float *xb = a.xm + (int64_t)p * a.ldm;
-      float acc = 0.f;
-      bool nan = false;
+      float mine = 0.f;   // the distance of this lane's own draw
       if (VEC4) {
-        const float4 *ua = reinterpret_cast<const float4 *>(xa);
-        const float4 *vb = reinterpret_cast<const float4 *>(xb);
-        for (int k = 0; k < (a.d >> 2); ++k) {
-          const float4 u = __ldg(ua + k), v = __ldg(vb + k);
-          pair_step<METRIC>(u.x, v.x, acc, nan);
-          pair_step<METRIC>(u.y, v.y, acc, nan);
-          pair_step<METRIC>(u.z, v.z, acc, nan);
-          pair_step<METRIC>(u.w, v.w, acc, nan);
+#pragma unroll
+        for (int step = 0; step < 4; ++step) {
+          // group g tests draw 8 step + g
+          const int32_t pg = __shfl_sync(kFullMask, p, 8 * step + g);
+          const float4 *vb = reinterpret_cast<const float4 *>(a.xm + (int64_t)pg * a.ldm);
+          // four independent partials (one per vector component), combined
+          // at the end: each term still sees at most d / 16 + 5 roundings
+          float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
+#pragma unroll
+          for (int t = 0; t < kSrcChunks; ++t) {
+            const int c = q + 4 * t;
+            if (c < nc) {
+              const float4 v = __ldg(vb + c);
+              ax = pair_combine<METRIC>(ax, fabsf(src[t].x - v.x));
+              ay = pair_combine<METRIC>(ay, fabsf(src[t].y - v.y));
+              az = pair_combine<METRIC>(az, fabsf(src[t].z - v.z));
+              aw = pair_combine<METRIC>(aw, fabsf(src[t].w - v.w));
+            }
+          }
+          for (int c = q + 4 * kSrcChunks; c < nc; c += 4) {
+            const float4 u = __ldg(reinterpret_cast<const float4 *>(xa) + c);
+            const float4 v = __ldg(vb + c);
+            ax = pair_combine<METRIC>(ax, fabsf(u.x - v.x));
+            ay = pair_combine<METRIC>(ay, fabsf(u.y - v.y));
+            az = pair_combine<METRIC>(az, fabsf(u.z - v.z));
+            aw = pair_combine<METRIC>(aw, fabsf(u.w - v.w));
+          }
+          float acc = pair_combine<METRIC>(pair_combine<METRIC>(ax, ay),
+                                           pair_combine<METRIC>(az, aw));
+          acc = pair_combine<METRIC>(acc, __shfl_xor_sync(kFullMask, acc, 1));
+          acc = pair_combine<METRIC>(acc, __shfl_xor_sync(kFullMask, acc, 2));
+          const float got = __shfl_sync(kFullMask, acc, 4 * (lane & 7));
+          if ((lane >> 3) == step) mine = got;
         }
       } else {
-        for (int k = 0; k < a.d; ++k) pair_step<METRIC>(__ldg(xa + k), __ldg(xb + k), acc, nan);
+        const float *xb = a.xm + (int64_t)p * a.ldm;
+        for (int k = 0; k < a.d; ++k)
+          mine = pair_combine<METRIC>(mine, fabsf(__ldg(xa + k) - __ldg(xb + k)));
       }
-      if (nan) acc = __int_as_float(0x7fc00000);
       bool keep = false;
       if (live) {
-        if (acc < a.lo_thr) {
+        if (mine < a.lo_thr) {
           keep = true;
-        } else if (!(acc > a.hi_thr)) {
+        } else if (!(mine > a.hi_thr)) {
           keep = recheck_pair_metric<METRIC>(a, i, p);   // the guard band or NaN
         }
         if (keep && a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
