@@ -1,6 +1,7 @@
 """Step 2 with the Manhattan (L1) and Chebyshev (L-inf) distances against the
 FP64 oracle: CSR, degrees, band counts and labels bit-exact -- over row
-widths that take the 16-byte and the scalar loads, padded rows holding junk,
+widths that take the 16-byte group layout (source row in registers up to 64
+values, reloaded past it) and the scalar loads, padded rows holding junk,
 integer coordinates with many pairs exactly at eps (kept, counted in the
 band), rows with NaN and inf, every degree mode, every-pair sampling and
 source-row ranges; and the forms these metrics do not take (BF16 points,
@@ -48,7 +49,7 @@ def _compare(orc, sng, torch, x, xg, p):
 
 @pytest.mark.parametrize("metric", [L1, LINF])
 @pytest.mark.parametrize("n,d", [(400, 1), (700, 3), (1000, 4), (900, 7), (1200, 16),
-                                 (2000, 64), (800, 65), (500, 130)])
+                                 (2000, 64), (800, 65), (600, 128), (500, 130), (400, 200)])
 def test_pair_metric_graph_and_labels_match_oracle(orc, metric, n, d):
     torch, sng = need_gpu()
     x = datagen.random_points(n, d, seed=n + d + metric)
