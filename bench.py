@@ -410,6 +410,19 @@ def bench_sng(args, w):
     # rate the SMs read from L2, measured here by the library's own probe
     l2_peak = sng.measure_l2_read(48 << 20, 200)
     achieved_l2 = alg_l2 / (g_ms * 1e-3) / 1e9
+    # the tensor-core forms fetch one row of the copy per query: their
+    # ceiling is the rate at which the SMs fetch random rows of that size
+    # from a buffer of the copy's size (the library's random-row probe)
+    random_rows = None
+    if stats["map_screen"] in (2, 3, 4):
+        rb = {2: 32 * stats["map_nch"], 3: 128, 4: 32 * stats["map_nch"]}[stats["map_screen"]]
+        if rb in (64, 128, 256):
+            probe = sng.measure_random_rows(n, rb, 1 << 30)
+            fetched = Q / (g_ms * 1e-3)
+            random_rows = {"row_bytes": rb, "probe_rows_per_s": probe,
+                           "gather_rows_per_s": fetched, "frac": fetched / probe,
+                           "note": "queries (one row of the copy each) per second of the "
+                                   "gather phase against the probe's random-row rate"}
     truth = w["truth"].astype(np.int32)
     ari_truth = sng.ari(labels, torch.from_numpy(truth).to(dev))
     out = {
@@ -451,6 +464,7 @@ def bench_sng(args, w):
                      "kernel": kname, "peak_kind": "measured (sng_measure_l2_read, this run)",
                      "algorithmic_bytes": alg_l2, "kernel_ms": g_ms,
                      "traffic_frac": (traffic / (g_ms * 1e-3) / 1e9 / peak) if traffic else None,
+                     "random_rows": random_rows,
                      "hbm_model": {"bound": "hbm", "algorithmic_bytes": alg,
                                    "achieved": alg / (g_ms * 1e-3) / 1e9, "peak": peak,
                                    "peak_kind": peak_kind, "unit": "GB/s",

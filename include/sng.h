@@ -509,6 +509,20 @@ sng_status sng_gather_mapping(const void *x, const sng_params *params, int32_t *
  */
 sng_status sng_measure_l2_read(int64_t bytes, int32_t passes, double *gbs, void *stream);
 
+/*
+ * Measurement aid (no counterpart in the paper): the rate at which the SMs
+ * of the current device fetch rows at random from a device buffer of n_rows
+ * rows of row_bytes (64, 128 or 256) bytes -- the tensor-core gather's
+ * access pattern (four lanes per row, eight rows per load instruction,
+ * loads that bypass L1) without its hashing, MMAs or decisions, with
+ * blocks_per_sm blocks of 8 warps per SM (0: as many as fit).  About
+ * `fetches` rows are read after a warm-up; *rows_per_s receives rows per
+ * second between two CUDA events.  The ceiling of a gather bound by random
+ * row fetches.  Allocates and frees its buffer; synchronises `stream`.
+ */
+sng_status sng_measure_random_rows(int64_t n_rows, int32_t row_bytes, int64_t fetches,
+                                   int32_t blocks_per_sm, double *rows_per_s, void *stream);
+
 /* Number of kernels this library has launched in this process. */
 int64_t sng_launch_count(void);
 

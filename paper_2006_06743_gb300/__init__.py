@@ -151,6 +151,9 @@ SIGNATURES = {
     "sng_cluster_noalloc": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P,
                                              ctypes.POINTER(sng_stats), _P]),
     "sng_gather_mapping": (ctypes.c_int32, [_P, ctypes.POINTER(sng_params), _P]),
+    "sng_measure_random_rows": (ctypes.c_int32, [ctypes.c_int64, ctypes.c_int32,
+                                                 ctypes.c_int64, ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_double), _P]),
     "sng_measure_l2_read": (ctypes.c_int32, [ctypes.c_int64, ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_double), _P]),
     "sng_launch_count": (ctypes.c_int64, []),
@@ -436,6 +439,17 @@ def measure_l2_read(bytes_: int = 48 << 20, passes: int = 200, stream=None) -> f
     v = ctypes.c_double()
     _check(lib().sng_measure_l2_read(int(bytes_), int(passes), ctypes.byref(v),
                                      _stream_ptr(stream)))
+    return float(v.value)
+
+
+def measure_random_rows(n_rows: int, row_bytes: int = 128, fetches: int = 1 << 30,
+                        blocks_per_sm: int = 0, stream=None) -> float:
+    """Rows per second the SMs fetch at random from a buffer of n_rows rows
+    (the library's own probe kernel; see sng_measure_random_rows)."""
+    v = ctypes.c_double()
+    _check(lib().sng_measure_random_rows(int(n_rows), int(row_bytes), int(fetches),
+                                         int(blocks_per_sm), ctypes.byref(v),
+                                         _stream_ptr(stream)))
     return float(v.value)
 
 

@@ -210,3 +210,21 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
                                   Params(eps=1.0, min_pts=5,
                                          metric=metric))
         assert len(one) == 1 and not one[0].get("screen")
+
+
+def test_random_row_probe_rejects_bad_arguments_on_host():
+    """The probe validates its sizes before any CUDA call."""
+    import paper_2006_06743_gb300 as sng
+    sng.build()
+    v = ctypes.c_double()
+    L = sng.lib()
+    assert L.sng_measure_random_rows(1 << 20, 96, 1 << 24, 0, ctypes.byref(v), None) \
+        == sng.SNG_EINVAL
+    assert "row_bytes" in sng.last_error()
+    assert L.sng_measure_random_rows(512, 128, 1 << 24, 0, ctypes.byref(v), None) \
+        == sng.SNG_EINVAL
+    assert L.sng_measure_random_rows(1 << 27, 128, 1 << 24, 0, ctypes.byref(v), None) \
+        == sng.SNG_EINVAL      # 16 GiB of rows
+    assert L.sng_measure_random_rows(1 << 20, 128, 100, 0, ctypes.byref(v), None) \
+        == sng.SNG_EINVAL
+    assert L.sng_measure_random_rows(1 << 20, 128, 1 << 24, 0, None, None) == sng.SNG_EINVAL
