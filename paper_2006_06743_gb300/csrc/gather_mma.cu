@@ -78,6 +78,11 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
   const int g = lane >> 2, q = lane & 3;
   const uint16_t *X = static_cast<const uint16_t *>(a.x);
   __shared__ unsigned int s_open;   // open pairs decided here (no room in the queue)
+  // at 4 blocks per SM (64 registers) each lane keeps its slice of the
+  // source row (the MMAs' B operand) in shared memory, word w at w * 32 +
+  // lane of its warp's block: only the lane itself reads it back
+  constexpr bool kBShared = MINB >= 4;
+  __shared__ uint32_t s_b[kBShared ? 8 : 1][kBShared ? 2 * KT * 32 : 1];
   if (threadIdx.x == 0) s_open = 0;
   __syncthreads();
   const float nrm_pmax = a.nrm_max[0];
@@ -94,8 +99,15 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
     const int32_t mi = a.m_row ? a.m_row[i] : a.m;
     const int32_t wi = a.w_row ? a.w_row[i] : 1;
     const uint64_t key = row_key(a.seed, i);
-    uint32_t b[2 * KT];
-    load_slice<KT>(X + (int64_t)i * a.ld, q, b);
+    uint32_t b[kBShared ? 1 : 2 * KT];
+    if constexpr (kBShared) {
+      uint32_t bl[2 * KT];
+      load_slice<KT>(X + (int64_t)i * a.ld, q, bl);
+#pragma unroll
+      for (int w = 0; w < 2 * KT; ++w) s_b[warp][w * 32 + lane] = bl[w];
+    } else {
+      load_slice<KT>(X + (int64_t)i * a.ld, q, b);
+    }
     const float2 ai = __ldg(a.nbe + i);   // {|a'|^2, |a - a'| bound}
     // the evaluation bound of d2 for this row against any partner
     const float nsum = __ldg(a.nrm + i) + nrm_pmax;
@@ -127,10 +139,16 @@ __global__ void __launch_bounds__(256, MINB) gather_mma_kernel(GatherArgs a) {
       float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int ks = 0; ks < KT; ++ks) {
-        mma_bf16_16816(c0, r[0][2 * ks], r[1][2 * ks], r[0][2 * ks + 1], r[1][2 * ks + 1],
-                       b[2 * ks], b[2 * ks + 1]);
-        mma_bf16_16816(c1, r[2][2 * ks], r[3][2 * ks], r[2][2 * ks + 1], r[3][2 * ks + 1],
-                       b[2 * ks], b[2 * ks + 1]);
+        uint32_t b0, b1;
+        if constexpr (kBShared) {
+          b0 = s_b[warp][(2 * ks) * 32 + lane];
+          b1 = s_b[warp][(2 * ks + 1) * 32 + lane];
+        } else {
+          b0 = b[2 * ks];
+          b1 = b[2 * ks + 1];
+        }
+        mma_bf16_16816(c0, r[0][2 * ks], r[1][2 * ks], r[0][2 * ks + 1], r[1][2 * ks + 1], b0, b1);
+        mma_bf16_16816(c1, r[2][2 * ks], r[3][2 * ks], r[2][2 * ks + 1], r[3][2 * ks + 1], b0, b1);
       }
       const float d00 = __shfl_sync(kFullMask, c0[0], src_lane);
       const float d02 = __shfl_sync(kFullMask, c0[2], src_lane);
