@@ -766,6 +766,66 @@ def bench_cosine(args):
             "steps": args.steps}
 
 
+def bench_pairmetric(args):
+    """Manhattan and Chebyshev distances at the headline's points (Gaussian
+    mixture, n = 10^6, m = 1000, d = 64 and 128, eps at the 1% quantile of
+    the metric over 2*10^5 seeded pairs): the pair-kernel gather over the
+    FP32 points and over the certified BF16 copy (SNG_FLAG_SCREEN16), labels
+    of the two compared, and the copy's partner-row reads against the
+    measured L2 read rate."""
+    import numpy as np
+    import torch
+
+    import paper_2006_06743_gb300 as sng
+    from paper_2006_06743_gb300 import datagen
+    n, m = args.pm_n, 1000
+    l2_peak = sng.measure_l2_read(48 << 20, 200)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    runs = {}
+    for d in args.pm_d:
+        x = datagen.gaussian_mixture(n, d, 100, 0.02, seed=args.seed)
+        xg = torch.from_numpy(x).cuda()
+        rng = np.random.default_rng(args.seed)
+        i, j = rng.integers(0, n, 200_000), rng.integers(0, n, 200_000)
+        diff = np.abs(x[i].astype(np.float64) - x[j].astype(np.float64))
+        del x
+        for metric, name, v in ((sng.SNG_METRIC_L1, "l1", diff.sum(1)),
+                                (sng.SNG_METRIC_LINF, "linf", diff.max(1))):
+            eps = float(np.float32(np.quantile(v, 0.01)))
+            labels = {}
+            for form, f in (("fp32", 0), ("bf16_screen", sng.SNG_FLAG_SCREEN16)):
+                p = sng.Params(eps=eps, min_pts=10, m=m, seed=args.seed, metric=metric,
+                               flags=f | sng.SNG_FLAG_TIMING)
+                for _ in range(args.warmup):
+                    sng.cluster(xg, p)
+
+                def step():
+                    flush.fill_(1)
+                    return sng.cluster(xg, p)
+                ms, (lab, st) = _timed(step, args.steps)
+                labels[form] = lab
+                g_ms = st["ms"]["gather"]
+                row = (2 if f else 4) * (-(-d // 8) * 8 if f else d)
+                runs[f"{name}_d{d}_{form}"] = {
+                    "ms": ms, "gather_ms": g_ms, "queries_per_s": n * m / (g_ms * 1e-3),
+                    "partner_row_bytes": row,
+                    "l2_frac": n * m * row / (g_ms * 1e-3) / 1e9 / l2_peak,
+                    "open_pairs": st["screen_pairs"], "recheck_pairs": st["recheck_pairs"],
+                    "band_pairs": st["band_pairs"], "kept_edges": st["kept_edges"],
+                    "clusters": st["clusters"]}
+            runs[f"{name}_d{d}_bf16_screen"]["labels_equal_fp32"] = bool(
+                torch.equal(labels["fp32"], labels["bf16_screen"]))
+            runs[f"{name}_d{d}_bf16_screen"]["speedup"] = (
+                runs[f"{name}_d{d}_fp32"]["gather_ms"] / runs[f"{name}_d{d}_bf16_screen"]["gather_ms"])
+        del xg
+    return {"form": "pairmetric", "metric": "sampled distance queries/s of the gather phase",
+            "value": runs[f"l1_d{args.pm_d[0]}_bf16_screen"]["queries_per_s"], "unit": "queries/s",
+            "runs": runs, "l2_read_peak_gbs": l2_peak,
+            "config": {"workload": f"mixture-n{n}", "d": args.pm_d, "m": m, "eps": "1% quantile",
+                       "min_pts": 10, "l2_flush": "512 MB buffer written before each step"},
+            "dtype": "f32", "steps": args.steps}
+
+
 def bench_graph(args):
     """One whole pass launched directly (sng_cluster, host reads E mid-way)
     against the same pass captured once as a CUDA graph
@@ -1216,7 +1276,9 @@ def main():
                          "dataset's rows split across ranks")
     ap.add_argument("--form", default="plain",
                     choices=["plain", "bf16", "batched", "surrogate", "balls", "sweep", "cosine",
-                             "graph"])
+                             "graph", "pairmetric"])
+    ap.add_argument("--pm-n", type=int, default=1_000_000)
+    ap.add_argument("--pm-d", type=int, nargs="+", default=[64, 128])
     ap.add_argument("--sweep-n", type=int, default=100_000)
     ap.add_argument("--sweep-eps-s", type=float, default=0.1,
                     help="sampling rate of the eps sweep (--form sweep)")
@@ -1260,7 +1322,7 @@ def main():
         fn = {"bf16": bench_bf16, "cosine": bench_cosine, "graph": bench_graph,
               "batched": bench_batched,
               "surrogate": bench_surrogate,
-              "balls": bench_balls, "sweep": bench_sweep}
+              "balls": bench_balls, "sweep": bench_sweep, "pairmetric": bench_pairmetric}
         print(json.dumps(fn[args.form](args)), flush=True)
         return
     w = make_workload(args.workload, seed=args.seed)

@@ -83,9 +83,15 @@ typedef int32_t sng_status;
                                a zero vector is similar to nothing            */
 #define SNG_METRIC_L1 3     /* edge iff sum_k |a_k - b_k| <= eps (Manhattan)   */
 #define SNG_METRIC_LINF 4   /* edge iff max_k |a_k - b_k| <= eps (Chebyshev);
-                               L1 / LINF: FP32 points, one lane per pair of the
-                               direct gather (no screens, no tiles); a NaN
-                               difference is within eps of nothing            */
+                               L1 / LINF: FP32 points, four lanes per pair of
+                               the direct gather (no tiles, no tensor-core
+                               screens); with SNG_FLAG_SCREEN16 or
+                               SNG_FLAG_SCREEN8 the pairs are tested on a BF16
+                               copy (map_screen = 1) and certified from each
+                               row's copy error bound (sqrt(d) times its
+                               Euclidean norm for L1, that norm for LINF);
+                               open pairs are decided from the FP32 points.
+                               A NaN difference is within eps of nothing      */
 
 /* flags */
 #define SNG_FLAG_TIMING 1u  /* fill sng_stats.ms with per-phase CUDA-event times */
@@ -122,11 +128,13 @@ typedef int32_t sng_status;
                                 points and decided as without the flag.
                                 Results are identical; stats report map_screen
                                 and screen_pairs.  On CUDA cores (Euclidean
-                                form only) the bound is 2^-8 of the two rows'
+                                form) the bound is 2^-8 of the two rows'
                                 norms and the direct and tiled gathers apply
                                 (the tiled one not with SNG_FLAG_NO_SYNC);
                                 ignored for BF16 points, one lane per row and
-                                map_passes > 1                                 */
+                                map_passes > 1.  The Manhattan and Chebyshev
+                                distances have a screen of their own (see
+                                SNG_METRIC_LINF)                               */
 #define SNG_FLAG_SCREEN_MMA 64u /* with SNG_FLAG_SCREEN16 and d <= 128: the direct
                                 gather takes each pair's dot product on the
                                 BF16 copy from tensor-core MMAs (16 partners at
@@ -143,7 +151,9 @@ typedef int32_t sng_status;
                                 SNG_FLAG_SCREEN_MMA on an FP8 (E4M3) copy of
                                 x * 2^k (one power of two for the point set;
                                 1 byte per value of scratch), with FP8 MMAs;
-                                every metric.  The copy's rounding is coarser,
+                                Euclidean, inner product and cosine (the
+                                Manhattan and Chebyshev distances take the BF16
+                                copy, as with SNG_FLAG_SCREEN16).  The copy's rounding is coarser,
                                 so more pairs are left open and decided from
                                 the FP32 points; results are identical.  Stats
                                 report map_screen = 4.  Same exclusions as

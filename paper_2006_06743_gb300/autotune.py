@@ -58,8 +58,15 @@ def candidates(x, p: Params, screen: bool = True) -> list[dict]:
     import torch
     n, d = x.shape
     if p.metric in (3, 4):
-        # Manhattan / Chebyshev: one pair-kernel gather, nothing to choose
-        return [dict(map_group=0, map_unroll=0, map_block=256, map_passes=0, prefetch=False)]
+        # Manhattan / Chebyshev: the pair-kernel gather over a certified BF16
+        # copy of FP32 points (2 bytes per value of scratch) where it fits,
+        # and over the points themselves
+        plain = dict(map_group=0, map_unroll=0, map_block=256, map_passes=0, prefetch=False)
+        if screen and x.dtype == torch.float32:
+            free = torch.cuda.mem_get_info(x.device)[0] if x.is_cuda else 0
+            if n * (-(-d // 8) * 8) * 2 < 0.25 * free:
+                return [dict(plain, screen=True), plain]
+        return [plain]
     esize = 2 if x.dtype == torch.bfloat16 else 4
     vec = 8 if esize == 2 else 4
     if x.stride(0) % vec:

@@ -599,6 +599,10 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
   // the TMA + tcgen05 form reads rows of 64 BF16 values (zero past d);
   // Euclidean only
   const bool tc05 = mma_kt && !sim && (p->flags & SNG_FLAG_TCGEN05) && p->d <= 64;
+  // Manhattan / Chebyshev distance: the BF16 copy screened on CUDA cores
+  // (either screen flag; gather_pair.cu)
+  const bool pair_screen =
+      pair_metric && (p->flags & (SNG_FLAG_SCREEN16 | SNG_FLAG_SCREEN8)) && p->dtype == SNG_F32;
   if (screen) {
     wait_inputs(st);
     if (fp8_ks) {
@@ -678,14 +682,39 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     pg = &pb;
     rg = &rb;
   }
+  if (pair_screen) {
+    wait_inputs(st);
+    if ((rc = make_shadow(static_cast<const float *>(x), p->ld, p->d, n, 0, s, &sh))) return rc;
+    ga.x = sh.xb;
+    ga.ld = sh.ldb;
+    ga.nbe = sh.nbe;
+    ga.err_max = sh.nmax + kErrMaxSlot;
+    ga.screen_vec4 = (p->d % 4 == 0) && (p->ld % 4 == 0) && ((uintptr_t)x % 16 == 0);
+    // the copy's FP32 distance: each term rounded at most 2 ceil(chunks / 4)
+    // + 5 times for L1 (difference, its partial, two combining levels, two
+    // shuffle levels), once for L-inf; c twice that plus 2^-22
+    const double u = std::ldexp(1.0, -24);
+    const int64_t chunks = sh.ldb / 8;
+    const double cpp = p->metric == SNG_METRIC_L1 ? (double)(2 * ((chunks + 3) / 4) + 5) * u : u;
+    const double c = 2.0 * cpp + std::ldexp(1.0, -22);
+    const double eps = (double)p->eps;
+    const double lo = eps * (1.0 - (double)r.band_rel - c);
+    float lof = (float)lo;
+    if ((double)lof > lo) lof = std::nextafter(lof, -INFINITY);
+    ga.pm_lo = lof;
+    ga.pm_hi = round_up_f(eps * (1.0 + (double)r.band_rel + c));
+    // |v|_1 <= sqrt(d) |v|_2, |v|_inf <= |v|_2 for the copy's error bounds
+    const double scale = p->metric == SNG_METRIC_L1 ? std::sqrt((double)p->d) : 1.0;
+    ga.pm_escale = round_up_f(scale * (1.0 + std::ldexp(1.0, -10)));
+  }
   const int grid = gather_grid(pg->dtype, rg->map, r.row_end - r.row_begin);
   bool tiled = false;
   if (!mma_kt && !fp8_ks && (p->flags & SNG_FLAG_TILED) &&
       (rc = run_tiled(pg, *rg, s, ga, gb, &tiled, screen ? &sh : nullptr)))
     return rc;
-  gb->screened = screen;
+  gb->screened = screen || pair_screen;
   gb->map = rg->map;
-  if (fp8_ks || mma_kt) {
+  if (fp8_ks || mma_kt || pair_screen) {
     // the queue of open pairs of the tensor-core forms: room for 1 in 32
     // draws of the row range (at most 2^26 entries); past it, or without
     // the memory, the gather decides open pairs itself
@@ -702,8 +731,18 @@ sng_status run_graph(const void *x, const sng_params *p, const Resolved &r, Scra
     }
     fp32_guard(r.eps2, r.band_rel, (p->d + 31) / 32, 5, &ga.q_lo_thr, &ga.q_hi_thr);
   }
-  if (pair_metric) {
-    // Manhattan / Chebyshev: one lane per pair over the FP32 points
+  if (pair_screen) {
+    // Manhattan / Chebyshev over the BF16 copy, four lanes per pair; the
+    // open pairs from the FP32 points after it
+    int kc = 0;
+    if ((rc = launch_gather_pair16(p->metric, ga, &kc, st))) return rc;
+    if ((rc = launch_pair_queue(p->metric, ga, st))) return rc;
+    gb->map.vec = 8;
+    gb->map.group = 4;
+    gb->map.nch = kc;
+    gb->map.unroll = 0;
+  } else if (pair_metric) {
+    // Manhattan / Chebyshev: four lanes per pair over the FP32 points
     wait_inputs(st);
     if ((rc = launch_gather_pair(p->metric, ga, st))) return rc;
   } else if (fp8_ks) {

@@ -103,6 +103,11 @@ struct GatherArgs {
   // relative to |a'| |b'|
   int32_t sim_screen;
   float sim_keep_thr, sim_drop_thr, sim_cm;
+  // BF16 screen of the Manhattan / Chebyshev distance (gather_pair.cu): the
+  // FP32 value over the copy keeps a pair at or below pm_lo - eta and drops
+  // it above pm_hi + eta, eta = (e_a + e_b) pm_escale from the rows' copy
+  // error bounds (nbe[i].y) -- directed roundings, NaN leaves it open
+  float pm_lo, pm_hi, pm_escale;
   uint32_t *bitmask;      // n x W
   int32_t *out_cnt;       // n, nullable
   int32_t *deg;           // n (zeroed before launch in multigraph mode)

@@ -12,4 +12,16 @@ namespace sng {
 // metric.
 sng_status launch_gather_pair(int metric, const GatherArgs &a, cudaStream_t st);
 
+// The same over the BF16 copy a.x (row stride a.ld values, a multiple of 8,
+// zero past d) with the copy's error bounds a.nbe / a.err_max and the
+// thresholds a.pm_lo, a.pm_hi, a.pm_escale; open pairs to the queue a.openq
+// (past its capacity decided from a.xm in the gather).  *kc receives the
+// 16-byte chunks of the source row each lane keeps in registers.
+sng_status launch_gather_pair16(int metric, const GatherArgs &a, int *kc, cudaStream_t st);
+
+// Decide the queued open pairs from the FP32 points as launch_gather_pair
+// would (its group order, guard band a.lo_thr .. a.hi_thr, FP64 recheck) and
+// fold the kept ones into a.bitmask, a.out_cnt and a.deg.
+sng_status launch_pair_queue(int metric, const GatherArgs &a, cudaStream_t st);
+
 }  // namespace sng

@@ -17,16 +17,6 @@
 
 namespace sng {
 
-// A kept pair into the gather's results: its keep bit, its row's count, the
-// degrees.
-__device__ __forceinline__ void queue_keep(const GatherArgs &a, int32_t i, int32_t p, uint32_t j,
-                                           int32_t wi) {
-  atomicOr(a.bitmask + (int64_t)i * a.W + (j >> 5), 1u << (j & 31));
-  if (a.out_cnt) atomicAdd(a.out_cnt + i, 1);
-  atomicAdd(a.deg + i, wi);
-  if (a.deg_mode == SNG_DEG_UNDIRECTED_MULTI) atomicAdd(a.deg + p, wi);
-}
-
 __global__ void __launch_bounds__(256) screen_queue_kernel(GatherArgs a) {
   const int lane = threadIdx.x & 31;
   const unsigned long long queued = *a.openq_cnt;

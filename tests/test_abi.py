@@ -204,11 +204,18 @@ def test_autotuner_offers_the_bf16_screen_for_fp32_points(monkeypatch):
     assert sim and all(c.get("mma") or c.get("fp8") for c in sim)
     assert screened(1_000_000, 200, m=1000, metric=2) == []
     assert screened(200_000, 64, sample_mode=1) == []
-    # Manhattan / Chebyshev: the one pair-kernel gather
+    # Manhattan / Chebyshev: the pair-kernel gather over the BF16 copy, then
+    # over the FP32 points; the latter alone for BF16 points
     for metric in (3, 4):
-        one = autotune.candidates(_FakeCudaRows(1_000_000, 64, torch.float32),
-                                  Params(eps=1.0, min_pts=5,
-                                         metric=metric))
+        two = screened(1_000_000, 64, metric=metric)
+        assert len(two) == 1 and not two[0].get("mma") and not two[0].get("fp8")
+        all_ = autotune.candidates(_FakeCudaRows(1_000_000, 64, torch.float32),
+                                   Params(eps=1.0, min_pts=5, metric=metric))
+        assert len(all_) == 2 and not all_[1].get("screen")
+        pm = autotune.apply(Params(eps=1.0, min_pts=5, metric=metric), {"mapping": two[0]})
+        assert pm.flags & SNG_FLAG_SCREEN16 and not pm.flags & SNG_FLAG_SCREEN_MMA
+        one = autotune.candidates(_FakeCudaRows(1_000_000, 64, torch.bfloat16),
+                                  Params(eps=1.0, min_pts=5, metric=metric))
         assert len(one) == 1 and not one[0].get("screen")
 
 
