@@ -262,8 +262,9 @@ static __device__ __noinline__ bool pair_fp32_decide(const GatherArgs &a, int32_
 // first KC chunks of each lane are held in registers (as FP32 for KC <= 2).
 // All 32 partner rows of a stage are fetched before any is tested -- four
 // steps of eight rows, KC chunks per lane each -- and the next stage's
-// partners are hashed while they are on their way.
-template <int METRIC, int KC>
+// partners are hashed while they are on their way.  FULL: the row has
+// exactly 4 KC chunks (no bounds tests).
+template <int METRIC, int KC, bool FULL>
 __global__ void __launch_bounds__(256, KC <= 2 ? 3 : 2) gather_pair16_kernel(GatherArgs a) {
   constexpr bool kSrcF32 = KC <= 2;
   const int lane = threadIdx.x & 31;
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(256, KC <= 2 ? 3 : 2) gather_pair16_kernel(Gat
 #pragma unroll
         for (int t = 0; t < KC; ++t) {
           const int c = q + 4 * t;
-          buf[step][t] = c < nc ? __ldg(vb + c) : make_uint4(0u, 0u, 0u, 0u);
+          buf[step][t] = FULL || c < nc ? __ldg(vb + c) : make_uint4(0u, 0u, 0u, 0u);
         }
       }
       // the next stage's partners, hashed while these rows are on their way
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(256, KC <= 2 ? 3 : 2) gather_pair16_kernel(Gat
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int t = 0; t < KC; ++t) {
-          if (q + 4 * t < nc) {
+          if (FULL || q + 4 * t < nc) {
             if constexpr (kSrcF32) {
               pm_chunk<METRIC>(acc, srcf[t], buf[step][t]);
             } else {
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(256, KC <= 2 ? 3 : 2) gather_pair16_kernel(Gat
             }
           }
         }
-        if (nc > 4 * KC) {
+        if (!FULL && nc > 4 * KC) {
           // rows past 32 KC values: the rest of both rows chunk by chunk
           const int32_t pg = __shfl_sync(kFullMask, p, 8 * step + g);
           const uint4 *vb = reinterpret_cast<const uint4 *>(X + (int64_t)pg * a.ld);
@@ -455,7 +456,10 @@ static void launch_pm16(const GatherArgs &a, int64_t rows, cudaStream_t st) {
   int64_t grid = (int64_t)device_sms() * (KC <= 2 ? 3 : 2);
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  gather_pair16_kernel<METRIC, KC><<<(int)grid, 256, 0, st>>>(a);
+  if (a.ld == 32 * KC)
+    gather_pair16_kernel<METRIC, KC, true><<<(int)grid, 256, 0, st>>>(a);
+  else
+    gather_pair16_kernel<METRIC, KC, false><<<(int)grid, 256, 0, st>>>(a);
 }
 
 template <int METRIC>
