@@ -67,8 +67,9 @@ __device__ __forceinline__ float pair_combine(float acc, float t) {
 // of 32 draws; each distance is handed back to the lane that drew it, which
 // decides it, so the stage's keep bits come from one ballot in draw order.
 // Rows whose length is not a multiple of 4 (or whose start is not 16-byte
-// aligned) take one lane per pair with scalar loads.
-template <int METRIC, bool VEC4>
+// aligned) take one lane per pair with scalar loads.  FULL: rows of exactly
+// 64 values (no bounds tests).
+template <int METRIC, bool VEC4, bool FULL>
 __global__ void __launch_bounds__(256) gather_pair_kernel(GatherArgs a) {
   constexpr int kSrcChunks = 4;   // source chunks a lane keeps (rows of <= 64 values)
   const int lane = threadIdx.x & 31;
@@ -87,8 +88,8 @@ __global__ void __launch_bounds__(256) gather_pair_kernel(GatherArgs a) {
 #pragma unroll
       for (int t = 0; t < kSrcChunks; ++t) {
         const int c = q + 4 * t;
-        src[t] = c < nc ? __ldg(reinterpret_cast<const float4 *>(xa) + c)
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        src[t] = FULL || c < nc ? __ldg(reinterpret_cast<const float4 *>(xa) + c)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     int cnt = 0;
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(256) gather_pair_kernel(GatherArgs a) {
 #pragma unroll
           for (int t = 0; t < kSrcChunks; ++t) {
             const int c = q + 4 * t;
-            if (c < nc) {
+            if (FULL || c < nc) {
               const float4 v = __ldg(vb + c);
               ax = pair_combine<METRIC>(ax, fabsf(src[t].x - v.x));
               ay = pair_combine<METRIC>(ay, fabsf(src[t].y - v.y));
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(256) gather_pair_kernel(GatherArgs a) {
               aw = pair_combine<METRIC>(aw, fabsf(src[t].w - v.w));
             }
           }
-          for (int c = q + 4 * kSrcChunks; c < nc; c += 4) {
+          for (int c = q + 4 * kSrcChunks; !FULL && c < nc; c += 4) {
             const float4 u = __ldg(reinterpret_cast<const float4 *>(xa) + c);
             const float4 v = __ldg(vb + c);
             ax = pair_combine<METRIC>(ax, fabsf(u.x - v.x));
@@ -172,7 +173,13 @@ static void launch_pm(const GatherArgs &a, int64_t rows, cudaStream_t st) {
   int64_t grid = (int64_t)device_sms() * 8;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  gather_pair_kernel<METRIC, VEC4><<<(int)grid, 256, 0, st>>>(a);
+  if constexpr (VEC4) {
+    if (a.d == 64) {
+      gather_pair_kernel<METRIC, true, true><<<(int)grid, 256, 0, st>>>(a);
+      return;
+    }
+  }
+  gather_pair_kernel<METRIC, VEC4, false><<<(int)grid, 256, 0, st>>>(a);
 }
 
 sng_status launch_gather_pair(int metric, const GatherArgs &a, cudaStream_t st) {
