@@ -12,6 +12,12 @@
 // ballot, degrees by atomics, as in the other gathers.  The group's order of
 // the additions (four partials per lane, their sum, then two shuffle levels)
 // keeps every term's roundings within the (d + 1) u of the guard band.
+//
+// With a screen flag the same test runs first over a BF16 copy of the
+// points (gather_pair16_kernel, below): half the bytes per partner row,
+// each decision certified by the rows' copy error bounds, and the pairs it
+// cannot certify decided from the FP32 points afterwards (pair_queue_kernel)
+// exactly as above.
 #include "api_common.cuh"
 #include "gather.cuh"
 #include "gather_pair.cuh"
