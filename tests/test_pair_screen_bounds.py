@@ -148,3 +148,57 @@ def test_decided_pairs_lie_outside_the_band(d, linf):
             decided += 1
             assert ex > Fraction(eps) * (1 + Fraction(band_rel)) and not in_band
     assert decided > 60, decided
+
+
+def fp32_group_order(a, b, linf):
+    """FP32 distance in the plain pair kernel's order over float4 chunks:
+    lane q takes chunks q, q + 4, ...; one partial per vector component;
+    (x + y) + (z + w); then two shuffle levels."""
+    d = a.size
+    nc = d // 4
+
+    def comb(x, y):
+        return np.float32(max(x, y)) if linf else np.float32(x + y)
+
+    lanes = []
+    for q in range(4):
+        acc = [np.float32(0.0)] * 4
+        for c in range(q, nc, 4):
+            for e in range(4):
+                k = 4 * c + e
+                acc[e] = comb(acc[e], np.float32(abs(np.float32(a[k] - b[k]))))
+        lanes.append(comb(comb(acc[0], acc[1]), comb(acc[2], acc[3])))
+    return float(comb(comb(lanes[0], lanes[1]), comb(lanes[2], lanes[3])))
+
+
+@pytest.mark.parametrize("band_rel", [1e-5, 0.0])
+@pytest.mark.parametrize("linf", [False, True])
+@pytest.mark.parametrize("d", [4, 8, 64, 128, 200])
+def test_fp32_pair_guard_certifies_every_decision(d, linf, band_rel):
+    """The plain pair kernel's guard band eps (1 -+ (band_rel + c)), c =
+    2 (d + 2) u + 2^-22 for L1 and 4 u + 2^-22 for L-inf (rounded outwards):
+    its FP32 value is within (d + 1) u (L1) or u (L-inf) of the exact
+    distance, so every decision outside the band is the FP64 oracle's."""
+    rng = np.random.default_rng(50 + d + 3 * linf + int(band_rel == 0))
+    decided = 0
+    for t in range(200):
+        a = _rows(rng, d, 15)
+        b = (a + _rows(rng, d, 2) * np.float32(rng.uniform(0.01, 1.0))).astype(np.float32)
+        ex = exact_linf(a, b) if linf else exact_l1(a, b)
+        if ex == 0:
+            continue
+        v = fp32_group_order(a, b, linf)
+        assert abs(Fraction(v) - ex) <= (Fraction(U) if linf else (d + 1) * Fraction(U)) * ex
+        rel = rng.choice([0.0, 5e-8, -5e-8, 3e-7, -3e-7, 3e-6, -3e-6, 1e-5, -1e-5, 1e-4, -1e-4,
+                          0.01, -0.01])
+        eps = np.float32(float(ex) * (1 + rel))
+        c = (4 * Fraction(U) if linf else 2 * (d + 2) * Fraction(U)) + Fraction(2) ** -22
+        lo = Fraction(float(eps)) * (1 - Fraction(float(np.float32(band_rel))) - c)
+        hi = Fraction(float(eps)) * (1 + Fraction(float(np.float32(band_rel))) + c)
+        if Fraction(v) < lo:
+            decided += 1
+            assert ex < Fraction(float(eps)) * (1 - Fraction(band_rel)), (d, t, rel)
+        elif Fraction(v) > hi:
+            decided += 1
+            assert ex > Fraction(float(eps)) * (1 + Fraction(band_rel)), (d, t, rel)
+    assert decided > 40, decided
