@@ -197,3 +197,70 @@ def test_tensor_core_screen_decides_only_outside_the_band(d, exact_copy, kind):
                 decided += 1
                 assert exact > eps2 * (1 + Fraction(band_rel)), (kind, d, t, sgn, rel)
     assert decided > 60 and kept > 30, (decided, kept)
+
+
+def _group_sum(ab, bb, lanes, vec):
+    """FP32 sum of (a'_k - b'_k)^2 with element k on lane (k // vec) % lanes,
+    fused multiply-adds in order per lane, then a pairwise tree."""
+    acc = [np.float32(0.0)] * lanes
+    for k in range(ab.size):
+        t = np.float32(ab[k] - bb[k])
+        lane = (k // vec) % lanes
+        acc[lane] = fma32(t, t, acc[lane])
+    while len(acc) > 1:
+        acc = [np.float32(acc[2 * i] + acc[2 * i + 1]) for i in range(len(acc) // 2)]
+    return acc[0]
+
+
+@pytest.mark.parametrize("exact_copy", [False, True])
+@pytest.mark.parametrize("d", [5, 16, 64, 130])
+def test_cuda_core_screen_decides_only_outside_the_band(d, exact_copy):
+    """The screen on CUDA cores: eta = 2^-8 (|a| + |b|) + 2^-60 from the
+    rows' norm bounds, the FP32 sum over the copy in the group order of the
+    BF16 mapping (8-value chunks, lanes a power of two), thresholds
+    (eps sqrt(1 -+ band_rel) -+ eta)^2 (1 -+ g); partner bound its own or the
+    largest of the set."""
+    rng = np.random.default_rng(300 + d + exact_copy)
+    band_rel = 1e-8 if exact_copy else 1e-5
+    chunks = -(-d // 8)
+    lanes = 1
+    while lanes < chunks and lanes < 32:
+        lanes <<= 1
+    screen_u = np.float32(2.0 ** -8 * (1 + 2.0 ** -20))
+    rows = [(rng.standard_normal(d) * np.float32(2.0 ** rng.integers(-3, 4))).astype(np.float32)
+            for _ in range(40)]
+    if exact_copy:
+        rows = [bf16(r) for r in rows]
+    nrms = [row_data(r, "bf16")[1] for r in rows]
+    nrm_max = max(nrms)
+    decided = 0
+    for t in range(250):
+        ia = int(rng.integers(0, len(rows)))
+        a = rows[ia]
+        direction = rng.standard_normal(d)
+        direction /= np.linalg.norm(direction)
+        b = (a + direction * float(np.linalg.norm(a)) * float(rng.uniform(0.05, 0.8))
+             ).astype(np.float32)
+        if exact_copy:
+            b = bf16(b)
+        nrm_b = row_data(b, "bf16")[1]
+        exact = sum((Fraction(float(u)) - Fraction(float(v))) ** 2 for u, v in zip(a, b))
+        rel = rng.choice([0.0, 3e-6, -3e-6, 1e-5, -1e-5, 1e-3, -1e-3, 0.02, -0.02, 0.1, -0.1])
+        eps = np.float32(math.sqrt(float(exact)) * (1 + rel))
+        lo_eps, hi_eps, g = host_constants(eps, band_rel, d)
+        s = _group_sum(bf16(a), bf16(b), lanes, 8)
+        for nrm_p in (nrm_b, nrm_max):
+            eta = fma32(screen_u, np.float32(nrms[ia] + nrm_p), np.float32(2.0 ** -60))
+            lo = np.float32(lo_eps - eta)
+            hi = np.float32(hi_eps + eta)
+            keep_thr = np.float32(np.float32(lo * lo) * np.float32(1 - g)) \
+                if lo > np.float32(2.0 ** -10) * lo_eps else np.float32(-1.0)
+            drop_thr = np.float32(np.float32(hi * hi) * np.float32(1 + g))
+            eps2 = Fraction(float(eps)) ** 2
+            if s <= keep_thr:
+                decided += 1
+                assert exact < eps2 * (1 - Fraction(band_rel)), (d, t, rel)
+            elif s > drop_thr:
+                decided += 1
+                assert exact > eps2 * (1 + Fraction(band_rel)), (d, t, rel)
+    assert decided > 60, decided
