@@ -59,7 +59,8 @@ def _compare(orc, sng, torch, x, xg, p):
 @pytest.mark.parametrize("screen", [False, True])
 @pytest.mark.parametrize("metric", [L1, LINF])
 @pytest.mark.parametrize("n,d", [(400, 1), (700, 3), (1000, 4), (900, 7), (1200, 16),
-                                 (2000, 64), (800, 65), (600, 128), (500, 130), (400, 200)])
+                                 (900, 24), (800, 32), (2000, 64), (800, 65), (600, 128),
+                                 (500, 130), (400, 200)])
 def test_pair_metric_graph_and_labels_match_oracle(orc, metric, n, d, screen):
     torch, sng = need_gpu()
     x = datagen.random_points(n, d, seed=n + d + metric)
