@@ -495,7 +495,7 @@ def bench_sng(args, w):
                                    "peak_kind": peak_kind, "unit": "GB/s",
                                    "frac": alg / (g_ms * 1e-3) / 1e9 / peak,
                                    "note": "256 B of FP32 partner row per query, all from HBM "
-                                           "(the survey's model); the gather reads a BF16 "
+                                           "(the per-query byte model); the gather reads a BF16 "
                                            "copy or L2-resident tiles instead"}},
         "phases_ms": {k: v for k, v in stats["ms"].items()},
         "stats": {k: stats[k] for k in ("kept_edges", "band_pairs", "band_points", "cores",
