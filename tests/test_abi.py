@@ -235,3 +235,48 @@ def test_random_row_probe_rejects_bad_arguments_on_host():
     assert L.sng_measure_random_rows(1 << 20, 128, 100, 0, ctypes.byref(v), None) \
         == sng.SNG_EINVAL
     assert L.sng_measure_random_rows(1 << 20, 128, 1 << 24, 0, None, None) == sng.SNG_EINVAL
+
+
+_REJECTIONS = [
+    # (params overrides, to_c overrides, keyword of the message)
+    (dict(), dict(n=1), "n must be"),
+    (dict(), dict(d=0), "d must be"),
+    (dict(), dict(ld=2), "ld must be"),
+    (dict(), dict(dtype=7), "unknown dtype"),
+    (dict(degree_mode=5), dict(), "degree_mode"),
+    (dict(sample_mode=3), dict(), "sample_mode"),
+    (dict(min_pts=0), dict(), "min_pts"),
+    (dict(metric=5), dict(), "unknown metric"),
+    (dict(eps=float("inf")), dict(), "finite"),
+    (dict(eps=1e-20), dict(), "eps must be in"),
+    (dict(eps=1e19, metric=3), dict(), "eps must be in"),
+    (dict(metric=4), dict(dtype="bf16", master=256), "Manhattan and Chebyshev"),
+    (dict(metric=1, map_passes=2), dict(), "one pass"),
+    (dict(flags=4 | 1), dict(), "phase timing"),
+    (dict(flags=4, degree_mode=2), dict(), "distinct-neighbour"),
+    (dict(band_rel=0.5), dict(), "band_rel"),
+    (dict(), dict(x=258), "aligned"),
+    (dict(), dict(dtype="bf16"), "x_f32_master"),
+    (dict(s=0.0, m=0), dict(), "s must be"),
+    (dict(m=2 ** 31), dict(), "m must be"),
+]
+
+
+@pytest.mark.parametrize("over,cover,word", _REJECTIONS)
+def test_every_parameter_rejection_happens_on_the_host(over, cover, word):
+    """Each invalid parameter is reported as SNG_EINVAL with its own message
+    before any CUDA call (so without a GPU)."""
+    import paper_2006_06743_gb300 as sng
+    sng.build()
+    kw = dict(eps=0.5, min_pts=3, s=0.1)
+    kw.update(over)
+    shape = dict(n=100, d=4, ld=4, dtype=sng.SNG_F32, master=0, x=256)
+    shape.update(cover)
+    if shape["dtype"] == "bf16":
+        shape["dtype"] = sng.SNG_BF16
+    p = sng.Params(**kw).to_c(shape["n"], shape["d"], shape["ld"], shape["dtype"], shape["master"])
+    st = sng.sng_stats()
+    rc = sng.lib().sng_cluster(ctypes.c_void_p(shape["x"]), ctypes.byref(p), ctypes.c_void_p(256),
+                               None, ctypes.byref(st), None)
+    assert rc == sng.SNG_EINVAL
+    assert word in sng.last_error(), sng.last_error()
