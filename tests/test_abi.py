@@ -280,3 +280,51 @@ def test_every_parameter_rejection_happens_on_the_host(over, cover, word):
                                None, ctypes.byref(st), None)
     assert rc == sng.SNG_EINVAL
     assert word in sng.last_error(), sng.last_error()
+
+
+def test_other_entry_points_reject_on_the_host():
+    """sng_build_graph, sng_cluster_host, sng_cluster_edges and the L2 probe
+    check their own arguments before any CUDA call."""
+    import paper_2006_06743_gb300 as sng
+    sng.build()
+    L = sng.lib()
+    ok = sng.Params(eps=0.5, min_pts=3, s=0.1)
+    st = sng.sng_stats()
+    x = ctypes.c_void_p(256)
+
+    def err(rc, word):
+        assert rc == sng.SNG_EINVAL
+        assert word in sng.last_error(), sng.last_error()
+
+    # sng_build_graph: no output, the no-sync flag
+    p = ok.to_c(100, 4, 4, sng.SNG_F32)
+    err(L.sng_build_graph(x, ctypes.byref(p), None, ctypes.byref(st), None), "out is NULL")
+    p = sng.Params(eps=0.5, min_pts=3, s=0.1, flags=sng.SNG_FLAG_NO_SYNC).to_c(100, 4, 4,
+                                                                           sng.SNG_F32)
+    g = sng.sng_graph()
+    err(L.sng_build_graph(x, ctypes.byref(p), ctypes.byref(g), ctypes.byref(st), None),
+        "SNG_FLAG_NO_SYNC")
+    # sng_cluster_host: NULL buffers, the no-sync flag, BF16 without master
+    p = ok.to_c(100, 4, 4, sng.SNG_F32)
+    err(L.sng_cluster_host(None, ctypes.byref(p), x, None, ctypes.byref(st), None), "NULL")
+    p = sng.Params(eps=0.5, min_pts=3, s=0.1, flags=sng.SNG_FLAG_NO_SYNC).to_c(100, 4, 4,
+                                                                           sng.SNG_F32)
+    err(L.sng_cluster_host(x, ctypes.byref(p), x, None, ctypes.byref(st), None), "synchronises")
+    p = ok.to_c(100, 4, 4, sng.SNG_BF16)
+    err(L.sng_cluster_host(x, ctypes.byref(p), x, None, ctypes.byref(st), None), "master")
+    # sng_cluster_edges: degrees, counts, edge arrays, MinPts
+    p = ok.to_c(100, 4, 4, sng.SNG_F32)
+    err(L.sng_cluster_edges(100, x, x, 5, None, ctypes.byref(p), x, None, None, None),
+        "deg is NULL")
+    err(L.sng_cluster_edges(0, x, x, 5, x, ctypes.byref(p), x, None, None, None), "n must be")
+    err(L.sng_cluster_edges(100, x, x, -1, x, ctypes.byref(p), x, None, None, None),
+        "num_edges")
+    err(L.sng_cluster_edges(100, None, x, 5, x, ctypes.byref(p), x, None, None, None),
+        "src / col")
+    p = sng.Params(eps=0.5, min_pts=0, s=0.1).to_c(100, 4, 4, sng.SNG_F32)
+    err(L.sng_cluster_edges(100, x, x, 5, x, ctypes.byref(p), x, None, None, None), "min_pts")
+    # the L2 read probe: buffer size and passes
+    v = ctypes.c_double()
+    err(L.sng_measure_l2_read(1024, 10, ctypes.byref(v), None), "bytes")
+    err(L.sng_measure_l2_read(1 << 24, 0, ctypes.byref(v), None), "passes")
+    err(L.sng_measure_l2_read(1 << 24, 10, None, None), "gbs is NULL")
